@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 lightcone hot path.
+
+One step = one realisation of the full-size map, the whole hot path:
+  bin 2 x 1024^3 particles of two nested boxes into 60 shells x Nside 1024
+  (Eq. 5, 8), kappa map + moments + PDF (Eq. 6, 12-13), statistics vector and
+  FP64 Welford covariance update (Eq. 10), adjoint d(var, skew)/d theta.
+The shell weights are per-cosmology constants computed once before timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank bins its own
+realisation (weak scaling, no data-path collective).  --impl reference times
+the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("G particles/s binned and kappa maps/s at Nside 1024 (% HBM roofline); "
+          "batched vs serial")
+UNIT = "Gparticles/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(scale_side: int | None):
+    from paper_1801_05745_gb300 import workloads
+    w = workloads.full() if scale_side is None else workloads.full(scale_side)
+    return w
+
+
+def shells(w, api=None, orc=None):
+    z = np.linspace(w.z_lo, w.z_hi, w.nshell + 1)
+    if api is not None:
+        chi = api.chi_edges(api.make_cosmo(w.omega_m, w.h, 1), z)
+    else:
+        chi = orc.chi_edges(w.omega_m, w.h, 1, z)
+    split = int(np.argmin(np.abs(chi - w.boxes[0].r_hi)))
+    return z, chi, split
+
+
+# ----------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        loaded = [v for v in sm if v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------- CPU baseline ----
+def cpu_baseline(w, parts_host, counts_host, A, C, dAC, seconds_budget=20.0):
+    """The oracle, as it stands, on a bounded sample of the workload:
+    binning of a particle sample, one full kappa map with moments and PDF,
+    and the complex-step gradient on a map of 1/16 the pixels (scaled)."""
+    import oracle
+    oracle.build()
+    z, chi, split = shells(w, orc=oracle)
+    boxes = [oracle.make_box(2000.0, [1000.0] * 3, w.boxes[0].n, 0, split),
+             oracle.make_box(6400.0, [3200.0] * 3, w.boxes[1].n, split, w.nshell)]
+    n_total = sum(b.n for b in w.boxes)
+    # binning sample: grow until ~40% of the budget
+    m = 1 << 18
+    t_bin = 0.0
+    done = 0
+    while True:
+        t0 = time.perf_counter()
+        for k in range(2):
+            oracle.keys(parts_host[k][:m], boxes[k], chi, w.nside)
+        t = time.perf_counter() - t0
+        t_bin, done = t, 2 * m
+        if t > 0.4 * seconds_budget or m >= len(parts_host[0]):
+            break
+        m = min(len(parts_host[0]), m * 4)
+    per_particle = t_bin / done
+    t0 = time.perf_counter()
+    kap = oracle.kappa_map(counts_host, A, C)
+    t_kappa = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mom = oracle.moments(kap)
+    oracle.pdf(kap, mom[0] - 6 * mom[1] ** 0.5, mom[0] + 6 * mom[1] ** 0.5, w.pdf_bins)
+    t_stats = time.perf_counter() - t0
+    # adjoint on a quarter-resolution map (1/16 of the pixels), scaled by 16
+    sub = counts_host.reshape(w.nshell, -1)[:, : counts_host.shape[1] // 16]
+    nside_sub = w.nside // 4
+    src = oracle.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    t0 = time.perf_counter()
+    oracle.kappa_stat_grads(np.ascontiguousarray(sub), nside_sub, w.omega_m, w.h, 1, boxes, z, src)
+    t_grad = (time.perf_counter() - t0) * 16
+    t_step = per_particle * n_total + t_kappa + t_stats + t_grad
+    return {
+        "value": n_total / t_step / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"oracle keys of {done} particles ({per_particle * 1e9:.0f} ns each, scaled to "
+                   f"{n_total}); one full Nside {w.nside} kappa map {t_kappa:.2f} s; moments+PDF "
+                   f"{t_stats:.2f} s; complex-step gradient on 1/16 of the pixels x16 = "
+                   f"{t_grad:.1f} s; estimated {t_step:.1f} s per step, single thread"),
+    }
+
+
+# ---------------------------------------------------------- reference arm ----
+def run_reference(args):
+    """The oracle as the reference arm: each step bins a bounded particle
+    sample of the workload and builds one full kappa map with statistics."""
+    import oracle
+    from paper_1801_05745_gb300 import synth
+    oracle.build()
+    w = workload(args.scale)
+    z, chi, split = shells(w, orc=oracle)
+    boxes = [oracle.make_box(2000.0, [1000.0] * 3, w.boxes[0].n, 0, split),
+             oracle.make_box(6400.0, [3200.0] * 3, w.boxes[1].n, split, w.nshell)]
+    src = oracle.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    A, B, C = oracle.kappa_coeffs(w.omega_m, w.h, 1, boxes, z, w.nside, src)
+    m = args.ref_sample
+    n_total = sum(b.n for b in w.boxes)
+    times = []
+    for step in range(args.warmup + args.steps):
+        parts = [synth.particles_numpy(m, 2000.0, 5.0, synth.seed_for(3, step, 0)),
+                 synth.particles_numpy(m, 6400.0, 20.0, synth.seed_for(3, step, 1))]
+        counts = np.zeros((w.nshell, 12 * w.nside ** 2), np.int32)
+        t0 = time.perf_counter()
+        for k in range(2):
+            oracle.bin_counts(parts[k], boxes[k], chi, w.nside, counts)
+        t_bin = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        kap = oracle.kappa_map(counts, A, C)
+        mom = oracle.moments(kap)
+        oracle.pdf(kap, -0.05, 0.2, w.pdf_bins)
+        t_map = time.perf_counter() - t0
+        est = t_bin / (2 * m) * n_total + t_map
+        if step >= args.warmup:
+            times.append(est)
+    t = float(np.mean(times))
+    val = n_total / t / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "particles": n_total, "nside": w.nside, "nshell": w.nshell},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{2 * m} particles binned per step (scaled to {n_total}) + one "
+                                   f"full Nside {w.nside} kappa map, moments and PDF"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main ----
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=int, default=None, help="particles per side per box (default 1024)")
+    ap.add_argument("--ref-sample", type=int, default=1_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1801_05745_gb300 import build as pbuild
+    pbuild.build()
+    from paper_1801_05745_gb300 import api, synth
+
+    w = workload(args.scale)
+    ctx = api.context(local)
+    cosmo = api.make_cosmo(w.omega_m, w.h, 1)
+    z, chi, split = shells(w, api=api)
+    boxes = [api.make_box(2000.0, [1000.0] * 3, w.boxes[0].n, 0, split),
+             api.make_box(6400.0, [3200.0] * 3, w.boxes[1].n, split, w.nshell)]
+    src = api.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    A, B, C, dA, dC = api.kappa_coeffs(cosmo, boxes, z, w.nside, src, derivs=True)
+    n_total = sum(b.n for b in w.boxes)
+
+    dev = torch.device("cuda", local)
+    parts = [synth.particles_torch(w.boxes[k].n, w.boxes[k].L, w.boxes[k].sigma,
+                                   synth.seed_for(3, rank, k), device=dev) for k in range(2)]
+    npix = 12 * w.nside ** 2
+    counts = torch.empty((w.nshell, npix), dtype=torch.int32, device=dev)
+    kap = torch.empty(npix, dtype=torch.float32, device=dev)
+    d = 6 + w.pdf_bins
+    wstate = api.welford_state(d, dev)
+    vec = torch.empty(d, dtype=torch.float64, device=dev)
+    ctx.reserve(w.nside, w.nshell, max(b.n for b in w.boxes))
+
+    # PDF range from a first map: mean +- 6 sigma, then fixed
+    ctx.bin(parts, boxes, chi, w.nside, counts=counts)
+    _, mom, _ = ctx.kappa_stats(counts, A, C, -1.0, 1.0, w.pdf_bins, kappa=kap)
+    m0 = mom.cpu().numpy()
+    lo, hi = float(m0[0] - 6 * m0[1] ** 0.5), float(m0[0] + 6 * m0[1] ** 0.5)
+
+    def step():
+        ctx.bin(parts, boxes, chi, w.nside, counts=counts)
+        _, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, w.pdf_bins, kappa=kap)
+        ctx.stats_vector(mom, pdf, out=vec)
+        ctx.welford_update(vec.view(1, d), wstate)
+        grad, _, _ = ctx.kappa_backward(counts, A, C, dA, dC, 1.0, 1.0)
+        return mom, pdf, grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = ctx.bin_info()
+
+    stream = torch.cuda.current_stream(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * n_total / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (by total time in the timed region)
+    peak, peak_src = hbm_peak()
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    launches = sum(c for _, c in prof.values())
+    fast_ms, fast_n = prof.get("k_fast", (0.0, 0))
+    fast_bytes = 12.0 * n_total * args.steps            # particle reads, all launches
+    bin_kernels = ["k_fast", "k_refine", "k_exact", "k_scan", "k_cursors", "k_scatter_group",
+                   "k_tiles", "k_scatter_bucket", "k_hist_block"]
+    bin_ms = sum(prof[k][0] for k in bin_kernels if k in prof) / args.steps
+    bin_bytes = 12.0 * n_total + 4.0 * w.nshell * npix
+    kap_ms = sum(prof[k][0] for k in ("k_kappa", "k_moments", "k_moments_final") if k in prof)
+    kap_launch = prof.get("k_kappa", (0.0, 1))
+    roof = {
+        "bound": "hbm", "kernel": "k_fast",
+        "achieved": fast_bytes / (fast_ms * 1e-3) / 1e9 if fast_ms else None,
+        "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs",
+        "traffic": None,
+        "per_launch_bytes": 12.0 * n_total / 2, "launches": fast_n,
+        "avg_launch_ms": fast_ms / max(fast_n, 1),
+    }
+    roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": w.name, "particles_per_gpu": n_total, "boxes": "2000 and 6400 Mpc/h",
+                   "nside": w.nside, "nshell": w.nshell, "source": "Smail n(z) a=2 b=1.5 z0=0.5",
+                   "l2": "inputs larger than L2 (25.8 GB of particles per step)",
+                   "parallelism": f"realisations x{world}"},
+        "kappa_maps_per_s": world * 1e3 / ms,
+        "roofline": roof,
+        "binning": {"ms": bin_ms, "algorithmic_bytes": bin_bytes,
+                    "frac_of_peak": bin_bytes / (bin_ms * 1e-3) / 1e9 / peak if bin_ms else None,
+                    "refined": info["refined"], "exact": info["exact"], "keyed": info["keyed"]},
+        "kappa_stats": {"ms": kap_ms / args.steps,
+                        "k_kappa_frac_of_peak": (4.0 * w.nshell * npix + 4.0 * npix) /
+                        (kap_launch[0] / kap_launch[1] * 1e-3) / 1e9 / peak if kap_launch[0] else None},
+        "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+        "top_kernel": top[0],
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # end to end: particles from pinned host memory through the C ABI each step
+    if not args.no_e2e:
+        host = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True) for p in parts]
+        for h_, p_ in zip(host, parts):
+            h_.copy_(p_)
+        out_h = torch.empty(10 + w.pdf_bins + 3, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        ke = max(2, min(args.steps, 4))
+
+        def e2e_step():
+            for h_, p_ in zip(host, parts):
+                p_.copy_(h_, non_blocking=True)
+            mom, pdf, grad = step()
+            out_h[:10].copy_(mom, non_blocking=True)
+            out_h[10:].copy_(pdf.to(torch.float64), non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / ke
+        if dist:
+            t = torch.tensor([ms_e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e = float(t.item())
+        line["e2e"] = {"value": world * n_total / (ms_e * 1e-3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in parts)),
+                       "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8 + w.nshell * 8),
+                       "ms_per_step": ms_e}
+        del host
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        parts_h = [p[: 1 << 24].cpu().numpy() for p in parts]
+        line["cpu_baseline"] = cpu_baseline(w, parts_h, counts.cpu().numpy(), A, C, (dA, dC))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * ufalcon.h -- C ABI of the GB300 lightcone library (libufalcon_gb300.so).
+ *
+ * The library computes the data-parallel hot path of the UFalcon
+ * multi-lens-plane method (Sgier, Refregier, Amara & Nicola, "Fast
+ * Generation of Covariance Matrices for Weak Lensing"):
+ *
+ *   particles of nested simulation boxes, observer at the centre (Sec. 2.4)
+ *     -> comoving shell (Eq. 8) and HEALPix RING pixel (Sec. 2.4)
+ *     -> per-shell count maps n_p(pix, Delta chi_b)          (Eq. 5)
+ *     -> Born-approximation convergence map kappa            (Eq. 2, 3, 6)
+ *     -> moments, variance of the variance and a PDF         (Eq. 12, 13, Sec. 3.3)
+ *     -> covariance and correlation over realisations        (Eq. 10, 11)
+ *   plus the adjoint of kappa's statistics with respect to (Omega_m, h, and
+ *   the n(z) parameters alpha, beta, z0), with the counts held fixed.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named *_dev are device memory of the context's device;
+ *    all others are host memory.  The caller owns every buffer it passes;
+ *    the library never frees or retains them after the call returns.
+ *  - Device work is enqueued on the context's stream (ufc_set_stream) and is
+ *    asynchronous unless a call says it synchronises.  Host outputs of a
+ *    call that enqueues device work are valid when the call returns.
+ *  - Positions are FP32 x,y,z triples (array of structures, 12 bytes per
+ *    particle) in the box's coordinates, lengths in Mpc/h (or Mpc when
+ *    ufc_cosmo.units_mpc_over_h = 0).
+ *  - Count maps are int32 [nshell][12*nside^2], shell-major, RING order.
+ *  - Every call returns UFC_OK or an error status; ufc_last_error() then
+ *    holds a one-line message.  Invalid arguments never reach the GPU.
+ *  - A context is not thread-safe: use one per host thread.
+ */
+#ifndef UFALCON_H
+#define UFALCON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UFC_MAX_SHELLS 256     /* shells per map                         */
+#define UFC_MAX_NSIDE 8192     /* HEALPix resolution (power of two)      */
+#define UFC_MAX_REPLICATE 8    /* periodic image layers per axis         */
+#define UFC_NMOMENTS 10        /* length of the moments vector           */
+
+typedef enum {
+  UFC_OK = 0,
+  UFC_ERR_ARG = 1,          /* invalid argument (nothing was enqueued)    */
+  UFC_ERR_CUDA = 2,         /* a CUDA runtime call failed                 */
+  UFC_ERR_ALLOC = 3,        /* device workspace could not be allocated    */
+  UFC_ERR_TIMEOUT = 4,      /* a device-side bounded wait ran out         */
+  UFC_ERR_UNSUPPORTED = 5,  /* valid request this build does not handle   */
+  UFC_ERR_CAPACITY = 6      /* a caller-sized or fixed buffer is too small */
+} ufc_status;
+
+typedef struct ufc_ctx ufc_ctx;
+
+/* Flat LambdaCDM cosmology (the paper uses h = 0.7, Omega_m = 0.276, Table 1).
+ * E(z) = sqrt(Omega_m (1+z)^3 + 1 - Omega_m).  units_mpc_over_h = 1: lengths
+ * in Mpc/h, c/H0 = 2997.92458 Mpc/h; 0: lengths in Mpc, c/H0 = 2997.92458/h. */
+typedef struct {
+  double omega_m;
+  double h;
+  int32_t units_mpc_over_h;
+} ufc_cosmo;
+
+/* One simulation box of the nesting scheme (Sec. 2.4).  obs is the observer
+ * (the paper places it at the box centre).  The box owns the shells
+ * [shell_lo, shell_hi): a particle of this box is counted only when its
+ * radius falls in one of them.  n_total is the particle count of the whole
+ * simulation box, which sets the mean density rho = m_p N / V of Eq. 6.
+ * replicate = R adds the periodic images (i,j,k) in [-R,R]^3 (the paper
+ * avoids replication; R = 0 reproduces that). */
+typedef struct {
+  double L;
+  double obs[3];
+  int64_t n_total;
+  int32_t shell_lo;
+  int32_t shell_hi;
+  int32_t replicate;
+} ufc_box;
+
+/* Lensing source (Sec. 2.3-2.4): kind 0 = single plane at z_s (Eq. 3);
+ * kind 1 = n(z) proportional to z^alpha exp(-(z/z0)^beta) on [0, z_max]. */
+typedef struct {
+  int32_t kind;
+  double z_s;
+  double alpha, beta, z0, z_max;
+} ufc_source;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`; the context owns its device
+ * workspace, which grows on demand and is freed by ufc_destroy. */
+ufc_status ufc_create(ufc_ctx **ctx, int32_t device);
+ufc_status ufc_destroy(ufc_ctx *ctx);
+/* Sets the CUDA stream (a cudaStream_t, NULL = legacy default stream). */
+ufc_status ufc_set_stream(ufc_ctx *ctx, void *stream);
+/* Waits for all work enqueued by this context; reports device-side errors. */
+ufc_status ufc_synchronize(ufc_ctx *ctx);
+/* Message of the last error on this context ("" if none). */
+const char *ufc_last_error(const ufc_ctx *ctx);
+/* Pre-allocates the workspace for binning up to n_max particles (times the
+ * image count) at (nside, nshell), so later calls allocate nothing. */
+ufc_status ufc_reserve(ufc_ctx *ctx, int32_t nside, int32_t nshell, int64_t n_max);
+
+/* Kernel timing (tracing; the paper has no counterpart).  While enabled,
+ * each kernel the library launches is bracketed by CUDA events on the
+ * context's stream (a few microseconds of overhead per launch). */
+ufc_status ufc_profile_enable(ufc_ctx *ctx, int32_t on);
+/* Synchronises, then reports the launches recorded since the last read,
+ * aggregated by kernel name: up to `max` entries of names (char[max][32],
+ * NUL-terminated), total milliseconds ms[max] and launch counts
+ * launches[max]; *n_out receives the number of distinct kernels (which may
+ * exceed max).  Clears the record. */
+ufc_status ufc_profile_read(ufc_ctx *ctx, int32_t max, char *names, double *ms,
+                            int64_t *launches, int32_t *n_out);
+
+/* ---- host cosmology (Eq. 1-3, Eq. 6, Eq. 8) -------------------------------- */
+
+/* Comoving distances chi(z) = (c/H0) int_0^z dz'/E(z') of the nshell+1 shell
+ * edges z_edges (Delta chi_b of Sec. 2.4).  z_edges must be increasing, >= 0. */
+ufc_status ufc_chi_edges(const ufc_cosmo *cosmo, const double *z_edges,
+                         int32_t nshell, double *chi_out);
+/* Inverse of chi(z) for n values (for shells of equal comoving thickness). */
+ufc_status ufc_z_of_chi(const ufc_cosmo *cosmo, const double *chi, int32_t n,
+                        double *z_out);
+/* Coefficients of kappa_p = sum_b A_b n_bp - C (Eq. 6):
+ *   A_b = 3/2 Omega_m W_b (H0/c) N_pix V_k / (4 pi N_k chi_b^2),
+ *   B_b = 3/2 Omega_m W_b (H0/c) Delta chi_b,  C = sum_b B_b,
+ * with W_b from Eq. 3 (plane) or its n(z) average, chi_b the shell's lower
+ * edge and (V_k = L^3, N_k = n_total) of the box owning shell b.  Every shell
+ * must be owned by exactly one box and z_edges[0] > 0.
+ * Optional dA [5][nshell] and dC [5] receive the derivatives with respect to
+ * theta = (Omega_m, h, alpha, beta, z0) (NULL to skip). */
+ufc_status ufc_kappa_coeffs(const ufc_cosmo *cosmo, const ufc_box *boxes,
+                            int32_t nbox, const double *z_edges, int32_t nshell,
+                            int32_t nside, const ufc_source *src, double *A,
+                            double *B, double *C, double *dA, double *dC);
+
+/* ---- binning (Eq. 5, Eq. 8, HEALPix pixelisation) ------------------------- */
+
+/* Shell and pixel of every particle of one box without replication:
+ * keys_dev[i] = shell * 12 nside^2 + pix, -1 when the radius is outside the
+ * box's shells, -2 when the particle is invalid (non-finite, or r == 0).
+ * chi_edges: nshell+1 increasing FP64 radii (host).  Membership is
+ * chi_b <= r < chi_{b+1} (Eq. 8 read half-open); the pixel is the RING pixel
+ * of the fixed FP64 procedure documented with the library (bit-exact). */
+ufc_status ufc_keys(ufc_ctx *ctx, const float *xyz_dev, int64_t n,
+                    const ufc_box *box, const double *chi_edges, int32_t nshell,
+                    int32_t nside, int32_t *keys_dev);
+
+#define UFC_BIN_ACCUMULATE 1   /* add to counts_dev instead of overwriting */
+
+/* Count maps of one lightcone made of nbox boxes: box k's particles are
+ * xyz_dev[k] (n[k] of them).  counts_dev [nshell][12 nside^2] is overwritten
+ * (or added to with UFC_BIN_ACCUMULATE).  nshell * 12 nside^2 < 2^30. */
+ufc_status ufc_bin(ufc_ctx *ctx, const float *const *xyz_dev, const int64_t *n,
+                   const ufc_box *boxes, int32_t nbox, const double *chi_edges,
+                   int32_t nshell, int32_t nside, int32_t flags,
+                   int32_t *counts_dev);
+/* Diagnostics of the last ufc_bin/ufc_keys call (synchronises):
+ * info[0] invalid particles, info[1] particle-images with a key,
+ * info[2] decisions refined past the FP32 stage, info[3] past the
+ * float-float stage (resolved by the FP64 procedure itself). */
+ufc_status ufc_bin_info(ufc_ctx *ctx, int64_t info[4]);
+
+/* ---- kappa map, moments, PDF (Eq. 6, Eq. 12-13, Sec. 3.3) ------------------ */
+
+/* kappa_p = sum_b A[b] n_bp - C accumulated to better than FP64's needs in
+ * double-float arithmetic, rounded once to FP32 (kappa_dev, may be NULL).
+ * moments_dev[10] (FP64): mean, mu2, mu3, mu4, skewness, excess kurtosis,
+ * <s^2> = (N-1) mu2/N, sigma^2_{s^2} (Eq. 13), s^2/sigma^2_{s^2}, N, where
+ * mu_k are the central moments of the FP32 map.  pdf_dev[nbins+3] (int64):
+ * counts of bin = floor((kappa - lo) * nbins/(hi - lo)), then underflow
+ * (kappa < lo), overflow (kappa >= hi) and NaN. A and C are host arrays. */
+ufc_status ufc_kappa_stats(ufc_ctx *ctx, const int32_t *counts_dev,
+                           int32_t nshell, int32_t nside, const double *A,
+                           double C, double pdf_lo, double pdf_hi,
+                           int32_t nbins, float *kappa_dev, double *moments_dev,
+                           int64_t *pdf_dev);
+
+/* ---- adjoint --------------------------------------------------------------- */
+
+/* Gradient of L = w_var var(kappa) + w_skew skew(kappa) + sum_p g_p kappa_p
+ * with respect to theta = (Omega_m, h, alpha, beta, z0), counts held fixed,
+ * for the unrounded map kappa_p = sum_b A_b n_bp - C:
+ *   dL/dtheta = sum_b dA_b/dtheta G_b - dC/dtheta H,
+ *   G_b = sum_p gbar_p n_bp,  H = sum_p gbar_p,  gbar = dL/dkappa.
+ * g_kappa_dev (FP32 [npix]) may be NULL.  dA [5][nshell], dC [5] come from
+ * ufc_kappa_coeffs.  grad_theta [5] (host) receives dL/dtheta; G [nshell]
+ * and H (host) may be NULL.  Synchronises. */
+ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
+                              int32_t nshell, int32_t nside, const double *A,
+                              double C, double w_var, double w_skew,
+                              const float *g_kappa_dev, const double *dA,
+                              const double *dC, double *grad_theta, double *G,
+                              double *H);
+
+/* ---- covariance over realisations (Eq. 10-11) ------------------------------ */
+
+/* Statistics vector of one map, the quantity whose covariance over
+ * realisations is estimated: v_dev[6 + nbins] = (mean, mu2, mu3, mu4, skew,
+ * excess kurtosis, pdf[0..nbins-1] / N) from ufc_kappa_stats's outputs. */
+ufc_status ufc_stats_vector(ufc_ctx *ctx, const double *moments_dev,
+                            const int64_t *pdf_dev, int32_t nbins, double *v_dev);
+
+/* A Welford state for d-dimensional vectors is 1 + d + d*d doubles:
+ * count, mean[d], M2[d][d].  ufc_welford_update adds the nvec vectors
+ * v_dev [nvec][d] in order (Welford/Chan update in FP64, device memory);
+ * ufc_welford_merge adds state b into state a (Chan et al. pairwise
+ * formula); ufc_welford_finalize writes mean, cov = M2/(n - ddof) and
+ * corr = cov_ij / sqrt(cov_ii cov_jj) (0 where a variance is 0), all device
+ * memory.  Zero a state (all doubles 0) before its first update. */
+ufc_status ufc_welford_update(ufc_ctx *ctx, const double *v_dev, int32_t nvec,
+                              int32_t d, double *state_dev);
+ufc_status ufc_welford_merge(ufc_ctx *ctx, double *state_a_dev,
+                             const double *state_b_dev, int32_t d);
+ufc_status ufc_welford_finalize(ufc_ctx *ctx, const double *state_dev,
+                                int32_t d, int32_t ddof, double *mean_dev,
+                                double *cov_dev, double *corr_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UFALCON_H */

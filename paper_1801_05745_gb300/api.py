@@ -1,0 +1,350 @@
+"""Python binding of the C ABI in ``include/ufalcon.h`` (libufalcon_gb300.so).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  Device buffers are torch tensors on the context's device; the
+calls are enqueued on torch's current CUDA stream.  There is no CPU
+fallback: importing this module raises if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libufalcon_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libufalcon_gb300.so is not built ({LIB_PATH}); run "
+                      "paper_1801_05745_gb300.build.build() or __graft_entry__.build()")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+D = ctypes.c_double
+DP = ctypes.POINTER(ctypes.c_double)
+
+UFC_OK = 0
+UFC_BIN_ACCUMULATE = 1
+NMOMENTS = 10
+MOMENT_NAMES = ("mean", "mu2", "mu3", "mu4", "skew", "kurt", "s2_expect", "var_s2",
+                "s2_over_var_s2", "n")
+
+
+class Cosmo(ctypes.Structure):
+    """ufc_cosmo: flat LambdaCDM (omega_m, h), lengths in Mpc/h if units_mpc_over_h."""
+    _fields_ = [("omega_m", D), ("h", D), ("units_mpc_over_h", I32)]
+
+
+class Box(ctypes.Structure):
+    """ufc_box: one box of the nesting scheme (observer, owned shells, n_total)."""
+    _fields_ = [("L", D), ("obs", D * 3), ("n_total", I64), ("shell_lo", I32),
+                ("shell_hi", I32), ("replicate", I32)]
+
+
+class Source(ctypes.Structure):
+    """ufc_source: kind 0 = plane at z_s, kind 1 = n(z) ~ z^alpha exp(-(z/z0)^beta)."""
+    _fields_ = [("kind", I32), ("z_s", D), ("alpha", D), ("beta", D), ("z0", D), ("z_max", D)]
+
+
+def make_cosmo(omega_m=0.3, h=0.7, units_mpc_over_h=1) -> Cosmo:
+    return Cosmo(float(omega_m), float(h), int(units_mpc_over_h))
+
+
+def make_box(L, obs, n_total, shell_lo, shell_hi, replicate=0) -> Box:
+    b = Box()
+    b.L = float(L)
+    for i in range(3):
+        b.obs[i] = float(obs[i])
+    b.n_total, b.shell_lo, b.shell_hi, b.replicate = int(n_total), int(shell_lo), int(shell_hi), int(replicate)
+    return b
+
+
+def make_source(kind=0, z_s=1.5, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5) -> Source:
+    return Source(int(kind), float(z_s), float(alpha), float(beta), float(z0), float(z_max))
+
+
+_SIGS = {
+    "ufc_create": [ctypes.POINTER(P), I32],
+    "ufc_destroy": [P],
+    "ufc_set_stream": [P, P],
+    "ufc_synchronize": [P],
+    "ufc_reserve": [P, I32, I32, I64],
+    "ufc_chi_edges": [ctypes.POINTER(Cosmo), P, I32, P],
+    "ufc_z_of_chi": [ctypes.POINTER(Cosmo), P, I32, P],
+    "ufc_kappa_coeffs": [ctypes.POINTER(Cosmo), P, I32, P, I32, I32, ctypes.POINTER(Source),
+                         P, P, P, P, P],
+    "ufc_keys": [P, P, I64, ctypes.POINTER(Box), P, I32, I32, P],
+    "ufc_bin": [P, P, P, P, I32, P, I32, I32, I32, P],
+    "ufc_bin_info": [P, P],
+    "ufc_kappa_stats": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
+    "ufc_kappa_backward": [P, P, I32, I32, P, D, D, D, P, P, P, P, P, P],
+    "ufc_welford_update": [P, P, I32, I32, P],
+    "ufc_welford_merge": [P, P, P, I32],
+    "ufc_welford_finalize": [P, P, I32, I32, P, P, P],
+    "ufc_stats_vector": [P, P, P, I32, P],
+    "ufc_profile_enable": [P, I32],
+    "ufc_profile_read": [P, I32, P, P, P, P],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.ufc_last_error.argtypes = [P]
+_lib.ufc_last_error.restype = ctypes.c_char_p
+
+
+class UfcError(RuntimeError):
+    pass
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(P)
+
+
+def _check(status: int, ctx=None, what=""):
+    if status != UFC_OK:
+        msg = _lib.ufc_last_error(ctx).decode() if ctx else ""
+        raise UfcError(f"{what} failed with status {status}: {msg}")
+
+
+# ---- host cosmology ---------------------------------------------------------------
+def chi_edges(cosmo: Cosmo, z_edges) -> np.ndarray:
+    """chi(z) of the shell edges (Delta chi_b of Sec. 2.4), FP64."""
+    z = np.ascontiguousarray(z_edges, dtype=np.float64)
+    out = np.empty_like(z)
+    _check(_lib.ufc_chi_edges(ctypes.byref(cosmo), _np_ptr(z), len(z) - 1, _np_ptr(out)),
+           what="ufc_chi_edges")
+    return out
+
+
+def z_of_chi(cosmo: Cosmo, chi) -> np.ndarray:
+    c = np.ascontiguousarray(np.atleast_1d(chi), dtype=np.float64)
+    out = np.empty_like(c)
+    _check(_lib.ufc_z_of_chi(ctypes.byref(cosmo), _np_ptr(c), len(c), _np_ptr(out)),
+           what="ufc_z_of_chi")
+    return out
+
+
+def kappa_coeffs(cosmo: Cosmo, boxes, z_edges, nside: int, source: Source, derivs=False):
+    """(A, B, C[, dA, dC]) of kappa_p = sum_b A_b n_bp - C (Eq. 6)."""
+    z = np.ascontiguousarray(z_edges, dtype=np.float64)
+    S = len(z) - 1
+    arr = (Box * len(boxes))(*boxes)
+    A, B = np.empty(S), np.empty(S)
+    C = ctypes.c_double()
+    dA = np.empty((5, S)) if derivs else None
+    dC = np.empty(5) if derivs else None
+    _check(_lib.ufc_kappa_coeffs(ctypes.byref(cosmo), ctypes.cast(arr, P), len(boxes), _np_ptr(z),
+                                 S, nside, ctypes.byref(source), _np_ptr(A), _np_ptr(B),
+                                 ctypes.byref(C), _np_ptr(dA) if derivs else None,
+                                 _np_ptr(dC) if derivs else None), what="ufc_kappa_coeffs")
+    if derivs:
+        return A, B, C.value, dA, dC
+    return A, B, C.value
+
+
+# ---- device context ---------------------------------------------------------------
+class Context:
+    """A library context on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0):
+        import torch  # noqa: F401  (device memory and streams)
+        self.device = int(device)
+        h = P()
+        st = _lib.ufc_create(ctypes.byref(h), self.device)
+        if st != UFC_OK:
+            raise UfcError(f"ufc_create({device}) failed with status {st}")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.ufc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        import torch
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _lib.ufc_set_stream(self.h, P(s))
+
+    def _ck(self, st, what):
+        _check(st, self.h, what)
+
+    def synchronize(self):
+        self._ck(_lib.ufc_synchronize(self.h), "ufc_synchronize")
+
+    def profile(self, on: bool = True):
+        """Bracket every library kernel launch with CUDA events (tracing)."""
+        self._ck(_lib.ufc_profile_enable(self.h, 1 if on else 0), "ufc_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{kernel name: (total ms, launches)} since the last read (synchronises)."""
+        mx = 64
+        names = ctypes.create_string_buffer(32 * mx)
+        ms = np.zeros(mx)
+        cnt = np.zeros(mx, dtype=np.int64)
+        n = ctypes.c_int32()
+        self._stream()
+        self._ck(_lib.ufc_profile_read(self.h, mx, names, _np_ptr(ms), _np_ptr(cnt), ctypes.byref(n)),
+                 "ufc_profile_read")
+        out = {}
+        for i in range(min(n.value, mx)):
+            nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+            out[nm] = (float(ms[i]), int(cnt[i]))
+        return out
+
+    def reserve(self, nside: int, nshell: int, n_max: int):
+        self._ck(_lib.ufc_reserve(self.h, nside, nshell, n_max), "ufc_reserve")
+
+    # -- binning --
+    def keys(self, xyz, box: Box, chi_edges, nside: int, out=None):
+        import torch
+        xyz = _dev_f32(xyz, self.device)
+        n = xyz.numel() // 3
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=xyz.device)
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        self._stream()
+        self._ck(_lib.ufc_keys(self.h, P(xyz.data_ptr()), n, ctypes.byref(box), _np_ptr(chi),
+                               len(chi) - 1, nside, P(out.data_ptr())), "ufc_keys")
+        return out
+
+    def bin(self, xyz_list, boxes, chi_edges, nside: int, counts=None, accumulate=False):
+        """int32 [nshell, 12 nside^2] count maps of the lightcone (Eq. 5, 8)."""
+        import torch
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        S = len(chi) - 1
+        npix = 12 * nside * nside
+        xs = [_dev_f32(x, self.device) for x in xyz_list]
+        if counts is None:
+            counts = torch.empty((S, npix), dtype=torch.int32, device=f"cuda:{self.device}")
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.numel() == S * npix
+        ptrs = (P * len(xs))(*[P(x.data_ptr()) for x in xs])
+        ns = (I64 * len(xs))(*[x.numel() // 3 for x in xs])
+        arr = (Box * len(boxes))(*boxes)
+        self._stream()
+        self._ck(_lib.ufc_bin(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P), ctypes.cast(arr, P),
+                              len(boxes), _np_ptr(chi), S, nside,
+                              UFC_BIN_ACCUMULATE if accumulate else 0, P(counts.data_ptr())),
+                 "ufc_bin")
+        return counts
+
+    def bin_info(self):
+        out = np.zeros(4, dtype=np.int64)
+        self._stream()
+        self._ck(_lib.ufc_bin_info(self.h, _np_ptr(out)), "ufc_bin_info")
+        return dict(invalid=int(out[0]), keyed=int(out[1]), refined=int(out[2]), exact=int(out[3]))
+
+    # -- kappa, moments, PDF --
+    def kappa_stats(self, counts, A, C, pdf_lo, pdf_hi, nbins=200, kappa=None, want_stats=True):
+        """(kappa FP32 [npix], moments FP64 [10], pdf int64 [nbins+3]) on the device."""
+        import torch
+        S, npix = counts.shape
+        nside = int(round((npix / 12) ** 0.5))
+        dev = counts.device
+        if kappa is None:
+            kappa = torch.empty(npix, dtype=torch.float32, device=dev)
+        mom = torch.empty(NMOMENTS, dtype=torch.float64, device=dev) if want_stats else None
+        pdf = torch.empty(nbins + 3, dtype=torch.int64, device=dev) if want_stats else None
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        self._stream()
+        self._ck(_lib.ufc_kappa_stats(self.h, P(counts.data_ptr()), S, nside, _np_ptr(A), float(C),
+                                      float(pdf_lo), float(pdf_hi), nbins, P(kappa.data_ptr()),
+                                      P(mom.data_ptr()) if want_stats else None,
+                                      P(pdf.data_ptr()) if want_stats else None),
+                 "ufc_kappa_stats")
+        return kappa, mom, pdf
+
+    def kappa_backward(self, counts, A, C, dA, dC, w_var=0.0, w_skew=0.0, g_kappa=None):
+        """(dL/dtheta [5], G [nshell], H) for L = w_var var + w_skew skew + <g, kappa>."""
+        S, npix = counts.shape
+        nside = int(round((npix / 12) ** 0.5))
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        dA = np.ascontiguousarray(dA, dtype=np.float64)
+        dC = np.ascontiguousarray(dC, dtype=np.float64)
+        grad = np.empty(5)
+        G = np.empty(S)
+        H = ctypes.c_double()
+        gp = None
+        if g_kappa is not None:
+            g_kappa = _dev_f32(g_kappa, self.device)
+            gp = P(g_kappa.data_ptr())
+        self._stream()
+        self._ck(_lib.ufc_kappa_backward(self.h, P(counts.data_ptr()), S, nside, _np_ptr(A),
+                                         float(C), float(w_var), float(w_skew), gp, _np_ptr(dA),
+                                         _np_ptr(dC), _np_ptr(grad), _np_ptr(G), ctypes.byref(H)),
+                 "ufc_kappa_backward")
+        return grad, G, H.value
+
+    # -- covariance --
+    def stats_vector(self, moments, pdf, out=None):
+        """(mean, mu2, mu3, mu4, skew, kurt, pdf/N) of one map, FP64 on the device."""
+        import torch
+        nbins = pdf.numel() - 3
+        if out is None:
+            out = torch.empty(6 + nbins, dtype=torch.float64, device=moments.device)
+        self._stream()
+        self._ck(_lib.ufc_stats_vector(self.h, P(moments.data_ptr()), P(pdf.data_ptr()), nbins,
+                                       P(out.data_ptr())), "ufc_stats_vector")
+        return out
+
+    def welford_update(self, v, state):
+        v = v.contiguous()
+        nvec, d = v.shape
+        self._stream()
+        self._ck(_lib.ufc_welford_update(self.h, P(v.data_ptr()), nvec, d, P(state.data_ptr())),
+                 "ufc_welford_update")
+
+    def welford_merge(self, a, b, d):
+        self._stream()
+        self._ck(_lib.ufc_welford_merge(self.h, P(a.data_ptr()), P(b.data_ptr()), d),
+                 "ufc_welford_merge")
+
+    def welford_finalize(self, state, d, ddof=1):
+        import torch
+        dev = state.device
+        mean = torch.empty(d, dtype=torch.float64, device=dev)
+        cov = torch.empty((d, d), dtype=torch.float64, device=dev)
+        corr = torch.empty((d, d), dtype=torch.float64, device=dev)
+        self._stream()
+        self._ck(_lib.ufc_welford_finalize(self.h, P(state.data_ptr()), d, ddof, P(mean.data_ptr()),
+                                           P(cov.data_ptr()), P(corr.data_ptr())),
+                 "ufc_welford_finalize")
+        return mean, cov, corr
+
+
+def welford_state(d: int, device="cuda"):
+    import torch
+    return torch.zeros(1 + d + d * d, dtype=torch.float64, device=device)
+
+
+def _dev_f32(x, device):
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("expected a CUDA float32 tensor")
+    if x.dtype != torch.float32 or not x.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    return x
+
+
+_ctx_lock = threading.Lock()
+_ctxs: dict[int, Context] = {}
+
+
+def context(device: int = 0) -> Context:
+    """Process-wide default context of a device."""
+    with _ctx_lock:
+        if device not in _ctxs:
+            _ctxs[device] = Context(device)
+        return _ctxs[device]

@@ -1,0 +1,844 @@
+// Particle -> (shell, RING pixel) keys and per-shell count maps (Eq. 5,
+// Eq. 8 and the HEALPix pixelisation of Sec. 2.4).
+//
+// Pipeline of one binning call:
+//   fast stage  k_fast    : one pass over the particles (FP32 arithmetic);
+//                           decided keys go to the output, undecided
+//                           particle images to queue 1.
+//   refine stage k_refine : double-float over queue 1; undecided to queue 2.
+//   exact stage k_exact   : the FP64 procedure over queue 2.
+// Outputs (mode):
+//   KEYS   : int32 key per particle (ufc_keys).
+//   DIRECT : atomicAdd into the count map (maps that sit in L2).
+//   DENSE  : keys packed as (bucket << 15 | offset) with bucket = shell *
+//            nblk + pix / 24576, appended per warp to a dense array while a
+//            shared-memory histogram counts buckets; then two scatter passes
+//            (by bucket group, then by bucket) and a shared-memory histogram
+//            per bucket that writes each 24576-pixel block of the count map
+//            once.  No global atomics on the count map.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "pixel.cuh"
+
+namespace ufc {
+
+enum Mode { kModeKeys = 0, kModeDirect = 1, kModeDense = 2 };
+
+constexpr int kBlockPix = 24576;        // pixels per count-map block (96 KB of u32)
+constexpr int kOffBits = 15;            // offset bits in a dense key
+constexpr uint32_t kSentinel = 0xFFFFFFFFu;
+constexpr int kChunk = 2048;            // dense keys reserved per warp at a time
+constexpr int kGroupBits = 8;           // buckets per group = 256
+constexpr int kSmemHistMax = 28672;     // buckets counted in shared memory
+constexpr int kFastThreads = 512;
+
+struct KeyOut {
+  int32_t* keys;               // KEYS
+  int32_t* counts;             // DIRECT
+  uint32_t* dense;             // DENSE
+  unsigned long long* dense_count;
+  uint32_t* hist;              // DENSE: global bucket histogram
+  int64_t dense_cap;
+  int32_t nblk;                // blocks per shell (DENSE)
+  int32_t nbuckets;
+  int32_t smem_hist;           // 1: histogram in shared memory
+};
+
+struct Queues {
+  uint64_t* q1;
+  uint64_t* q2;
+  int64_t cap1, cap2;
+  BinCounters* cnt;
+};
+
+// ---------------------------------------------------------------- emission --
+struct WarpChunk {
+  int64_t base;   // start of the warp's current chunk (-1: none)
+  int32_t fill;
+};
+
+__device__ __forceinline__ uint32_t dense_key(int32_t key, int32_t npix, int32_t nblk) {
+  int32_t b = key / npix;
+  int32_t pix = key - b * npix;
+  int32_t blk = pix / kBlockPix;
+  return (uint32_t(b * nblk + blk) << kOffBits) | uint32_t(pix - blk * kBlockPix);
+}
+
+// Appends the keys of lanes with `want` to the warp's chunk of the dense
+// array (all 32 lanes call this together).
+__device__ __forceinline__ void dense_append(WarpChunk& wc, bool want, uint32_t v,
+                                             const KeyOut& o) {
+  const unsigned full = 0xFFFFFFFFu;
+  unsigned m = __ballot_sync(full, want);
+  if (m == 0) return;
+  int lane = threadIdx.x & 31;
+  int cnt = __popc(m);
+  int rank = __popc(m & ((1u << lane) - 1u));
+  if (wc.base < 0) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(o.dense_count, (unsigned long long)kChunk);
+    wc.base = (int64_t)__shfl_sync(full, b, 0);
+    wc.fill = 0;
+  }
+  int room = kChunk - wc.fill;
+  if (want && rank < room) {
+    int64_t idx = wc.base + wc.fill + rank;
+    if (idx < o.dense_cap) o.dense[idx] = v;
+  }
+  if (cnt >= room) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(o.dense_count, (unsigned long long)kChunk);
+    int64_t nb = (int64_t)__shfl_sync(full, b, 0);
+    if (want && rank >= room && nb + (rank - room) < o.dense_cap) o.dense[nb + (rank - room)] = v;
+    wc.base = nb;
+    wc.fill = cnt - room;
+  } else {
+    wc.fill += cnt;
+  }
+}
+
+__device__ __forceinline__ void dense_close(WarpChunk& wc, const KeyOut& o) {
+  if (wc.base < 0) return;
+  int lane = threadIdx.x & 31;
+  for (int i = wc.fill + lane; i < kChunk; i += 32)
+    if (wc.base + i < o.dense_cap) o.dense[wc.base + i] = kSentinel;
+}
+
+// Warp-aggregated push of undecided entries; returns false for lanes whose
+// entry did not fit (they must resolve it themselves).
+__device__ __forceinline__ bool queue_push(bool want, uint64_t e, uint64_t* q,
+                                           int64_t cap, unsigned long long* count) {
+  const unsigned full = 0xFFFFFFFFu;
+  unsigned m = __ballot_sync(full, want);
+  if (m == 0) return true;
+  int lane = threadIdx.x & 31;
+  unsigned long long b = 0;
+  if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(m));
+  b = __shfl_sync(full, b, 0);
+  int64_t idx = (int64_t)b + __popc(m & ((1u << lane) - 1u));
+  if (!want) return true;
+  if (idx < cap) { q[idx] = e; return true; }
+  return false;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// ----------------------------------------------------------- fast stage ----
+template <int MODE>
+__global__ void __launch_bounds__(kFastThreads)
+k_fast(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
+       ShellTable st, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
+  extern __shared__ uint32_t hist_s[];
+  __shared__ float lo2_s[kMaxShells + 1], hi2_s[kMaxShells + 1];
+  __shared__ float shf_s[3][kMaxImg1D], shlo_s[3][kMaxImg1D];
+  for (int i = threadIdx.x; i <= st.nshell; i += blockDim.x) {
+    lo2_s[i] = st.lo2[i];
+    hi2_s[i] = st.hi2[i];
+  }
+  for (int i = threadIdx.x; i < 3 * kMaxImg1D; i += blockDim.x) {
+    shf_s[i / kMaxImg1D][i % kMaxImg1D] = bg.shf[i / kMaxImg1D][i % kMaxImg1D];
+    shlo_s[i / kMaxImg1D][i % kMaxImg1D] = bg.shlo[i / kMaxImg1D][i % kMaxImg1D];
+  }
+  if (MODE == kModeDense && o.smem_hist)
+    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) hist_s[i] = 0;
+  __syncthreads();
+
+  const int lo = bg.shell_lo, hi = bg.shell_hi;
+  const int n1 = 2 * bg.R + 1;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (n + stride - 1) / stride;
+  unsigned long long n_invalid = 0, n_keyed = 0;
+  WarpChunk wc{-1, 0};
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < iters; ++it, p += stride) {
+    const bool have = p < n;
+    float x = 0.f, y = 0.f, zc = 0.f;
+    if (have) {
+      x = __ldg(xyz + 3 * p);
+      y = __ldg(xyz + 3 * p + 1);
+      zc = __ldg(xyz + 3 * p + 2);
+    }
+    const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
+    if (have && !finite) ++n_invalid;
+    for (int img = 0; img < bg.nimg; ++img) {
+      int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
+      int32_t key = kKeyOutside;
+      uint32_t dkey = 0u;
+      if (finite) {
+        float dx = (x + shf_s[0][ii]) + shlo_s[0][ii];
+        float dy = (y + shf_s[1][jj]) + shlo_s[1][jj];
+        float dz = (zc + shf_s[2][kk]) + shlo_s[2][kk];
+        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        if (!(r2 >= bd.r2_min)) {
+          key = kKeyUndecided;
+        } else {
+          int32_t b = shell_fast(lo2_s, hi2_s, lo, hi, r2);
+          if (b == -2) key = kKeyUndecided;
+          else if (b >= 0) {
+            int32_t pix = pixel_fast(N, bd, dx, dy, dz, r2);
+            key = (pix == kKeyUndecided) ? kKeyUndecided : b * npix + pix;
+            if (MODE == kModeDense && pix != kKeyUndecided) {
+              uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
+              dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
+                     (uint32_t(pix) - blk * uint32_t(kBlockPix));
+            }
+          }
+        }
+      }
+      const bool und = key == kKeyUndecided;
+      if (!queue_push(und, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
+        // queue full: resolve with the FP64 procedure here
+        key = key_exact(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii], bg.sh64[1][jj],
+                        bg.sh64[2][kk]);
+        if (key == kKeyInvalid) ++n_invalid;
+        if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o.nblk);
+      }
+      if (MODE == kModeKeys) {
+        if (have) o.keys[p] = finite ? key : kKeyInvalid;
+      } else if (MODE == kModeDirect) {
+        if (key >= 0) atomicAdd(o.counts + key, 1);
+      } else {
+        if (key >= 0) {
+          uint32_t bucket = dkey >> kOffBits;
+          if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
+          else atomicAdd(o.hist + bucket, 1u);
+        }
+        dense_append(wc, key >= 0, dkey, o);
+      }
+      n_keyed += key >= 0;
+    }
+  }
+  if (MODE == kModeDense) dense_close(wc, o);
+  n_invalid = warp_sum(n_invalid);
+  n_keyed = warp_sum(n_keyed);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_invalid) atomicAdd(&qs.cnt->invalid, n_invalid);
+    if (n_keyed) atomicAdd(&qs.cnt->keyed, n_keyed);
+  }
+  if (MODE == kModeDense && o.smem_hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x)
+      if (hist_s[i]) atomicAdd(o.hist + i, hist_s[i]);
+  }
+}
+
+// ------------------------------------------------ refine and exact stages --
+template <int MODE>
+__device__ __forceinline__ void emit_late(int32_t key, int64_t p, int32_t npix,
+                                          const KeyOut& o, WarpChunk& wc) {
+  if (MODE == kModeKeys) {
+    o.keys[p] = key;
+  } else if (MODE == kModeDirect) {
+    if (key >= 0) atomicAdd(o.counts + key, 1);
+  } else {
+    uint32_t dk = key >= 0 ? dense_key(key, npix, o.nblk) : 0u;
+    if (key >= 0) atomicAdd(o.hist + (dk >> kOffBits), 1u);
+    dense_append(wc, key >= 0, dk, o);
+  }
+}
+
+struct BoxesParam {
+  BoxGeom box[kMaxBoxes];
+  const float* xyz[kMaxBoxes];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues qs) {
+  const unsigned long long total = qs.cnt->q1;
+  const int64_t m = (int64_t)min((unsigned long long)qs.cap1, total);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (m + stride - 1) / stride;
+  WarpChunk wc{-1, 0};
+  unsigned long long n_ref = 0, n_invalid = 0, n_keyed = 0;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < iters; ++it, i += stride) {
+    const bool have = i < m;
+    int32_t key = kKeyOutside;
+    int64_t p = 0;
+    uint64_t e = 0;
+    if (have) {
+      e = qs.q1[i];
+      const int b = qbox(e), img = qimg(e);
+      p = qidx(e);
+      const BoxGeom& g = bp.box[b];
+      const int n1 = 2 * g.R + 1;
+      const int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
+      const float* xp = bp.xyz[b] + 3 * p;
+      float x = xp[0], y = xp[1], zc = xp[2];
+      key = key_refine(st, g.shell_lo, g.shell_hi, N, npix, x, y, zc, g.shf[0][ii],
+                       g.shf[1][jj], g.shf[2][kk], g.shlo[0][ii], g.shlo[1][jj],
+                       g.shlo[2][kk]);
+      ++n_ref;
+    }
+    const bool und = have && key == kKeyUndecided;
+    if (!queue_push(und, e, qs.q2, qs.cap2, &qs.cnt->q2)) {
+      const int b = qbox(e), img = qimg(e);
+      const BoxGeom& g = bp.box[b];
+      const int n1 = 2 * g.R + 1;
+      const int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
+      const float* xp = bp.xyz[b] + 3 * p;
+      key = key_exact(st, g.shell_lo, g.shell_hi, N, npix, xp[0], xp[1], xp[2],
+                      g.sh64[0][ii], g.sh64[1][jj], g.sh64[2][kk]);
+      if (key == kKeyInvalid) ++n_invalid;
+    }
+    const bool done = have && key != kKeyUndecided;
+    n_keyed += done && key >= 0;
+    if (MODE == kModeDense) {
+      emit_late<MODE>(done ? key : kKeyOutside, p, npix, o, wc);
+    } else if (done) {
+      emit_late<MODE>(key, p, npix, o, wc);
+    }
+  }
+  if (MODE == kModeDense) dense_close(wc, o);
+  n_ref = warp_sum(n_ref);
+  n_invalid = warp_sum(n_invalid);
+  n_keyed = warp_sum(n_keyed);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_ref) atomicAdd(&qs.cnt->refined, n_ref);
+    if (n_invalid) atomicAdd(&qs.cnt->invalid, n_invalid);
+    if (n_keyed) atomicAdd(&qs.cnt->keyed, n_keyed);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_exact(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues qs) {
+  const unsigned long long total = qs.cnt->q2;
+  const int64_t m = (int64_t)min((unsigned long long)qs.cap2, total);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t iters = (m + stride - 1) / stride;
+  WarpChunk wc{-1, 0};
+  unsigned long long n_ex = 0, n_invalid = 0, n_keyed = 0;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t it = 0; it < iters; ++it, i += stride) {
+    const bool have = i < m;
+    int32_t key = kKeyOutside;
+    int64_t p = 0;
+    if (have) {
+      const uint64_t e = qs.q2[i];
+      const int b = qbox(e), img = qimg(e);
+      p = qidx(e);
+      const BoxGeom& g = bp.box[b];
+      const int n1 = 2 * g.R + 1;
+      const int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
+      const float* xp = bp.xyz[b] + 3 * p;
+      key = key_exact(st, g.shell_lo, g.shell_hi, N, npix, xp[0], xp[1], xp[2],
+                      g.sh64[0][ii], g.sh64[1][jj], g.sh64[2][kk]);
+      ++n_ex;
+      if (key == kKeyInvalid) ++n_invalid;
+      n_keyed += key >= 0;
+    }
+    if (MODE == kModeDense) emit_late<MODE>(have ? key : kKeyOutside, p, npix, o, wc);
+    else if (have) emit_late<MODE>(key, p, npix, o, wc);
+  }
+  if (MODE == kModeDense) dense_close(wc, o);
+  n_ex = warp_sum(n_ex);
+  n_invalid = warp_sum(n_invalid);
+  n_keyed = warp_sum(n_keyed);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_ex) atomicAdd(&qs.cnt->exact, n_ex);
+    if (n_invalid) atomicAdd(&qs.cnt->invalid, n_invalid);
+    if (n_keyed) atomicAdd(&qs.cnt->keyed, n_keyed);
+  }
+}
+
+// ------------------------------------------------------ dense pipeline -----
+// Exclusive scan of hist[nb] into off[nb+1] (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ hist, int nb,
+                                               int64_t* __restrict__ off) {
+  __shared__ int64_t part[1024];
+  const int t = threadIdx.x;
+  const int per = (nb + 1023) / 1024;
+  const int a = t * per, b = min(nb, a + per);
+  int64_t s = 0;
+  for (int i = a; i < b; ++i) s += hist[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int64_t v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = t ? part[t - 1] : 0;
+  for (int i = a; i < b; ++i) {
+    off[i] = run;
+    run += hist[i];
+  }
+  if (t == 1023) off[nb] = part[1023];
+}
+
+// Cursor initialisation: gcur[g] = off[g << kGroupBits], bcur[b] = off[b].
+__global__ void k_cursors(const int64_t* __restrict__ off, int nb, int ng,
+                          unsigned long long* __restrict__ gcur,
+                          unsigned long long* __restrict__ bcur) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nb) bcur[i] = (unsigned long long)off[i];
+  if (i < ng) gcur[i] = (unsigned long long)off[min(nb, i << kGroupBits)];
+}
+
+// Exclusive scan of cnt[0..n) into start[] by the first warp.
+__device__ __forceinline__ void warp_exclusive_scan(const uint32_t* cnt, uint32_t* start, int n) {
+  const int lane = threadIdx.x & 31;
+  const int per = (n + 31) / 32;
+  const int a = lane * per, b = min(n, a + per);
+  uint32_t s = 0;
+  for (int i = a; i < b; ++i) s += cnt[i];
+  uint32_t incl = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  uint32_t run = incl - s;
+  for (int i = a; i < b; ++i) { start[i] = run; run += cnt[i]; }
+}
+
+constexpr int kScatThreads = 256;
+constexpr int kScatPer = 16;
+constexpr int kScatTile = kScatThreads * kScatPer;   // 4096 keys
+
+// Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.
+__global__ void __launch_bounds__(kScatThreads)
+k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* dense_count,
+                int64_t dense_cap, int ng, unsigned long long* __restrict__ gcur, uint32_t* __restrict__ out) {
+  extern __shared__ uint32_t sm[];
+  uint32_t* cnt = sm;                      // [ng]
+  uint32_t* start = sm + ng;               // [ng]
+  unsigned long long* base = (unsigned long long*)(sm + 2 * ng);  // [ng], 8-aligned
+  uint32_t* tile = (uint32_t*)(base + ng); // [kScatTile]
+  const int64_t total = (int64_t)min(*dense_count, (unsigned long long)dense_cap);
+  const int64_t ntiles = (total + kScatTile - 1) / kScatTile;
+  const int shift = kOffBits + kGroupBits;
+  for (int64_t tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    uint32_t v[kScatPer];
+    uint32_t slot[kScatPer];
+    const int64_t t0 = tIdx * kScatTile;
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) {
+      int64_t i = t0 + k * kScatThreads + threadIdx.x;
+      v[k] = i < total ? dense[i] : kSentinel;
+      slot[k] = v[k] != kSentinel ? atomicAdd(cnt + (v[k] >> shift), 1u) : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) warp_exclusive_scan(cnt, start, ng);
+    __syncthreads();
+    for (int g = threadIdx.x; g < ng; g += blockDim.x)
+      base[g] = cnt[g] ? atomicAdd(gcur + g, (unsigned long long)cnt[g]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k)
+      if (v[k] != kSentinel) tile[start[v[k] >> shift] + slot[k]] = v[k];
+    __syncthreads();
+    uint32_t used = start[ng - 1] + cnt[ng - 1];
+    for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) {
+      uint32_t val = tile[i];
+      uint32_t g = val >> shift;
+      out[base[g] + (i - start[g])] = val;
+    }
+    __syncthreads();
+  }
+}
+
+struct Tile { int32_t group; int32_t len; int64_t start; };
+
+// Tile list of pass B: every group's range split into kScatTile pieces.
+__global__ void __launch_bounds__(1024) k_tiles(const int64_t* __restrict__ off, int nb, int ng,
+                                                Tile* __restrict__ tiles,
+                                                unsigned long long* __restrict__ ntiles) {
+  __shared__ int64_t pre[1025];
+  const int t = threadIdx.x;
+  int64_t mine = 0;
+  for (int g = t; g < ng; g += 1024) {
+    int64_t a = off[min(nb, g << kGroupBits)], b = off[min(nb, (g + 1) << kGroupBits)];
+    mine += (b - a + kScatTile - 1) / kScatTile;
+  }
+  pre[t + 1] = mine;
+  if (t == 0) pre[0] = 0;
+  __syncthreads();
+  if (t == 0)
+    for (int i = 1; i <= 1024; ++i) pre[i] += pre[i - 1];
+  __syncthreads();
+  int64_t w = pre[t];
+  for (int g = t; g < ng; g += 1024) {
+    int64_t a = off[min(nb, g << kGroupBits)], b = off[min(nb, (g + 1) << kGroupBits)];
+    for (int64_t s = a; s < b; s += kScatTile)
+      tiles[w++] = Tile{g, (int32_t)((b - s) < kScatTile ? (b - s) : kScatTile), s};
+  }
+  if (t == 0) *ntiles = (unsigned long long)pre[1024];
+}
+
+// Pass B: grouped keys -> per-bucket u16 offsets.
+__global__ void __launch_bounds__(kScatThreads)
+k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ tiles,
+                 const unsigned long long* __restrict__ ntiles_p,
+                 unsigned long long* __restrict__ bcur, uint16_t* __restrict__ out) {
+  constexpr int NS = 1 << kGroupBits;
+  __shared__ uint32_t cnt[NS], start[NS];
+  __shared__ unsigned long long base[NS];
+  __shared__ uint16_t tile[kScatTile];
+  __shared__ uint8_t tsub[kScatTile];
+  const int64_t ntiles = (int64_t)*ntiles_p;
+  for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    const Tile T = tiles[ti];
+    for (int i = threadIdx.x; i < NS; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    uint32_t v[kScatPer], slot[kScatPer];
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) {
+      int i = k * kScatThreads + threadIdx.x;
+      v[k] = i < T.len ? grouped[T.start + i] : kSentinel;
+      slot[k] = v[k] != kSentinel
+                    ? atomicAdd(cnt + ((v[k] >> kOffBits) & (NS - 1)), 1u) : 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) warp_exclusive_scan(cnt, start, NS);
+    __syncthreads();
+    for (int sIdx = threadIdx.x; sIdx < NS; sIdx += blockDim.x)
+      base[sIdx] = cnt[sIdx] ? atomicAdd(bcur + ((int64_t)T.group << kGroupBits) + sIdx,
+                                         (unsigned long long)cnt[sIdx]) : 0ull;
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k)
+      if (v[k] != kSentinel) {
+        uint32_t sub = (v[k] >> kOffBits) & (NS - 1);
+        uint32_t pos = start[sub] + slot[k];
+        tile[pos] = uint16_t(v[k] & ((1u << kOffBits) - 1u));
+        tsub[pos] = uint8_t(sub);
+      }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T.len; i += blockDim.x) {
+      uint32_t sub = tsub[i];
+      out[base[sub] + (i - start[sub])] = tile[i];
+    }
+    __syncthreads();
+  }
+}
+
+// Count map of each bucket from its u16 offsets, in shared memory.
+constexpr int kHistThreads = 512;
+__global__ void __launch_bounds__(kHistThreads)
+k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off, int nb,
+             int32_t* __restrict__ counts, int accumulate) {
+  extern __shared__ uint32_t h[];   // [kBlockPix]
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    for (int i = threadIdx.x; i < kBlockPix; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t a = off[b], e = off[b + 1];
+    for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) atomicAdd(h + offs[i], 1u);
+    __syncthreads();
+    int4* dst = reinterpret_cast<int4*>(counts + (int64_t)b * kBlockPix);
+    const uint4* src = reinterpret_cast<const uint4*>(h);
+    for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) {
+      uint4 s = src[i];
+      int4 d = make_int4(int(s.x), int(s.y), int(s.z), int(s.w));
+      if (accumulate) {
+        int4 o = dst[i];
+        d.x += o.x; d.y += o.y; d.z += o.z; d.w += o.w;
+      }
+      dst[i] = d;
+    }
+    __syncthreads();
+  }
+}
+
+// ================================================================ host ======
+
+static float f_down(double v) {
+  float f = (float)v;
+  if ((double)f > v) f = nextafterf(f, -INFINITY);
+  return f;
+}
+static float f_up(double v) {
+  float f = (float)v;
+  if ((double)f < v) f = nextafterf(f, INFINITY);
+  return f;
+}
+
+// FP32-stage bands (error analysis in pixel.cuh and DESIGN):
+//  r2  : |r2f - R2| <= 7u R2      -> band 14u (x2)
+//  z   : |zf - Z| <= 10.5u |Z|   -> band 21u
+//  eq  : |w - W| <= 14u N (+u)   -> band 28u N + 2u
+//  cap : |v - V| <= 29u N        -> band 58u N + 2u
+//  ip  : |w3 - W3| <= 7.5u ir    -> band 15u ir (+2u)
+// plus guards that keep the absolute input error (2u^2 smax) negligible.
+static void make_bands(int N, float smax, Bands& bd) {
+  const double u = std::ldexp(1.0, -24);
+  const double two3 = 2.0 / 3.0;
+  bd.z_eq = f_down(two3 / (1.0 + 21.0 * u) * (1.0 - 1e-12));
+  bd.z_cap = f_up(two3 / (1.0 - 21.0 * u) * (1.0 + 1e-12));
+  bd.eq = f_up(28.0 * u * N + 2.0 * u);
+  bd.cap = f_up(58.0 * u * N + 2.0 * u);
+  bd.ip_per_ir = f_up(17.0 * u);
+  double g = std::ldexp(1.0, 11) * u * std::max<double>(smax, 1.0);
+  bd.r2_min = f_up(g * g);
+  bd.axy_min = f_up(g);
+  bd.pad_ = 0.f;
+}
+
+static ufc_status make_table(ufc_ctx* c, const double* chi, int nshell, ShellTable& st) {
+  const double u = std::ldexp(1.0, -24);
+  std::memset(&st, 0, sizeof st);
+  st.nshell = nshell;
+  for (int e = 0; e <= nshell; ++e) {
+    if (!std::isfinite(chi[e]) || chi[e] < 0.0)
+      return set_err(c, UFC_ERR_ARG, "chi_edges[%d] = %g is not a finite radius >= 0", e, chi[e]);
+    if (e > 0 && !(chi[e] > chi[e - 1]))
+      return set_err(c, UFC_ERR_ARG, "chi_edges must increase (edge %d)", e);
+    st.chi64[e] = chi[e];
+    double c2 = chi[e] * chi[e];
+    st.lo2[e] = f_down(c2 * (1.0 - 14.0 * u) * (1.0 - 1e-12));
+    st.hi2[e] = f_up(c2 * (1.0 + 14.0 * u) * (1.0 + 1e-12));
+    if (e > 0 && !(st.hi2[e - 1] <= st.lo2[e]))
+      return set_err(c, UFC_ERR_UNSUPPORTED,
+                     "shell edges %d and %d are closer than 3e-6 relative", e - 1, e);
+  }
+  return UFC_OK;
+}
+
+static ufc_status make_box(ufc_ctx* c, const ufc_box& b, int nshell, BoxGeom& g) {
+  std::memset(&g, 0, sizeof g);
+  if (!(b.L > 0.0) || !std::isfinite(b.L))
+    return set_err(c, UFC_ERR_ARG, "box side L must be finite and > 0");
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(b.obs[a])) return set_err(c, UFC_ERR_ARG, "observer must be finite");
+  if (b.shell_lo < 0 || b.shell_hi > nshell || b.shell_lo >= b.shell_hi)
+    return set_err(c, UFC_ERR_ARG, "box shells [%d,%d) outside [0,%d)", b.shell_lo,
+                   b.shell_hi, nshell);
+  if (b.replicate < 0 || b.replicate > UFC_MAX_REPLICATE)
+    return set_err(c, UFC_ERR_ARG, "replicate must be in [0,%d]", UFC_MAX_REPLICATE);
+  g.shell_lo = b.shell_lo;
+  g.shell_hi = b.shell_hi;
+  g.R = b.replicate;
+  const int n1 = 2 * b.replicate + 1;
+  g.nimg = n1 * n1 * n1;
+  float smax = 0.f;
+  for (int a = 0; a < 3; ++a)
+    for (int i = -b.replicate; i <= b.replicate; ++i) {
+      double s = (double)i * b.L - b.obs[a];     // fl(fl(i L) - o)
+      float hi = (float)s;
+      float lo = (float)(s - (double)hi);
+      g.sh64[a][i + b.replicate] = s;
+      g.shf[a][i + b.replicate] = hi;
+      g.shlo[a][i + b.replicate] = lo;
+      smax = std::max(smax, std::fabs(hi));
+    }
+  g.smax = smax;
+  return UFC_OK;
+}
+
+struct BinPlan {
+  int mode;
+  int nblk, nbuckets, ng, smem_hist;
+};
+
+// Runs the key pipeline for nbox boxes.  counts (DIRECT/DENSE) or keys (KEYS).
+ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
+                             const int64_t* n, const ufc_box* boxes, int nbox,
+                             const double* chi, int nshell, int nside, int flags,
+                             int32_t* counts, int32_t* keys) {
+  if (nbox < 1 || nbox > kMaxBoxes)
+    return set_err(c, UFC_ERR_ARG, "nbox must be in [1,%d]", kMaxBoxes);
+  if (nshell < 1 || nshell > kMaxShells)
+    return set_err(c, UFC_ERR_ARG, "nshell must be in [1,%d]", kMaxShells);
+  if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1)))
+    return set_err(c, UFC_ERR_ARG, "nside must be a power of two in [1,%d]", UFC_MAX_NSIDE);
+  const int64_t npix = 12ll * nside * nside;
+  if ((int64_t)nshell * npix >= (1ll << 30))
+    return set_err(c, UFC_ERR_ARG, "nshell * 12 nside^2 must be < 2^30");
+  ShellTable st;
+  ufc_status s = make_table(c, chi, nshell, st);
+  if (s) return s;
+  BoxesParam bp;
+  std::memset(&bp, 0, sizeof bp);
+  int64_t total_img = 0;
+  float smax = 0.f;
+  int maxR = 0;
+  for (int k = 0; k < nbox; ++k) {
+    if (n[k] < 0) return set_err(c, UFC_ERR_ARG, "n[%d] < 0", k);
+    if (n[k] > 0 && !xyz[k]) return set_err(c, UFC_ERR_ARG, "xyz[%d] is NULL", k);
+    if (n[k] >= (1ll << 47)) return set_err(c, UFC_ERR_ARG, "n[%d] too large", k);
+    if (n[k] > 0 && (reinterpret_cast<uintptr_t>(xyz[k]) & 3))
+      return set_err(c, UFC_ERR_ARG, "xyz[%d] is not 4-byte aligned", k);
+    s = make_box(c, boxes[k], nshell, bp.box[k]);
+    if (s) return s;
+    bp.xyz[k] = xyz[k];
+    total_img += n[k] * bp.box[k].nimg;
+    smax = std::max(smax, bp.box[k].smax);
+    maxR = std::max(maxR, (int)boxes[k].replicate);
+  }
+  Bands bd;
+  make_bands(nside, smax, bd);
+
+  BinPlan plan{};
+  plan.mode = mode_req;
+  if (mode_req != kModeKeys) {
+    const int64_t map_bytes = (int64_t)nshell * npix * 4;
+    const bool dense_ok = nside >= 64 && maxR == 0 &&
+                          (int64_t)nshell * (npix / kBlockPix) < (1ll << 17);
+    const bool aligned = (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
+    plan.mode = (dense_ok && aligned && map_bytes > (32ll << 20)) ? kModeDense : kModeDirect;
+  }
+  if (plan.mode == kModeDense) {
+    plan.nblk = (int)(npix / kBlockPix);
+    plan.nbuckets = nshell * plan.nblk;
+    plan.ng = (plan.nbuckets + (1 << kGroupBits) - 1) >> kGroupBits;
+    plan.smem_hist = plan.nbuckets <= kSmemHistMax;
+  }
+
+  // workspace
+  const int64_t cap1 = std::max<int64_t>(1 << 20, total_img / 16);
+  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64);
+  Queues qs;
+  qs.cap1 = cap1;
+  qs.cap2 = cap2;
+  qs.q1 = (uint64_t*)ws_get(c, kSlotQueue1, cap1 * 8);
+  qs.q2 = (uint64_t*)ws_get(c, kSlotQueue2, cap2 * 8);
+  if (!qs.q1 || !qs.q2) return UFC_ERR_ALLOC;
+  qs.cnt = (BinCounters*)c->counters;
+  UFC_CUDA(c, cudaMemsetAsync(qs.cnt, 0, sizeof(BinCounters), c->stream));
+
+  KeyOut o;
+  std::memset(&o, 0, sizeof o);
+  o.keys = keys;
+  o.counts = counts;
+  o.dense_count = &qs.cnt->dense;
+  int grid = 0, smem = 0;
+  if (plan.mode == kModeDense) {
+    // every warp of every launch may leave one partly filled chunk
+    const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kFastThreads / 32) +
+                           2ll * 4 * c->num_sms * (256 / 32) + 64;
+    o.dense_cap = total_img + nwarps * kChunk;
+    o.dense = (uint32_t*)ws_get(c, kSlotDense, o.dense_cap * 4);
+    o.hist = (uint32_t*)ws_get(c, kSlotHist, (size_t)plan.nbuckets * 4);
+    if (!o.dense || !o.hist) return UFC_ERR_ALLOC;
+    o.nblk = plan.nblk;
+    o.nbuckets = plan.nbuckets;
+    o.smem_hist = plan.smem_hist;
+    UFC_CUDA(c, cudaMemsetAsync(o.hist, 0, (size_t)plan.nbuckets * 4, c->stream));
+    smem = plan.smem_hist ? plan.nbuckets * 4 : 0;
+  } else if (plan.mode == kModeDirect) {
+    if (!(flags & UFC_BIN_ACCUMULATE))
+      UFC_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nshell * npix * 4, c->stream));
+  }
+  // fast stage per box
+  for (int k = 0; k < nbox; ++k) {
+    if (n[k] == 0) continue;
+    if (plan.mode == kModeDense) {
+      UFC_CUDA(c, cudaFuncSetAttribute(k_fast<kModeDense>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<kModeDense>, kFastThreads, smem);
+      grid = std::max(1, std::min(per_sm, 2)) * c->num_sms;
+      {
+        ProfScope ps_(c, "k_fast");
+        k_fast<kModeDense><<<grid, kFastThreads, smem, c->stream>>>(
+            xyz[k], n[k], k, bp.box[k], st, bd, nside, (int32_t)npix, o, qs);
+      }
+    } else if (plan.mode == kModeDirect) {
+      grid = 2 * c->num_sms;
+      {
+        ProfScope ps_(c, "k_fast");
+        k_fast<kModeDirect><<<grid, kFastThreads, 0, c->stream>>>(
+            xyz[k], n[k], k, bp.box[k], st, bd, nside, (int32_t)npix, o, qs);
+      }
+    } else {
+      grid = 2 * c->num_sms;
+      {
+        ProfScope ps_(c, "k_fast");
+        k_fast<kModeKeys><<<grid, kFastThreads, 0, c->stream>>>(
+            xyz[k], n[k], k, bp.box[k], st, bd, nside, (int32_t)npix, o, qs);
+      }
+    }
+    UFC_CUDA(c, cudaGetLastError());
+  }
+  const int lgrid = 4 * c->num_sms;
+  if (plan.mode == kModeDense) {
+    {
+      ProfScope ps_(c, "k_refine");
+      k_refine<kModeDense><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+    {
+      ProfScope ps_(c, "k_exact");
+      k_exact<kModeDense><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+  } else if (plan.mode == kModeDirect) {
+    {
+      ProfScope ps_(c, "k_refine");
+      k_refine<kModeDirect><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+    {
+      ProfScope ps_(c, "k_exact");
+      k_exact<kModeDirect><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+  } else {
+    {
+      ProfScope ps_(c, "k_refine");
+      k_refine<kModeKeys><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+    {
+      ProfScope ps_(c, "k_exact");
+      k_exact<kModeKeys><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  if (plan.mode != kModeDense) return UFC_OK;
+
+  // ---- dense pipeline: scan, two scatter passes, per-bucket histograms ----
+  const int nb = plan.nbuckets, ng = plan.ng;
+  int64_t* off = (int64_t*)ws_get(c, kSlotOff, (size_t)(nb + 1) * 8);
+  unsigned long long* cur = (unsigned long long*)ws_get(c, kSlotCursors, (size_t)(nb + ng + 1) * 8);
+  uint32_t* grouped = (uint32_t*)ws_get(c, kSlotGrouped, (size_t)o.dense_cap * 4);
+  uint16_t* b16 = (uint16_t*)ws_get(c, kSlotBucket16, (size_t)o.dense_cap * 2);
+  const int64_t max_tiles = o.dense_cap / kScatTile + ng + 1;
+  Tile* tiles = (Tile*)ws_get(c, kSlotTiles, (size_t)max_tiles * sizeof(Tile));
+  if (!off || !cur || !grouped || !b16 || !tiles) return UFC_ERR_ALLOC;
+  unsigned long long* gcur = cur;
+  unsigned long long* bcur = cur + ng;
+  unsigned long long* ntiles = &qs.cnt->pad_;
+  {
+    ProfScope ps_(c, "k_scan");
+    k_scan<<<1, 1024, 0, c->stream>>>(o.hist, nb, off);
+  }
+  {
+    ProfScope ps_(c, "k_cursors");
+    k_cursors<<<(std::max(nb, ng) + 255) / 256, 256, 0, c->stream>>>(off, nb, ng, gcur, bcur);
+  }
+  const int smemA = (3 * ng + 2) * 8 + kScatTile * 4;
+  UFC_CUDA(c, cudaFuncSetAttribute(k_scatter_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smemA));
+  {
+    ProfScope ps_(c, "k_scatter_group");
+    k_scatter_group<<<4 * c->num_sms, kScatThreads, smemA, c->stream>>>(
+        o.dense, o.dense_count, o.dense_cap, ng, gcur, grouped);
+  }
+  {
+    ProfScope ps_(c, "k_tiles");
+    k_tiles<<<1, 1024, 0, c->stream>>>(off, nb, ng, tiles, ntiles);
+  }
+  {
+    ProfScope ps_(c, "k_scatter_bucket");
+    k_scatter_bucket<<<4 * c->num_sms, kScatThreads, 0, c->stream>>>(grouped, tiles, ntiles,
+                                                                     bcur, b16);
+  }
+  const int smemH = kBlockPix * 4;
+  UFC_CUDA(c, cudaFuncSetAttribute(k_hist_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smemH));
+  {
+    ProfScope ps_(c, "k_hist_block");
+    k_hist_block<<<2 * c->num_sms, kHistThreads, smemH, c->stream>>>(
+        b16, off, nb, counts, (flags & UFC_BIN_ACCUMULATE) ? 1 : 0);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+}  // namespace ufc

@@ -1,0 +1,349 @@
+// C ABI of libufalcon_gb300.so: argument checks, context, workspace, and the
+// calls into the binning, statistics and cosmology code.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace ufc {
+ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
+                             const int64_t* n, const ufc_box* boxes, int nbox,
+                             const double* chi, int nshell, int nside, int flags,
+                             int32_t* counts, int32_t* keys);
+ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                           const double* A, double C, double lo, double hi, int nbins,
+                           float* kappa, double* moments, int64_t* pdf);
+ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                              const double* A, double C, double w_var, double w_skew,
+                              const float* g, const double* dA, const double* dC,
+                              double* grad, double* G, double* H);
+ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, double* st);
+ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins, double* v);
+ufc_status run_welford_merge(ufc_ctx* c, double* a, const double* b, int d);
+ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, double* mean,
+                                double* cov, double* corr);
+ufc_status cosmo_chi_edges(const ufc_cosmo& c, const double* z, int n, double* chi);
+ufc_status cosmo_z_of_chi(const ufc_cosmo& c, const double* chi, int n, double* zout);
+ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
+                              const double* z, int S, int nside, const ufc_source& src,
+                              double* A, double* B, double* C, double* dA, double* dC);
+
+void* ws_get(ufc_ctx* c, int s, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  if (c->cap[s] >= bytes) return c->buf[s];
+  if (c->buf[s]) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->buf[s]);
+    c->buf[s] = nullptr;
+    c->cap[s] = 0;
+  }
+  size_t want = bytes + bytes / 8;   // some headroom against repeated growth
+  if (cudaMalloc(&c->buf[s], want) != cudaSuccess) {
+    cudaGetLastError();
+    c->buf[s] = nullptr;
+    set_err(c, UFC_ERR_ALLOC, "cudaMalloc of %zu bytes for workspace slot %d failed", want, s);
+    return nullptr;
+  }
+  c->cap[s] = want;
+  return c->buf[s];
+}
+
+static cudaEvent_t prof_event(ufc_ctx* c) {
+  if (c->prof_pool_used == c->prof_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->prof_pool.push_back(e);
+  }
+  return c->prof_pool[c->prof_pool_used++];
+}
+
+void prof_begin(ufc_ctx* c, const char* name) {
+  if (!c->prof) return;
+  cudaEvent_t a = prof_event(c), b = prof_event(c);
+  if (!a || !b) return;
+  cudaEventRecord(a, c->stream);
+  c->prof_recs.push_back({name, a, b});
+}
+
+void prof_end(ufc_ctx* c) {
+  if (!c->prof || c->prof_recs.empty()) return;
+  cudaEventRecord(c->prof_recs.back().b, c->stream);
+}
+
+static ufc_status check_cosmo(ufc_ctx* c, const ufc_cosmo* cs) {
+  if (!cs) return set_err(c, UFC_ERR_ARG, "cosmo is NULL");
+  if (!(cs->omega_m >= 0.0 && cs->omega_m <= 1.0))
+    return set_err(c, UFC_ERR_ARG, "omega_m must be in [0,1]");
+  if (!(cs->h > 0.0) || !std::isfinite(cs->h)) return set_err(c, UFC_ERR_ARG, "h must be > 0");
+  if (cs->units_mpc_over_h != 0 && cs->units_mpc_over_h != 1)
+    return set_err(c, UFC_ERR_ARG, "units_mpc_over_h must be 0 or 1");
+  return UFC_OK;
+}
+
+static ufc_status check_z(ufc_ctx* c, const double* z, int n) {
+  if (!z) return set_err(c, UFC_ERR_ARG, "z_edges is NULL");
+  for (int i = 0; i < n; ++i) {
+    if (!std::isfinite(z[i]) || z[i] < 0.0 || z[i] > 20.0)
+      return set_err(c, UFC_ERR_ARG, "z_edges[%d] = %g outside [0,20]", i, z[i]);
+    if (i && !(z[i] > z[i - 1])) return set_err(c, UFC_ERR_ARG, "z_edges must increase");
+  }
+  return UFC_OK;
+}
+
+}  // namespace ufc
+
+using namespace ufc;
+
+extern "C" {
+
+ufc_status ufc_create(ufc_ctx** out, int32_t device) {
+  if (!out) return UFC_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return UFC_ERR_CUDA;
+  }
+  ufc_ctx* c = new (std::nothrow) ufc_ctx();
+  if (!c) return UFC_ERR_ALLOC;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return UFC_ERR_CUDA; }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMalloc(&c->counters, sizeof(BinCounters)) != cudaSuccess) { delete c; return UFC_ERR_ALLOC; }
+  cudaMemset(c->counters, 0, sizeof(BinCounters));
+  *out = c;
+  return UFC_OK;
+}
+
+ufc_status ufc_destroy(ufc_ctx* c) {
+  if (!c) return UFC_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (int s = 0; s < ufc_ctx::kSlots; ++s)
+    if (c->buf[s]) cudaFree(c->buf[s]);
+  if (c->counters) cudaFree(c->counters);
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  delete c;
+  return UFC_OK;
+}
+
+ufc_status ufc_set_stream(ufc_ctx* c, void* stream) {
+  if (!c) return UFC_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return UFC_OK;
+}
+
+ufc_status ufc_synchronize(ufc_ctx* c) {
+  if (!c) return UFC_ERR_ARG;
+  UFC_CUDA(c, cudaStreamSynchronize(c->stream));
+  return UFC_OK;
+}
+
+const char* ufc_last_error(const ufc_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+ufc_status ufc_reserve(ufc_ctx* c, int32_t nside, int32_t nshell, int64_t n_max) {
+  if (!c || nside < 1 || nshell < 1 || n_max < 0) return UFC_ERR_ARG;
+  cudaSetDevice(c->device);
+  const int64_t npix = 12ll * nside * nside;
+  const int64_t cap1 = std::max<int64_t>(1 << 20, n_max / 16);
+  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64);
+  if (!ws_get(c, kSlotQueue1, cap1 * 8) || !ws_get(c, kSlotQueue2, cap2 * 8)) return UFC_ERR_ALLOC;
+  if (nside >= 64 && npix * nshell * 4 > (32ll << 20)) {
+    const int64_t nwarps = 2ll * 2 * c->num_sms * 16 + 2ll * 4 * c->num_sms * 8 + 64;
+    const int64_t cap = n_max + nwarps * 2048;
+    const int64_t nb = nshell * (npix / 24576);
+    if (!ws_get(c, kSlotDense, cap * 4) || !ws_get(c, kSlotGrouped, cap * 4) ||
+        !ws_get(c, kSlotBucket16, cap * 2) || !ws_get(c, kSlotHist, nb * 4) ||
+        !ws_get(c, kSlotOff, (nb + 1) * 8))
+      return UFC_ERR_ALLOC;
+  }
+  return UFC_OK;
+}
+
+ufc_status ufc_profile_enable(ufc_ctx* c, int32_t on) {
+  if (!c) return UFC_ERR_ARG;
+  c->prof = on != 0;
+  return UFC_OK;
+}
+
+ufc_status ufc_profile_read(ufc_ctx* c, int32_t max, char* names, double* ms,
+                            int64_t* launches, int32_t* n_out) {
+  if (!c || max < 0 || !n_out || (max > 0 && (!names || !ms || !launches))) return UFC_ERR_ARG;
+  cudaSetDevice(c->device);
+  UFC_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<std::string> keys;
+  std::vector<double> tot;
+  std::vector<int64_t> cnt;
+  for (const auto& r : c->prof_recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { cudaGetLastError(); continue; }
+    size_t i = 0;
+    while (i < keys.size() && keys[i] != r.name) ++i;
+    if (i == keys.size()) { keys.push_back(r.name); tot.push_back(0.0); cnt.push_back(0); }
+    tot[i] += t;
+    cnt[i] += 1;
+  }
+  const int n = (int)keys.size();
+  for (int i = 0; i < n && i < max; ++i) {
+    std::memset(names + 32 * i, 0, 32);
+    std::strncpy(names + 32 * i, keys[i].c_str(), 31);
+    ms[i] = tot[i];
+    launches[i] = cnt[i];
+  }
+  *n_out = n;
+  c->prof_recs.clear();
+  c->prof_pool_used = 0;
+  return UFC_OK;
+}
+
+ufc_status ufc_chi_edges(const ufc_cosmo* cosmo, const double* z_edges, int32_t nshell,
+                         double* chi_out) {
+  ufc_status s = check_cosmo(nullptr, cosmo);
+  if (s) return s;
+  if (nshell < 1 || !chi_out) return UFC_ERR_ARG;
+  s = check_z(nullptr, z_edges, nshell + 1);
+  if (s) return s;
+  return cosmo_chi_edges(*cosmo, z_edges, nshell + 1, chi_out);
+}
+
+ufc_status ufc_z_of_chi(const ufc_cosmo* cosmo, const double* chi, int32_t n, double* z_out) {
+  ufc_status s = check_cosmo(nullptr, cosmo);
+  if (s) return s;
+  if (n < 0 || (n && (!chi || !z_out))) return UFC_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(chi[i]) || chi[i] < 0.0) return UFC_ERR_ARG;
+  return cosmo_z_of_chi(*cosmo, chi, n, z_out);
+}
+
+ufc_status ufc_kappa_coeffs(const ufc_cosmo* cosmo, const ufc_box* boxes, int32_t nbox,
+                            const double* z_edges, int32_t nshell, int32_t nside,
+                            const ufc_source* src, double* A, double* B, double* C,
+                            double* dA, double* dC) {
+  ufc_status s = check_cosmo(nullptr, cosmo);
+  if (s) return s;
+  if (!boxes || nbox < 1 || nshell < 1 || nshell > UFC_MAX_SHELLS || !src || !A || !C)
+    return UFC_ERR_ARG;
+  if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1))) return UFC_ERR_ARG;
+  s = check_z(nullptr, z_edges, nshell + 1);
+  if (s) return s;
+  if (!(z_edges[0] > 0.0)) return UFC_ERR_ARG;   // Eq. 6 divides by chi(z_0)^2
+  for (int b = 0; b < nshell; ++b) {
+    int owners = 0;
+    for (int k = 0; k < nbox; ++k)
+      owners += (b >= boxes[k].shell_lo && b < boxes[k].shell_hi);
+    if (owners != 1) return UFC_ERR_ARG;
+  }
+  for (int k = 0; k < nbox; ++k)
+    if (!(boxes[k].L > 0.0) || boxes[k].n_total < 1) return UFC_ERR_ARG;
+  if (src->kind == 0) {
+    if (!(src->z_s > 0.0) || src->z_s > 20.0) return UFC_ERR_ARG;
+  } else if (src->kind == 1) {
+    if (!(src->z_max > 0.0) || src->z_max > 20.0 || !(src->z0 > 0.0) || !(src->beta > 0.0) ||
+        !(src->alpha > -1.0))
+      return UFC_ERR_ARG;
+  } else {
+    return UFC_ERR_ARG;
+  }
+  return cosmo_kappa_coeffs(*cosmo, boxes, nbox, z_edges, nshell, nside, *src, A, B, C, dA, dC);
+}
+
+ufc_status ufc_keys(ufc_ctx* c, const float* xyz_dev, int64_t n, const ufc_box* box,
+                    const double* chi_edges, int32_t nshell, int32_t nside,
+                    int32_t* keys_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!box || !chi_edges) return set_err(c, UFC_ERR_ARG, "box and chi_edges are required");
+  if (n > 0 && !keys_dev) return set_err(c, UFC_ERR_ARG, "keys_dev is NULL");
+  if (box->replicate != 0) return set_err(c, UFC_ERR_ARG, "ufc_keys needs replicate = 0");
+  cudaSetDevice(c->device);
+  return run_keys_pipeline(c, 0, &xyz_dev, &n, box, 1, chi_edges, nshell, nside, 0, nullptr,
+                           keys_dev);
+}
+
+ufc_status ufc_bin(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
+                   const ufc_box* boxes, int32_t nbox, const double* chi_edges,
+                   int32_t nshell, int32_t nside, int32_t flags, int32_t* counts_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!xyz_dev || !n || !boxes || !chi_edges || !counts_dev)
+    return set_err(c, UFC_ERR_ARG, "NULL argument to ufc_bin");
+  if (flags & ~UFC_BIN_ACCUMULATE) return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if (reinterpret_cast<uintptr_t>(counts_dev) & 3)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 4-byte aligned");
+  cudaSetDevice(c->device);
+  return run_keys_pipeline(c, 1, xyz_dev, n, boxes, nbox, chi_edges, nshell, nside, flags,
+                           counts_dev, nullptr);
+}
+
+ufc_status ufc_bin_info(ufc_ctx* c, int64_t info[4]) {
+  if (!c || !info) return UFC_ERR_ARG;
+  BinCounters h;
+  cudaSetDevice(c->device);
+  UFC_CUDA(c, cudaMemcpyAsync(&h, c->counters, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  UFC_CUDA(c, cudaStreamSynchronize(c->stream));
+  info[0] = (int64_t)h.invalid;
+  info[1] = (int64_t)h.keyed;
+  info[2] = (int64_t)h.refined;
+  info[3] = (int64_t)h.exact;
+  return UFC_OK;
+}
+
+ufc_status ufc_kappa_stats(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell, int32_t nside,
+                           const double* A, double C, double pdf_lo, double pdf_hi,
+                           int32_t nbins, float* kappa_dev, double* moments_dev,
+                           int64_t* pdf_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_kappa_stats(c, counts_dev, nshell, nside, A, C, pdf_lo, pdf_hi, nbins, kappa_dev,
+                         moments_dev, pdf_dev);
+}
+
+ufc_status ufc_kappa_backward(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell,
+                              int32_t nside, const double* A, double C, double w_var,
+                              double w_skew, const float* g_kappa_dev, const double* dA,
+                              const double* dC, double* grad_theta, double* G, double* H) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!std::isfinite(w_var) || !std::isfinite(w_skew))
+    return set_err(c, UFC_ERR_ARG, "weights must be finite");
+  cudaSetDevice(c->device);
+  return run_kappa_backward(c, counts_dev, nshell, nside, A, C, w_var, w_skew, g_kappa_dev, dA,
+                            dC, grad_theta, G, H);
+}
+
+ufc_status ufc_stats_vector(ufc_ctx* c, const double* moments_dev, const int64_t* pdf_dev,
+                            int32_t nbins, double* v_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_stats_vector(c, moments_dev, pdf_dev, nbins, v_dev);
+}
+
+ufc_status ufc_welford_update(ufc_ctx* c, const double* v_dev, int32_t nvec, int32_t d,
+                              double* state_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_welford_update(c, v_dev, nvec, d, state_dev);
+}
+
+ufc_status ufc_welford_merge(ufc_ctx* c, double* a, const double* b, int32_t d) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_welford_merge(c, a, b, d);
+}
+
+ufc_status ufc_welford_finalize(ufc_ctx* c, const double* st, int32_t d, int32_t ddof,
+                                double* mean, double* cov, double* corr) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_welford_finalize(c, st, d, ddof, mean, cov, corr);
+}
+
+}  // extern "C"

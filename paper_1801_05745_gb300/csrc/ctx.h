@@ -1,0 +1,82 @@
+// Library context and device workspace (internal).
+#pragma once
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ufalcon.h"
+
+struct ufc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int num_sms = 0;
+  // grow-only device buffers, one per slot
+  static constexpr int kSlots = 16;
+  void* buf[kSlots] = {};
+  size_t cap[kSlots] = {};
+  void* counters = nullptr;      // ufc::BinCounters of the last binning call
+  // kernel timing: events bracketing each launch while enabled
+  bool prof = false;
+  struct ProfRec { const char* name; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_recs;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_pool_used = 0;
+};
+
+namespace ufc {
+
+enum Slot {
+  kSlotQueue1 = 0,
+  kSlotQueue2,
+  kSlotDense,
+  kSlotGrouped,
+  kSlotBucket16,
+  kSlotHist,
+  kSlotOff,
+  kSlotCursors,
+  kSlotTiles,
+  kSlotPartials,
+  kSlotCoeffs,
+  kSlotMisc,
+};
+
+inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define UFC_CUDA(c, call)                                                       \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess)                                                      \
+      return ::ufc::set_err((c), UFC_ERR_CUDA, "%s: %s (%s:%d)", #call,         \
+                            cudaGetErrorString(e_), __FILE__, __LINE__);        \
+  } while (0)
+
+// Kernel timing.  prof_begin/prof_end bracket one launch on the context's
+// stream when timing is enabled (ufc_profile_enable).
+void prof_begin(ufc_ctx* c, const char* name);
+void prof_end(ufc_ctx* c);
+
+struct ProfScope {
+  ufc_ctx* c;
+  ProfScope(ufc_ctx* c_, const char* name) : c(c_) { prof_begin(c, name); }
+  ~ProfScope() { prof_end(c); }
+};
+
+// Ensures slot `s` holds at least `bytes`; returns nullptr (and sets the
+// error) when the allocation fails.  Growing frees the old buffer, which
+// waits for the device.
+void* ws_get(ufc_ctx* c, int s, size_t bytes);
+
+}  // namespace ufc

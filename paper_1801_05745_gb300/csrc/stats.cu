@@ -1,0 +1,669 @@
+// kappa map (Eq. 6), moments (Eq. 12-13), PDF (Sec. 3.3), adjoint sums, and
+// the Welford covariance over realisations (Eq. 10-11).
+//
+// GB300 runs FP64 at ~1/64 of FP32, so the per-pixel sums over shells are
+// carried in double-float (pairs of FP32, ~2^-44 relative) and converted to
+// FP64 only per thread or per block.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace ufc {
+
+// ------------------------------------------------------------ helpers -----
+struct f2 { float h, l; };
+
+__device__ __forceinline__ f2 f2_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ f2 f2_norm(float h, float l) {
+  float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+// acc += (a_h + a_l) * n, n an exactly representable count.
+__device__ __forceinline__ void f2_mac(f2& acc, float ah, float al, float n) {
+  float ph = __fmul_rn(ah, n);
+  float pe = __fmaf_rn(ah, n, -ph);
+  f2 s = f2_two_sum(acc.h, ph);
+  acc.h = s.h;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, __fmaf_rn(al, n, pe)));
+}
+__device__ __forceinline__ f2 f2_add(f2 x, f2 y) {
+  f2 s = f2_two_sum(x.h, y.h);
+  return f2_norm(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ f2 f2_mul(f2 x, f2 y) {
+  float p = __fmul_rn(x.h, y.h);
+  float e = __fmaf_rn(x.h, y.h, -p);
+  e = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e));
+  return f2_norm(p, e);
+}
+__device__ __forceinline__ double f2_to_d(f2 x) { return double(x.h) + double(x.l); }
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+// Block sum of a double in fixed order (lane order, then warp order).
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  v = warp_sum_d(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; ++i) t += sh[i];
+  return t;   // valid in thread 0
+}
+
+struct Coef {
+  float ah[kMaxShells];
+  float al[kMaxShells];
+  float ch, cl;        // C as double-float
+  int32_t nshell;
+  int32_t npix;
+};
+
+// ------------------------------------------------- kappa + adjoint sums ---
+// One pass over the counts.  Each thread owns one pixel of a 256-pixel
+// tile; kappa_p = sum_b A_b n_bp - C is accumulated in double-float.
+//   KAPPA  : writes FP32 kappa and per-block partial sums of kappa.
+//   ADJ    : per-shell sums S1_b = sum_p e_p n_bp, S2_b = sum_p e_p^2 n_bp,
+//            T_b = sum_p g_p n_bp, N_b = sum_p n_bp and global sums
+//            P_k = sum_p e_p^k (k = 1..3), Q = sum_p g_p, e_p = unrounded kappa_p.
+//            The per-pixel factors are quantised per tile to 31-bit integers
+//            (scale 2^s from the tile maximum) and multiplied by the counts
+//            in exact 64-bit integer arithmetic.
+constexpr int kKT = 256;   // threads (pixels) per tile
+
+struct AdjOut {
+  double* part;   // [grid][4*nshell + 4]: S1, S2, T, N per shell, then P1, P2, P3, Q
+  const float* g; // may be null
+};
+
+// Splits v (double-float) into two integers with v 2^s = hi + lo 2^-30 to
+// within 2^-31: hi = rint(v 2^s), lo = rint((v 2^s - hi) 2^30).
+__device__ __forceinline__ void quant2(f2 v, int s, int& hi, int& lo) {
+  const float a = ldexpf(v.h, s);
+  const float r = rintf(a);
+  const float rem = __fadd_rn(__fsub_rn(a, r), ldexpf(v.l, s));   // a - r is exact
+  hi = __float2int_rn(r);
+  lo = __float2int_rn(ldexpf(rem, 30));
+}
+
+template <bool KAPPA, bool ADJ>
+__global__ void __launch_bounds__(kKT)
+k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
+        double* __restrict__ ksum_part, AdjOut ao) {
+  extern __shared__ int32_t cnt_s[];            // ADJ: [nshell][kKT], then 4 doubles/shell
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ double red[kKT / 32];
+  __shared__ int q_s[6][kKT];                   // hi/lo of e, e^2, g
+  __shared__ float fmax_s[4][kKT / 32];
+  const int S = cf.nshell;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+  double* rows = reinterpret_cast<double*>(cnt_s + S * kKT);
+  if (ADJ)
+    for (int i = threadIdx.x; i < 4 * S; i += blockDim.x) rows[i] = 0.0;
+  f2 ks{0.f, 0.f}, p1{0.f, 0.f}, p2{0.f, 0.f}, p3{0.f, 0.f}, qg{0.f, 0.f};
+  __syncthreads();
+  const bool use_g = ADJ && ao.g != nullptr;
+  const int ntile = (cf.npix + kKT - 1) / kKT;
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int p = tile * kKT + threadIdx.x;
+    const bool have = p < cf.npix;
+    f2 acc{0.f, 0.f};
+    int nmax = 0;
+#pragma unroll 4
+    for (int b = 0; b < S; ++b) {
+      int n = have ? __ldcs(counts + (size_t)b * cf.npix + p) : 0;
+      if (ADJ) {
+        cnt_s[b * kKT + threadIdx.x] = n;
+        nmax = max(nmax, n);
+      }
+      f2_mac(acc, ah_s[b], al_s[b], float(n));
+    }
+    // e = acc - C (unrounded), kappa = round(e)
+    f2 e = f2_add(f2_norm(acc.h, acc.l), f2{-cf.ch, -cf.cl});
+    if (KAPPA && have) {
+      float kf = __fadd_rn(e.h, e.l);
+      kappa[p] = kf;
+      ks = f2_add(ks, f2{kf, 0.f});
+    }
+    if (ADJ) {
+      f2 e2 = f2_mul(e, e);
+      float gv = (use_g && have) ? ao.g[p] : 0.f;
+      if (have) {
+        p1 = f2_add(p1, e);
+        p2 = f2_add(p2, e2);
+        p3 = f2_add(p3, f2_mul(e2, e));
+        qg = f2_add(qg, f2{gv, 0.f});
+      } else {
+        e = {0.f, 0.f};
+        e2 = {0.f, 0.f};
+      }
+      // tile maxima -> power-of-two scales with max 2^s < 2^29
+      float m1 = fabsf(e.h), m2 = fabsf(e2.h), m3 = fabsf(gv), mn = float(nmax);
+      for (int o = 16; o > 0; o >>= 1) {
+        m1 = fmaxf(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
+        m2 = fmaxf(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
+        m3 = fmaxf(m3, __shfl_xor_sync(0xFFFFFFFFu, m3, o));
+        mn = fmaxf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+      }
+      if ((threadIdx.x & 31) == 0) {
+        fmax_s[0][threadIdx.x >> 5] = m1;
+        fmax_s[1][threadIdx.x >> 5] = m2;
+        fmax_s[2][threadIdx.x >> 5] = m3;
+        fmax_s[3][threadIdx.x >> 5] = mn;
+      }
+      __syncthreads();
+      float M1 = 0.f, M2 = 0.f, M3 = 0.f, MN = 0.f;
+      for (int i = 0; i < kKT / 32; ++i) {
+        M1 = fmaxf(M1, fmax_s[0][i]);
+        M2 = fmaxf(M2, fmax_s[1][i]);
+        M3 = fmaxf(M3, fmax_s[2][i]);
+        MN = fmaxf(MN, fmax_s[3][i]);
+      }
+      const int s1 = M1 > 0.f ? 28 - ilogbf(M1) : 0;
+      const int s2 = M2 > 0.f ? 28 - ilogbf(M2) : 0;
+      const int s3 = M3 > 0.f ? 28 - ilogbf(M3) : 0;
+      int h, l;
+      quant2(e, s1, h, l);
+      q_s[0][threadIdx.x] = h;
+      q_s[1][threadIdx.x] = l;
+      quant2(e2, s2, h, l);
+      q_s[2][threadIdx.x] = h;
+      q_s[3][threadIdx.x] = l;
+      quant2(f2{gv, 0.f}, s3, h, l);
+      q_s[4][threadIdx.x] = h;
+      q_s[5][threadIdx.x] = l;
+      __syncthreads();
+      // phase 2: warp w owns shells w, w+8, ...; lane l pixels l, l+32, ...
+      // |q| < 2^30, counts < 2^24: an 8-term lane sum stays below 2^57 and
+      // the warp sum below 2^62.  Larger counts take the FP64 branch.
+      const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+      const double sc1 = ldexp(1.0, -s1), sc2 = ldexp(1.0, -s2), sc3 = ldexp(1.0, -s3);
+      const double lo30 = ldexp(1.0, -30);
+      if (MN < 16777216.0f) {
+        int qv[6][kKT / 32];
+#pragma unroll
+        for (int k = 0; k < kKT / 32; ++k)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) qv[j][k] = q_s[j][ln + 32 * k];
+        for (int b = w; b < S; b += kKT / 32) {
+          long long a[6] = {0, 0, 0, 0, 0, 0};
+          int an = 0;
+#pragma unroll
+          for (int k = 0; k < kKT / 32; ++k) {
+            const int n = cnt_s[b * kKT + ln + 32 * k];
+            an += n;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[j] += (long long)qv[j][k] * n;
+            if (use_g) {
+              a[4] += (long long)qv[4][k] * n;
+              a[5] += (long long)qv[5][k] * n;
+            }
+          }
+          long long an64 = an;
+#pragma unroll
+          for (int j = 0; j < 6; ++j) a[j] = warp_sum_ll(a[j]);
+          an64 = warp_sum_ll(an64);
+          if (ln == 0) {
+            double* row = rows + 4 * b;
+            row[0] += (double(a[0]) + double(a[1]) * lo30) * sc1;
+            row[1] += (double(a[2]) + double(a[3]) * lo30) * sc2;
+            row[2] += (double(a[4]) + double(a[5]) * lo30) * sc3;
+            row[3] += double(an64);
+          }
+        }
+      } else {
+        for (int b = w; b < S; b += kKT / 32) {
+          double a1 = 0.0, a2 = 0.0, a3 = 0.0, an = 0.0;
+          for (int k = 0; k < kKT / 32; ++k) {
+            const int t = ln + 32 * k;
+            const double n = cnt_s[b * kKT + t];
+            a1 += n * (double(q_s[0][t]) + double(q_s[1][t]) * lo30);
+            a2 += n * (double(q_s[2][t]) + double(q_s[3][t]) * lo30);
+            a3 += n * (double(q_s[4][t]) + double(q_s[5][t]) * lo30);
+            an += n;
+          }
+          a1 = warp_sum_d(a1);
+          a2 = warp_sum_d(a2);
+          a3 = warp_sum_d(a3);
+          an = warp_sum_d(an);
+          if (ln == 0) {
+            double* row = rows + 4 * b;
+            row[0] += a1 * sc1;
+            row[1] += a2 * sc2;
+            row[2] += a3 * sc3;
+            row[3] += an;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (KAPPA) {
+    double t = block_sum_d<kKT>(f2_to_d(ks), red);
+    if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
+  }
+  if (ADJ) {
+    double* dst = ao.part + (size_t)blockIdx.x * (4 * S + 4);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * S; i += blockDim.x) dst[i] = rows[i];
+    double v1 = block_sum_d<kKT>(f2_to_d(p1), red);
+    if (threadIdx.x == 0) dst[4 * S + 0] = v1;
+    double v2 = block_sum_d<kKT>(f2_to_d(p2), red);
+    if (threadIdx.x == 0) dst[4 * S + 1] = v2;
+    double v3 = block_sum_d<kKT>(f2_to_d(p3), red);
+    if (threadIdx.x == 0) dst[4 * S + 2] = v3;
+    double v4 = block_sum_d<kKT>(f2_to_d(qg), red);
+    if (threadIdx.x == 0) dst[4 * S + 3] = v4;
+  }
+}
+
+// ------------------------------------------------ moments + PDF pass -----
+// Second pass over the FP32 map (L2-resident at these sizes): central
+// power sums about the exact FP64 mean in double-float, and the PDF.
+// PDF bin = floor((kappa - lo) * scale) in FP64; an FP32 estimate decides
+// all but the values within a proven band of a bin edge.
+constexpr int kMT = 256;
+constexpr int kMaxBins = 4096;
+
+struct PdfParam {
+  double lo, hi, scale;     // scale = nbins / (hi - lo)
+  float lo_f, scale_f, band_rel;
+  float lo_dn, lo_up, hi_dn, hi_up;   // FP32 brackets of lo and hi
+  int32_t nbins;
+};
+
+__global__ void __launch_bounds__(kMT)
+k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ ksum_part,
+          int nksum, PdfParam pp, double* __restrict__ part /*[grid][3]*/,
+          unsigned long long* __restrict__ pdf /*[nbins+3]*/) {
+  extern __shared__ unsigned int hist[];   // [nbins + 3]
+  __shared__ double red[kMT / 32];
+  __shared__ double mean_s;
+  for (int i = threadIdx.x; i < pp.nbins + 3; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nksum; ++i) s += ksum_part[i];   // fixed order
+    mean_s = s / double(npix);
+  }
+  __syncthreads();
+  const double mean = mean_s;
+  const float mh = (float)mean;
+  const float ml = (float)(mean - (double)mh);
+  f2 a2{0.f, 0.f}, a3{0.f, 0.f}, a4{0.f, 0.f};
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
+    const float k = kappa[p];
+    f2 d = f2_add(f2_two_sum(k, -mh), f2{-ml, 0.f});
+    f2 d2 = f2_mul(d, d);
+    a2 = f2_add(a2, d2);
+    a3 = f2_add(a3, f2_mul(d2, d));
+    a4 = f2_add(a4, f2_mul(d2, d2));
+    // PDF
+    int slot;
+    // k < lo and k >= hi decided in FP32 unless k lies between the FP32
+    // neighbours of lo (resp. hi)
+    const bool under = k < pp.lo_dn || (k < pp.lo_up && (double)k < pp.lo);
+    const bool over = k >= pp.hi_up || (k >= pp.hi_dn && (double)k >= pp.hi);
+    if (isnan(k)) slot = pp.nbins + 2;
+    else if (under) slot = pp.nbins;
+    else if (over) slot = pp.nbins + 1;
+    else {
+      float x = (k - pp.lo_f) * pp.scale_f;
+      float f = floorf(x);
+      float rem = x - f;
+      float band = pp.band_rel * (fabsf(x) + 1.0f);
+      int b;
+      if (rem >= band && rem < 1.0f - band) b = (int)f;
+      else b = (int)floor(__dmul_rn(__dsub_rn((double)k, pp.lo), pp.scale));
+      b = b >= pp.nbins ? pp.nbins - 1 : (b < 0 ? 0 : b);
+      slot = b;
+    }
+    atomicAdd(hist + slot, 1u);
+  }
+  double v2 = block_sum_d<kMT>(f2_to_d(a2), red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 0] = v2;
+  double v3 = block_sum_d<kMT>(f2_to_d(a3), red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = v3;
+  double v4 = block_sum_d<kMT>(f2_to_d(a4), red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = v4;
+  __syncthreads();
+  for (int i = threadIdx.x; i < pp.nbins + 3; i += blockDim.x)
+    if (hist[i]) atomicAdd(pdf + i, (unsigned long long)hist[i]);
+}
+
+// moments[10] from the partial sums (one thread, fixed order).
+__global__ void k_moments_final(const double* __restrict__ ksum_part, int nksum,
+                                const double* __restrict__ part, int npart, int npix,
+                                double* __restrict__ m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int i = 0; i < nksum; ++i) s += ksum_part[i];
+  const double N = double(npix);
+  double s2 = 0.0, s3 = 0.0, s4 = 0.0;
+  for (int i = 0; i < npart; ++i) {
+    s2 += part[3 * i];
+    s3 += part[3 * i + 1];
+    s4 += part[3 * i + 2];
+  }
+  const double mu2 = s2 / N, mu3 = s3 / N, mu4 = s4 / N;
+  m[0] = s / N;
+  m[1] = mu2;
+  m[2] = mu3;
+  m[3] = mu4;
+  m[4] = mu3 / (mu2 * sqrt(mu2));
+  m[5] = mu4 / (mu2 * mu2) - 3.0;
+  m[6] = (N - 1.0) * mu2 / N;
+  const double N3 = N * N * N;
+  m[7] = (N - 1.0) * (N - 1.0) / N3 * mu4 - (N - 1.0) * (N - 3.0) / N3 * mu2 * mu2;
+  m[8] = mu2 / m[7];
+  m[9] = N;
+}
+
+// Statistics vector of one map for the covariance (Eq. 10): the first six
+// moments (mean, mu2, mu3, mu4, skew, kurtosis) then the PDF bins divided by
+// the pixel count.
+__global__ void k_stats_vector(const double* __restrict__ m, const unsigned long long* __restrict__ pdf,
+                               int nbins, double* __restrict__ v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 6 + nbins; i += gridDim.x * blockDim.x)
+    v[i] = i < 6 ? m[i] : double(pdf[i - 6]) / m[9];
+}
+
+// ---------------------------------------------------------- Welford -----
+__global__ void __launch_bounds__(1024)
+k_welford_update(const double* __restrict__ v, int nvec, int d, double* __restrict__ st) {
+  extern __shared__ double sh[];   // delta_old[d], delta_new[d]
+  double* dold = sh;
+  double* dnew = sh + d;
+  double* mean = st + 1;
+  double* M2 = st + 1 + d;
+  for (int r = 0; r < nvec; ++r) {
+    const double* x = v + (size_t)r * d;
+    const double n = st[0] + 1.0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) {
+      double delta = x[i] - mean[i];
+      double mn = mean[i] + delta / n;
+      dold[i] = delta;
+      dnew[i] = x[i] - mn;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < d * d; k += blockDim.x) {
+      const int i = k / d, j = k - i * d;
+      M2[k] += dold[i] * dnew[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < d; i += blockDim.x) mean[i] += dold[i] / n;
+    __syncthreads();
+    if (threadIdx.x == 0) st[0] = n;
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+k_welford_merge(double* __restrict__ a, const double* __restrict__ b, int d) {
+  const double na = a[0], nb = b[0], n = na + nb;
+  if (nb == 0.0) return;
+  double* ma = a + 1;
+  const double* mb = b + 1;
+  double* Ma = a + 1 + d;
+  const double* Mb = b + 1 + d;
+  const double f = (n > 0.0) ? na * nb / n : 0.0;
+  for (int k = threadIdx.x; k < d * d; k += blockDim.x) {
+    const int i = k / d, j = k - i * d;
+    Ma[k] += Mb[k] + (mb[i] - ma[i]) * (mb[j] - ma[j]) * f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < d; i += blockDim.x) ma[i] += (mb[i] - ma[i]) * nb / n;
+  __syncthreads();
+  if (threadIdx.x == 0) a[0] = n;
+}
+
+__global__ void __launch_bounds__(1024)
+k_welford_final(const double* __restrict__ st, int d, int ddof, double* __restrict__ mean,
+                double* __restrict__ cov, double* __restrict__ corr) {
+  const double n = st[0];
+  const double den = n - double(ddof);
+  for (int i = threadIdx.x; i < d; i += blockDim.x) mean[i] = st[1 + i];
+  for (int k = threadIdx.x; k < d * d; k += blockDim.x) cov[k] = st[1 + d + k] / den;
+  __syncthreads();
+  for (int k = threadIdx.x; k < d * d; k += blockDim.x) {
+    const int i = k / d, j = k - i * d;
+    const double q = sqrt((st[1 + d + i * d + i] / den) * (st[1 + d + j * d + j] / den));
+    corr[k] = q > 0.0 ? (st[1 + d + k] / den) / q : 0.0;
+  }
+}
+
+// ============================================================== host =====
+
+static void make_coef(const double* A, double C, int S, int npix, Coef& cf) {
+  std::memset(&cf, 0, sizeof cf);
+  for (int b = 0; b < S; ++b) {
+    cf.ah[b] = (float)A[b];
+    cf.al[b] = (float)(A[b] - (double)cf.ah[b]);
+  }
+  cf.ch = (float)C;
+  cf.cl = (float)(C - (double)cf.ch);
+  cf.nshell = S;
+  cf.npix = npix;
+}
+
+static ufc_status check_kappa_args(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                   const double* A, double C) {
+  if (!counts) return set_err(c, UFC_ERR_ARG, "counts_dev is NULL");
+  if (S < 1 || S > kMaxShells) return set_err(c, UFC_ERR_ARG, "nshell must be in [1,%d]", kMaxShells);
+  if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1)))
+    return set_err(c, UFC_ERR_ARG, "nside must be a power of two in [1,%d]", UFC_MAX_NSIDE);
+  if ((int64_t)S * 12 * nside * nside >= (1ll << 31))
+    return set_err(c, UFC_ERR_ARG, "nshell * 12 nside^2 must be < 2^31");
+  if (!A) return set_err(c, UFC_ERR_ARG, "A is NULL");
+  for (int b = 0; b < S; ++b)
+    if (!std::isfinite(A[b])) return set_err(c, UFC_ERR_ARG, "A[%d] is not finite", b);
+  if (!std::isfinite(C)) return set_err(c, UFC_ERR_ARG, "C is not finite");
+  return UFC_OK;
+}
+
+static int kappa_grid(ufc_ctx* c, int npix) {
+  const int ntile = (npix + kKT - 1) / kKT;
+  return std::max(1, std::min(ntile, 8 * c->num_sms));
+}
+
+ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                           const double* A, double C, double lo, double hi, int nbins,
+                           float* kappa, double* moments, int64_t* pdf) {
+  ufc_status s = check_kappa_args(c, counts, S, nside, A, C);
+  if (s) return s;
+  const int npix = 12 * nside * nside;
+  const bool want_stats = moments || pdf;
+  if (want_stats) {
+    if (nbins < 1 || nbins > kMaxBins)
+      return set_err(c, UFC_ERR_ARG, "nbins must be in [1,%d]", kMaxBins);
+    if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+      return set_err(c, UFC_ERR_ARG, "PDF range needs finite lo < hi");
+    if (!moments || !pdf)
+      return set_err(c, UFC_ERR_ARG, "moments_dev and pdf_dev go together");
+  }
+  Coef cf;
+  make_coef(A, C, S, npix, cf);
+  const int grid = kappa_grid(c, npix);
+  const int mgrid = 2 * c->num_sms;
+  double* ksum = (double*)ws_get(c, kSlotPartials, (size_t)(grid + 3 * mgrid) * 8);
+  if (!ksum) return UFC_ERR_ALLOC;
+  double* mpart = ksum + grid;
+  float* kmap = kappa;
+  if (!kmap && want_stats) {
+    kmap = (float*)ws_get(c, kSlotMisc, (size_t)npix * 4);
+    if (!kmap) return UFC_ERR_ALLOC;
+  }
+  if (!kmap) return UFC_OK;   // nothing requested
+  {
+    ProfScope ps_(c, "k_kappa");
+    k_kappa<true, false><<<grid, kKT, 0, c->stream>>>(counts, cf, kmap, ksum, AdjOut{nullptr, nullptr});
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  if (!want_stats) return UFC_OK;
+  PdfParam pp;
+  pp.lo = lo;
+  pp.hi = hi;
+  pp.scale = (double)nbins / (hi - lo);
+  pp.lo_f = (float)lo;
+  pp.scale_f = (float)pp.scale;
+  pp.nbins = nbins;
+  // |x_f - x_64| <= 3u |x| + u |lo| s + 2^-52 |x| (u = 2^-24); when
+  // |lo| s < 16 that is below 68u (|x| + 1) < 2^-16 (|x| + 1), the band
+  // used; other ranges send every value through the FP64 expression.
+  pp.band_rel = std::fabs(lo) * pp.scale < 16.0 ? std::ldexp(1.0f, -16) : 2.0f;
+  auto fdn = [](double v) { float f = (float)v; return (double)f > v ? nextafterf(f, -INFINITY) : f; };
+  auto fup = [](double v) { float f = (float)v; return (double)f < v ? nextafterf(f, INFINITY) : f; };
+  pp.lo_dn = fdn(lo);
+  pp.lo_up = fup(lo);
+  pp.hi_dn = fdn(hi);
+  pp.hi_up = fup(hi);
+  UFC_CUDA(c, cudaMemsetAsync(pdf, 0, (size_t)(nbins + 3) * 8, c->stream));
+  const int smem = (nbins + 3) * 4;
+  {
+    ProfScope ps_(c, "k_moments");
+    k_moments<<<mgrid, kMT, smem, c->stream>>>(kmap, npix, ksum, grid, pp, mpart,
+                                               (unsigned long long*)pdf);
+  }
+  {
+    ProfScope ps_(c, "k_moments_final");
+    k_moments_final<<<1, 32, 0, c->stream>>>(ksum, grid, mpart, mgrid, npix, moments);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+// Adjoint sums -> gradients (host FP64 assembly).  Synchronises.
+ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                              const double* A, double C, double w_var, double w_skew,
+                              const float* g, const double* dA, const double* dC,
+                              double* grad, double* G, double* H) {
+  ufc_status s = check_kappa_args(c, counts, S, nside, A, C);
+  if (s) return s;
+  if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
+  if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
+  if (S > 96) return set_err(c, UFC_ERR_UNSUPPORTED, "the adjoint supports nshell <= 96");
+  const int npix = 12 * nside * nside;
+  Coef cf;
+  make_coef(A, C, S, npix, cf);
+  const int grid = kappa_grid(c, npix);
+  const size_t prow = 4 * S + 4;
+  double* part = (double*)ws_get(c, kSlotPartials, (size_t)grid * prow * 8);
+  if (!part) return UFC_ERR_ALLOC;
+  const int smem = S * kKT * 4 + 4 * S * 8;
+  UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<false, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  {
+    ProfScope ps_(c, "k_kappa");
+    k_kappa<false, true><<<grid, kKT, smem, c->stream>>>(counts, cf, nullptr, nullptr,
+                                                        AdjOut{part, g});
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  std::vector<double> hp((size_t)grid * prow);
+  UFC_CUDA(c, cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  UFC_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<double> S1(S, 0.0), S2(S, 0.0), T(S, 0.0), Nb(S, 0.0);
+  double P1 = 0, P2 = 0, P3 = 0, Q = 0;
+  for (int i = 0; i < grid; ++i) {
+    const double* r = hp.data() + (size_t)i * prow;
+    for (int b = 0; b < S; ++b) {
+      S1[b] += r[4 * b];
+      S2[b] += r[4 * b + 1];
+      T[b] += r[4 * b + 2];
+      Nb[b] += r[4 * b + 3];
+    }
+    P1 += r[4 * S];
+    P2 += r[4 * S + 1];
+    P3 += r[4 * S + 2];
+    Q += r[4 * S + 3];
+  }
+  // central moments of the unrounded map from the raw sums about 0
+  const double N = npix;
+  const double m1 = P1 / N, r2 = P2 / N, r3 = P3 / N;
+  const double mu2 = r2 - m1 * m1;
+  const double mu3 = r3 - 3.0 * m1 * r2 + 2.0 * m1 * m1 * m1;
+  // G_b = sum_p gbar_p n_bp with
+  //   dvar/dk_p  = 2 (k_p - m)/N
+  //   dskew/dk_p = 3[(k_p - m)^2 - mu2] mu2^-3/2 / N - 3 mu3 mu2^-5/2 (k_p - m)/N
+  std::vector<double> Gb(S);
+  const double i32 = 1.0 / (mu2 * std::sqrt(mu2));
+  const double i52 = i32 / mu2;
+  for (int b = 0; b < S; ++b) {
+    const double c1 = S1[b] - m1 * Nb[b];                             // sum (k-m) n
+    const double c2 = S2[b] - 2.0 * m1 * S1[b] + m1 * m1 * Nb[b];     // sum (k-m)^2 n
+    const double gv = 2.0 * c1 / N;
+    const double gs = 3.0 * (c2 - mu2 * Nb[b]) * i32 / N - 3.0 * mu3 * i52 * c1 / N;
+    Gb[b] = w_var * gv + w_skew * gs + T[b];
+  }
+  const double Hs = Q;   // var and skew are shift invariant: their H is 0
+  for (int j = 0; j < 5; ++j) {
+    double acc = 0.0;
+    for (int b = 0; b < S; ++b) acc += dA[j * S + b] * Gb[b];
+    grad[j] = acc - dC[j] * Hs;
+  }
+  if (G)
+    for (int b = 0; b < S; ++b) G[b] = Gb[b];
+  if (H) *H = Hs;
+  return UFC_OK;
+}
+
+ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins,
+                            double* v) {
+  if (!m || !pdf || !v || nbins < 1 || nbins > kMaxBins)
+    return set_err(c, UFC_ERR_ARG, "stats_vector: bad arguments");
+  {
+    ProfScope ps_(c, "k_stats_vector");
+    k_stats_vector<<<1, 256, 0, c->stream>>>(m, (const unsigned long long*)pdf, nbins, v);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, double* st) {
+  if (!v || !st || nvec < 0 || d < 1 || d > 8192)
+    return set_err(c, UFC_ERR_ARG, "welford_update: bad arguments");
+  if (nvec == 0) return UFC_OK;
+  {
+    ProfScope ps_(c, "k_welford_update");
+    k_welford_update<<<1, 1024, 2 * d * 8, c->stream>>>(v, nvec, d, st);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+ufc_status run_welford_merge(ufc_ctx* c, double* a, const double* b, int d) {
+  if (!a || !b || d < 1 || d > 8192) return set_err(c, UFC_ERR_ARG, "welford_merge: bad arguments");
+  {
+    ProfScope ps_(c, "k_welford_merge");
+    k_welford_merge<<<1, 1024, 0, c->stream>>>(a, b, d);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, double* mean,
+                                double* cov, double* corr) {
+  if (!st || !mean || !cov || !corr || d < 1 || d > 8192 || ddof < 0)
+    return set_err(c, UFC_ERR_ARG, "welford_finalize: bad arguments");
+  {
+    ProfScope ps_(c, "k_welford_final");
+    k_welford_final<<<1, 1024, 0, c->stream>>>(st, d, ddof, mean, cov, corr);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+}  // namespace ufc

@@ -1,0 +1,83 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+the header declares, and its host cosmology (Eq. 1-3, 6) agrees with the
+independent oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ufalcon.h")
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1801_05745_gb300 import build
+    build.build()
+    from paper_1801_05745_gb300 import api as a
+    return a
+
+
+def test_header_symbols_exported(api):
+    text = open(HEADER).read()
+    names = sorted(set(re.findall(r"\b(ufc_[a-z_0-9]+)\s*\(", text)))
+    assert len(names) >= 15
+    import ctypes
+    lib = ctypes.CDLL(api.LIB_PATH)
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_chi_edges_vs_oracle(api, orc):
+    z = np.linspace(0.1, 1.5, 61)
+    for om, units in [(0.3, 1), (0.276, 1), (1.0, 1), (0.3, 0)]:
+        got = api.chi_edges(api.make_cosmo(om, 0.7, units), z)
+        ref = orc.chi_edges(om, 0.7, units, z)
+        assert np.allclose(got, ref, rtol=1e-13, atol=0)
+
+
+def test_z_of_chi_vs_oracle(api, orc):
+    cosmo = api.make_cosmo(0.3, 0.7, 1)
+    chi = np.linspace(292.0, 1322.0, 11)
+    got = api.z_of_chi(cosmo, chi)
+    ref = np.array([orc.z_of_chi(0.3, 0.7, 1, c) for c in chi])
+    assert np.allclose(got, ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_kappa_coeffs_vs_oracle(api, orc, kind):
+    z = np.linspace(0.1, 1.5, 21)
+    boxes_a = [api.make_box(2000.0, [1000.0] * 3, 512 ** 3, 0, 8),
+               api.make_box(6400.0, [3200.0] * 3, 512 ** 3, 8, 20)]
+    boxes_o = [orc.make_box(2000.0, [1000.0] * 3, 512 ** 3, 0, 8),
+               orc.make_box(6400.0, [3200.0] * 3, 512 ** 3, 8, 20)]
+    kw = dict(kind=kind, z_s=1.5, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    A, B, C = api.kappa_coeffs(api.make_cosmo(0.3, 0.7, 1), boxes_a, z, 512, api.make_source(**kw))
+    Ao, Bo, Co = orc.kappa_coeffs(0.3, 0.7, 1, boxes_o, z, 512, orc.make_source(**kw))
+    assert np.allclose(A, Ao, rtol=1e-12, atol=0)
+    assert np.allclose(B, Bo, rtol=1e-12, atol=0)
+    assert C == pytest.approx(Co, rel=1e-12)
+
+
+@pytest.mark.parametrize("kind,units", [(0, 1), (1, 1), (1, 0)])
+def test_coefficient_derivatives_vs_oracle_complex_step(api, orc, kind, units):
+    """Dual-number dA/dtheta, dC/dtheta against the oracle's complex-step
+    gradient of <g, kappa> with g = e_p picking single shells."""
+    z = np.linspace(0.2, 1.0, 4)
+    nside = 2
+    npix = 48
+    kw = dict(kind=kind, z_s=1.1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    boxes_a = [api.make_box(2000.0, [1000.0] * 3, 64 ** 3, 0, 3)]
+    boxes_o = [orc.make_box(2000.0, [1000.0] * 3, 64 ** 3, 0, 3)]
+    A, B, C, dA, dC = api.kappa_coeffs(api.make_cosmo(0.3, 0.7, units), boxes_a, z, nside,
+                                       api.make_source(**kw), derivs=True)
+    # counts: one particle in shell b at pixel b; g = indicator of pixel b
+    for b in range(3):
+        counts = np.zeros((3, npix), np.int32)
+        counts[b, b] = 1
+        g = np.zeros(npix, np.float32)
+        g[b] = 1.0
+        G = orc.kappa_stat_grads(counts, nside, 0.3, 0.7, units, boxes_o, z, orc.make_source(**kw), g)
+        # <g, kappa> = A_b - C  ->  d/dtheta = dA_b - dC
+        assert np.allclose(G[2], dA[:, b] - dC, rtol=1e-11, atol=1e-14 * np.abs(dA).max())

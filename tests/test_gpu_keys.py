@@ -1,0 +1,85 @@
+"""GPU parity of the fused shell + RING pixel key (Eq. 8, Sec. 2.4
+pixelisation): bit-exact against the oracle's FP64 procedure, on seeded
+particles, edge-hugging particles and degenerate inputs."""
+import numpy as np
+import pytest
+
+from paper_1801_05745_gb300 import synth
+from tests.gpu_common import api_ctx, boundary_points, both_boxes, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("nside", [1, 4, 64, 1024])
+def test_keys_random_particles(orc, nside):
+    api, ctx = api_ctx()
+    L = 2000.0
+    xyz = synth.particles_numpy(300_000, L, 5.0, synth.seed_for(1, 7, nside % 97))
+    chi = orc.chi_edges(0.3, 0.7, 1, np.linspace(0.05, 0.45, 17))
+    ba, bo = both_boxes(api, orc, L, [L / 2] * 3, len(xyz), 0, 16)
+    got = ctx.keys(to_dev(xyz), ba, chi, nside).cpu().numpy()
+    ref = orc.keys(xyz, bo, chi, nside)
+    assert np.array_equal(got, ref.astype(np.int32)), np.nonzero(got != ref)[0][:10]
+    assert (ref >= 0).sum() > 10_000
+
+
+@pytest.mark.parametrize("nside", [2, 16, 256, 2048])
+def test_keys_on_pixel_and_shell_edges(orc, nside):
+    """Directions on pixel edges and radii on shell edges, rounded to FP32:
+    exercises the refine and exact stages."""
+    api, ctx = api_ctx()
+    L = 6400.0
+    obs = np.array([3200.0, 3200.0, 3200.0])
+    chi = orc.chi_edges(0.3, 0.7, 1, np.linspace(0.1, 0.9, 9))
+    d = boundary_points(orc, nside, 40_000, chi[0], chi[-1], seed=nside)
+    # radii on shell edges along random directions
+    rng = np.random.default_rng(nside + 1)
+    u = rng.normal(size=(4000, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    e = chi[rng.integers(0, len(chi), 4000)]
+    d = np.concatenate([d, u * e[:, None]])
+    # axes, diagonals, poles
+    special = []
+    for r in (chi[0] * 1.01, chi[3], chi[-1] * 0.99):
+        for v in ([1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                  [1, 1, 0], [-1, 1, 0], [1, -1, 0.3], [1, 1, 1], [3, 4, 0], [0, 3, 4]):
+            v = np.array(v, float)
+            special.append(r * v / np.linalg.norm(v))
+    d = np.concatenate([d, np.array(special)])
+    xyz = (d + obs).astype(np.float32)
+    ba, bo = both_boxes(api, orc, L, obs, len(xyz), 0, 8)
+    got = ctx.keys(to_dev(xyz), ba, chi, nside).cpu().numpy()
+    info = ctx.bin_info()
+    ref = orc.keys(xyz, bo, chi, nside)
+    bad = np.nonzero(got != ref)[0]
+    assert len(bad) == 0, (len(bad), bad[:5], got[bad[:5]], ref[bad[:5]])
+    assert info["refined"] > 1000 and info["exact"] > 0, info
+
+
+def test_keys_degenerate_inputs(orc):
+    api, ctx = api_ctx()
+    chi = np.array([0.0, 1.0, 2.0, 3.0])
+    xyz = np.array([[0, 0, 0], [np.nan, 0, 0], [0, np.inf, 0], [1, 0, 0], [2, 0, 0],
+                    [3, 0, 0], [1e-30, 0, 0], [0, 0, 2.5], [0, 0, -2.5],
+                    [-0.0, 0.0, 1.5], [0.7, 0.7, 0.0], [-0.7, -0.7, 0.0]], np.float32)
+    ba, bo = both_boxes(api, orc, 10.0, [0.0, 0.0, 0.0], 10, 0, 3)
+    for nside in (1, 8, 4096):
+        got = ctx.keys(to_dev(xyz), ba, chi, nside).cpu().numpy()
+        ref = orc.keys(xyz, bo, chi, nside)
+        assert np.array_equal(got, ref.astype(np.int32)), (nside, got, ref)
+    # empty input
+    out = ctx.keys(to_dev(np.zeros((0, 3), np.float32)), ba, chi, 8)
+    assert out.numel() == 0
+
+
+def test_keys_observer_not_representable_in_fp32(orc):
+    """An observer with FP64-only coordinates exercises the split shift."""
+    api, ctx = api_ctx()
+    L = 1000.0
+    obs = [500.1234567890123, 499.98765432101234, 500.000000001]
+    xyz = synth.particles_numpy(200_000, L, 5.0, 4242)
+    chi = np.linspace(50.0, 480.0, 11)
+    ba, bo = both_boxes(api, orc, L, obs, len(xyz), 0, 10)
+    got = ctx.keys(to_dev(xyz), ba, chi, 128).cpu().numpy()
+    ref = orc.keys(xyz, bo, chi, 128)
+    assert np.array_equal(got, ref.astype(np.int32))

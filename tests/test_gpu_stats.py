@@ -1,0 +1,108 @@
+"""GPU parity of the kappa map (Eq. 6), moments (Eq. 12-13), PDF (Sec. 3.3),
+adjoint gradients and the Welford covariance (Eq. 10-11)."""
+import numpy as np
+import pytest
+
+from paper_1801_05745_gb300 import synth
+from tests.gpu_common import api_ctx, both_boxes, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _map(orc, api, ctx, nside, nshell, n, seed, kind=1):
+    x1 = synth.particles_numpy(n, 2000.0, 5.0, seed)
+    x2 = synth.particles_numpy(n, 6400.0, 20.0, seed + 1)
+    z = np.linspace(0.1, 1.5, nshell + 1)
+    chi = orc.chi_edges(0.3, 0.7, 1, z)
+    split = int(np.argmin(np.abs(chi - 1000.0)))
+    b1a, b1o = both_boxes(api, orc, 2000.0, [1000.0] * 3, n, 0, split)
+    b2a, b2o = both_boxes(api, orc, 6400.0, [3200.0] * 3, n, split, nshell)
+    counts = ctx.bin([to_dev(x1), to_dev(x2)], [b1a, b2a], chi, nside)
+    kw = dict(kind=kind, z_s=1.5, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    return counts, z, (b1a, b2a), (b1o, b2o), kw
+
+
+def kappa_gate(k_gpu, k_or, A, counts):
+    """|dk| <= 1e-5 max(|k|, sum_b |A_b| n_bp + |C|) (scale of the cancelling terms)."""
+    scale = (np.abs(A)[:, None] * counts).sum(0)
+    return np.abs(k_gpu.astype(np.float64) - k_or.astype(np.float64)) <= 1e-5 * np.maximum(
+        np.abs(k_or), scale) + 1e-30
+
+
+@pytest.mark.parametrize("nside,nshell,kind", [(16, 8, 0), (64, 20, 1), (256, 40, 1)])
+def test_kappa_moments_pdf(orc, nside, nshell, kind):
+    api, ctx = api_ctx()
+    counts, z, ba, bo, kw = _map(orc, api, ctx, nside, nshell, 400_000, 1234 + nside, kind)
+    A, B, C = orc.kappa_coeffs(0.3, 0.7, 1, list(bo), z, nside, orc.make_source(**kw))
+    k_or = orc.kappa_map(counts.cpu().numpy(), A, C)
+    lo, hi = float(k_or.min()) * 0.9, float(k_or.max()) * 0.8
+    kap, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, 200)
+    kg = kap.cpu().numpy()
+    cn = counts.cpu().numpy()
+    assert kappa_gate(kg, k_or, A, cn).all()
+    assert (kg == k_or).mean() > 0.999     # nearly always the same rounding
+    # moments and PDF on the GPU's own kappa
+    m_or = orc.moments(kg)
+    mg = mom.cpu().numpy()
+    for i in range(10):
+        assert mg[i] == pytest.approx(m_or[i], rel=1e-9, abs=1e-15 * abs(m_or[1]) ** 0.5 * (i == 0)), i
+    assert np.array_equal(pdf.cpu().numpy(), orc.pdf(kg, lo, hi, 200))
+
+
+def test_pdf_values_on_bin_edges(orc):
+    """kappa = n 2^-12 lands exactly on the edges of 96 bins over
+    [0, 96 2^-12): the half-open rule and the exact FP64 fallback decide."""
+    api, ctx = api_ctx()
+    npix = 12 * 16 * 16
+    counts = torch.from_numpy((np.arange(npix, dtype=np.int32) % 98).reshape(1, npix)).cuda()
+    A = np.array([2.0 ** -12])
+    lo, hi, nb = 0.0, 96 * 2.0 ** -12, 96
+    kap, mom, pdf = ctx.kappa_stats(counts, A, 0.0, lo, hi, nb)
+    kg = kap.cpu().numpy()
+    assert np.array_equal(kg, (np.arange(npix) % 98) * np.float32(2.0 ** -12))
+    p = pdf.cpu().numpy()
+    assert np.array_equal(p, orc.pdf(kg, lo, hi, nb))
+    assert p[nb + 1] > 0 and p[:nb].min() > 0     # values at hi overflow
+    # a range with an offset lo and a non-power-of-two width
+    kap2, _, pdf2 = ctx.kappa_stats(counts, A, 0.0, 0.001, 0.0191, 37)
+    assert np.array_equal(pdf2.cpu().numpy(), orc.pdf(kap2.cpu().numpy(), 0.001, 0.0191, 37))
+
+
+@pytest.mark.parametrize("kind,units", [(0, 1), (1, 1), (1, 0)])
+def test_backward_vs_complex_step(orc, kind, units):
+    api, ctx = api_ctx()
+    nside, nshell = 32, 12
+    counts, z, ba, bo, kw = _map(orc, api, ctx, nside, nshell, 300_000, 99 + kind, kind)
+    kw["z_s"] = 1.5
+    cosmo = api.make_cosmo(0.3, 0.7, units)
+    A, B, C, dA, dC = api.kappa_coeffs(cosmo, list(ba), z, nside, api.make_source(**kw), derivs=True)
+    rng = np.random.default_rng(5)
+    g = rng.normal(size=counts.shape[1]).astype(np.float32)
+    cn = counts.cpu().numpy()
+    G_or = orc.kappa_stat_grads(cn, nside, 0.3, 0.7, units, list(bo), z, orc.make_source(**kw), g)
+    for wv, ws, use_g in [(1.0, 0.0, False), (0.0, 1.0, False), (0.0, 0.0, True), (0.7, -0.3, True)]:
+        grad, Gb, H = ctx.kappa_backward(counts, A, C, dA, dC, wv, ws, to_dev(g) if use_g else None)
+        ref = wv * G_or[0] + ws * G_or[1] + (G_or[2] if use_g else 0.0)
+        scale = np.abs(wv * G_or[0]).max() + np.abs(ws * G_or[1]).max() + (np.abs(G_or[2]).max() if use_g else 0)
+        assert np.allclose(grad, ref, rtol=1e-9, atol=1e-9 * scale), (wv, ws, use_g, grad, ref)
+
+
+def test_welford_vs_oracle_covariance(orc):
+    api, ctx = api_ctx()
+    rng = np.random.default_rng(3)
+    v = rng.normal(size=(150, 33)) @ rng.normal(size=(33, 33)) + 5.0
+    d = v.shape[1]
+    st = api.welford_state(d)
+    vt = torch.from_numpy(v).cuda()
+    ctx.welford_update(vt[:70], st)
+    # a second state merged in (the realisation-sharded path)
+    st2 = api.welford_state(d)
+    ctx.welford_update(vt[70:], st2)
+    ctx.welford_merge(st, st2, d)
+    for ddof in (0, 1):
+        mean, cov, corr = ctx.welford_finalize(st, d, ddof)
+        m_o, c_o, r_o = orc.covariance(v, ddof)
+        assert np.allclose(mean.cpu().numpy(), m_o, rtol=1e-12, atol=1e-12)
+        assert np.allclose(cov.cpu().numpy(), c_o, rtol=1e-9, atol=1e-12)
+        assert np.allclose(corr.cpu().numpy(), r_o, rtol=1e-9, atol=1e-12)
