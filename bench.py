@@ -215,6 +215,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--scale", type=int, default=None, help="particles per side per box (default 1024)")
+    ap.add_argument("--nside", type=int, default=None, help="HEALPix Nside (default 1024)")
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -240,6 +241,8 @@ def main():
     from paper_1801_05745_gb300 import api, synth
 
     w = workload(args.scale)
+    if args.nside:
+        w.nside = args.nside
     ctx = api.context(local)
     cosmo = api.make_cosmo(w.omega_m, w.h, 1)
     z, chi, split = shells(w, api=api)

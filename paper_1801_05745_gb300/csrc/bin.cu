@@ -34,7 +34,7 @@ constexpr int kOffBits = 15;            // offset bits in a dense key
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;
 constexpr int kChunk = 2048;            // dense keys reserved per warp at a time
 constexpr int kGroupBits = 8;           // buckets per group = 256
-constexpr int kSmemHistMax = 28672;     // buckets counted in shared memory
+constexpr int kSmemHistMax = 31744;     // buckets counted in shared memory (124 KB)
 constexpr int kFastThreads = 512;
 
 struct KeyOut {
@@ -109,21 +109,59 @@ __device__ __forceinline__ void dense_close(WarpChunk& wc, const KeyOut& o) {
     if (wc.base + i < o.dense_cap) o.dense[wc.base + i] = kSentinel;
 }
 
-// Warp-aggregated push of undecided entries; returns false for lanes whose
-// entry did not fit (they must resolve it themselves).
-__device__ __forceinline__ bool queue_push(bool want, uint64_t e, uint64_t* q,
+// Warp-aggregated push of undecided entries into per-warp chunks of
+// kQChunk queue slots (one atomic per chunk, not per push); returns false for
+// lanes whose entry did not fit (they resolve it themselves).  Unused slots
+// of a warp's last chunk hold kQEmpty.
+constexpr int kQChunk = 256;
+constexpr uint64_t kQEmpty = ~0ull;
+struct QChunk {
+  int64_t base;   // -1: none
+  int32_t fill;
+};
+
+__device__ __forceinline__ bool queue_push(QChunk& qc, bool want, uint64_t e, uint64_t* q,
                                            int64_t cap, unsigned long long* count) {
   const unsigned full = 0xFFFFFFFFu;
-  unsigned m = __ballot_sync(full, want);
+  const unsigned m = __ballot_sync(full, want);
   if (m == 0) return true;
-  int lane = threadIdx.x & 31;
-  unsigned long long b = 0;
-  if (lane == 0) b = atomicAdd(count, (unsigned long long)__popc(m));
-  b = __shfl_sync(full, b, 0);
-  int64_t idx = (int64_t)b + __popc(m & ((1u << lane) - 1u));
+  const int lane = threadIdx.x & 31;
+  const int cnt = __popc(m);
+  const int rank = __popc(m & ((1u << lane) - 1u));
+  if (qc.base < 0) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(count, (unsigned long long)kQChunk);
+    qc.base = (int64_t)__shfl_sync(full, b, 0);
+    qc.fill = 0;
+  }
+  const int room = kQChunk - qc.fill;
+  int64_t idx;
+  if (rank < room) {
+    idx = qc.base + qc.fill + rank;
+  } else {
+    idx = -1;
+  }
+  if (cnt >= room) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(count, (unsigned long long)kQChunk);
+    const int64_t nb = (int64_t)__shfl_sync(full, b, 0);
+    if (rank >= room) idx = nb + (rank - room);
+    qc.base = nb;
+    qc.fill = cnt - room;
+  } else {
+    qc.fill += cnt;
+  }
   if (!want) return true;
   if (idx < cap) { q[idx] = e; return true; }
   return false;
+}
+
+// Marks the unused slots of the warp's last queue chunk.
+__device__ __forceinline__ void queue_close(QChunk& qc, uint64_t* q, int64_t cap) {
+  if (qc.base < 0) return;
+  const int lane = threadIdx.x & 31;
+  for (int i = qc.fill + lane; i < kQChunk; i += 32)
+    if (qc.base + i < cap) q[qc.base + i] = kQEmpty;
 }
 
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
@@ -132,31 +170,151 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // ----------------------------------------------------------- fast stage ----
+constexpr int kLutBits = 11;                 // shell lookup table over r^2
+constexpr int kLut = 1 << kLutBits;
+
+struct FastShared {
+  float lo2[kMaxShells + 2], hi2[kMaxShells + 2];
+  float shf[3][kMaxImg1D], shlo[3][kMaxImg1D];
+  uint16_t lut[kLut];                        // edges with lo2 <= bin start
+};
+
+// Shell of r2 via the lookup table: the table gives the edge count at the
+// start of r2's bin; a short scan moves past edges below r2, then the band
+// test of shell_fast applies.  -1 outside, -2 undecided.
+__device__ __forceinline__ int32_t shell_lut(const FastShared& fs, int32_t lo, int32_t hi,
+                                             float lut_scale, float r2) {
+  if (r2 < fs.lo2[lo]) return -1;
+  if (r2 >= fs.hi2[hi]) return -1;
+  const int bin = min(kLut - 1, __float2int_rz(r2 * lut_scale));
+  int a = min(max(int(fs.lut[bin]) - 1, lo), hi);
+  while (a > lo && r2 < fs.lo2[a]) --a;         // the bin index may round up
+  while (a < hi && r2 >= fs.lo2[a + 1]) ++a;    // r2 in [lo2[a], lo2[a+1])
+  if (r2 < fs.hi2[a]) return -2;
+  return (a < hi) ? a : -1;
+}
+
+struct FastCtx {
+  WarpChunk wc;
+  QChunk qc;
+  unsigned long long n_invalid, n_keyed;
+};
+
+// All images of one particle (warp-collective: every lane calls it).
+template <int MODE>
+__device__ __forceinline__ void fast_particle(bool have, float x, float y, float zc, int64_t p,
+                                              int32_t box_id, const BoxGeom& bg,
+                                              const FastShared& fs, float lut_scale,
+                                              const ShellTable& st, const Bands& bd, int32_t N,
+                                              int32_t npix, const KeyOut& o, const Queues& qs,
+                                              uint32_t* hist_s, FastCtx& fc) {
+  const int lo = bg.shell_lo, hi = bg.shell_hi;
+  const int n1 = 2 * bg.R + 1;
+  const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
+  if (have && !finite) ++fc.n_invalid;
+  int ii = 0, jj = 0, kk = 0;                   // image (ii, jj, kk), img = (ii n1 + jj) n1 + kk
+  for (int img = 0; img < bg.nimg; ++img) {
+    if (img) {
+      if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
+    }
+    int32_t key = kKeyOutside;
+    uint32_t dkey = 0u;
+    if (finite) {
+      const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
+      const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
+      const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
+      const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+      if (!(r2 >= bd.r2_min)) {
+        key = kKeyUndecided;
+      } else {
+        const int32_t b = shell_lut(fs, lo, hi, lut_scale, r2);
+        if (b == -2) {
+          key = kKeyUndecided;
+        } else if (b >= 0) {
+          const int32_t pix = pixel_fast(N, bd, dx, dy, dz, r2);
+          key = (pix == kKeyUndecided) ? kKeyUndecided : b * npix + pix;
+          if (MODE == kModeDense && pix != kKeyUndecided) {
+            const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
+            dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
+                   (uint32_t(pix) - blk * uint32_t(kBlockPix));
+          }
+        }
+      }
+    }
+    const bool und = key == kKeyUndecided;
+    if (!queue_push(fc.qc, und, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
+      // queue full: resolve with the FP64 procedure here
+      key = key_exact(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii], bg.sh64[1][jj],
+                      bg.sh64[2][kk]);
+      if (key == kKeyInvalid) ++fc.n_invalid;
+      if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o.nblk);
+    }
+    if (MODE == kModeKeys) {
+      if (have) o.keys[p] = finite ? key : kKeyInvalid;
+    } else if (MODE == kModeDirect) {
+      if (key >= 0) atomicAdd(o.counts + key, 1);
+    } else {
+      if (key >= 0) {
+        const uint32_t bucket = dkey >> kOffBits;
+        if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
+        else atomicAdd(o.hist + bucket, 1u);
+      }
+      dense_append(fc.wc, key >= 0, dkey, o);
+    }
+    fc.n_keyed += key >= 0;
+  }
+}
+
+__device__ __forceinline__ void fast_init_shared(FastShared& fs, const BoxGeom& bg,
+                                                 const ShellTable& st, const uint16_t* lut) {
+  for (int i = threadIdx.x; i <= st.nshell; i += blockDim.x) {
+    fs.lo2[i] = st.lo2[i];
+    fs.hi2[i] = st.hi2[i];
+  }
+  if (threadIdx.x == 0) {
+    fs.lo2[st.nshell + 1] = INFINITY;
+    fs.hi2[st.nshell + 1] = INFINITY;
+  }
+  for (int i = threadIdx.x; i < 3 * kMaxImg1D; i += blockDim.x) {
+    fs.shf[i / kMaxImg1D][i % kMaxImg1D] = bg.shf[i / kMaxImg1D][i % kMaxImg1D];
+    fs.shlo[i / kMaxImg1D][i % kMaxImg1D] = bg.shlo[i / kMaxImg1D][i % kMaxImg1D];
+  }
+  for (int i = threadIdx.x; i < kLut; i += blockDim.x) fs.lut[i] = lut[i];
+}
+
+template <int MODE>
+__device__ __forceinline__ void fast_finish(FastCtx& fc, const KeyOut& o, const Queues& qs,
+                                            uint32_t* hist_s) {
+  if (MODE == kModeDense) dense_close(fc.wc, o);
+  queue_close(fc.qc, qs.q1, qs.cap1);
+  const unsigned long long ni = warp_sum(fc.n_invalid), nk = warp_sum(fc.n_keyed);
+  if ((threadIdx.x & 31) == 0) {
+    if (ni) atomicAdd(&qs.cnt->invalid, ni);
+    if (nk) atomicAdd(&qs.cnt->keyed, nk);
+  }
+  if (MODE == kModeDense && o.smem_hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x)
+      if (hist_s[i]) atomicAdd(o.hist + i, hist_s[i]);
+  }
+}
+
+struct LutParam { uint16_t v[kLut]; float scale; };
+
+// Fast stage with plain per-thread loads (any 4-byte aligned input).
 template <int MODE>
 __global__ void __launch_bounds__(kFastThreads)
 k_fast(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
-       ShellTable st, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
+       ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
   extern __shared__ uint32_t hist_s[];
-  __shared__ float lo2_s[kMaxShells + 1], hi2_s[kMaxShells + 1];
-  __shared__ float shf_s[3][kMaxImg1D], shlo_s[3][kMaxImg1D];
-  for (int i = threadIdx.x; i <= st.nshell; i += blockDim.x) {
-    lo2_s[i] = st.lo2[i];
-    hi2_s[i] = st.hi2[i];
-  }
-  for (int i = threadIdx.x; i < 3 * kMaxImg1D; i += blockDim.x) {
-    shf_s[i / kMaxImg1D][i % kMaxImg1D] = bg.shf[i / kMaxImg1D][i % kMaxImg1D];
-    shlo_s[i / kMaxImg1D][i % kMaxImg1D] = bg.shlo[i / kMaxImg1D][i % kMaxImg1D];
-  }
+  __shared__ FastShared fs;
+  fast_init_shared(fs, bg, st, lp.v);
   if (MODE == kModeDense && o.smem_hist)
     for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) hist_s[i] = 0;
   __syncthreads();
-
-  const int lo = bg.shell_lo, hi = bg.shell_hi;
-  const int n1 = 2 * bg.R + 1;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t iters = (n + stride - 1) / stride;
-  unsigned long long n_invalid = 0, n_keyed = 0;
-  WarpChunk wc{-1, 0};
+  FastCtx fc{{-1, 0}, {-1, 0}, 0, 0};
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t it = 0; it < iters; ++it, p += stride) {
     const bool have = p < n;
@@ -166,68 +324,271 @@ k_fast(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
       y = __ldg(xyz + 3 * p + 1);
       zc = __ldg(xyz + 3 * p + 2);
     }
-    const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
-    if (have && !finite) ++n_invalid;
-    for (int img = 0; img < bg.nimg; ++img) {
-      int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
-      int32_t key = kKeyOutside;
-      uint32_t dkey = 0u;
-      if (finite) {
-        float dx = (x + shf_s[0][ii]) + shlo_s[0][ii];
-        float dy = (y + shf_s[1][jj]) + shlo_s[1][jj];
-        float dz = (zc + shf_s[2][kk]) + shlo_s[2][kk];
-        float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        if (!(r2 >= bd.r2_min)) {
-          key = kKeyUndecided;
-        } else {
-          int32_t b = shell_fast(lo2_s, hi2_s, lo, hi, r2);
-          if (b == -2) key = kKeyUndecided;
-          else if (b >= 0) {
-            int32_t pix = pixel_fast(N, bd, dx, dy, dz, r2);
-            key = (pix == kKeyUndecided) ? kKeyUndecided : b * npix + pix;
-            if (MODE == kModeDense && pix != kKeyUndecided) {
-              uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
-              dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
-                     (uint32_t(pix) - blk * uint32_t(kBlockPix));
+    fast_particle<MODE>(have, x, y, zc, p, box_id, bg, fs, lp.scale, st, bd, N, npix, o, qs,
+                        hist_s, fc);
+  }
+  fast_finish<MODE>(fc, o, qs, hist_s);
+}
+
+// ---- fast stage fed by bulk asynchronous copies (TMA, 1-D) ----------------
+// Persistent blocks; chunks of kTChunk particles (12 KB per 1024) stream
+// through a ring of kStages shared-memory buffers (72 KB) filled by
+// cp.async.bulk and tracked by mbarriers.  Requires a 16-byte aligned xyz.
+constexpr int kTThreads = 768;
+constexpr int kTChunk = 1536;                 // particles per chunk (18 KB)
+constexpr int kStages = 4;
+constexpr long long kWaitLimit = 1ll << 28;   // try_wait polls before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// The FP64 procedure for an image whose queue slot did not fit (rare); kept
+// out of line so that the fast stage's register budget is not spent on it.
+__device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo, int32_t hi,
+                                               int32_t N, int32_t npix, float x, float y,
+                                               float zc, double shx, double shy, double shz) {
+  return key_exact(st, lo, hi, N, npix, x, y, zc, shx, shy, shz);
+}
+
+// Emission of one decided or undecided key (warp-collective).
+template <int MODE>
+__device__ __forceinline__ void fast_emit(bool have, int32_t key, uint32_t dkey, int32_t box_id,
+                                          int img, int64_t p, const BoxGeom& bg,
+                                          const ShellTable& st, int32_t N, int32_t npix,
+                                          const KeyOut& o, const Queues& qs, uint32_t* hist_s,
+                                          FastCtx& fc, float x, float y, float zc, int ii, int jj,
+                                          int kk) {
+  const bool und = have && key == kKeyUndecided;
+  if (!queue_push(fc.qc, und, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
+    key = key_exact_slow(st, bg.shell_lo, bg.shell_hi, N, npix, x, y, zc, bg.sh64[0][ii],
+                         bg.sh64[1][jj], bg.sh64[2][kk]);
+    if (key == kKeyInvalid) ++fc.n_invalid;
+    if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o.nblk);
+  }
+  const bool ok = have && key >= 0;
+  if (MODE == kModeKeys) {
+    if (have) o.keys[p] = key;
+  } else if (MODE == kModeDirect) {
+    if (ok) atomicAdd(o.counts + key, 1);
+  } else {
+    if (ok) {
+      const uint32_t bucket = dkey >> kOffBits;
+      if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
+      else atomicAdd(o.hist + bucket, 1u);
+    }
+    dense_append(fc.wc, ok, dkey, o);
+  }
+  fc.n_keyed += ok;
+}
+
+// Warp-aggregated append to a shared-memory list.
+__device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list, int* count) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
+  if (m == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (want) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kTThreads, 1)
+k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
+           ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
+  extern __shared__ __align__(128) uint8_t dyn[];
+  float* ring = reinterpret_cast<float*>(dyn);                       // [kStages][3 kTChunk]
+  uint32_t* eq_list = reinterpret_cast<uint32_t*>(dyn + kStages * kTChunk * 12);
+  uint32_t* cap_list = eq_list + kTChunk;
+  uint32_t* hist_s = cap_list + kTChunk;
+  __shared__ FastShared fs;
+  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ int abort_s, neq_s, ncap_s;
+  fast_init_shared(fs, bg, st, lp.v);
+  if (MODE == kModeDense && o.smem_hist)
+    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) hist_s[i] = 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_s = 0;
+    neq_s = 0;
+    ncap_s = 0;
+  }
+  __syncthreads();
+
+  const int lo = bg.shell_lo, hi = bg.shell_hi;
+  const int n1 = 2 * bg.R + 1;
+  const int64_t nchunks = (n + kTChunk - 1) / kTChunk;
+  const int64_t mine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  auto chunk_bytes = [&](int64_t c) -> uint32_t {
+    const int64_t rest = n - c * kTChunk;
+    const int64_t cnt = rest < kTChunk ? rest : (int64_t)kTChunk;
+    return uint32_t((cnt * 12) & ~15ll);       // bulk copies move multiples of 16 bytes
+  };
+  auto issue = [&](int64_t k) {                // k-th chunk of this block
+    const int64_t c = blockIdx.x + k * gridDim.x;
+    const int s = int(k % kStages);
+    const uint32_t bytes = chunk_bytes(c);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[s], bytes);
+    if (bytes) bulk_g2s(ring + s * 3 * kTChunk, xyz + c * kTChunk * 3, bytes, &bar[s]);
+  };
+  int64_t issued = 0;                          // meaningful in thread 0
+  if (threadIdx.x == 0)
+    for (; issued < mine && issued < kStages; ++issued) issue(issued);
+
+  FastCtx fc{{-1, 0}, {-1, 0}, 0, 0};
+  int64_t k = 0;
+  for (; k < mine; ++k) {
+    const int64_t c = blockIdx.x + k * gridDim.x;
+    const int s = int(k % kStages);
+    if (!mbar_wait(&bar[s], uint32_t((k / kStages) & 1))) abort_s = 1;
+    __syncthreads();
+    if (abort_s) break;
+    const float* buf = ring + s * 3 * kTChunk;
+    const uint32_t bytes = chunk_bytes(c);
+    const int64_t base = c * kTChunk;
+    auto load = [&](int j, float& x, float& y, float& zc) {
+      if ((uint32_t)(12 * j + 12) <= bytes) {
+        x = buf[3 * j];
+        y = buf[3 * j + 1];
+        zc = buf[3 * j + 2];
+      } else {                                 // ragged tail outside the bulk copy
+        const int64_t p = base + j;
+        x = __ldg(xyz + 3 * p);
+        y = __ldg(xyz + 3 * p + 1);
+        zc = __ldg(xyz + 3 * p + 2);
+      }
+    };
+    // ---- phase A: radius, shell and zone; in-cone images go to the lists
+#pragma unroll 1
+    for (int j = threadIdx.x; j < kTChunk; j += kTThreads) {
+      const int64_t p = base + j;
+      const bool have = p < n;
+      float x = 0.f, y = 0.f, zc = 0.f;
+      if (have) load(j, x, y, zc);
+      const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
+      if (have && !finite) ++fc.n_invalid;
+      int ii = 0, jj = 0, kk = 0;
+      for (int img = 0; img < bg.nimg; ++img) {
+        if (img) {
+          if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
+        }
+        int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap
+        int32_t b = -1;
+        if (finite) {
+          const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
+          const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
+          const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          if (!(r2 >= bd.r2_min)) {
+            cls = 1;
+          } else {
+            b = shell_lut(fs, lo, hi, lp.scale, r2);
+            if (b == -2) cls = 1;
+            else if (b >= 0) {
+              const float za = fabsf(dz * rsqrtf(r2));
+              cls = za <= bd.z_eq ? 2 : (za > bd.z_cap ? 3 : 1);
             }
           }
         }
+        const uint32_t entry = uint32_t(j) | (uint32_t(b) << 11) | (uint32_t(img) << 19);
+        list_push(cls == 2, entry, eq_list, &neq_s);
+        list_push(cls == 3, entry, cap_list, &ncap_s);
+        // outside, invalid and undecided images are final here
+        const int32_t key = !finite ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
+        const bool here = have && (cls < 2);
+        fast_emit<MODE>(here, key, 0u, box_id, img, p, bg, st, N, npix, o, qs, hist_s, fc, x, y,
+                        zc, ii, jj, kk);
       }
-      const bool und = key == kKeyUndecided;
-      if (!queue_push(und, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
-        // queue full: resolve with the FP64 procedure here
-        key = key_exact(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii], bg.sh64[1][jj],
-                        bg.sh64[2][kk]);
-        if (key == kKeyInvalid) ++n_invalid;
-        if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o.nblk);
-      }
-      if (MODE == kModeKeys) {
-        if (have) o.keys[p] = finite ? key : kKeyInvalid;
-      } else if (MODE == kModeDirect) {
-        if (key >= 0) atomicAdd(o.counts + key, 1);
-      } else {
-        if (key >= 0) {
-          uint32_t bucket = dkey >> kOffBits;
-          if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
-          else atomicAdd(o.hist + bucket, 1u);
+    }
+    __syncthreads();
+    // ---- phase B: pixels of the dense belt and cap lists
+    const int neq = neq_s, ncap = ncap_s;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int cnt = pass == 0 ? neq : ncap;
+      const uint32_t* list = pass == 0 ? eq_list : cap_list;
+      const int rounds = (cnt + kTThreads - 1) / kTThreads;
+#pragma unroll 1
+      for (int rr = 0; rr < rounds; ++rr) {
+        const int i = rr * kTThreads + threadIdx.x;
+        const bool have = i < cnt;
+        const uint32_t e = have ? list[i] : 0u;
+        const int j = int(e & 2047u), b = int((e >> 11) & 255u), img = int(e >> 19);
+        const int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
+        float x = 0.f, y = 0.f, zc = 0.f;
+        if (have) load(j, x, y, zc);
+        const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
+        const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
+        const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        const float rinv = rsqrtf(r2);
+        const float z = dz * rinv;
+        int32_t pix = kKeyUndecided;
+        if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
+                                  : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
+        const int32_t key = pix == kKeyUndecided ? kKeyUndecided : b * npix + pix;
+        uint32_t dkey = 0u;
+        if (MODE == kModeDense && pix != kKeyUndecided) {
+          const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
+          dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
+                 (uint32_t(pix) - blk * uint32_t(kBlockPix));
         }
-        dense_append(wc, key >= 0, dkey, o);
+        fast_emit<MODE>(have, key, dkey, box_id, img, base + j, bg, st, N, npix, o, qs, hist_s, fc,
+                        x, y, zc, ii, jj, kk);
       }
-      n_keyed += key >= 0;
+    }
+    __syncthreads();                           // buffer s and the lists fully consumed
+    if (threadIdx.x == 0) {
+      neq_s = 0;
+      ncap_s = 0;
+      if (issued < mine) issue(issued++);
     }
   }
-  if (MODE == kModeDense) dense_close(wc, o);
-  n_invalid = warp_sum(n_invalid);
-  n_keyed = warp_sum(n_keyed);
-  if ((threadIdx.x & 31) == 0) {
-    if (n_invalid) atomicAdd(&qs.cnt->invalid, n_invalid);
-    if (n_keyed) atomicAdd(&qs.cnt->keyed, n_keyed);
+  if (abort_s) {
+    // a wait ran out: wait (bounded) for the copies still in flight, report
+    if (threadIdx.x == 0) {
+      atomicAdd(&qs.cnt->timeouts, 1ull);
+      for (int64_t kk = k; kk < issued; ++kk)
+        mbar_wait(&bar[kk % kStages], uint32_t((kk / kStages) & 1));
+    }
+    return;
   }
-  if (MODE == kModeDense && o.smem_hist) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x)
-      if (hist_s[i]) atomicAdd(o.hist + i, hist_s[i]);
-  }
+  fast_finish<MODE>(fc, o, qs, hist_s);
 }
 
 // ------------------------------------------------ refine and exact stages --
@@ -260,13 +621,15 @@ k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues
   WarpChunk wc{-1, 0};
   unsigned long long n_ref = 0, n_invalid = 0, n_keyed = 0;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  QChunk qc{-1, 0};
   for (int64_t it = 0; it < iters; ++it, i += stride) {
-    const bool have = i < m;
+    bool have = i < m;
     int32_t key = kKeyOutside;
     int64_t p = 0;
     uint64_t e = 0;
+    if (have) e = qs.q1[i];
+    have = have && e != kQEmpty;
     if (have) {
-      e = qs.q1[i];
       const int b = qbox(e), img = qimg(e);
       p = qidx(e);
       const BoxGeom& g = bp.box[b];
@@ -280,7 +643,7 @@ k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues
       ++n_ref;
     }
     const bool und = have && key == kKeyUndecided;
-    if (!queue_push(und, e, qs.q2, qs.cap2, &qs.cnt->q2)) {
+    if (!queue_push(qc, und, e, qs.q2, qs.cap2, &qs.cnt->q2)) {
       const int b = qbox(e), img = qimg(e);
       const BoxGeom& g = bp.box[b];
       const int n1 = 2 * g.R + 1;
@@ -299,6 +662,7 @@ k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues
     }
   }
   if (MODE == kModeDense) dense_close(wc, o);
+  queue_close(qc, qs.q2, qs.cap2);
   n_ref = warp_sum(n_ref);
   n_invalid = warp_sum(n_invalid);
   n_keyed = warp_sum(n_keyed);
@@ -320,11 +684,13 @@ k_exact(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues 
   unsigned long long n_ex = 0, n_invalid = 0, n_keyed = 0;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t it = 0; it < iters; ++it, i += stride) {
-    const bool have = i < m;
+    bool have = i < m;
     int32_t key = kKeyOutside;
     int64_t p = 0;
+    uint64_t e = kQEmpty;
+    if (have) e = qs.q2[i];
+    have = have && e != kQEmpty;
     if (have) {
-      const uint64_t e = qs.q2[i];
       const int b = qbox(e), img = qimg(e);
       p = qidx(e);
       const BoxGeom& g = bp.box[b];
@@ -695,8 +1061,11 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   }
 
   // workspace
-  const int64_t cap1 = std::max<int64_t>(1 << 20, total_img / 16);
-  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64);
+  // queue slots: expected undecided entries plus one partly used chunk per warp
+  const int64_t qwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
+                         4ll * c->num_sms * (256 / 32);
+  const int64_t cap1 = std::max<int64_t>(1 << 20, total_img / 16) + qwarps * kQChunk;
+  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64) + qwarps * kQChunk;
   Queues qs;
   qs.cap1 = cap1;
   qs.cap2 = cap2;
@@ -714,7 +1083,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   int grid = 0, smem = 0;
   if (plan.mode == kModeDense) {
     // every warp of every launch may leave one partly filled chunk
-    const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kFastThreads / 32) +
+    const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
                            2ll * 4 * c->num_sms * (256 / 32) + 64;
     o.dense_cap = total_img + nwarps * kChunk;
     o.dense = (uint32_t*)ws_get(c, kSlotDense, o.dense_cap * 4);
@@ -729,34 +1098,44 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     if (!(flags & UFC_BIN_ACCUMULATE))
       UFC_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nshell * npix * 4, c->stream));
   }
+  // shell lookup table over r^2: lut[i] = edges with lo2 <= i / scale
+  LutParam lp;
+  {
+    const double r2max = (double)st.hi2[nshell] * (1.0 + 1e-6) + 1e-30;
+    lp.scale = (float)(kLut / r2max);
+    int e = 0;
+    for (int i = 0; i < kLut; ++i) {
+      const double v = (double)i / (double)lp.scale;
+      while (e <= nshell && (double)st.lo2[e] <= v) ++e;
+      lp.v[i] = (uint16_t)e;
+    }
+  }
   // fast stage per box
+  const int tma_smem = kStages * kTChunk * 12 + 2 * kTChunk * 4 + (plan.mode == kModeDense ? smem : 0);
   for (int k = 0; k < nbox; ++k) {
     if (n[k] == 0) continue;
-    if (plan.mode == kModeDense) {
-      UFC_CUDA(c, cudaFuncSetAttribute(k_fast<kModeDense>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fast<kModeDense>, kFastThreads, smem);
-      grid = std::max(1, std::min(per_sm, 2)) * c->num_sms;
-      {
-        ProfScope ps_(c, "k_fast");
-        k_fast<kModeDense><<<grid, kFastThreads, smem, c->stream>>>(
-            xyz[k], n[k], k, bp.box[k], st, bd, nside, (int32_t)npix, o, qs);
-      }
-    } else if (plan.mode == kModeDirect) {
-      grid = 2 * c->num_sms;
-      {
-        ProfScope ps_(c, "k_fast");
-        k_fast<kModeDirect><<<grid, kFastThreads, 0, c->stream>>>(
-            xyz[k], n[k], k, bp.box[k], st, bd, nside, (int32_t)npix, o, qs);
-      }
+    const bool tma = (reinterpret_cast<uintptr_t>(xyz[k]) & 15) == 0;
+    ProfScope ps_(c, "k_fast");
+    if (tma) {
+#define UFC_LAUNCH_TMA(M)                                                                      \
+  UFC_CUDA(c, cudaFuncSetAttribute(k_fast_tma<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                   tma_smem));                                                  \
+  k_fast_tma<M><<<c->num_sms, kTThreads, tma_smem, c->stream>>>(xyz[k], n[k], k, bp.box[k], st, \
+                                                                 lp, bd, nside, (int32_t)npix, o, qs)
+      if (plan.mode == kModeDense) { UFC_LAUNCH_TMA(kModeDense); }
+      else if (plan.mode == kModeDirect) { UFC_LAUNCH_TMA(kModeDirect); }
+      else { UFC_LAUNCH_TMA(kModeKeys); }
+#undef UFC_LAUNCH_TMA
     } else {
-      grid = 2 * c->num_sms;
-      {
-        ProfScope ps_(c, "k_fast");
-        k_fast<kModeKeys><<<grid, kFastThreads, 0, c->stream>>>(
-            xyz[k], n[k], k, bp.box[k], st, bd, nside, (int32_t)npix, o, qs);
-      }
+      const int ssm = plan.mode == kModeDense ? smem : 0;
+#define UFC_LAUNCH_PLAIN(M)                                                                     \
+  UFC_CUDA(c, cudaFuncSetAttribute(k_fast<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm)); \
+  k_fast<M><<<(ssm > 0 ? 1 : 2) * c->num_sms, kFastThreads, ssm, c->stream>>>(                    \
+      xyz[k], n[k], k, bp.box[k], st, lp, bd, nside, (int32_t)npix, o, qs)
+      if (plan.mode == kModeDense) { UFC_LAUNCH_PLAIN(kModeDense); }
+      else if (plan.mode == kModeDirect) { UFC_LAUNCH_PLAIN(kModeDirect); }
+      else { UFC_LAUNCH_PLAIN(kModeKeys); }
+#undef UFC_LAUNCH_PLAIN
     }
     UFC_CUDA(c, cudaGetLastError());
   }
@@ -803,7 +1182,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   if (!off || !cur || !grouped || !b16 || !tiles) return UFC_ERR_ALLOC;
   unsigned long long* gcur = cur;
   unsigned long long* bcur = cur + ng;
-  unsigned long long* ntiles = &qs.cnt->pad_;
+  unsigned long long* ntiles = &qs.cnt->ntiles;
   {
     ProfScope ps_(c, "k_scan");
     k_scan<<<1, 1024, 0, c->stream>>>(o.hist, nb, off);

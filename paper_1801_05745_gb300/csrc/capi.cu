@@ -148,11 +148,12 @@ ufc_status ufc_reserve(ufc_ctx* c, int32_t nside, int32_t nshell, int64_t n_max)
   if (!c || nside < 1 || nshell < 1 || n_max < 0) return UFC_ERR_ARG;
   cudaSetDevice(c->device);
   const int64_t npix = 12ll * nside * nside;
-  const int64_t cap1 = std::max<int64_t>(1 << 20, n_max / 16);
-  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64);
+  const int64_t qwarps = 2ll * 2 * c->num_sms * 32 + 4ll * c->num_sms * 8;
+  const int64_t cap1 = std::max<int64_t>(1 << 20, n_max / 16) + qwarps * 256;
+  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64) + qwarps * 256;
   if (!ws_get(c, kSlotQueue1, cap1 * 8) || !ws_get(c, kSlotQueue2, cap2 * 8)) return UFC_ERR_ALLOC;
   if (nside >= 64 && npix * nshell * 4 > (32ll << 20)) {
-    const int64_t nwarps = 2ll * 2 * c->num_sms * 16 + 2ll * 4 * c->num_sms * 8 + 64;
+    const int64_t nwarps = 2ll * 2 * c->num_sms * 32 + 2ll * 4 * c->num_sms * 8 + 64;
     const int64_t cap = n_max + nwarps * 2048;
     const int64_t nb = nshell * (npix / 24576);
     if (!ws_get(c, kSlotDense, cap * 4) || !ws_get(c, kSlotGrouped, cap * 4) ||

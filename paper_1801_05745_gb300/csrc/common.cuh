@@ -73,7 +73,9 @@ struct BinCounters {
   unsigned long long q1;        // entries in queue 1
   unsigned long long q2;        // entries in queue 2
   unsigned long long dense;     // keys written by the compaction stage
-  unsigned long long pad_;
+  unsigned long long ntiles;    // tiles of the second scatter pass
+  unsigned long long timeouts;  // bounded device waits that ran out
+  unsigned long long range;     // adjoint inputs outside the fixed-point range
 };
 
 // Queue entry of an undecided particle image: box (4 bits), image (13 bits),

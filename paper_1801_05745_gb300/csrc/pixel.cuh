@@ -130,13 +130,97 @@ __device__ __forceinline__ int32_t key_exact(const ShellTable& st, int32_t lo,
 
 // ============================ fast stage (FP32) =============================
 
+// Exact FP32 helpers that avoid the conversion instructions (float->int,
+// round-to-integral), which GB300 executes on its narrow FP64 pipe.  Valid
+// for |w| < 2^22: adding 1.5 * 2^23 leaves round(w) in the low mantissa bits.
+constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr int32_t kMagicBits = 0x4B400000;     // bit pattern of kMagic
+
+// floor(w) as int and as float, |w| < 2^22.
+__device__ __forceinline__ int32_t floor_fast(float w, float& fl) {
+  const float r = __fadd_rn(w, kMagic);        // round to nearest integer
+  const float rf = __fsub_rn(r, kMagic);       // that integer, exactly
+  const bool up = rf > w;
+  fl = up ? __fsub_rn(rf, 1.0f) : rf;
+  return (__float_as_int(r) - kMagicBits) - (up ? 1 : 0);
+}
+// float(k) for |k| < 2^22.
+__device__ __forceinline__ float i2f_fast(int32_t k) {
+  return __fsub_rn(__int_as_float(kMagicBits + k), kMagic);
+}
+
 // Floor of w when w is farther than `band` from every integer, else marks
 // the decision open.
 __device__ __forceinline__ int32_t floor_certain(float w, float band, bool& open) {
-  float f = floorf(w);
-  float rem = w - f;   // exact for |w| < 2^23
-  open |= !(rem >= band) || !(rem < 1.0f - band);
-  return int32_t(f);
+  float f;
+  const int32_t k = floor_fast(w, f);
+  const float rem = __fsub_rn(w, f);           // exact for |w| < 2^22
+  open |= !(rem >= band) || !(rem < 1.0f - band) || !(fabsf(w) < 4194304.0f);
+  return k;
+}
+
+// Azimuth of the fast stage: t = base + sgn * a (exact-real identity of the
+// quadrant/octant cases of the FP64 procedure), a in [0, 1/2] quarter turns.
+struct Azim { float a, sa; int32_t base; bool sgn_pos; };
+
+__device__ __forceinline__ Azim azimuth_fast(float dx, float dy, const Bands& bd, bool& open) {
+  const float ax = fabsf(dx), ay = fabsf(dy);
+  open |= fmaxf(ax, ay) < bd.axy_min;
+  const bool sw = ay > ax;
+  const float q = sw ? __fdividef(ax, ay) : __fdividef(ay, ax);
+  Azim r;
+  r.a = atanf(q) * 0.636619772367581343f;      // quarter turns, [0, 1/2]
+  const bool xp = dx >= 0.0f, yp = dy >= 0.0f;
+  // (base, sgn): Q0 (0,+)|(1,-)  Q1 (2,-)|(1,+)  Q2 (2,+)|(3,-)  Q3 (4,-)|(3,+)
+  r.base = xp ? (yp ? (sw ? 1 : 0) : (sw ? 3 : 4)) : (yp ? (sw ? 1 : 2) : (sw ? 3 : 2));
+  r.sgn_pos = (xp == yp) != sw;
+  r.sa = r.sgn_pos ? r.a : -r.a;
+  return r;
+}
+
+// Equatorial-belt pixel (|z| certainly <= 2/3), or kKeyUndecided.
+__device__ __forceinline__ int32_t pixel_fast_eq(int32_t N, const Bands& bd, float dx, float dy,
+                                                 float z) {
+  bool open = false;
+  const Azim az = azimuth_fast(dx, dy, bd, open);
+  // floor(N(1/2 + t) -+ 0.75 N z) = I0 + floor(N sa (+1/2 if N = 1) -+ 0.75 N z)
+  const float fN = i2f_fast(N);
+  const float c = fmaf(fN, az.sa, N == 1 ? 0.5f : 0.0f);
+  const int32_t I0 = (N == 1) ? az.base : (N >> 1) * (2 * az.base + 1);
+  const float n75 = 0.75f * fN;
+  const int32_t jp = I0 + floor_certain(fmaf(-n75, z, c), bd.eq, open);
+  const int32_t jm = I0 + floor_certain(fmaf(n75, z, c), bd.eq, open);
+  const int32_t ir = N + 1 + jp - jm;
+  open |= ir < 1 || ir > 2 * N + 1;
+  const int32_t ks = 1 - (ir & 1);
+  const int32_t ip = ((jp + jm - N + ks + 1 + 8 * N) >> 1) & (4 * N - 1);
+  return open ? kKeyUndecided : 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
+}
+
+// Polar-cap pixel (|z| certainly > 2/3), or kKeyUndecided.
+__device__ __forceinline__ int32_t pixel_fast_cap(int32_t N, const Bands& bd, float dx, float dy,
+                                                  float dz, float r2, float rinv, float z) {
+  bool open = false;
+  const Azim az = azimuth_fast(dx, dy, bd, open);
+  const float s2 = fmaf(dx, dx, dy * dy);
+  const float r = r2 * rinv;
+  const float omz = __fdividef(s2, r * (r + fabsf(dz)));
+  const float o3 = 3.0f * omz;
+  float tmp = i2f_fast(N) * (o3 * rsqrtf(o3));
+  if (!(o3 > 0.0f)) { tmp = 0.0f; open = true; }
+  const float tp = az.sgn_pos ? az.a : 1.0f - az.a;
+  const int32_t jp = floor_certain(tp * tmp, bd.cap, open);
+  const int32_t jm = floor_certain((1.0f - tp) * tmp, bd.cap, open);
+  int32_t ir = jp + jm + 1;
+  open |= ir > N;
+  ir = ir > N ? N : ir;
+  const float fir = i2f_fast(ir);
+  const int32_t fl = floor_certain(az.sa * fir, bd.ip_per_ir * fir, open);
+  int32_t ip = az.base * ir + fl;              // in [-ir, 4.5 ir]
+  const int32_t m = 4 * ir;
+  ip = ip < 0 ? ip + m : (ip >= m ? ip - m : ip);
+  const int32_t pix = (z > 0.0f) ? 2 * ir * (ir - 1) + ip : 12 * N * N - 2 * ir * (ir + 1) + ip;
+  return open ? kKeyUndecided : pix;
 }
 
 // Pixel by the fast stage, or kKeyUndecided.  (dx,dy,dz) are the FP32
@@ -144,63 +228,12 @@ __device__ __forceinline__ int32_t floor_certain(float w, float band, bool& open
 // r2 = fmaf(dz,dz,fmaf(dy,dy,dx*dx)) > bands.r2_min.
 __device__ __forceinline__ int32_t pixel_fast(int32_t N, const Bands& bd, float dx,
                                               float dy, float dz, float r2) {
-  bool open = false;
-  float rinv = rsqrtf(r2);
-  float z = dz * rinv;
-  float za = fabsf(z);
-  bool eq = za <= bd.z_eq;
-  open |= !eq && !(za > bd.z_cap);
-  float ax = fabsf(dx), ay = fabsf(dy);
-  open |= fmaxf(ax, ay) < bd.axy_min;
-  bool sw = ay > ax;
-  float q = sw ? __fdividef(ax, ay) : __fdividef(ay, ax);
-  float a = atanf(q) * 0.636619772367581343f;   // quarter turns, [0, 1/2]
-  // t = base + sgn * a  (exact-real identity of the quadrant/octant cases)
-  int32_t base;
-  float sgn;
-  if (dx >= 0.0f) {
-    if (dy >= 0.0f) { base = sw ? 1 : 0; sgn = sw ? -1.0f : 1.0f; }
-    else            { base = sw ? 3 : 4; sgn = sw ? 1.0f : -1.0f; }
-  } else {
-    if (dy >= 0.0f) { base = sw ? 1 : 2; sgn = sw ? 1.0f : -1.0f; }
-    else            { base = sw ? 3 : 2; sgn = sw ? -1.0f : 1.0f; }
-  }
-  float sa = sgn * a;
-  int32_t pix;
-  if (eq) {
-    // floor(N(1/2 + t) -+ 0.75 N z) = I0 + floor(N sa (+1/2 if N = 1) -+ 0.75 N z)
-    float fN = float(N);
-    float c = fN * sa + (N == 1 ? 0.5f : 0.0f);
-    int32_t I0 = (N == 1) ? base : N * (2 * base + 1) / 2;
-    float n75 = 0.75f * fN;
-    int32_t jp = I0 + floor_certain(fmaf(-n75, z, c), bd.eq, open);
-    int32_t jm = I0 + floor_certain(fmaf(n75, z, c), bd.eq, open);
-    int32_t ir = N + 1 + jp - jm;
-    open |= ir < 1 || ir > 2 * N + 1;
-    int32_t ks = 1 - (ir & 1);
-    int32_t ip = ((jp + jm - N + ks + 1 + 8 * N) >> 1) & (4 * N - 1);
-    pix = 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
-  } else {
-    float s2 = fmaf(dx, dx, dy * dy);
-    float r = r2 * rinv;
-    float omz = __fdividef(s2, r * (r + fabsf(dz)));
-    float o3 = 3.0f * omz;
-    float tmp = float(N) * (o3 * rsqrtf(o3));
-    if (!(o3 > 0.0f)) { tmp = 0.0f; open = true; }
-    float tp = sgn > 0.0f ? a : 1.0f - a;
-    int32_t jp = floor_certain(tp * tmp, bd.cap, open);
-    int32_t jm = floor_certain((1.0f - tp) * tmp, bd.cap, open);
-    int32_t ir = jp + jm + 1;
-    open |= ir > N;
-    ir = ir > N ? N : ir;
-    float w3 = sa * float(ir);
-    int32_t fl = floor_certain(w3, bd.ip_per_ir * float(ir), open);
-    int32_t ip = base * ir + fl;
-    int32_t m = 4 * ir;
-    ip = ((ip % m) + m) % m;
-    pix = (z > 0.0f) ? 2 * ir * (ir - 1) + ip : 12 * N * N - 2 * ir * (ir + 1) + ip;
-  }
-  return open ? kKeyUndecided : pix;
+  const float rinv = rsqrtf(r2);
+  const float z = dz * rinv;
+  const float za = fabsf(z);
+  if (za <= bd.z_eq) return pixel_fast_eq(N, bd, dx, dy, z);
+  if (za > bd.z_cap) return pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
+  return kKeyUndecided;
 }
 
 // Shell of r2 within edges [lo, hi] by the fast stage: returns the shell, -1

@@ -74,6 +74,8 @@ struct Coef {
   float ch, cl;        // C as double-float
   int32_t nshell;
   int32_t npix;
+  int32_t nst;         // stages of the staged kernels
+  int32_t pad_;
 };
 
 // ------------------------------------------------- kappa + adjoint sums ---
@@ -91,50 +93,178 @@ constexpr int kKT = 256;   // threads (pixels) per tile
 struct AdjOut {
   double* part;   // [grid][4*nshell + 4]: S1, S2, T, N per shell, then P1, P2, P3, Q
   const float* g; // may be null
+  unsigned long long* range_flag;   // set when |e| or |g| exceeds 2^14
 };
 
-// Splits v (double-float) into two integers with v 2^s = hi + lo 2^-30 to
-// within 2^-31: hi = rint(v 2^s), lo = rint((v 2^s - hi) 2^30).
+// Exact FP32 helpers that avoid the conversion instructions (float->int,
+// round-to-integral), which GB300 executes on its narrow FP64 pipe.
+constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
+constexpr int32_t kMagicBits = 0x4B400000;
+// round(x) as int for |x| < 2^22, and the rounded value as float
+__device__ __forceinline__ int32_t round_fast(float x, float& xr) {
+  const float r = __fadd_rn(x, kMagic);
+  xr = __fsub_rn(r, kMagic);
+  return __float_as_int(r) - kMagicBits;
+}
+// 2^s as float for s in [-126, 127]
+__device__ __forceinline__ float pow2f(int s) { return __int_as_float((127 + s) << 23); }
+// floor(log2(x)) of a normal float x > 0
+__device__ __forceinline__ int ilog2f(float x) { return ((__float_as_int(x) >> 23) & 0xFF) - 127; }
+
+// Splits v (double-float, |v| 2^s < 2^22) into two integers with
+// v 2^s = hi + lo 2^-22 to within 2^-23: hi = round(v.h 2^s), lo the rounded
+// remainder (|remainder| <= 3/4, so |lo| < 2^22).
 __device__ __forceinline__ void quant2(f2 v, int s, int& hi, int& lo) {
-  const float a = ldexpf(v.h, s);
-  const float r = rintf(a);
-  const float rem = __fadd_rn(__fsub_rn(a, r), ldexpf(v.l, s));   // a - r is exact
-  hi = __float2int_rn(r);
-  lo = __float2int_rn(ldexpf(rem, 30));
+  const float sc = pow2f(s);
+  const float a = __fmul_rn(v.h, sc);
+  float ar;
+  hi = round_fast(a, ar);
+  const float rem = __fadd_rn(__fsub_rn(a, ar), __fmul_rn(v.l, sc));   // a - ar is exact
+  float dummy;
+  lo = round_fast(__fmul_rn(rem, 4194304.0f), dummy);                  // 2^22
 }
 
+// 128-bit two's-complement fixed-point accumulator (integer operations only).
+struct I128 { unsigned long long lo; long long hi; };
+// acc += v * 2^sh, sh in [-127, 62]; bits below 2^0 of the result are dropped.
+__device__ __forceinline__ void i128_add(I128& acc, long long v, int sh) {
+  unsigned long long lo;
+  long long hi;
+  if (sh >= 64) {
+    lo = 0ull;
+    hi = v << (sh - 64);
+  } else if (sh > 0) {
+    lo = (unsigned long long)v << sh;
+    hi = v >> (64 - sh);
+  } else if (sh == 0) {
+    lo = (unsigned long long)v;
+    hi = v < 0 ? -1ll : 0ll;
+  } else if (sh > -64) {
+    const long long t = v >> (-sh);
+    lo = (unsigned long long)t;
+    hi = t < 0 ? -1ll : 0ll;
+  } else {
+    lo = v < 0 ? ~0ull : 0ull;
+    hi = v < 0 ? -1ll : 0ll;
+  }
+  const unsigned long long nlo = acc.lo + lo;
+  acc.hi += hi + (nlo < acc.lo ? 1ll : 0ll);
+  acc.lo = nlo;
+}
+__device__ __forceinline__ double i128_to_d(I128 a, int frac_bits) {
+  return ldexp((double)a.hi * 18446744073709551616.0 + (double)a.lo, -frac_bits);
+}
+// Fractional bits of the adjoint sums S1 (e n), S2 (e^2 n), T (g n); with
+// |e|, |g| < 2^14 and |e|^2 < 2^28 every sum fits the 128-bit range.
+constexpr int kFrac1 = 72, kFrac2 = 56, kFrac3 = 72;
+struct AdjRow { I128 s[3]; long long n; long long pad_; };
+
+// --- bulk-copy helpers (TMA, 1-D) ---
+__device__ __forceinline__ uint32_t s_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(n));
+}
+__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(s_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+constexpr long long kPollLimit = 1ll << 28;
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+  for (long long i = 0; i < kPollLimit; ++i)
+    if (bar_try(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          s_u32(dst)),
+      "l"(src), "r"(bytes), "r"(s_u32(b))
+      : "memory");
+}
+
+constexpr int kKMaxStages = 4;
+
+// Tiles of kKT pixels x nshell counts arrive by nshell row copies of
+// kKT*4 bytes into a two-stage ring; counts must be 16-byte aligned and
+// 12 nside^2 is a multiple of 4, so every row copy is a multiple of 16 bytes.
 template <bool KAPPA, bool ADJ>
 __global__ void __launch_bounds__(kKT)
 k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
-        double* __restrict__ ksum_part, AdjOut ao) {
-  extern __shared__ int32_t cnt_s[];            // ADJ: [nshell][kKT], then 4 doubles/shell
+        double* __restrict__ ksum_part, AdjOut ao, unsigned long long* timeouts) {
+  extern __shared__ __align__(128) int32_t ring_s[];   // [kKStages][nshell][kKT], then 4 doubles/shell
   __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
   __shared__ double red[kKT / 32];
   __shared__ int q_s[6][kKT];                   // hi/lo of e, e^2, g
   __shared__ float fmax_s[4][kKT / 32];
+  __shared__ __align__(8) uint64_t kbar[kKMaxStages];
+  __shared__ int abort_s;
   const int S = cf.nshell;
   for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
-  double* rows = reinterpret_cast<double*>(cnt_s + S * kKT);
+  AdjRow* rows = reinterpret_cast<AdjRow*>(ring_s + cf.nst * S * kKT);
   if (ADJ)
-    for (int i = threadIdx.x; i < 4 * S; i += blockDim.x) rows[i] = 0.0;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) rows[i] = AdjRow{};
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < cf.nst; ++st) bar_init(&kbar[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_s = 0;
+  }
   f2 ks{0.f, 0.f}, p1{0.f, 0.f}, p2{0.f, 0.f}, p3{0.f, 0.f}, qg{0.f, 0.f};
   __syncthreads();
   const bool use_g = ADJ && ao.g != nullptr;
   const int ntile = (cf.npix + kKT - 1) / kKT;
-  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+  const int mine = ntile > (int)blockIdx.x ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  auto issue = [&](int k) {
+    const int tile = blockIdx.x + k * gridDim.x;
+    const int st = k % cf.nst;
+    const int cnt = min(kKT, cf.npix - tile * kKT);
+    const uint32_t rb = uint32_t(cnt) * 4u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    bar_expect(&kbar[st], rb * uint32_t(S));
+    for (int b = 0; b < S; ++b)
+      bulk_copy(ring_s + (st * S + b) * kKT, counts + (size_t)b * cf.npix + (size_t)tile * kKT, rb,
+                &kbar[st]);
+  };
+  int issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < mine && issued < cf.nst; ++issued) issue(issued);
+  int k = 0;
+  for (; k < mine; ++k) {
+    const int tile = blockIdx.x + k * gridDim.x;
+    const int st = k % cf.nst;
+    if (!bar_wait(&kbar[st], uint32_t((k / cf.nst) & 1))) abort_s = 1;
+    __syncthreads();
+    if (abort_s) break;
+    const int32_t* cnt_s = ring_s + st * S * kKT;
     const int p = tile * kKT + threadIdx.x;
     const bool have = p < cf.npix;
-    f2 acc{0.f, 0.f};
+    f2 acc{0.f, 0.f}, acc2{0.f, 0.f};
     int nmax = 0;
-#pragma unroll 4
-    for (int b = 0; b < S; ++b) {
-      int n = have ? __ldcs(counts + (size_t)b * cf.npix + p) : 0;
-      if (ADJ) {
-        cnt_s[b * kKT + threadIdx.x] = n;
-        nmax = max(nmax, n);
-      }
-      f2_mac(acc, ah_s[b], al_s[b], float(n));
+    int b = 0;
+    for (; b + 1 < S; b += 2) {                 // two chains for latency
+      const int n0 = have ? cnt_s[b * kKT + threadIdx.x] : 0;
+      const int n1 = have ? cnt_s[(b + 1) * kKT + threadIdx.x] : 0;
+      nmax = max(nmax, max(n0, n1));
+      f2_mac(acc, ah_s[b], al_s[b], float(n0));
+      f2_mac(acc2, ah_s[b + 1], al_s[b + 1], float(n1));
     }
+    if (b < S) {
+      const int n0 = have ? cnt_s[b * kKT + threadIdx.x] : 0;
+      nmax = max(nmax, n0);
+      f2_mac(acc, ah_s[b], al_s[b], float(n0));
+    }
+    acc = f2_add(f2_norm(acc.h, acc.l), f2_norm(acc2.h, acc2.l));
     // e = acc - C (unrounded), kappa = round(e)
     f2 e = f2_add(f2_norm(acc.h, acc.l), f2{-cf.ch, -cf.cl});
     if (KAPPA && have) {
@@ -176,9 +306,11 @@ k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
         M3 = fmaxf(M3, fmax_s[2][i]);
         MN = fmaxf(MN, fmax_s[3][i]);
       }
-      const int s1 = M1 > 0.f ? 28 - ilogbf(M1) : 0;
-      const int s2 = M2 > 0.f ? 28 - ilogbf(M2) : 0;
-      const int s3 = M3 > 0.f ? 28 - ilogbf(M3) : 0;
+      if (threadIdx.x == 0 && (M1 >= 16384.0f || M3 >= 16384.0f || M2 >= 268435456.0f))
+        atomicAdd(ao.range_flag, 1ull);
+      const int s1 = M1 > 0.f ? min(120, 21 - ilog2f(M1)) : 0;
+      const int s2 = M2 > 0.f ? min(120, 21 - ilog2f(M2)) : 0;
+      const int s3 = M3 > 0.f ? min(120, 21 - ilog2f(M3)) : 0;
       int h, l;
       quant2(e, s1, h, l);
       q_s[0][threadIdx.x] = h;
@@ -191,69 +323,56 @@ k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
       q_s[5][threadIdx.x] = l;
       __syncthreads();
       // phase 2: warp w owns shells w, w+8, ...; lane l pixels l, l+32, ...
-      // |q| < 2^30, counts < 2^24: an 8-term lane sum stays below 2^57 and
-      // the warp sum below 2^62.  Larger counts take the FP64 branch.
+      // |q| < 2^22 and counts < 2^31 keep the 8-term lane sums below 2^56
+      // and the warp sums below 2^61; the owner lane folds them into the
+      // block's 128-bit fixed-point sums with integer operations only.
       const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-      const double sc1 = ldexp(1.0, -s1), sc2 = ldexp(1.0, -s2), sc3 = ldexp(1.0, -s3);
-      const double lo30 = ldexp(1.0, -30);
-      if (MN < 16777216.0f) {
-        int qv[6][kKT / 32];
+      int qv[6][kKT / 32];
 #pragma unroll
-        for (int k = 0; k < kKT / 32; ++k)
+      for (int q = 0; q < kKT / 32; ++q)
 #pragma unroll
-          for (int j = 0; j < 6; ++j) qv[j][k] = q_s[j][ln + 32 * k];
-        for (int b = w; b < S; b += kKT / 32) {
-          long long a[6] = {0, 0, 0, 0, 0, 0};
-          int an = 0;
+        for (int j = 0; j < 6; ++j) qv[j][q] = q_s[j][ln + 32 * q];
+      for (int b = w; b < S; b += kKT / 32) {
+        long long a[6] = {0, 0, 0, 0, 0, 0};
+        long long an = 0;
 #pragma unroll
-          for (int k = 0; k < kKT / 32; ++k) {
-            const int n = cnt_s[b * kKT + ln + 32 * k];
-            an += n;
+        for (int q = 0; q < kKT / 32; ++q) {
+          const int n = cnt_s[b * kKT + ln + 32 * q];
+          an += n;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) a[j] += (long long)qv[j][k] * n;
-            if (use_g) {
-              a[4] += (long long)qv[4][k] * n;
-              a[5] += (long long)qv[5][k] * n;
-            }
-          }
-          long long an64 = an;
-#pragma unroll
-          for (int j = 0; j < 6; ++j) a[j] = warp_sum_ll(a[j]);
-          an64 = warp_sum_ll(an64);
-          if (ln == 0) {
-            double* row = rows + 4 * b;
-            row[0] += (double(a[0]) + double(a[1]) * lo30) * sc1;
-            row[1] += (double(a[2]) + double(a[3]) * lo30) * sc2;
-            row[2] += (double(a[4]) + double(a[5]) * lo30) * sc3;
-            row[3] += double(an64);
+          for (int j = 0; j < 4; ++j) a[j] += (long long)qv[j][q] * n;
+          if (use_g) {
+            a[4] += (long long)qv[4][q] * n;
+            a[5] += (long long)qv[5][q] * n;
           }
         }
-      } else {
-        for (int b = w; b < S; b += kKT / 32) {
-          double a1 = 0.0, a2 = 0.0, a3 = 0.0, an = 0.0;
-          for (int k = 0; k < kKT / 32; ++k) {
-            const int t = ln + 32 * k;
-            const double n = cnt_s[b * kKT + t];
-            a1 += n * (double(q_s[0][t]) + double(q_s[1][t]) * lo30);
-            a2 += n * (double(q_s[2][t]) + double(q_s[3][t]) * lo30);
-            a3 += n * (double(q_s[4][t]) + double(q_s[5][t]) * lo30);
-            an += n;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) a[j] = warp_sum_ll(a[j]);
+        an = warp_sum_ll(an);
+        if (ln == 0) {
+          AdjRow& row = rows[b];
+          i128_add(row.s[0], a[0], kFrac1 - s1);
+          i128_add(row.s[0], a[1], kFrac1 - s1 - 22);
+          i128_add(row.s[1], a[2], kFrac2 - s2);
+          i128_add(row.s[1], a[3], kFrac2 - s2 - 22);
+          if (use_g) {
+            i128_add(row.s[2], a[4], kFrac3 - s3);
+            i128_add(row.s[2], a[5], kFrac3 - s3 - 22);
           }
-          a1 = warp_sum_d(a1);
-          a2 = warp_sum_d(a2);
-          a3 = warp_sum_d(a3);
-          an = warp_sum_d(an);
-          if (ln == 0) {
-            double* row = rows + 4 * b;
-            row[0] += a1 * sc1;
-            row[1] += a2 * sc2;
-            row[2] += a3 * sc3;
-            row[3] += an;
-          }
+          row.n += an;
         }
       }
       __syncthreads();
     }
+    __syncthreads();                           // stage st fully consumed
+    if (threadIdx.x == 0 && issued < mine) issue(issued++);
+  }
+  if (abort_s) {
+    if (threadIdx.x == 0) {
+      atomicAdd(timeouts, 1ull);
+      for (int kk = k; kk < issued; ++kk) bar_wait(&kbar[kk % cf.nst], uint32_t((kk / cf.nst) & 1));
+    }
+    return;
   }
   if (KAPPA) {
     double t = block_sum_d<kKT>(f2_to_d(ks), red);
@@ -262,7 +381,12 @@ k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
   if (ADJ) {
     double* dst = ao.part + (size_t)blockIdx.x * (4 * S + 4);
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * S; i += blockDim.x) dst[i] = rows[i];
+    for (int b = threadIdx.x; b < S; b += blockDim.x) {
+      dst[4 * b + 0] = i128_to_d(rows[b].s[0], kFrac1);
+      dst[4 * b + 1] = i128_to_d(rows[b].s[1], kFrac2);
+      dst[4 * b + 2] = i128_to_d(rows[b].s[2], kFrac3);
+      dst[4 * b + 3] = (double)rows[b].n;
+    }
     double v1 = block_sum_d<kKT>(f2_to_d(p1), red);
     if (threadIdx.x == 0) dst[4 * S + 0] = v1;
     double v2 = block_sum_d<kKT>(f2_to_d(p2), red);
@@ -272,6 +396,31 @@ k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
     double v4 = block_sum_d<kKT>(f2_to_d(qg), red);
     if (threadIdx.x == 0) dst[4 * S + 3] = v4;
   }
+}
+
+// Forward pass without staging, for maps with more shells than the staged
+// tile holds (nshell > 96).
+__global__ void __launch_bounds__(kKT)
+k_kappa_plain(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
+              double* __restrict__ ksum_part) {
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ double red[kKT / 32];
+  const int S = cf.nshell;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+  __syncthreads();
+  f2 ks{0.f, 0.f};
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < cf.npix; p += gridDim.x * blockDim.x) {
+    f2 acc{0.f, 0.f};
+#pragma unroll 8
+    for (int b = 0; b < S; ++b)
+      f2_mac(acc, ah_s[b], al_s[b], float(__ldcs(counts + (size_t)b * cf.npix + p)));
+    f2 e = f2_add(f2_norm(acc.h, acc.l), f2{-cf.ch, -cf.cl});
+    const float kf = __fadd_rn(e.h, e.l);
+    kappa[p] = kf;
+    ks = f2_add(ks, f2{kf, 0.f});
+  }
+  const double t = block_sum_d<kKT>(f2_to_d(ks), red);
+  if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
 }
 
 // ------------------------------------------------ moments + PDF pass -----
@@ -324,13 +473,14 @@ k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ 
     else if (under) slot = pp.nbins;
     else if (over) slot = pp.nbins + 1;
     else {
-      float x = (k - pp.lo_f) * pp.scale_f;
-      float f = floorf(x);
-      float rem = x - f;
-      float band = pp.band_rel * (fabsf(x) + 1.0f);
-      int b;
-      if (rem >= band && rem < 1.0f - band) b = (int)f;
-      else b = (int)floor(__dmul_rn(__dsub_rn((double)k, pp.lo), pp.scale));
+      const float x = (k - pp.lo_f) * pp.scale_f;   // in [-1, nbins + 1] up to rounding
+      float xr;
+      int b = round_fast(x, xr);
+      if (xr > x) { b -= 1; xr -= 1.0f; }          // floor
+      const float rem = x - xr;
+      const float band = pp.band_rel * (fabsf(x) + 1.0f);
+      if (!(rem >= band && rem < 1.0f - band))
+        b = (int)floor(__dmul_rn(__dsub_rn((double)k, pp.lo), pp.scale));
       b = b >= pp.nbins ? pp.nbins - 1 : (b < 0 ? 0 : b);
       slot = b;
     }
@@ -450,8 +600,10 @@ k_welford_final(const double* __restrict__ st, int d, int ddof, double* __restri
 
 // ============================================================== host =====
 
+static int kappa_stages(int S);
 static void make_coef(const double* A, double C, int S, int npix, Coef& cf) {
   std::memset(&cf, 0, sizeof cf);
+  cf.nst = kappa_stages(S);
   for (int b = 0; b < S; ++b) {
     cf.ah[b] = (float)A[b];
     cf.al[b] = (float)(A[b] - (double)cf.ah[b]);
@@ -477,9 +629,19 @@ static ufc_status check_kappa_args(ufc_ctx* c, const int32_t* counts, int S, int
   return UFC_OK;
 }
 
+constexpr int kStagedMaxShells = 96;
+
 static int kappa_grid(ufc_ctx* c, int npix) {
   const int ntile = (npix + kKT - 1) / kKT;
-  return std::max(1, std::min(ntile, 8 * c->num_sms));
+  return std::max(1, std::min(ntile, c->num_sms));
+}
+// Stages that fit 200 KB of shared memory (at most 4).
+static int kappa_stages(int S) { return std::max(2, std::min(kKMaxStages, (200 * 1024) / (S * kKT * 4))); }
+static size_t kappa_smem(int S, bool adj) {
+  return (size_t)kappa_stages(S) * S * kKT * 4 + (adj ? (size_t)S * sizeof(AdjRow) : 0);
+}
+static unsigned long long* timeout_counter(ufc_ctx* c) {
+  return &reinterpret_cast<BinCounters*>(c->counters)->timeouts;
 }
 
 ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
@@ -499,7 +661,10 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
   }
   Coef cf;
   make_coef(A, C, S, npix, cf);
-  const int grid = kappa_grid(c, npix);
+  if (reinterpret_cast<uintptr_t>(counts) & 15)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
+  const bool staged = S <= kStagedMaxShells;
+  const int grid = staged ? kappa_grid(c, npix) : 8 * c->num_sms;
   const int mgrid = 2 * c->num_sms;
   double* ksum = (double*)ws_get(c, kSlotPartials, (size_t)(grid + 3 * mgrid) * 8);
   if (!ksum) return UFC_ERR_ALLOC;
@@ -510,9 +675,16 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
     if (!kmap) return UFC_ERR_ALLOC;
   }
   if (!kmap) return UFC_OK;   // nothing requested
-  {
+  if (staged) {
+    const size_t sm = kappa_smem(S, false);
+    UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     ProfScope ps_(c, "k_kappa");
-    k_kappa<true, false><<<grid, kKT, 0, c->stream>>>(counts, cf, kmap, ksum, AdjOut{nullptr, nullptr});
+    k_kappa<true, false><<<grid, kKT, sm, c->stream>>>(counts, cf, kmap, ksum,
+                                                      AdjOut{nullptr, nullptr, nullptr}, timeout_counter(c));
+  } else {
+    ProfScope ps_(c, "k_kappa");
+    k_kappa_plain<<<grid, kKT, 0, c->stream>>>(counts, cf, kmap, ksum);
   }
   UFC_CUDA(c, cudaGetLastError());
   if (!want_stats) return UFC_OK;
@@ -561,22 +733,31 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
   const int npix = 12 * nside * nside;
   Coef cf;
   make_coef(A, C, S, npix, cf);
+  if (reinterpret_cast<uintptr_t>(counts) & 15)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
   const int grid = kappa_grid(c, npix);
   const size_t prow = 4 * S + 4;
   double* part = (double*)ws_get(c, kSlotPartials, (size_t)grid * prow * 8);
   if (!part) return UFC_ERR_ALLOC;
-  const int smem = S * kKT * 4 + 4 * S * 8;
+  const size_t smem = kappa_smem(S, true);
   UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<false, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BinCounters* bc = reinterpret_cast<BinCounters*>(c->counters);
+  UFC_CUDA(c, cudaMemsetAsync(&bc->range, 0, sizeof(unsigned long long), c->stream));
   {
-    ProfScope ps_(c, "k_kappa");
+    ProfScope ps_(c, "k_kappa_adjoint");
     k_kappa<false, true><<<grid, kKT, smem, c->stream>>>(counts, cf, nullptr, nullptr,
-                                                        AdjOut{part, g});
+                                                        AdjOut{part, g, &bc->range}, timeout_counter(c));
   }
   UFC_CUDA(c, cudaGetLastError());
   std::vector<double> hp((size_t)grid * prow);
+  unsigned long long range_hits = 0;
   UFC_CUDA(c, cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  UFC_CUDA(c, cudaMemcpyAsync(&range_hits, &bc->range, 8, cudaMemcpyDeviceToHost, c->stream));
   UFC_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (range_hits)
+    return set_err(c, UFC_ERR_UNSUPPORTED,
+                   "adjoint needs |kappa_p| < 2^14 and |g_p| < 2^14 (fixed-point range)");
   std::vector<double> S1(S, 0.0), S2(S, 0.0), T(S, 0.0), Nb(S, 0.0);
   double P1 = 0, P2 = 0, P3 = 0, Q = 0;
   for (int i = 0; i < grid; ++i) {
