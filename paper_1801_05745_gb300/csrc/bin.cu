@@ -413,8 +413,11 @@ __device__ __forceinline__ void fast_emit(bool have, int32_t key, uint32_t dkey,
   fc.n_keyed += ok;
 }
 
-// Warp-aggregated append to a shared-memory list.
-__device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list, int* count) {
+// Warp-aggregated append to a shared-memory list of `cap` entries.  A round
+// appends at most one entry per particle of the chunk, so idx < cap always
+// holds; the check keeps any violation inside the list.
+__device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list, int* count,
+                                          int cap) {
   const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
   if (m == 0) return;
   const int lane = threadIdx.x & 31;
@@ -422,7 +425,8 @@ __device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list,
   int base = 0;
   if (lane == leader) base = atomicAdd(count, __popc(m));
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (want) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+  const int idx = base + __popc(m & ((1u << lane) - 1u));
+  if (want && idx < cap) list[idx] = v;
 }
 
 template <int MODE>
@@ -436,7 +440,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
   uint32_t* hist_s = cap_list + kTChunk;
   __shared__ FastShared fs;
   __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ int abort_s, neq_s, ncap_s;
+  __shared__ int abort_s, neq_s[2], ncap_s[2];
   fast_init_shared(fs, bg, st, lp.v);
   if (MODE == kModeDense && o.smem_hist)
     for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) hist_s[i] = 0;
@@ -444,8 +448,8 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
-    neq_s = 0;
-    ncap_s = 0;
+    neq_s[0] = neq_s[1] = 0;
+    ncap_s[0] = ncap_s[1] = 0;
   }
   __syncthreads();
 
@@ -471,6 +475,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
     for (; issued < mine && issued < kStages; ++issued) issue(issued);
 
   FastCtx fc{{-1, 0}, {-1, 0}, 0, 0};
+  uint32_t rnd = 0;                            // list rounds so far (selects the counters)
   int64_t k = 0;
   for (; k < mine; ++k) {
     const int64_t c = blockIdx.x + k * gridDim.x;
@@ -493,20 +498,27 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
         zc = __ldg(xyz + 3 * p + 2);
       }
     };
-    // ---- phase A: radius, shell and zone; in-cone images go to the lists
+    // One round per periodic image: phase A classifies radius, shell and zone
+    // of every particle of the chunk and lists the in-cone images (at most
+    // one entry per particle per round); phase B computes their pixels over
+    // the dense belt and cap lists.  List counters alternate between rounds.
+    int ii = 0, jj = 0, kk = 0;
 #pragma unroll 1
-    for (int j = threadIdx.x; j < kTChunk; j += kTThreads) {
-      const int64_t p = base + j;
-      const bool have = p < n;
-      float x = 0.f, y = 0.f, zc = 0.f;
-      if (have) load(j, x, y, zc);
-      const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
-      if (have && !finite) ++fc.n_invalid;
-      int ii = 0, jj = 0, kk = 0;
-      for (int img = 0; img < bg.nimg; ++img) {
-        if (img) {
-          if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
-        }
+    for (int img = 0; img < bg.nimg; ++img) {
+      if (img) {
+        if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
+      }
+      int* neq_c = &neq_s[rnd & 1];
+      int* ncap_c = &ncap_s[rnd & 1];
+      // ---- phase A
+#pragma unroll 1
+      for (int j = threadIdx.x; j < kTChunk; j += kTThreads) {
+        const int64_t p = base + j;
+        const bool have = p < n;
+        float x = 0.f, y = 0.f, zc = 0.f;
+        if (have) load(j, x, y, zc);
+        const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
+        if (img == 0 && have && !finite) ++fc.n_invalid;
         int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap
         int32_t b = -1;
         if (finite) {
@@ -525,59 +537,60 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
             }
           }
         }
-        const uint32_t entry = uint32_t(j) | (uint32_t(b) << 11) | (uint32_t(img) << 19);
-        list_push(cls == 2, entry, eq_list, &neq_s);
-        list_push(cls == 3, entry, cap_list, &ncap_s);
+        const uint32_t entry = uint32_t(j) | (uint32_t(b & 255) << 11);
+        list_push(cls == 2, entry, eq_list, neq_c, kTChunk);
+        list_push(cls == 3, entry, cap_list, ncap_c, kTChunk);
         // outside, invalid and undecided images are final here
         const int32_t key = !finite ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
         const bool here = have && (cls < 2);
         fast_emit<MODE>(here, key, 0u, box_id, img, p, bg, st, N, npix, o, qs, hist_s, fc, x, y,
                         zc, ii, jj, kk);
       }
-    }
-    __syncthreads();
-    // ---- phase B: pixels of the dense belt and cap lists
-    const int neq = neq_s, ncap = ncap_s;
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-      const int cnt = pass == 0 ? neq : ncap;
-      const uint32_t* list = pass == 0 ? eq_list : cap_list;
-      const int rounds = (cnt + kTThreads - 1) / kTThreads;
-#pragma unroll 1
-      for (int rr = 0; rr < rounds; ++rr) {
-        const int i = rr * kTThreads + threadIdx.x;
-        const bool have = i < cnt;
-        const uint32_t e = have ? list[i] : 0u;
-        const int j = int(e & 2047u), b = int((e >> 11) & 255u), img = int(e >> 19);
-        const int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
-        float x = 0.f, y = 0.f, zc = 0.f;
-        if (have) load(j, x, y, zc);
-        const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
-        const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
-        const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        const float rinv = rsqrtf(r2);
-        const float z = dz * rinv;
-        int32_t pix = kKeyUndecided;
-        if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
-                                  : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
-        const int32_t key = pix == kKeyUndecided ? kKeyUndecided : b * npix + pix;
-        uint32_t dkey = 0u;
-        if (MODE == kModeDense && pix != kKeyUndecided) {
-          const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
-          dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
-                 (uint32_t(pix) - blk * uint32_t(kBlockPix));
-        }
-        fast_emit<MODE>(have, key, dkey, box_id, img, base + j, bg, st, N, npix, o, qs, hist_s, fc,
-                        x, y, zc, ii, jj, kk);
+      __syncthreads();
+      if (threadIdx.x == 0) {                  // counters of the next round
+        neq_s[(rnd + 1) & 1] = 0;
+        ncap_s[(rnd + 1) & 1] = 0;
       }
+      // ---- phase B
+      const int neq = min(*neq_c, kTChunk), ncap = min(*ncap_c, kTChunk);
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        const int cnt = pass == 0 ? neq : ncap;
+        const uint32_t* list = pass == 0 ? eq_list : cap_list;
+        const int rounds = (cnt + kTThreads - 1) / kTThreads;
+#pragma unroll 1
+        for (int rr = 0; rr < rounds; ++rr) {
+          const int i = rr * kTThreads + threadIdx.x;
+          const bool have = i < cnt;
+          const uint32_t e = have ? list[i] : 0u;
+          const int j = int(e & 2047u), b = int((e >> 11) & 255u);
+          float x = 0.f, y = 0.f, zc = 0.f;
+          if (have) load(j, x, y, zc);
+          const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
+          const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
+          const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          const float rinv = rsqrtf(r2);
+          const float z = dz * rinv;
+          int32_t pix = kKeyUndecided;
+          if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
+                                    : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
+          const int32_t key = pix == kKeyUndecided ? kKeyUndecided : b * npix + pix;
+          uint32_t dkey = 0u;
+          if (MODE == kModeDense && pix != kKeyUndecided) {
+            const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
+            dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
+                   (uint32_t(pix) - blk * uint32_t(kBlockPix));
+          }
+          fast_emit<MODE>(have, key, dkey, box_id, img, base + j, bg, st, N, npix, o, qs, hist_s,
+                          fc, x, y, zc, ii, jj, kk);
+        }
+      }
+      __syncthreads();                         // lists consumed before the next round
+      ++rnd;
     }
-    __syncthreads();                           // buffer s and the lists fully consumed
-    if (threadIdx.x == 0) {
-      neq_s = 0;
-      ncap_s = 0;
-      if (issued < mine) issue(issued++);
-    }
+    // buffer s and the lists are consumed (barrier at the end of the last round)
+    if (threadIdx.x == 0 && issued < mine) issue(issued++);
   }
   if (abort_s) {
     // a wait ran out: wait (bounded) for the copies still in flight, report
@@ -960,6 +973,8 @@ static ufc_status make_table(ufc_ctx* c, const double* chi, int nshell, ShellTab
     if (e > 0 && !(chi[e] > chi[e - 1]))
       return set_err(c, UFC_ERR_ARG, "chi_edges must increase (edge %d)", e);
     st.chi64[e] = chi[e];
+    st.chih[e] = (float)chi[e];
+    st.chil[e] = (float)(chi[e] - (double)st.chih[e]);
     double c2 = chi[e] * chi[e];
     st.lo2[e] = f_down(c2 * (1.0 - 14.0 * u) * (1.0 - 1e-12));
     st.hi2[e] = f_up(c2 * (1.0 + 14.0 * u) * (1.0 + 1e-12));

@@ -37,6 +37,8 @@ struct BoxGeom {
 // hi2[e] certainly at or above it.
 struct ShellTable {
   double chi64[kMaxShells + 1];
+  float chih[kMaxShells + 1];   // chi64 as double-float (hi + lo)
+  float chil[kMaxShells + 1];
   float lo2[kMaxShells + 1];
   float hi2[kMaxShells + 1];
   int32_t nshell;

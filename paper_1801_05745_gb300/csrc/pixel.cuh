@@ -307,10 +307,13 @@ __device__ __forceinline__ df df_sqrt(df x) {
   float c = __fdiv_rn(e.h, __fmul_rn(2.0f, s));
   return df_add({s, 0.0f}, {c, 0.0f});
 }
-__device__ __forceinline__ df df_from_double(double v) {
-  float h = __double2float_rn(v);
-  return {h, __double2float_rn(v - double(h))};
+// Double-float constants folded at compile time (no conversion at run time).
+struct dfc { float h, l; };
+__host__ __device__ constexpr dfc make_dfc(double v) {
+  return dfc{(float)v, (float)(v - (double)(float)v)};
 }
+__device__ __forceinline__ df to_df(dfc c) { return {c.h, c.l}; }
+
 
 // atan(u) in quarter turns for u in [0,1] by the same two half-angle steps
 // and a 9-term Maclaurin sum (w < tan(pi/16): truncation below 2^-40).
@@ -320,26 +323,31 @@ __device__ __forceinline__ df atanq_df(df u) {
   df v = df_div(u, df_add(one, df_sqrt(df_add(one, df_mul(u, u)))));
   df w = df_div(v, df_add(one, df_sqrt(df_add(one, df_mul(v, v)))));
   df s = df_mul(w, w);
-  df p = df_from_double(1.0 / 17.0);
-  p = df_add(df_mul(p, s), df_from_double(-1.0 / 15.0));
-  p = df_add(df_mul(p, s), df_from_double(1.0 / 13.0));
-  p = df_add(df_mul(p, s), df_from_double(-1.0 / 11.0));
-  p = df_add(df_mul(p, s), df_from_double(1.0 / 9.0));
-  p = df_add(df_mul(p, s), df_from_double(-1.0 / 7.0));
-  p = df_add(df_mul(p, s), df_from_double(1.0 / 5.0));
-  p = df_add(df_mul(p, s), df_from_double(-1.0 / 3.0));
+  constexpr dfc c17 = make_dfc(1.0 / 17.0), c15 = make_dfc(-1.0 / 15.0),
+                c13 = make_dfc(1.0 / 13.0), c11 = make_dfc(-1.0 / 11.0), c9 = make_dfc(1.0 / 9.0),
+                c7 = make_dfc(-1.0 / 7.0), c5 = make_dfc(1.0 / 5.0), c3 = make_dfc(-1.0 / 3.0);
+  df p = to_df(c17);
+  p = df_add(df_mul(p, s), to_df(c15));
+  p = df_add(df_mul(p, s), to_df(c13));
+  p = df_add(df_mul(p, s), to_df(c11));
+  p = df_add(df_mul(p, s), to_df(c9));
+  p = df_add(df_mul(p, s), to_df(c7));
+  p = df_add(df_mul(p, s), to_df(c5));
+  p = df_add(df_mul(p, s), to_df(c3));
   p = df_add(df_mul(p, s), one);
-  return df_mul(df_mul(w, p), df_from_double(0x1.45f306dc9c883p+1));
+  constexpr dfc k8pi = make_dfc(0x1.45f306dc9c883p+1);
+  return df_mul(df_mul(w, p), to_df(k8pi));
 }
 
 // Floor of v when v is farther than band from every integer.
 __device__ __forceinline__ int32_t floor_df_certain(df v, float band, bool& open) {
-  float f = floorf(v.h);
+  float f;
+  int32_t k = floor_fast(v.h, f);
   float rem = __fadd_rn(__fsub_rn(v.h, f), v.l);
-  if (rem < 0.0f) { f -= 1.0f; rem += 1.0f; }
-  if (rem >= 1.0f) { f += 1.0f; rem -= 1.0f; }
-  open |= !(rem >= band) || !(rem < 1.0f - band);
-  return int32_t(f);
+  if (rem < 0.0f) { k -= 1; rem += 1.0f; }
+  if (rem >= 1.0f) { k += 1; rem -= 1.0f; }
+  open |= !(rem >= band) || !(rem < 1.0f - band) || !(fabsf(v.h) < 4194304.0f);
+  return k;
 }
 
 // Relative band of the refine stage: every refined quantity is within
@@ -364,7 +372,7 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
   // shell: compare r with the FP64 edges (linear scan; this stage is rare)
   int32_t b = -1;
   for (int32_t e = lo; e <= hi; ++e) {
-    df c = df_from_double(st.chi64[e]);
+    df c = {st.chih[e], st.chil[e]};
     df dd = df_sub(r, c);
     float tol = 4.0f * kRefineRel * r.h;
     if (fabsf(dd.h) <= tol) return kKeyUndecided;
@@ -374,7 +382,8 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
   bool open = false;
   df z = df_div(dz, r);
   df zabs = (z.h < 0.0f) ? df_neg(z) : z;
-  df zd = df_sub(zabs, df_from_double(2.0 / 3.0));   // |z| - 2/3
+  constexpr dfc k23 = make_dfc(2.0 / 3.0);
+  df zd = df_sub(zabs, to_df(k23));                  // |z| - 2/3
   if (fabsf(zd.h) <= 4.0f * kRefineRel) return kKeyUndecided;
   bool eq = zd.h < 0.0f;
   float ax = fabsf(dx.h), ay = fabsf(dy.h);
@@ -394,7 +403,7 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
     else              { base = sw ? 3 : 2; sgn = sw ? -1.0f : 1.0f; }
   }
   df sa = (sgn > 0.0f) ? a : df_neg(a);
-  const float fN = float(N);
+  const float fN = i2f_fast(N);
   int32_t pix;
   if (eq) {
     df c = df_mulf(sa, fN);
@@ -420,7 +429,7 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
     int32_t ir = jp + jm + 1;
     open |= ir > N;
     ir = ir > N ? N : ir;
-    int32_t fl = floor_df_certain(df_mulf(sa, float(ir)), kRefineRel * 8.0f * float(ir + 1), open);
+    int32_t fl = floor_df_certain(df_mulf(sa, i2f_fast(ir)), kRefineRel * 8.0f * i2f_fast(ir + 1), open);
     int32_t ip = base * ir + fl;
     int32_t m = 4 * ir;
     ip = ((ip % m) + m) % m;

@@ -335,9 +335,11 @@ k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
       for (int b = w; b < S; b += kKT / 32) {
         long long a[6] = {0, 0, 0, 0, 0, 0};
         long long an = 0;
+        const int valid = cf.npix - tile * kKT;     // pixels of this tile (last tile may be short)
 #pragma unroll
         for (int q = 0; q < kKT / 32; ++q) {
-          const int n = cnt_s[b * kKT + ln + 32 * q];
+          const int t = ln + 32 * q;
+          const int n = t < valid ? cnt_s[b * kKT + t] : 0;
           an += n;
 #pragma unroll
           for (int j = 0; j < 4; ++j) a[j] += (long long)qv[j][q] * n;
