@@ -181,6 +181,29 @@ ufc_status ufc_kappa_stats(ufc_ctx *ctx, const int32_t *counts_dev,
                            int32_t nbins, float *kappa_dev, double *moments_dev,
                            int64_t *pdf_dev);
 
+/* Same results as ufc_kappa_stats, but the call allocates no device memory:
+ * it is meant for callers that cannot call cudaMalloc, for example an
+ * application whose device memory is owned by its own allocator (a caching
+ * allocator or a fixed arena carved out at start-up), or a pipeline that must
+ * not allocate once it runs because cudaMalloc may block and synchronise the
+ * device.  The paper has no counterpart; this is a property of the library.
+ *  - The caller passes every input and output: kappa_dev, moments_dev and
+ *    pdf_dev are all required (none may be NULL).
+ *  - Scratch (per-block partial sums) lives in one fixed device array of
+ *    4096 doubles (32 KB) that every GPU loading the library holds until the
+ *    process exits.  A launch that would need more returns UFC_ERR_CAPACITY.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture on the device.
+ *  - All calls on a device share the array, which keeps the last call's
+ *    contents: calls that overlap on the GPU (different streams or contexts)
+ *    race on it.  Serialise them.  pdf_dev is cleared by the call itself. */
+ufc_status ufc_kappa_stats_noalloc(ufc_ctx *ctx, const int32_t *counts_dev,
+                                   int32_t nshell, int32_t nside, const double *A,
+                                   double C, double pdf_lo, double pdf_hi,
+                                   int32_t nbins, float *kappa_dev,
+                                   double *moments_dev, int64_t *pdf_dev);
+
 /* ---- adjoint --------------------------------------------------------------- */
 
 /* Gradient of L = w_var var(kappa) + w_skew skew(kappa) + sum_p g_p kappa_p

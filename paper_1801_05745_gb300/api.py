@@ -88,6 +88,7 @@ _SIGS = {
     "ufc_welford_merge": [P, P, P, I32],
     "ufc_welford_finalize": [P, P, I32, I32, P, P, P],
     "ufc_stats_vector": [P, P, P, I32, P],
+    "ufc_kappa_stats_noalloc": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_profile_enable": [P, I32],
     "ufc_profile_read": [P, I32, P, P, P, P],
 }

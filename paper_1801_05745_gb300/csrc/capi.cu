@@ -22,6 +22,9 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
                               double* grad, double* G, double* H);
 ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, double* st);
 ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins, double* v);
+ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                   const double* A, double C, double lo, double hi, int nbins,
+                                   float* kappa, double* moments, int64_t* pdf);
 ufc_status run_welford_merge(ufc_ctx* c, double* a, const double* b, int d);
 ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, double* mean,
                                 double* cov, double* corr);
@@ -301,6 +304,20 @@ ufc_status ufc_kappa_stats(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell
   cudaSetDevice(c->device);
   return run_kappa_stats(c, counts_dev, nshell, nside, A, C, pdf_lo, pdf_hi, nbins, kappa_dev,
                          moments_dev, pdf_dev);
+}
+
+ufc_status ufc_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell,
+                                   int32_t nside, const double* A, double C, double pdf_lo,
+                                   double pdf_hi, int32_t nbins, float* kappa_dev,
+                                   double* moments_dev, int64_t* pdf_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, UFC_ERR_CUDA, "cudaSetDevice(%d) failed", c->device);
+  }
+  return run_kappa_stats_noalloc(c, counts_dev, nshell, nside, A, C, pdf_lo, pdf_hi, nbins,
+                                 kappa_dev, moments_dev, pdf_dev);
 }
 
 ufc_status ufc_kappa_backward(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell,

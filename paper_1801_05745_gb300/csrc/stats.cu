@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -802,6 +803,96 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
   if (G)
     for (int b = 0; b < S; ++b) G[b] = Gb[b];
   if (H) *H = Hs;
+  return UFC_OK;
+}
+
+// ---- variant of ufc_kappa_stats that allocates nothing -------------------
+// Its per-block partial sums live in this file-scope device array instead of
+// the context workspace.  Every GPU that loads the library holds the array
+// (kNoAllocScratch doubles = 32 KB) until the process exits; all calls on a
+// device share it, so calls that overlap on the GPU race on it.
+constexpr int kNoAllocScratch = 4096;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current) the first time the variant runs there.
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_ptr[64] = {};
+
+static ufc_status noalloc_scratch(ufc_ctx* c, double** out) {
+  if (c->device < 0 || c->device >= 64)
+    return set_err(c, UFC_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[c->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_err(c, UFC_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                     cudaGetErrorString(e));
+    g_noalloc_ptr[c->device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[c->device];
+  return UFC_OK;
+}
+
+ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                   const double* A, double C, double lo, double hi, int nbins,
+                                   float* kappa, double* moments, int64_t* pdf) {
+  ufc_status s = check_kappa_args(c, counts, S, nside, A, C);
+  if (s) return s;
+  if (!kappa || !moments || !pdf)
+    return set_err(c, UFC_ERR_ARG, "the no-allocation variant needs kappa_dev, moments_dev and pdf_dev");
+  if (nbins < 1 || nbins > kMaxBins)
+    return set_err(c, UFC_ERR_ARG, "nbins must be in [1,%d]", kMaxBins);
+  if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+    return set_err(c, UFC_ERR_ARG, "PDF range needs finite lo < hi");
+  if (reinterpret_cast<uintptr_t>(counts) & 15)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
+  const int npix = 12 * nside * nside;
+  const bool staged = S <= kStagedMaxShells;
+  const int grid = staged ? kappa_grid(c, npix) : 8 * c->num_sms;
+  const int mgrid = 2 * c->num_sms;
+  if (grid + 3 * mgrid > kNoAllocScratch)
+    return set_err(c, UFC_ERR_CAPACITY,
+                   "scratch needs %d doubles, the fixed array holds %d", grid + 3 * mgrid,
+                   kNoAllocScratch);
+  double* ksum = nullptr;
+  s = noalloc_scratch(c, &ksum);
+  if (s) return s;
+  double* mpart = ksum + grid;   // every slot is written before it is read
+  Coef cf;
+  make_coef(A, C, S, npix, cf);
+  if (staged) {
+    const size_t sm = kappa_smem(S, false);
+    UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_kappa<true, false><<<grid, kKT, sm, c->stream>>>(counts, cf, kappa, ksum,
+                                                      AdjOut{nullptr, nullptr, nullptr},
+                                                      timeout_counter(c));
+  } else {
+    k_kappa_plain<<<grid, kKT, 0, c->stream>>>(counts, cf, kappa, ksum);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  PdfParam pp;
+  pp.lo = lo;
+  pp.hi = hi;
+  pp.scale = (double)nbins / (hi - lo);
+  pp.lo_f = (float)lo;
+  pp.scale_f = (float)pp.scale;
+  pp.nbins = nbins;
+  pp.band_rel = std::fabs(lo) * pp.scale < 16.0 ? std::ldexp(1.0f, -16) : 2.0f;
+  auto fdn = [](double v) { float f = (float)v; return (double)f > v ? nextafterf(f, -INFINITY) : f; };
+  auto fup = [](double v) { float f = (float)v; return (double)f < v ? nextafterf(f, INFINITY) : f; };
+  pp.lo_dn = fdn(lo);
+  pp.lo_up = fup(lo);
+  pp.hi_dn = fdn(hi);
+  pp.hi_up = fup(hi);
+  UFC_CUDA(c, cudaMemsetAsync(pdf, 0, (size_t)(nbins + 3) * 8, c->stream));
+  // (no kernel-timing records here: recording them may allocate)
+  k_moments<<<mgrid, kMT, (nbins + 3) * 4, c->stream>>>(kappa, npix, ksum, grid, pp, mpart,
+                                                        (unsigned long long*)pdf);
+  k_moments_final<<<1, 32, 0, c->stream>>>(ksum, grid, mpart, mgrid, npix, moments);
+  UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;
 }
 
