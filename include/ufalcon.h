@@ -152,10 +152,16 @@ ufc_status ufc_keys(ufc_ctx *ctx, const float *xyz_dev, int64_t n,
                     int32_t nside, int32_t *keys_dev);
 
 #define UFC_BIN_ACCUMULATE 1   /* add to counts_dev instead of overwriting */
+#define UFC_BIN_FORCE_DIRECT 2 /* L2-atomic path regardless of map size      */
+#define UFC_BIN_FORCE_DENSE 4  /* dense-key path (needs nside >= 64, no
+                                  replication, 16-byte aligned counts)       */
 
 /* Count maps of one lightcone made of nbox boxes: box k's particles are
  * xyz_dev[k] (n[k] of them).  counts_dev [nshell][12 nside^2] is overwritten
- * (or added to with UFC_BIN_ACCUMULATE).  nshell * 12 nside^2 < 2^30. */
+ * (or added to with UFC_BIN_ACCUMULATE).  nshell * 12 nside^2 < 2^30.
+ * The library picks the output path (L2 atomics for maps up to 32 MB, the
+ * dense-key scatter and shared-memory histograms above); the FORCE flags
+ * override the choice (used by the autotuner).  Results are identical. */
 ufc_status ufc_bin(ufc_ctx *ctx, const float *const *xyz_dev, const int64_t *n,
                    const ufc_box *boxes, int32_t nbox, const double *chi_edges,
                    int32_t nshell, int32_t nside, int32_t flags,
@@ -222,6 +228,29 @@ ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
                               double *H);
 
 /* ---- covariance over realisations (Eq. 10-11) ------------------------------ */
+
+#define UFC_BATCH_GRAPH 1      /* capture the whole batch into one CUDA graph */
+
+/* Statistics of nreal realisations in one call (Sec. 3.2 averages over 150
+ * realisations).  Realisation r has nbox particle sets xyz_dev[r*nbox + k]
+ * with n[r*nbox + k] particles in boxes[r*nbox + k]; the shell edges, nside
+ * and PDF range are shared; A [nreal][nshell] and C [nreal] are that
+ * realisation's kappa coefficients (they depend on its n_total).  For each r
+ * the library bins, builds kappa in kappa_dev (scratch, [npix]) from
+ * counts_dev (scratch, [nshell][npix]), writes moments_dev[r][10],
+ * pdf_dev[r][nbins+3] and stats_dev[r][6 + nbins] (ufc_stats_vector), and
+ * finally adds all nreal vectors to the Welford state state_dev in order.
+ * The workspace is grown once up front; with UFC_BATCH_GRAPH the per-
+ * realisation work is captured into one CUDA graph and launched once (the
+ * context stream must not be capturing already).  Asynchronous. */
+ufc_status ufc_batched_stats(ufc_ctx *ctx, int32_t nreal, int32_t nbox,
+                             const float *const *xyz_dev, const int64_t *n,
+                             const ufc_box *boxes, const double *chi_edges,
+                             int32_t nshell, int32_t nside, const double *A,
+                             const double *C, double pdf_lo, double pdf_hi,
+                             int32_t nbins, int32_t *counts_dev, float *kappa_dev,
+                             double *moments_dev, int64_t *pdf_dev,
+                             double *stats_dev, double *state_dev, int32_t flags);
 
 /* Statistics vector of one map, the quantity whose covariance over
  * realisations is estimated: v_dev[6 + nbins] = (mean, mu2, mu3, mu4, skew,

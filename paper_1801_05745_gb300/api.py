@@ -31,6 +31,9 @@ DP = ctypes.POINTER(ctypes.c_double)
 
 UFC_OK = 0
 UFC_BIN_ACCUMULATE = 1
+UFC_BIN_FORCE_DIRECT = 2
+UFC_BIN_FORCE_DENSE = 4
+UFC_BATCH_GRAPH = 1
 NMOMENTS = 10
 MOMENT_NAMES = ("mean", "mu2", "mu3", "mu4", "skew", "kurt", "s2_expect", "var_s2",
                 "s2_over_var_s2", "n")
@@ -88,6 +91,7 @@ _SIGS = {
     "ufc_welford_merge": [P, P, P, I32],
     "ufc_welford_finalize": [P, P, I32, I32, P, P, P],
     "ufc_stats_vector": [P, P, P, I32, P],
+    "ufc_batched_stats": [P, I32, I32, P, P, P, P, I32, I32, P, P, D, D, I32, P, P, P, P, P, P, I32],
     "ufc_kappa_stats_noalloc": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_profile_enable": [P, I32],
     "ufc_profile_read": [P, I32, P, P, P, P],
@@ -221,8 +225,10 @@ class Context:
                                len(chi) - 1, nside, P(out.data_ptr())), "ufc_keys")
         return out
 
-    def bin(self, xyz_list, boxes, chi_edges, nside: int, counts=None, accumulate=False):
-        """int32 [nshell, 12 nside^2] count maps of the lightcone (Eq. 5, 8)."""
+    def bin(self, xyz_list, boxes, chi_edges, nside: int, counts=None, accumulate=False,
+            path: str | None = None):
+        """int32 [nshell, 12 nside^2] count maps of the lightcone (Eq. 5, 8).
+        path: None (library choice), "direct" or "dense" (see UFC_BIN_FORCE_*)."""
         import torch
         chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
         S = len(chi) - 1
@@ -235,9 +241,15 @@ class Context:
         ns = (I64 * len(xs))(*[x.numel() // 3 for x in xs])
         arr = (Box * len(boxes))(*boxes)
         self._stream()
+        flags = UFC_BIN_ACCUMULATE if accumulate else 0
+        if path == "direct":
+            flags |= UFC_BIN_FORCE_DIRECT
+        elif path == "dense":
+            flags |= UFC_BIN_FORCE_DENSE
+        elif path is not None:
+            raise ValueError(f"unknown binning path {path!r}")
         self._ck(_lib.ufc_bin(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P), ctypes.cast(arr, P),
-                              len(boxes), _np_ptr(chi), S, nside,
-                              UFC_BIN_ACCUMULATE if accumulate else 0, P(counts.data_ptr())),
+                              len(boxes), _np_ptr(chi), S, nside, flags, P(counts.data_ptr())),
                  "ufc_bin")
         return counts
 
@@ -287,6 +299,41 @@ class Context:
                                          _np_ptr(dC), _np_ptr(grad), _np_ptr(G), ctypes.byref(H)),
                  "ufc_kappa_backward")
         return grad, G, H.value
+
+    # -- batched realisations --
+    def batched_stats(self, xyz, boxes, chi_edges, nside, A, C, pdf_lo, pdf_hi, nbins,
+                      state, graph=True, counts=None, kappa=None):
+        """Statistics of many realisations in one call (ufc_batched_stats).
+        xyz[r][k]: particles of realisation r, box k; boxes[r][k]: its box;
+        A [nreal, nshell], C [nreal].  Returns (moments [nreal,10],
+        pdf [nreal, nbins+3], stats [nreal, 6+nbins]); updates `state`."""
+        import torch
+        nreal, nbox = len(xyz), len(xyz[0])
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        S = len(chi) - 1
+        npix = 12 * nside * nside
+        dev = torch.device("cuda", self.device)
+        flat = [_dev_f32(x, self.device) for row in xyz for x in row]
+        ptrs = (P * len(flat))(*[P(x.data_ptr()) for x in flat])
+        ns = (I64 * len(flat))(*[x.numel() // 3 for x in flat])
+        bx = (Box * len(flat))(*[b for row in boxes for b in row])
+        A = np.ascontiguousarray(A, dtype=np.float64).reshape(nreal, S)
+        C = np.ascontiguousarray(C, dtype=np.float64).reshape(nreal)
+        if counts is None:
+            counts = torch.empty((S, npix), dtype=torch.int32, device=dev)
+        if kappa is None:
+            kappa = torch.empty(npix, dtype=torch.float32, device=dev)
+        mom = torch.empty((nreal, NMOMENTS), dtype=torch.float64, device=dev)
+        pdf = torch.empty((nreal, nbins + 3), dtype=torch.int64, device=dev)
+        stats = torch.empty((nreal, 6 + nbins), dtype=torch.float64, device=dev)
+        self._stream()
+        self._ck(_lib.ufc_batched_stats(self.h, nreal, nbox, ctypes.cast(ptrs, P), ctypes.cast(ns, P),
+                                        ctypes.cast(bx, P), _np_ptr(chi), S, nside, _np_ptr(A),
+                                        _np_ptr(C), float(pdf_lo), float(pdf_hi), nbins,
+                                        P(counts.data_ptr()), P(kappa.data_ptr()), P(mom.data_ptr()),
+                                        P(pdf.data_ptr()), P(stats.data_ptr()), P(state.data_ptr()),
+                                        UFC_BATCH_GRAPH if graph else 0), "ufc_batched_stats")
+        return mom, pdf, stats
 
     # -- covariance --
     def stats_vector(self, moments, pdf, out=None):

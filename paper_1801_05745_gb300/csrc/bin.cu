@@ -429,18 +429,35 @@ __device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list,
   if (want && idx < cap) list[idx] = v;
 }
 
+// Fast stage fed by bulk copies.  Each warp owns 64 consecutive particles of
+// a chunk (two per lane).  Per round (one periodic image):
+//   A : radius, shell and zone of every particle; the warp lists its belt
+//       and cap particles in its own 64-slot region (belt from the front, cap
+//       from the back) using ballots, no atomics; undecided images are queued;
+//   A2: each warp copies its entries into the block's dense belt/cap lists at
+//       offsets from a prefix over the 24 warp counts;
+//   B : pixels of the listed particles; in DENSE mode the keys are staged in
+//       shared memory in list order and
+//   F : flushed to the dense array with one reservation per round.
 template <int MODE>
 __global__ void __launch_bounds__(kTThreads, 1)
 k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
            ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
+  constexpr int kWarps = kTThreads / 32;
+  constexpr int kPerWarp = kTChunk / kWarps;   // 64
+  static_assert(kPerWarp == 64, "two particles per lane");
   extern __shared__ __align__(128) uint8_t dyn[];
-  float* ring = reinterpret_cast<float*>(dyn);                       // [kStages][3 kTChunk]
-  uint32_t* eq_list = reinterpret_cast<uint32_t*>(dyn + kStages * kTChunk * 12);
+  float* ring = reinterpret_cast<float*>(dyn);                        // [kStages][3 kTChunk]
+  uint32_t* ent = reinterpret_cast<uint32_t*>(dyn + kStages * kTChunk * 12);  // warp regions / staged keys
+  uint32_t* eq_list = ent + kTChunk;
   uint32_t* cap_list = eq_list + kTChunk;
   uint32_t* hist_s = cap_list + kTChunk;
+  uint32_t* kstage = ent;                      // reused after A2
   __shared__ FastShared fs;
   __shared__ __align__(8) uint64_t bar[kStages];
-  __shared__ int abort_s, neq_s[2], ncap_s[2];
+  __shared__ int abort_s;
+  __shared__ int wne_s[kWarps], wnc_s[kWarps];
+  __shared__ unsigned long long flush_base_s;
   fast_init_shared(fs, bg, st, lp.v);
   if (MODE == kModeDense && o.smem_hist)
     for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) hist_s[i] = 0;
@@ -448,13 +465,14 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
     for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
-    neq_s[0] = neq_s[1] = 0;
-    ncap_s[0] = ncap_s[1] = 0;
   }
   __syncthreads();
 
   const int lo = bg.shell_lo, hi = bg.shell_hi;
   const int n1 = 2 * bg.R + 1;
+  const float lo2_first = fs.lo2[lo], hi2_last = fs.hi2[hi];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const int64_t nchunks = (n + kTChunk - 1) / kTChunk;
   const int64_t mine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   auto chunk_bytes = [&](int64_t c) -> uint32_t {
@@ -475,7 +493,6 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
     for (; issued < mine && issued < kStages; ++issued) issue(issued);
 
   FastCtx fc{{-1, 0}, {-1, 0}, 0, 0};
-  uint32_t rnd = 0;                            // list rounds so far (selects the counters)
   int64_t k = 0;
   for (; k < mine; ++k) {
     const int64_t c = blockIdx.x + k * gridDim.x;
@@ -498,37 +515,35 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
         zc = __ldg(xyz + 3 * p + 2);
       }
     };
-    // One round per periodic image: phase A classifies radius, shell and zone
-    // of every particle of the chunk and lists the in-cone images (at most
-    // one entry per particle per round); phase B computes their pixels over
-    // the dense belt and cap lists.  List counters alternate between rounds.
     int ii = 0, jj = 0, kk = 0;
 #pragma unroll 1
     for (int img = 0; img < bg.nimg; ++img) {
       if (img) {
         if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
       }
-      int* neq_c = &neq_s[rnd & 1];
-      int* ncap_c = &ncap_s[rnd & 1];
-      // ---- phase A
-#pragma unroll 1
-      for (int j = threadIdx.x; j < kTChunk; j += kTThreads) {
+      const float sx = fs.shf[0][ii], sy = fs.shf[1][jj], sz = fs.shf[2][kk];
+      const float lx = fs.shlo[0][ii], ly = fs.shlo[1][jj], lz = fs.shlo[2][kk];
+      // ---- A: classify
+      int ne = 0, nc = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = warp * kPerWarp + 32 * h + lane;
         const int64_t p = base + j;
         const bool have = p < n;
         float x = 0.f, y = 0.f, zc = 0.f;
         if (have) load(j, x, y, zc);
-        const bool finite = have && isfinite(x) && isfinite(y) && isfinite(zc);
-        if (img == 0 && have && !finite) ++fc.n_invalid;
-        int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap
-        int32_t b = -1;
-        if (finite) {
-          const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
-          const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
-          const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
-          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          if (!(r2 >= bd.r2_min)) {
+        const float dx = (x + sx) + lx;
+        const float dy = (y + sy) + ly;
+        const float dz = (zc + sz) + lz;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+        int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap, 4 invalid
+        int32_t b = 0;
+        if (have) {
+          if (!(r2 <= 3.0e38f)) {              // NaN or overflow: inspect the coordinates
+            if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) cls = 4;
+          } else if (!(r2 >= bd.r2_min)) {     // near the observer (r == 0 is invalid)
             cls = 1;
-          } else {
+          } else if (r2 >= lo2_first && r2 < hi2_last) {
             b = shell_lut(fs, lo, hi, lp.scale, r2);
             if (b == -2) cls = 1;
             else if (b >= 0) {
@@ -537,26 +552,62 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
             }
           }
         }
+        if (cls == 4 && img == 0) ++fc.n_invalid;
         const uint32_t entry = uint32_t(j) | (uint32_t(b & 255) << 11);
-        list_push(cls == 2, entry, eq_list, neq_c, kTChunk);
-        list_push(cls == 3, entry, cap_list, ncap_c, kTChunk);
-        // outside, invalid and undecided images are final here
-        const int32_t key = !finite ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
-        const bool here = have && (cls < 2);
-        fast_emit<MODE>(here, key, 0u, box_id, img, p, bg, st, N, npix, o, qs, hist_s, fc, x, y,
-                        zc, ii, jj, kk);
+        const unsigned meq = __ballot_sync(0xFFFFFFFFu, cls == 2);
+        const unsigned mcap = __ballot_sync(0xFFFFFFFFu, cls == 3);
+        if (cls == 2) ent[warp * kPerWarp + ne + __popc(meq & lt_mask)] = entry;
+        if (cls == 3) ent[warp * kPerWarp + kPerWarp - 1 - (nc + __popc(mcap & lt_mask))] = entry;
+        ne += __popc(meq);
+        nc += __popc(mcap);
+        // undecided images wait in queue 1; outside/invalid are final
+        if (!queue_push(fc.qc, cls == 1, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
+          const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
+                                            bg.sh64[1][jj], bg.sh64[2][kk]);
+          if (kx == kKeyInvalid) ++fc.n_invalid;
+          if (kx >= 0) {
+            ++fc.n_keyed;
+            if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
+            if (MODE == kModeDense) {            // rare: straight to the global histogram
+              const uint32_t dk = dense_key(kx, npix, o.nblk);
+              atomicAdd(o.hist + (dk >> kOffBits), 1u);
+              const unsigned long long at = atomicAdd(o.dense_count, 1ull);
+              if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
+            }
+          }
+          if (MODE == kModeKeys && have) o.keys[p] = kx;
+        } else if (MODE == kModeKeys && have && cls != 2 && cls != 3) {
+          o.keys[p] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
+        }
+      }
+      if (lane == 0) {
+        wne_s[warp] = ne;
+        wnc_s[warp] = nc;
       }
       __syncthreads();
-      if (threadIdx.x == 0) {                  // counters of the next round
-        neq_s[(rnd + 1) & 1] = 0;
-        ncap_s[(rnd + 1) & 1] = 0;
+      // ---- A2: warp prefix over the 24 counts, copy into the block lists
+      int cne = lane < kWarps ? wne_s[lane] : 0;
+      int cnc = lane < kWarps ? wnc_s[lane] : 0;
+      int ie = cne, ic = cnc;                  // inclusive scans over lanes = warps
+#pragma unroll
+      for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const int te = __shfl_up_sync(0xFFFFFFFFu, ie, o2);
+        const int tc = __shfl_up_sync(0xFFFFFFFFu, ic, o2);
+        if (lane >= o2) { ie += te; ic += tc; }
       }
-      // ---- phase B
-      const int neq = min(*neq_c, kTChunk), ncap = min(*ncap_c, kTChunk);
+      const int NE = __shfl_sync(0xFFFFFFFFu, ie, kWarps - 1);
+      const int NC = __shfl_sync(0xFFFFFFFFu, ic, kWarps - 1);
+      const int pe = __shfl_sync(0xFFFFFFFFu, ie - cne, warp);
+      const int pc = __shfl_sync(0xFFFFFFFFu, ic - cnc, warp);
+      for (int i = lane; i < ne; i += 32) eq_list[pe + i] = ent[warp * kPerWarp + i];
+      for (int i = lane; i < nc; i += 32) cap_list[pc + i] = ent[warp * kPerWarp + kPerWarp - 1 - i];
+      __syncthreads();
+      // ---- B: pixels over the dense lists (belt first, then cap)
 #pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
-        const int cnt = pass == 0 ? neq : ncap;
+        const int cnt = pass == 0 ? NE : NC;
         const uint32_t* list = pass == 0 ? eq_list : cap_list;
+        const int slot0 = pass == 0 ? 0 : NE;
         const int rounds = (cnt + kTThreads - 1) / kTThreads;
 #pragma unroll 1
         for (int rr = 0; rr < rounds; ++rr) {
@@ -566,30 +617,66 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
           const int j = int(e & 2047u), b = int((e >> 11) & 255u);
           float x = 0.f, y = 0.f, zc = 0.f;
           if (have) load(j, x, y, zc);
-          const float dx = (x + fs.shf[0][ii]) + fs.shlo[0][ii];
-          const float dy = (y + fs.shf[1][jj]) + fs.shlo[1][jj];
-          const float dz = (zc + fs.shf[2][kk]) + fs.shlo[2][kk];
+          const float dx = (x + sx) + lx;
+          const float dy = (y + sy) + ly;
+          const float dz = (zc + sz) + lz;
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           const float rinv = rsqrtf(r2);
           const float z = dz * rinv;
           int32_t pix = kKeyUndecided;
           if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
                                     : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
-          const int32_t key = pix == kKeyUndecided ? kKeyUndecided : b * npix + pix;
-          uint32_t dkey = 0u;
-          if (MODE == kModeDense && pix != kKeyUndecided) {
-            const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
-            dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
-                   (uint32_t(pix) - blk * uint32_t(kBlockPix));
+          const bool ok = have && pix != kKeyUndecided;
+          const int64_t p = base + j;
+          const int32_t key = b * npix + pix;
+          const bool queued = queue_push(fc.qc, have && !ok, qpack(box_id, img, p), qs.q1,
+                                         qs.cap1, &qs.cnt->q1);
+          if (!queued) {
+            const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
+                                              bg.sh64[1][jj], bg.sh64[2][kk]);
+            if (kx >= 0) {
+              ++fc.n_keyed;
+              if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
+              if (MODE == kModeDense) {
+                const uint32_t dk = dense_key(kx, npix, o.nblk);
+                atomicAdd(o.hist + (dk >> kOffBits), 1u);
+                const unsigned long long at = atomicAdd(o.dense_count, 1ull);
+                if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
+              }
+            }
+            if (MODE == kModeKeys) o.keys[p] = kx;
           }
-          fast_emit<MODE>(have, key, dkey, box_id, img, base + j, bg, st, N, npix, o, qs, hist_s,
-                          fc, x, y, zc, ii, jj, kk);
+          if (MODE == kModeKeys) {
+            if (have && queued) o.keys[p] = ok ? key : kKeyUndecided;
+          } else if (MODE == kModeDirect) {
+            if (ok) atomicAdd(o.counts + key, 1);
+          } else if (have) {
+            uint32_t dk = kSentinel;
+            if (ok) {
+              const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
+              const uint32_t bucket = uint32_t(b) * uint32_t(o.nblk) + blk;
+              dk = (bucket << kOffBits) | (uint32_t(pix) - blk * uint32_t(kBlockPix));
+              if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
+              else atomicAdd(o.hist + bucket, 1u);
+            }
+            kstage[slot0 + i] = dk;
+          }
+          fc.n_keyed += ok;
         }
       }
-      __syncthreads();                         // lists consumed before the next round
-      ++rnd;
+      // ---- F: one reservation per round for the staged keys
+      if (MODE == kModeDense) {
+        __syncthreads();
+        const int total = NE + NC;
+        if (threadIdx.x == 0)
+          flush_base_s = total ? atomicAdd(o.dense_count, (unsigned long long)total) : 0ull;
+        __syncthreads();
+        const int64_t fb = (int64_t)flush_base_s;
+        for (int i = threadIdx.x; i < total; i += kTThreads)
+          if (fb + i < o.dense_cap) o.dense[fb + i] = kstage[i];
+      }
+      __syncthreads();                         // lists and staged keys consumed
     }
-    // buffer s and the lists are consumed (barrier at the end of the last round)
     if (threadIdx.x == 0 && issued < mine) issue(issued++);
   }
   if (abort_s) {
@@ -785,7 +872,9 @@ constexpr int kScatThreads = 256;
 constexpr int kScatPer = 16;
 constexpr int kScatTile = kScatThreads * kScatPer;   // 4096 keys
 
-// Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.
+// Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.  The
+// next tile's keys are loaded into registers while the current tile is
+// sorted in shared memory and written out.
 __global__ void __launch_bounds__(kScatThreads)
 k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* dense_count,
                 int64_t dense_cap, int ng, unsigned long long* __restrict__ gcur, uint32_t* __restrict__ out) {
@@ -797,18 +886,25 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
   const int64_t total = (int64_t)min(*dense_count, (unsigned long long)dense_cap);
   const int64_t ntiles = (total + kScatTile - 1) / kScatTile;
   const int shift = kOffBits + kGroupBits;
-  for (int64_t tIdx = blockIdx.x; tIdx < ntiles; tIdx += gridDim.x) {
-    for (int i = threadIdx.x; i < ng; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    uint32_t v[kScatPer];
-    uint32_t slot[kScatPer];
-    const int64_t t0 = tIdx * kScatTile;
+  uint32_t v[kScatPer], nv[kScatPer];
+  auto fetch = [&](int64_t t, uint32_t* dst) {
+    const int64_t t0 = t * kScatTile;
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k) {
-      int64_t i = t0 + k * kScatThreads + threadIdx.x;
-      v[k] = i < total ? dense[i] : kSentinel;
-      slot[k] = v[k] != kSentinel ? atomicAdd(cnt + (v[k] >> shift), 1u) : 0u;
+      const int64_t i = t0 + k * kScatThreads + threadIdx.x;
+      dst[k] = (t < ntiles && i < total) ? __ldcs(dense + i) : kSentinel;
     }
+  };
+  int64_t tIdx = blockIdx.x;
+  fetch(tIdx, v);
+  for (; tIdx < ntiles; tIdx += gridDim.x) {
+    fetch(tIdx + gridDim.x, nv);           // prefetch the next tile
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    uint32_t slot[kScatPer];
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k)
+      slot[k] = v[k] != kSentinel ? atomicAdd(cnt + (v[k] >> shift), 1u) : 0u;
     __syncthreads();
     if (threadIdx.x < 32) warp_exclusive_scan(cnt, start, ng);
     __syncthreads();
@@ -818,13 +914,15 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
     for (int k = 0; k < kScatPer; ++k)
       if (v[k] != kSentinel) tile[start[v[k] >> shift] + slot[k]] = v[k];
     __syncthreads();
-    uint32_t used = start[ng - 1] + cnt[ng - 1];
+    const uint32_t used = start[ng - 1] + cnt[ng - 1];
     for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) {
-      uint32_t val = tile[i];
-      uint32_t g = val >> shift;
+      const uint32_t val = tile[i];
+      const uint32_t g = val >> shift;
       out[base[g] + (i - start[g])] = val;
     }
     __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) v[k] = nv[k];
   }
 }
 
@@ -856,7 +954,7 @@ __global__ void __launch_bounds__(1024) k_tiles(const int64_t* __restrict__ off,
   if (t == 0) *ntiles = (unsigned long long)pre[1024];
 }
 
-// Pass B: grouped keys -> per-bucket u16 offsets.
+// Pass B: grouped keys -> per-bucket u16 offsets (next tile prefetched).
 __global__ void __launch_bounds__(kScatThreads)
 k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ tiles,
                  const unsigned long long* __restrict__ ntiles_p,
@@ -867,18 +965,26 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
   __shared__ uint16_t tile[kScatTile];
   __shared__ uint8_t tsub[kScatTile];
   const int64_t ntiles = (int64_t)*ntiles_p;
-  for (int64_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    const Tile T = tiles[ti];
-    for (int i = threadIdx.x; i < NS; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    uint32_t v[kScatPer], slot[kScatPer];
+  uint32_t v[kScatPer], nv[kScatPer];
+  Tile T{0, 0, 0}, NT{0, 0, 0};
+  auto fetch = [&](int64_t ti, Tile& tt, uint32_t* dst) {
+    if (ti < ntiles) tt = tiles[ti]; else tt = Tile{0, 0, 0};
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k) {
-      int i = k * kScatThreads + threadIdx.x;
-      v[k] = i < T.len ? grouped[T.start + i] : kSentinel;
-      slot[k] = v[k] != kSentinel
-                    ? atomicAdd(cnt + ((v[k] >> kOffBits) & (NS - 1)), 1u) : 0u;
+      const int i = k * kScatThreads + threadIdx.x;
+      dst[k] = i < tt.len ? __ldcs(grouped + tt.start + i) : kSentinel;
     }
+  };
+  int64_t ti = blockIdx.x;
+  fetch(ti, T, v);
+  for (; ti < ntiles; ti += gridDim.x) {
+    fetch(ti + gridDim.x, NT, nv);
+    for (int i = threadIdx.x; i < NS; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    uint32_t slot[kScatPer];
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k)
+      slot[k] = v[k] != kSentinel ? atomicAdd(cnt + ((v[k] >> kOffBits) & (NS - 1)), 1u) : 0u;
     __syncthreads();
     if (threadIdx.x < 32) warp_exclusive_scan(cnt, start, NS);
     __syncthreads();
@@ -888,42 +994,73 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k)
       if (v[k] != kSentinel) {
-        uint32_t sub = (v[k] >> kOffBits) & (NS - 1);
-        uint32_t pos = start[sub] + slot[k];
+        const uint32_t sub = (v[k] >> kOffBits) & (NS - 1);
+        const uint32_t pos = start[sub] + slot[k];
         tile[pos] = uint16_t(v[k] & ((1u << kOffBits) - 1u));
         tsub[pos] = uint8_t(sub);
       }
     __syncthreads();
     for (int i = threadIdx.x; i < T.len; i += blockDim.x) {
-      uint32_t sub = tsub[i];
+      const uint32_t sub = tsub[i];
       out[base[sub] + (i - start[sub])] = tile[i];
     }
     __syncthreads();
+    T = NT;
+#pragma unroll
+    for (int k = 0; k < kScatPer; ++k) v[k] = nv[k];
   }
 }
 
-// Count map of each bucket from its u16 offsets, in shared memory.
+// Count map of each bucket from its u16 offsets, in shared memory.  The
+// bucket's offsets are read with 16-byte loads (8 offsets each), two per
+// thread in flight, plus scalar head and tail.
 constexpr int kHistThreads = 512;
 __global__ void __launch_bounds__(kHistThreads)
 k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off, int nb,
              int32_t* __restrict__ counts, int accumulate) {
   extern __shared__ uint32_t h[];   // [kBlockPix]
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-    for (int i = threadIdx.x; i < kBlockPix; i += blockDim.x) h[i] = 0;
+    uint4* h4 = reinterpret_cast<uint4*>(h);
+    for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) h4[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     const int64_t a = off[b], e = off[b + 1];
-    for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) atomicAdd(h + offs[i], 1u);
+    const int64_t a8r = (a + 7) & ~7ll, e8r = e & ~7ll;
+    const int64_t a8 = a8r < e ? a8r : e;                  // first 16-byte boundary
+    const int64_t e8 = e8r > a8 ? e8r : a8;                // last one
+    if (threadIdx.x < a8 - a) atomicAdd(h + offs[a + threadIdx.x], 1u);
+    if (threadIdx.x < e - e8) atomicAdd(h + offs[e8 + threadIdx.x], 1u);
+    const uint4* body = reinterpret_cast<const uint4*>(offs + a8);
+    const int64_t nvec = (e8 - a8) >> 3;
+    for (int64_t i = threadIdx.x; i < nvec; i += 2 * kHistThreads) {
+      const uint4 p = __ldcs(body + i);
+      const bool two = i + kHistThreads < nvec;
+      const uint4 q = two ? __ldcs(body + i + kHistThreads) : make_uint4(0, 0, 0, 0);
+      const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        atomicAdd(h + (w[k] & 0xFFFFu), 1u);
+        atomicAdd(h + (w[k] >> 16), 1u);
+      }
+      if (two) {
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          atomicAdd(h + (u[k] & 0xFFFFu), 1u);
+          atomicAdd(h + (u[k] >> 16), 1u);
+        }
+      }
+    }
     __syncthreads();
     int4* dst = reinterpret_cast<int4*>(counts + (int64_t)b * kBlockPix);
     const uint4* src = reinterpret_cast<const uint4*>(h);
     for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) {
-      uint4 s = src[i];
-      int4 d = make_int4(int(s.x), int(s.y), int(s.z), int(s.w));
+      const uint4 sv = src[i];
+      int4 d = make_int4(int(sv.x), int(sv.y), int(sv.z), int(sv.w));
       if (accumulate) {
-        int4 o = dst[i];
+        const int4 o = dst[i];
         d.x += o.x; d.y += o.y; d.z += o.z; d.w += o.w;
       }
-      dst[i] = d;
+      __stcs(dst + i, d);
     }
     __syncthreads();
   }
@@ -1021,6 +1158,30 @@ struct BinPlan {
   int nblk, nbuckets, ng, smem_hist;
 };
 
+// Grows the workspace for a binning call of total_img particle images at
+// (nside, nshell) with nbox boxes, so that the call itself allocates nothing.
+ufc_status reserve_bin_workspace(ufc_ctx* c, int nbox, int64_t total_img, int nshell, int nside) {
+  const int64_t npix = 12ll * nside * nside;
+  const int64_t qwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
+                         4ll * c->num_sms * (256 / 32);
+  const int64_t cap1 = std::max<int64_t>(1 << 20, total_img / 16) + qwarps * kQChunk;
+  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64) + qwarps * kQChunk;
+  if (!ws_get(c, kSlotQueue1, cap1 * 8) || !ws_get(c, kSlotQueue2, cap2 * 8)) return UFC_ERR_ALLOC;
+  if (nside >= 64 && npix * nshell * 4 > (32ll << 20) && nshell * (npix / kBlockPix) < (1ll << 17)) {
+    const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
+                           2ll * 4 * c->num_sms * (256 / 32) + 64;
+    const int64_t dense_cap = total_img + cap1 + nwarps * kChunk;
+    const int64_t nb = nshell * (npix / kBlockPix);
+    const int64_t ng = (nb + (1 << kGroupBits) - 1) >> kGroupBits;
+    if (!ws_get(c, kSlotDense, dense_cap * 4) || !ws_get(c, kSlotGrouped, dense_cap * 4) ||
+        !ws_get(c, kSlotBucket16, dense_cap * 2) || !ws_get(c, kSlotHist, nb * 4) ||
+        !ws_get(c, kSlotOff, (nb + 1) * 8) || !ws_get(c, kSlotCursors, (nb + ng + 1) * 8) ||
+        !ws_get(c, kSlotTiles, (size_t)(dense_cap / kScatTile + ng + 1) * sizeof(Tile)))
+      return UFC_ERR_ALLOC;
+  }
+  return UFC_OK;
+}
+
 // Runs the key pipeline for nbox boxes.  counts (DIRECT/DENSE) or keys (KEYS).
 ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
                              const int64_t* n, const ufc_box* boxes, int nbox,
@@ -1067,6 +1228,14 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
                           (int64_t)nshell * (npix / kBlockPix) < (1ll << 17);
     const bool aligned = (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
     plan.mode = (dense_ok && aligned && map_bytes > (32ll << 20)) ? kModeDense : kModeDirect;
+    if (flags & UFC_BIN_FORCE_DIRECT) plan.mode = kModeDirect;
+    if (flags & UFC_BIN_FORCE_DENSE) {
+      if (!(dense_ok && aligned))
+        return set_err(c, UFC_ERR_UNSUPPORTED,
+                       "the dense path needs nside >= 64, no replication, 16-byte aligned counts "
+                       "and nshell * 12 nside^2 / 24576 < 2^17");
+      plan.mode = kModeDense;
+    }
   }
   if (plan.mode == kModeDense) {
     plan.nblk = (int)(npix / kBlockPix);
@@ -1100,7 +1269,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     // every warp of every launch may leave one partly filled chunk
     const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
                            2ll * 4 * c->num_sms * (256 / 32) + 64;
-    o.dense_cap = total_img + nwarps * kChunk;
+    o.dense_cap = total_img + cap1 + nwarps * kChunk;   // + sentinel slots of undecided images
     o.dense = (uint32_t*)ws_get(c, kSlotDense, o.dense_cap * 4);
     o.hist = (uint32_t*)ws_get(c, kSlotHist, (size_t)plan.nbuckets * 4);
     if (!o.dense || !o.hist) return UFC_ERR_ALLOC;
@@ -1126,7 +1295,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     }
   }
   // fast stage per box
-  const int tma_smem = kStages * kTChunk * 12 + 2 * kTChunk * 4 + (plan.mode == kModeDense ? smem : 0);
+  const int tma_smem = kStages * kTChunk * 12 + 3 * kTChunk * 4 + (plan.mode == kModeDense ? smem : 0);
   for (int k = 0; k < nbox; ++k) {
     if (n[k] == 0) continue;
     const bool tma = (reinterpret_cast<uintptr_t>(xyz[k]) & 15) == 0;

@@ -1,5 +1,6 @@
 // C ABI of libufalcon_gb300.so: argument checks, context, workspace, and the
 // calls into the binning, statistics and cosmology code.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -28,6 +29,7 @@ ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int
 ufc_status run_welford_merge(ufc_ctx* c, double* a, const double* b, int d);
 ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, double* mean,
                                 double* cov, double* corr);
+ufc_status reserve_bin_workspace(ufc_ctx* c, int nbox, int64_t total_img, int nshell, int nside);
 ufc_status cosmo_chi_edges(const ufc_cosmo& c, const double* z, int n, double* chi);
 ufc_status cosmo_z_of_chi(const ufc_cosmo& c, const double* chi, int n, double* zout);
 ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
@@ -274,7 +276,10 @@ ufc_status ufc_bin(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
   c->err.clear();
   if (!xyz_dev || !n || !boxes || !chi_edges || !counts_dev)
     return set_err(c, UFC_ERR_ARG, "NULL argument to ufc_bin");
-  if (flags & ~UFC_BIN_ACCUMULATE) return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if (flags & ~(UFC_BIN_ACCUMULATE | UFC_BIN_FORCE_DIRECT | UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if ((flags & UFC_BIN_FORCE_DIRECT) && (flags & UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "FORCE_DIRECT and FORCE_DENSE exclude each other");
   if (reinterpret_cast<uintptr_t>(counts_dev) & 3)
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 4-byte aligned");
   cudaSetDevice(c->device);
@@ -339,6 +344,78 @@ ufc_status ufc_stats_vector(ufc_ctx* c, const double* moments_dev, const int64_t
   c->err.clear();
   cudaSetDevice(c->device);
   return run_stats_vector(c, moments_dev, pdf_dev, nbins, v_dev);
+}
+
+ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const float* const* xyz,
+                             const int64_t* n, const ufc_box* boxes, const double* chi,
+                             int32_t nshell, int32_t nside, const double* A, const double* C,
+                             double lo, double hi, int32_t nbins, int32_t* counts, float* kappa,
+                             double* moments, int64_t* pdf, double* stats, double* state,
+                             int32_t flags) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (nreal < 1 || nbox < 1 || !xyz || !n || !boxes || !chi || !A || !C || !counts || !kappa ||
+      !moments || !pdf || !stats || !state)
+    return set_err(c, UFC_ERR_ARG, "ufc_batched_stats: bad arguments");
+  if (flags & ~UFC_BATCH_GRAPH) return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if (nshell < 1 || nshell > UFC_MAX_SHELLS) return set_err(c, UFC_ERR_ARG, "bad nshell");
+  if (nbins < 1 || nbins > 4096) return set_err(c, UFC_ERR_ARG, "bad nbins");
+  cudaSetDevice(c->device);
+  // grow every workspace slot once for the largest realisation
+  int64_t max_img = 0;
+  for (int r = 0; r < nreal; ++r) {
+    int64_t t = 0;
+    for (int k = 0; k < nbox; ++k) {
+      const int R = boxes[r * nbox + k].replicate;
+      t += n[r * nbox + k] * (int64_t)(2 * R + 1) * (2 * R + 1) * (2 * R + 1);
+    }
+    max_img = std::max(max_img, t);
+  }
+  ufc_status s = reserve_bin_workspace(c, nbox, max_img, nshell, nside);
+  if (s) return s;
+  // per-block partial sums of the kappa and moment kernels
+  if (!ws_get(c, kSlotPartials, (size_t)16 * c->num_sms * 8)) return UFC_ERR_ALLOC;
+  const int d = 6 + nbins;
+  const bool graph = (flags & UFC_BATCH_GRAPH) != 0;
+  const bool prof = c->prof;
+  cudaGraph_t g = nullptr;
+  if (graph) {
+    c->prof = false;   // event records would become graph nodes
+    cudaStreamCaptureStatus cs;
+    UFC_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+      c->prof = prof;
+      return set_err(c, UFC_ERR_ARG, "the context stream is already capturing");
+    }
+    if (c->stream == nullptr) {
+      c->prof = prof;
+      return set_err(c, UFC_ERR_ARG, "UFC_BATCH_GRAPH needs a non-default stream");
+    }
+    UFC_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  }
+  for (int r = 0; r < nreal && !s; ++r) {
+    s = run_keys_pipeline(c, 1, xyz + r * nbox, n + r * nbox, boxes + r * nbox, nbox, chi, nshell,
+                          nside, 0, counts, nullptr);
+    if (!s)
+      s = run_kappa_stats(c, counts, nshell, nside, A + (size_t)r * nshell, C[r], lo, hi, nbins,
+                          kappa, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r);
+    if (!s) s = run_stats_vector(c, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r, nbins,
+                                 stats + (size_t)d * r);
+  }
+  if (!s) s = run_welford_update(c, stats, nreal, d, state);
+  if (graph) {
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    c->prof = prof;
+    if (s) { if (g) cudaGraphDestroy(g); return s; }
+    if (e != cudaSuccess) return set_err(c, UFC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ge = nullptr;
+    e = cudaGraphInstantiate(&ge, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
+    if (ge) cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return set_err(c, UFC_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(e));
+  }
+  return s;
 }
 
 ufc_status ufc_welford_update(ufc_ctx* c, const double* v_dev, int32_t nvec, int32_t d,

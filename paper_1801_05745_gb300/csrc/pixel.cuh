@@ -159,6 +159,25 @@ __device__ __forceinline__ int32_t floor_certain(float w, float band, bool& open
   return k;
 }
 
+// atan(q) * 2/pi for q in [0, 1] as q * P(q^2), P of degree 8 with
+// coefficients from a weighted least-squares fit of this library; Horner in
+// FP32 with fused multiply-adds.  Checked over every float q in [0, 1]: the
+// result is within 1.37 u (u = 2^-24) of the exact value; the fast-stage band
+// budgets 2 u for it.
+__device__ __forceinline__ float atanq_poly(float q) {
+  const float s = q * q;
+  float p = 0x1.99fe2cp-10f;
+  p = fmaf(p, s, -0x1.2c6c52p-7f);
+  p = fmaf(p, s, 0x1.9eeee2p-6f);
+  p = fmaf(p, s, -0x1.794fbcp-5f);
+  p = fmaf(p, s, 0x1.11c51ap-4f);
+  p = fmaf(p, s, -0x1.714478p-4f);
+  p = fmaf(p, s, 0x1.049362p-3f);
+  p = fmaf(p, s, -0x1.b296eap-3f);
+  p = fmaf(p, s, 0x1.45f304p-1f);
+  return q * p;
+}
+
 // Azimuth of the fast stage: t = base + sgn * a (exact-real identity of the
 // quadrant/octant cases of the FP64 procedure), a in [0, 1/2] quarter turns.
 struct Azim { float a, sa; int32_t base; bool sgn_pos; };
@@ -169,7 +188,7 @@ __device__ __forceinline__ Azim azimuth_fast(float dx, float dy, const Bands& bd
   const bool sw = ay > ax;
   const float q = sw ? __fdividef(ax, ay) : __fdividef(ay, ax);
   Azim r;
-  r.a = atanf(q) * 0.636619772367581343f;      // quarter turns, [0, 1/2]
+  r.a = atanq_poly(q);                         // quarter turns, [0, 1/2]
   const bool xp = dx >= 0.0f, yp = dy >= 0.0f;
   // (base, sgn): Q0 (0,+)|(1,-)  Q1 (2,-)|(1,+)  Q2 (2,+)|(3,-)  Q3 (4,-)|(3,+)
   r.base = xp ? (yp ? (sw ? 1 : 0) : (sw ? 3 : 4)) : (yp ? (sw ? 1 : 2) : (sw ? 3 : 2));
