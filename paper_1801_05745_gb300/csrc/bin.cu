@@ -34,7 +34,7 @@ constexpr int kOffBits = 15;            // offset bits in a dense key
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;
 constexpr int kChunk = 2048;            // dense keys reserved per warp at a time
 constexpr int kGroupBits = 8;           // buckets per group = 256
-constexpr int kSmemHistMax = 31744;     // buckets counted in shared memory (124 KB)
+constexpr int kSmemHistMax = 49152;     // buckets counted in shared memory (16-bit, 96 KB)
 constexpr int kFastThreads = 512;
 
 struct KeyOut {
@@ -429,40 +429,55 @@ __device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list,
   if (want && idx < cap) list[idx] = v;
 }
 
-// Fast stage fed by bulk copies.  Each warp owns 64 consecutive particles of
-// a chunk (two per lane).  Per round (one periodic image):
-//   A : radius, shell and zone of every particle; the warp lists its belt
-//       and cap particles in its own 64-slot region (belt from the front, cap
-//       from the back) using ballots, no atomics; undecided images are queued;
-//   A2: each warp copies its entries into the block's dense belt/cap lists at
-//       offsets from a prefix over the 24 warp counts;
-//   B : pixels of the listed particles; in DENSE mode the keys are staged in
-//       shared memory in list order and
-//   F : flushed to the dense array with one reservation per round.
+// Fast stage fed by bulk copies, warp-autonomous.  A ring of kStages chunks
+// of kTChunk particles streams in by cp.async.bulk.  Each warp owns a fixed
+// slice of kPerWarp particles of every chunk and works through it alone:
+//   A: radius, shell and zone of 32 particles at a time; the warp lists its
+//      belt and cap particles in its own shared-memory region (belt from the
+//      front, cap from the back) with ballots;
+//   B: pixels of the listed particles, 32 at a time, keys appended to the
+//      dense array through the warp's chunk, bucket counts in shared memory;
+// then lane 0 counts the warp out of the stage; the last warp to finish a
+// stage issues the bulk copy that refills it.  No block-wide barrier in the
+// steady state.  Bucket counters are 16-bit halves of 32-bit words; an
+// overflow (65536 particles of one bucket in one block) is carried to the
+// global histogram exactly.
+constexpr int kWThreads = 512;
+constexpr int kWChunk = 3072;                  // particles per chunk (36 KB)
+constexpr int kWStages = 3;
+constexpr int kWWarps = kWThreads / 32;
+constexpr int kWPerWarp = kWChunk / kWWarps;  // 192
+
+__device__ __forceinline__ void hist16_inc(uint32_t* h32, uint32_t* ghist, uint32_t bucket) {
+  const uint32_t shift = (bucket & 1u) << 4;
+  const uint32_t old = atomicAdd(h32 + (bucket >> 1), 1u << shift);
+  if (((old >> shift) & 0xFFFFu) == 0xFFFFu) {           // this increment wrapped the half
+    if (shift == 0) atomicSub(h32 + (bucket >> 1), 1u << 16);   // undo the carry
+    atomicAdd(ghist + bucket, 65536u);
+  }
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kTThreads, 1)
+__global__ void __launch_bounds__(kWThreads, 1)
 k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
            ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
-  constexpr int kWarps = kTThreads / 32;
-  constexpr int kPerWarp = kTChunk / kWarps;   // 64
-  static_assert(kPerWarp == 64, "two particles per lane");
   extern __shared__ __align__(128) uint8_t dyn[];
-  float* ring = reinterpret_cast<float*>(dyn);                        // [kStages][3 kTChunk]
-  uint32_t* ent = reinterpret_cast<uint32_t*>(dyn + kStages * kTChunk * 12);  // warp regions / staged keys
-  uint32_t* eq_list = ent + kTChunk;
-  uint32_t* cap_list = eq_list + kTChunk;
-  uint32_t* hist_s = cap_list + kTChunk;
-  uint32_t* kstage = ent;                      // reused after A2
+  float* ring = reinterpret_cast<float*>(dyn);                        // [kWStages][3 kWChunk]
+  uint32_t* regions = reinterpret_cast<uint32_t*>(dyn + kWStages * kWChunk * 12);  // [warps][kWPerWarp]
+  uint32_t* h32 = regions + kWChunk;                                 // 16-bit bucket counters
   __shared__ FastShared fs;
-  __shared__ __align__(8) uint64_t bar[kStages];
+  __shared__ __align__(8) uint64_t bar[kWStages];
+  __shared__ int done_s[kWStages];
   __shared__ int abort_s;
-  __shared__ int wne_s[kWarps], wnc_s[kWarps];
-  __shared__ unsigned long long flush_base_s;
   fast_init_shared(fs, bg, st, lp.v);
+  const int nwords = (o.nbuckets + 1) >> 1;
   if (MODE == kModeDense && o.smem_hist)
-    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) hist_s[i] = 0;
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) h32[i] = 0u;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < kWStages; ++s) {
+      mbar_init(&bar[s], 1);
+      done_s[s] = 0;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_s = 0;
   }
@@ -473,36 +488,41 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
   const float lo2_first = fs.lo2[lo], hi2_last = fs.hi2[hi];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  const int64_t nchunks = (n + kTChunk - 1) / kTChunk;
+  uint32_t* region = regions + warp * kWPerWarp;
+  const int64_t nchunks = (n + kWChunk - 1) / kWChunk;
   const int64_t mine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   auto chunk_bytes = [&](int64_t c) -> uint32_t {
-    const int64_t rest = n - c * kTChunk;
-    const int64_t cnt = rest < kTChunk ? rest : (int64_t)kTChunk;
+    const int64_t rest = n - c * kWChunk;
+    const int64_t cnt = rest < kWChunk ? rest : (int64_t)kWChunk;
     return uint32_t((cnt * 12) & ~15ll);       // bulk copies move multiples of 16 bytes
   };
-  auto issue = [&](int64_t k) {                // k-th chunk of this block
+  auto issue = [&](int64_t k) {                // k-th chunk of this block into stage k % kWStages
     const int64_t c = blockIdx.x + k * gridDim.x;
-    const int s = int(k % kStages);
+    const int s = int(k % kWStages);
     const uint32_t bytes = chunk_bytes(c);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&bar[s], bytes);
-    if (bytes) bulk_g2s(ring + s * 3 * kTChunk, xyz + c * kTChunk * 3, bytes, &bar[s]);
+    if (bytes) bulk_g2s(ring + s * 3 * kWChunk, xyz + c * kWChunk * 3, bytes, &bar[s]);
   };
-  int64_t issued = 0;                          // meaningful in thread 0
   if (threadIdx.x == 0)
-    for (; issued < mine && issued < kStages; ++issued) issue(issued);
+    for (int64_t kk = 0; kk < mine && kk < kWStages; ++kk) issue(kk);
 
   FastCtx fc{{-1, 0}, {-1, 0}, 0, 0};
+  uint32_t* ghist = o.hist;
   int64_t k = 0;
+  bool aborted = false;
   for (; k < mine; ++k) {
     const int64_t c = blockIdx.x + k * gridDim.x;
-    const int s = int(k % kStages);
-    if (!mbar_wait(&bar[s], uint32_t((k / kStages) & 1))) abort_s = 1;
-    __syncthreads();
-    if (abort_s) break;
-    const float* buf = ring + s * 3 * kTChunk;
+    const int s = int(k % kWStages);
+    // every lane waits on the stage's full barrier (bounded)
+    if (!mbar_wait(&bar[s], uint32_t((k / kWStages) & 1))) {
+      aborted = true;
+      abort_s = 1;
+    }
+    if (__any_sync(0xFFFFFFFFu, aborted) || abort_s) { aborted = true; break; }
+    const float* buf = ring + s * 3 * kWChunk;
     const uint32_t bytes = chunk_bytes(c);
-    const int64_t base = c * kTChunk;
+    const int64_t base = c * kWChunk;
     auto load = [&](int j, float& x, float& y, float& zc) {
       if ((uint32_t)(12 * j + 12) <= bytes) {
         x = buf[3 * j];
@@ -523,11 +543,11 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
       }
       const float sx = fs.shf[0][ii], sy = fs.shf[1][jj], sz = fs.shf[2][kk];
       const float lx = fs.shlo[0][ii], ly = fs.shlo[1][jj], lz = fs.shlo[2][kk];
-      // ---- A: classify
+      // ---- A: classify this warp's slice
       int ne = 0, nc = 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = warp * kPerWarp + 32 * h + lane;
+#pragma unroll 2
+      for (int h = 0; h < kWPerWarp / 32; ++h) {
+        const int j = warp * kWPerWarp + 32 * h + lane;
         const int64_t p = base + j;
         const bool have = p < n;
         float x = 0.f, y = 0.f, zc = 0.f;
@@ -553,11 +573,11 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
           }
         }
         if (cls == 4 && img == 0) ++fc.n_invalid;
-        const uint32_t entry = uint32_t(j) | (uint32_t(b & 255) << 11);
+        const uint32_t entry = uint32_t(j) | (uint32_t(b & 255) << 12);
         const unsigned meq = __ballot_sync(0xFFFFFFFFu, cls == 2);
         const unsigned mcap = __ballot_sync(0xFFFFFFFFu, cls == 3);
-        if (cls == 2) ent[warp * kPerWarp + ne + __popc(meq & lt_mask)] = entry;
-        if (cls == 3) ent[warp * kPerWarp + kPerWarp - 1 - (nc + __popc(mcap & lt_mask))] = entry;
+        if (cls == 2) region[ne + __popc(meq & lt_mask)] = entry;
+        if (cls == 3) region[kWPerWarp - 1 - (nc + __popc(mcap & lt_mask))] = entry;
         ne += __popc(meq);
         nc += __popc(mcap);
         // undecided images wait in queue 1; outside/invalid are final
@@ -570,7 +590,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
             if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
             if (MODE == kModeDense) {            // rare: straight to the global histogram
               const uint32_t dk = dense_key(kx, npix, o.nblk);
-              atomicAdd(o.hist + (dk >> kOffBits), 1u);
+              atomicAdd(ghist + (dk >> kOffBits), 1u);
               const unsigned long long at = atomicAdd(o.dense_count, 1ull);
               if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
             }
@@ -580,41 +600,17 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
           o.keys[p] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
         }
       }
-      if (lane == 0) {
-        wne_s[warp] = ne;
-        wnc_s[warp] = nc;
-      }
-      __syncthreads();
-      // ---- A2: warp prefix over the 24 counts, copy into the block lists
-      int cne = lane < kWarps ? wne_s[lane] : 0;
-      int cnc = lane < kWarps ? wnc_s[lane] : 0;
-      int ie = cne, ic = cnc;                  // inclusive scans over lanes = warps
-#pragma unroll
-      for (int o2 = 1; o2 < 32; o2 <<= 1) {
-        const int te = __shfl_up_sync(0xFFFFFFFFu, ie, o2);
-        const int tc = __shfl_up_sync(0xFFFFFFFFu, ic, o2);
-        if (lane >= o2) { ie += te; ic += tc; }
-      }
-      const int NE = __shfl_sync(0xFFFFFFFFu, ie, kWarps - 1);
-      const int NC = __shfl_sync(0xFFFFFFFFu, ic, kWarps - 1);
-      const int pe = __shfl_sync(0xFFFFFFFFu, ie - cne, warp);
-      const int pc = __shfl_sync(0xFFFFFFFFu, ic - cnc, warp);
-      for (int i = lane; i < ne; i += 32) eq_list[pe + i] = ent[warp * kPerWarp + i];
-      for (int i = lane; i < nc; i += 32) cap_list[pc + i] = ent[warp * kPerWarp + kPerWarp - 1 - i];
-      __syncthreads();
-      // ---- B: pixels over the dense lists (belt first, then cap)
+      __syncwarp();
+      // ---- B: pixels of this warp's list, 32 at a time (belt, then cap)
 #pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
-        const int cnt = pass == 0 ? NE : NC;
-        const uint32_t* list = pass == 0 ? eq_list : cap_list;
-        const int slot0 = pass == 0 ? 0 : NE;
-        const int rounds = (cnt + kTThreads - 1) / kTThreads;
+        const int cnt = pass == 0 ? ne : nc;
 #pragma unroll 1
-        for (int rr = 0; rr < rounds; ++rr) {
-          const int i = rr * kTThreads + threadIdx.x;
+        for (int r0 = 0; r0 < cnt; r0 += 32) {
+          const int i = r0 + lane;
           const bool have = i < cnt;
-          const uint32_t e = have ? list[i] : 0u;
-          const int j = int(e & 2047u), b = int((e >> 11) & 255u);
+          const uint32_t e = have ? (pass == 0 ? region[i] : region[kWPerWarp - 1 - i]) : 0u;
+          const int j = int(e & 4095u), b = int((e >> 12) & 255u);
           float x = 0.f, y = 0.f, zc = 0.f;
           if (have) load(j, x, y, zc);
           const float dx = (x + sx) + lx;
@@ -639,7 +635,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
               if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
               if (MODE == kModeDense) {
                 const uint32_t dk = dense_key(kx, npix, o.nblk);
-                atomicAdd(o.hist + (dk >> kOffBits), 1u);
+                atomicAdd(ghist + (dk >> kOffBits), 1u);
                 const unsigned long long at = atomicAdd(o.dense_count, 1ull);
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
               }
@@ -650,45 +646,58 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
             if (have && queued) o.keys[p] = ok ? key : kKeyUndecided;
           } else if (MODE == kModeDirect) {
             if (ok) atomicAdd(o.counts + key, 1);
-          } else if (have) {
-            uint32_t dk = kSentinel;
+          } else {
+            uint32_t dk = 0u;
             if (ok) {
               const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
               const uint32_t bucket = uint32_t(b) * uint32_t(o.nblk) + blk;
               dk = (bucket << kOffBits) | (uint32_t(pix) - blk * uint32_t(kBlockPix));
-              if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
-              else atomicAdd(o.hist + bucket, 1u);
+              if (o.smem_hist) hist16_inc(h32, ghist, bucket);
+              else atomicAdd(ghist + bucket, 1u);
             }
-            kstage[slot0 + i] = dk;
+            dense_append(fc.wc, ok, dk, o);
           }
           fc.n_keyed += ok;
         }
       }
-      // ---- F: one reservation per round for the staged keys
-      if (MODE == kModeDense) {
-        __syncthreads();
-        const int total = NE + NC;
-        if (threadIdx.x == 0)
-          flush_base_s = total ? atomicAdd(o.dense_count, (unsigned long long)total) : 0ull;
-        __syncthreads();
-        const int64_t fb = (int64_t)flush_base_s;
-        for (int i = threadIdx.x; i < total; i += kTThreads)
-          if (fb + i < o.dense_cap) o.dense[fb + i] = kstage[i];
-      }
-      __syncthreads();                         // lists and staged keys consumed
+      __syncwarp();
     }
-    if (threadIdx.x == 0 && issued < mine) issue(issued++);
+    // this warp is done with stage s; the last warp refills it
+    if (lane == 0) {
+      __threadfence_block();
+      const int prev = atomicAdd(&done_s[s], 1);
+      if (prev == kWWarps - 1) {
+        atomicExch(&done_s[s], 0);
+        if (k + kWStages < mine) issue(k + kWStages);
+      }
+    }
+    __syncwarp();
   }
-  if (abort_s) {
-    // a wait ran out: wait (bounded) for the copies still in flight, report
-    if (threadIdx.x == 0) {
+  if (aborted) {
+    // a wait ran out: report, then wait (bounded) for the copies that may
+    // still be in flight into this block's shared memory, and leave
+    if (lane == 0) {
       atomicAdd(&qs.cnt->timeouts, 1ull);
-      for (int64_t kk = k; kk < issued; ++kk)
-        mbar_wait(&bar[kk % kStages], uint32_t((kk / kStages) & 1));
+      for (int64_t kk = k; kk < mine && kk < k + kWStages; ++kk)
+        mbar_wait(&bar[kk % kWStages], uint32_t((kk / kWStages) & 1));
     }
     return;
   }
-  fast_finish<MODE>(fc, o, qs, hist_s);
+  // ---- end: close the warp's chunks, counters, bucket counts
+  if (MODE == kModeDense) dense_close(fc.wc, o);
+  queue_close(fc.qc, qs.q1, qs.cap1);
+  const unsigned long long ni = warp_sum(fc.n_invalid), nk = warp_sum(fc.n_keyed);
+  if (lane == 0) {
+    if (ni) atomicAdd(&qs.cnt->invalid, ni);
+    if (nk) atomicAdd(&qs.cnt->keyed, nk);
+  }
+  if (MODE == kModeDense && o.smem_hist) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < o.nbuckets; i += blockDim.x) {
+      const uint32_t v = (h32[i >> 1] >> ((i & 1) << 4)) & 0xFFFFu;
+      if (v) atomicAdd(ghist + i, v);
+    }
+  }
 }
 
 // ------------------------------------------------ refine and exact stages --
@@ -1295,7 +1304,8 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     }
   }
   // fast stage per box
-  const int tma_smem = kStages * kTChunk * 12 + 3 * kTChunk * 4 + (plan.mode == kModeDense ? smem : 0);
+  const int tma_smem = kWStages * kWChunk * 12 + kWChunk * 4 +
+                       (plan.mode == kModeDense && plan.smem_hist ? ((plan.nbuckets + 1) / 2) * 4 : 0);
   for (int k = 0; k < nbox; ++k) {
     if (n[k] == 0) continue;
     const bool tma = (reinterpret_cast<uintptr_t>(xyz[k]) & 15) == 0;
@@ -1304,7 +1314,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
 #define UFC_LAUNCH_TMA(M)                                                                      \
   UFC_CUDA(c, cudaFuncSetAttribute(k_fast_tma<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                    tma_smem));                                                  \
-  k_fast_tma<M><<<c->num_sms, kTThreads, tma_smem, c->stream>>>(xyz[k], n[k], k, bp.box[k], st, \
+  k_fast_tma<M><<<c->num_sms, kWThreads, tma_smem, c->stream>>>(xyz[k], n[k], k, bp.box[k], st, \
                                                                  lp, bd, nside, (int32_t)npix, o, qs)
       if (plan.mode == kModeDense) { UFC_LAUNCH_TMA(kModeDense); }
       else if (plan.mode == kModeDirect) { UFC_LAUNCH_TMA(kModeDirect); }
