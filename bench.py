@@ -159,6 +159,97 @@ def cpu_baseline(w, parts_host, counts_host, A, C, dAC, seconds_budget=20.0):
     }
 
 
+# ------------------------------------------------- batched vs serial leg ----
+def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8):
+    """Covariance of n_real realisations of the nested Nside-512 map, each box
+    holding Poisson(f n_side^3) particles, f ~ U(0.5, 1.5): one graph-captured
+    ufc_batched_stats call against the same maps one at a time through
+    ufc_bin + ufc_kappa_stats + ufc_stats_vector + ufc_welford_update.
+
+    Positions come from nbuf seeded buffers per box, 1.5 n_side^3 (+6 sigma)
+    particles each; realisation r takes its own seeded count and a seeded
+    48-byte-aligned start inside buffer r mod nbuf, so every realisation is a
+    different particle set of its drawn size."""
+    import torch
+    from paper_1801_05745_gb300 import workloads
+    wb = workloads.batched(n_real, n_side)
+    z, chi, split = shells(wb, api=api)
+    cosmo = api.make_cosmo(wb.omega_m, wb.h, 1)
+    src = api.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    mean = wb.boxes[0].n
+    cap = int(1.5 * mean + 6 * (1.5 * mean) ** 0.5) + 8
+    bufs = [[synth.particles_torch(cap, wb.boxes[k].L, wb.boxes[k].sigma,
+                                   synth.seed_for(4, 1000 + i, k), device=dev) for k in range(2)]
+            for i in range(nbuf)]
+    obs = [[1000.0] * 3, [3200.0] * 3]
+    rng = np.random.default_rng(synth.seed_for(4, 999, 0))
+    xyz, boxes, A, C, n_tot = [], [], [], [], 0
+    for r in range(n_real):
+        row, brow = [], []
+        for k in range(2):
+            n_rk = min(synth.poisson_count(mean, synth.seed_for(4, r, k)), cap)
+            o = 4 * int(rng.integers(0, (cap - n_rk) // 4 + 1))
+            row.append(bufs[r % nbuf][k][o:o + n_rk])
+            lo_, hi_ = (0, split) if k == 0 else (split, wb.nshell)
+            brow.append(api.make_box(wb.boxes[k].L, obs[k], n_rk, lo_, hi_))
+            n_tot += n_rk
+        a, _, c = api.kappa_coeffs(cosmo, brow, z, wb.nside, src)
+        xyz.append(row)
+        boxes.append(brow)
+        A.append(a)
+        C.append(c)
+    A, C = np.array(A), np.array(C)
+    npix = 12 * wb.nside ** 2
+    counts = torch.empty((wb.nshell, npix), dtype=torch.int32, device=dev)
+    kap = torch.empty(npix, dtype=torch.float32, device=dev)
+    nb = wb.pdf_bins
+    d = 6 + nb
+    ctx.reserve(wb.nside, wb.nshell, max(x.shape[0] for row in xyz for x in row))
+    ctx.bin(xyz[0], boxes[0], chi, wb.nside, counts=counts)
+    _, m0, _ = ctx.kappa_stats(counts, A[0], C[0], -1.0, 1.0, nb, kappa=kap)
+    m0 = m0.cpu().numpy()
+    lo, hi = float(m0[0] - 6 * m0[1] ** 0.5), float(m0[0] + 6 * m0[1] ** 0.5)
+    vec = torch.empty(d, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def serial(state):
+        for r in range(n_real):
+            ctx.bin(xyz[r], boxes[r], chi, wb.nside, counts=counts)
+            _, mom, pdf = ctx.kappa_stats(counts, A[r], C[r], lo, hi, nb, kappa=kap)
+            ctx.stats_vector(mom, pdf, out=vec)
+            ctx.welford_update(vec.view(1, d), state)
+
+    def batched(state):
+        ctx.batched_stats(xyz, boxes, chi, wb.nside, A, C, lo, hi, nb, state, graph=True,
+                          counts=counts, kappa=kap)
+
+    out = {}
+    states = {}
+    for name, fn_ in (("serial", serial), ("batched", batched)):
+        fn_(api.welford_state(d, dev))             # warm-up (graph instantiation, workspace)
+        st = api.welford_state(d, dev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn_(st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"ms": ms, "maps_per_s": n_real / (ms * 1e-3),
+                     "gparticles_per_s": n_tot / (ms * 1e-3) / 1e9}
+        states[name] = st
+    out["states_equal"] = bool(torch.allclose(states["serial"], states["batched"], rtol=1e-9,
+                                              atol=0.0))
+    out["speedup"] = out["serial"]["ms"] / out["batched"]["ms"]
+    out["config"] = {"workload": wb.name, "realisations": n_real, "nside": wb.nside,
+                     "nshell": wb.nshell, "particles": n_tot,
+                     "per_box": f"Poisson(f {n_side}^3), f ~ U(0.5, 1.5)",
+                     "position_buffers": nbuf}
+    del bufs, xyz
+    return out
+
+
 # ---------------------------------------------------------- reference arm ----
 def run_reference(args):
     """The oracle as the reference arm: each step bins a bounded particle
@@ -219,6 +310,9 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=1_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-real", type=int, default=150)
+    ap.add_argument("--batched-side", type=int, default=512)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -269,8 +363,11 @@ def main():
     m0 = mom.cpu().numpy()
     lo, hi = float(m0[0] - 6 * m0[1] ** 0.5), float(m0[0] + 6 * m0[1] ** 0.5)
 
-    def step():
-        ctx.bin(parts, boxes, chi, w.nside, counts=counts)
+    def step(host=None):
+        if host is None:
+            ctx.bin(parts, boxes, chi, w.nside, counts=counts)
+        else:                                    # host buffers through ufc_bin_host
+            ctx.bin_host(host, boxes, chi, w.nside, counts=counts)
         _, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, w.pdf_bins, kappa=kap)
         ctx.stats_vector(mom, pdf, out=vec)
         ctx.welford_update(vec.view(1, d), wstate)
@@ -334,7 +431,7 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "particles_per_gpu": n_total, "boxes": "2000 and 6400 Mpc/h",
                    "nside": w.nside, "nshell": w.nshell, "source": "Smail n(z) a=2 b=1.5 z0=0.5",
-                   "l2": "inputs larger than L2 (25.8 GB of particles per step)",
+                   "l2": f"inputs larger than L2 ({12 * n_total / 1e9:.1f} GB of particles per step)",
                    "parallelism": f"realisations x{world}"},
         "kappa_maps_per_s": world * 1e3 / ms,
         "roofline": roof,
@@ -350,7 +447,13 @@ def main():
         "clocks": clk,
     }
 
-    # end to end: particles from pinned host memory through the C ABI each step
+    if not args.no_batched:
+        line["batched_vs_serial"] = batched_leg(ctx, api, synth, dev, args.batched_real,
+                                                args.batched_side)
+
+    # end to end: particles from pinned host memory through the C ABI each
+    # step (ufc_bin_host copies them in chunks, overlapped with the binning),
+    # moments and PDF back to pinned host memory
     if not args.no_e2e:
         host = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True) for p in parts]
         for h_, p_ in zip(host, parts):
@@ -360,9 +463,7 @@ def main():
         ke = max(2, min(args.steps, 4))
 
         def e2e_step():
-            for h_, p_ in zip(host, parts):
-                p_.copy_(h_, non_blocking=True)
-            mom, pdf, grad = step()
+            mom, pdf, grad = step(host)
             out_h[:10].copy_(mom, non_blocking=True)
             out_h[10:].copy_(pdf.to(torch.float64), non_blocking=True)
         e2e_step()

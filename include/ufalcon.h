@@ -101,8 +101,9 @@ ufc_status ufc_set_stream(ufc_ctx *ctx, void *stream);
 ufc_status ufc_synchronize(ufc_ctx *ctx);
 /* Message of the last error on this context ("" if none). */
 const char *ufc_last_error(const ufc_ctx *ctx);
-/* Pre-allocates the workspace for binning up to n_max particles (times the
- * image count) at (nside, nshell), so later calls allocate nothing. */
+/* Pre-allocates the workspace of a ufc_bin call with up to two boxes and up
+ * to n_max particle images (particles times images) at (nside, nshell), so
+ * that such calls allocate nothing. */
 ufc_status ufc_reserve(ufc_ctx *ctx, int32_t nside, int32_t nshell, int64_t n_max);
 
 /* Kernel timing (tracing; the paper has no counterpart).  While enabled,
@@ -166,6 +167,23 @@ ufc_status ufc_bin(ufc_ctx *ctx, const float *const *xyz_dev, const int64_t *n,
                    const ufc_box *boxes, int32_t nbox, const double *chi_edges,
                    int32_t nshell, int32_t nside, int32_t flags,
                    int32_t *counts_dev);
+/* ufc_bin with the positions in host memory (end-to-end use; the paper's
+ * particles arrive from the simulation's output on the host).  Box k's
+ * xyz_host[k] (n[k] particles, 12 bytes each) is copied into a device
+ * staging buffer owned by the context (grown on demand, kept for later
+ * calls) in chunks of about 31M particles on a second stream of the
+ * context; the fast stage of each chunk starts on the context stream as
+ * soon as the chunk has landed, so transfer and binning overlap.  Results
+ * are identical to ufc_bin's.  Page-locked host memory (cudaHostAlloc,
+ * cudaHostRegister) lets the copies run asynchronously; pageable memory
+ * works, the copies then serialise with the host.  The host buffers must
+ * not change until the call's work has finished (ufc_synchronize).
+ * UFC_ERR_UNSUPPORTED while the context stream is capturing a graph.
+ * Asynchronous otherwise, like ufc_bin. */
+ufc_status ufc_bin_host(ufc_ctx *ctx, const float *const *xyz_host, const int64_t *n,
+                        const ufc_box *boxes, int32_t nbox, const double *chi_edges,
+                        int32_t nshell, int32_t nside, int32_t flags,
+                        int32_t *counts_dev);
 /* Diagnostics of the last ufc_bin/ufc_keys call (synchronises):
  * info[0] invalid particles, info[1] particle-images with a key,
  * info[2] decisions refined past the FP32 stage, info[3] past the

@@ -84,6 +84,7 @@ _SIGS = {
                          P, P, P, P, P],
     "ufc_keys": [P, P, I64, ctypes.POINTER(Box), P, I32, I32, P],
     "ufc_bin": [P, P, P, P, I32, P, I32, I32, I32, P],
+    "ufc_bin_host": [P, P, P, P, I32, P, I32, I32, I32, P],
     "ufc_bin_info": [P, P],
     "ufc_kappa_stats": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_kappa_backward": [P, P, I32, I32, P, D, D, D, P, P, P, P, P, P],
@@ -241,16 +242,33 @@ class Context:
         ns = (I64 * len(xs))(*[x.numel() // 3 for x in xs])
         arr = (Box * len(boxes))(*boxes)
         self._stream()
-        flags = UFC_BIN_ACCUMULATE if accumulate else 0
-        if path == "direct":
-            flags |= UFC_BIN_FORCE_DIRECT
-        elif path == "dense":
-            flags |= UFC_BIN_FORCE_DENSE
-        elif path is not None:
-            raise ValueError(f"unknown binning path {path!r}")
+        flags = _bin_flags(accumulate, path)
         self._ck(_lib.ufc_bin(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P), ctypes.cast(arr, P),
                               len(boxes), _np_ptr(chi), S, nside, flags, P(counts.data_ptr())),
                  "ufc_bin")
+        return counts
+
+    def bin_host(self, xyz_list, boxes, chi_edges, nside: int, counts=None, accumulate=False,
+                 path: str | None = None):
+        """bin() with the positions in host memory (ufc_bin_host): float32
+        [n, 3] CPU tensors (page-locked for overlapped copies) or numpy
+        arrays.  They must stay unchanged until the stream has finished."""
+        import torch
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        S = len(chi) - 1
+        npix = 12 * nside * nside
+        xs = [_host_f32(x) for x in xyz_list]
+        if counts is None:
+            counts = torch.empty((S, npix), dtype=torch.int32, device=f"cuda:{self.device}")
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.numel() == S * npix
+        ptrs = (P * len(xs))(*[P(a) for a, _ in xs])
+        ns = (I64 * len(xs))(*[m // 3 for _, m in xs])
+        arr = (Box * len(boxes))(*boxes)
+        self._stream()
+        self._ck(_lib.ufc_bin_host(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P),
+                                   ctypes.cast(arr, P), len(boxes), _np_ptr(chi), S, nside,
+                                   _bin_flags(accumulate, path), P(counts.data_ptr())),
+                 "ufc_bin_host")
         return counts
 
     def bin_info(self):
@@ -375,6 +393,31 @@ class Context:
 def welford_state(d: int, device="cuda"):
     import torch
     return torch.zeros(1 + d + d * d, dtype=torch.float64, device=device)
+
+
+def _bin_flags(accumulate, path):
+    flags = UFC_BIN_ACCUMULATE if accumulate else 0
+    if path == "direct":
+        flags |= UFC_BIN_FORCE_DIRECT
+    elif path == "dense":
+        flags |= UFC_BIN_FORCE_DENSE
+    elif path is not None:
+        raise ValueError(f"unknown binning path {path!r}")
+    return flags
+
+
+def _host_f32(x):
+    """(address, element count) of a contiguous float32 host array."""
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("expected a contiguous float32 CPU tensor")
+        return x.data_ptr(), x.numel()
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags.c_contiguous:
+            raise TypeError("expected a C-contiguous float32 array")
+        return x.ctypes.data, x.size
+    raise TypeError("expected a float32 CPU tensor or numpy array")
 
 
 def _dev_f32(x, device):

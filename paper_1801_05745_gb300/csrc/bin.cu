@@ -34,7 +34,7 @@ constexpr int kOffBits = 15;            // offset bits in a dense key
 constexpr uint32_t kSentinel = 0xFFFFFFFFu;
 constexpr int kChunk = 2048;            // dense keys reserved per warp at a time
 constexpr int kGroupBits = 8;           // buckets per group = 256
-constexpr int kSmemHistMax = 49152;     // buckets counted in shared memory (16-bit, 96 KB)
+constexpr int kSmemHistMax = 45056;     // buckets counted in shared memory
 constexpr int kFastThreads = 512;
 
 struct KeyOut {
@@ -170,28 +170,38 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 }
 
 // ----------------------------------------------------------- fast stage ----
-constexpr int kLutBits = 11;                 // shell lookup table over r^2
+// Shell lookup table over r^2.  Bin i holds the r2 values whose FP32
+// v = fminf(r2 * scale, kLut - 1) rounds to i; its low 15 bits count the
+// edges e certainly at or below every such r2 (hi2[e] <= the bin's lowest
+// possible r2), and bit 15 is set unless the next edge is certainly above
+// every such r2 (lo2[e0] > the bin's highest possible r2).  A clean bin
+// gives the shell with one load; the others scan the edges (exact).
+constexpr int kLutBits = 13;
 constexpr int kLut = 1 << kLutBits;
+constexpr uint16_t kLutScan = 0x8000;
 
 struct FastShared {
   float lo2[kMaxShells + 2], hi2[kMaxShells + 2];
   float shf[3][kMaxImg1D], shlo[3][kMaxImg1D];
-  uint16_t lut[kLut];                        // edges with lo2 <= bin start
+  uint16_t lut[kLut];
 };
 
-// Shell of r2 via the lookup table: the table gives the edge count at the
-// start of r2's bin; a short scan moves past edges below r2, then the band
-// test of shell_fast applies.  -1 outside, -2 undecided.
+// Shell of r2 (finite, >= 0) among the box's shells [lo, hi): -1 outside,
+// -2 undecided.
 __device__ __forceinline__ int32_t shell_lut(const FastShared& fs, int32_t lo, int32_t hi,
                                              float lut_scale, float r2) {
-  if (r2 < fs.lo2[lo]) return -1;
-  if (r2 >= fs.hi2[hi]) return -1;
-  const int bin = min(kLut - 1, __float2int_rz(r2 * lut_scale));
-  int a = min(max(int(fs.lut[bin]) - 1, lo), hi);
-  while (a > lo && r2 < fs.lo2[a]) --a;         // the bin index may round up
-  while (a < hi && r2 >= fs.lo2[a + 1]) ++a;    // r2 in [lo2[a], lo2[a+1])
-  if (r2 < fs.hi2[a]) return -2;
-  return (a < hi) ? a : -1;
+  const float v = fminf(r2 * lut_scale, float(kLut - 1));
+  const int bin = __float_as_int(v + 8388608.0f) - 0x4B000000;   // round(v), exact
+  const uint32_t e = fs.lut[bin];
+  int a = int(e & 0x7FFFu) - 1;
+  if (e & kLutScan) {
+    for (;;) {                                  // ends at the +inf sentinel
+      if (r2 < fs.lo2[a + 1]) break;            // certainly below edge a+1
+      if (r2 < fs.hi2[a + 1]) return -2;        // inside edge a+1's band
+      ++a;
+    }
+  }
+  return (a >= lo && a < hi) ? a : -1;
 }
 
 struct FastCtx {
@@ -304,7 +314,7 @@ struct LutParam { uint16_t v[kLut]; float scale; };
 // Fast stage with plain per-thread loads (any 4-byte aligned input).
 template <int MODE>
 __global__ void __launch_bounds__(kFastThreads)
-k_fast(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
+k_fast(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_id, BoxGeom bg,
        ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
   extern __shared__ uint32_t hist_s[];
   __shared__ FastShared fs;
@@ -324,19 +334,13 @@ k_fast(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
       y = __ldg(xyz + 3 * p + 1);
       zc = __ldg(xyz + 3 * p + 2);
     }
-    fast_particle<MODE>(have, x, y, zc, p, box_id, bg, fs, lp.scale, st, bd, N, npix, o, qs,
-                        hist_s, fc);
+    fast_particle<MODE>(have, x, y, zc, p_off + p, box_id, bg, fs, lp.scale, st, bd, N, npix, o,
+                        qs, hist_s, fc);
   }
   fast_finish<MODE>(fc, o, qs, hist_s);
 }
 
-// ---- fast stage fed by bulk asynchronous copies (TMA, 1-D) ----------------
-// Persistent blocks; chunks of kTChunk particles (12 KB per 1024) stream
-// through a ring of kStages shared-memory buffers (72 KB) filled by
-// cp.async.bulk and tracked by mbarriers.  Requires a 16-byte aligned xyz.
-constexpr int kTThreads = 768;
-constexpr int kTChunk = 1536;                 // particles per chunk (18 KB)
-constexpr int kStages = 4;
+// ---- bulk asynchronous copies (1-D TMA) and mbarriers ----------------------
 constexpr long long kWaitLimit = 1ll << 28;   // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -382,71 +386,38 @@ __device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo,
   return key_exact(st, lo, hi, N, npix, x, y, zc, shx, shy, shz);
 }
 
-// Emission of one decided or undecided key (warp-collective).
-template <int MODE>
-__device__ __forceinline__ void fast_emit(bool have, int32_t key, uint32_t dkey, int32_t box_id,
-                                          int img, int64_t p, const BoxGeom& bg,
-                                          const ShellTable& st, int32_t N, int32_t npix,
-                                          const KeyOut& o, const Queues& qs, uint32_t* hist_s,
-                                          FastCtx& fc, float x, float y, float zc, int ii, int jj,
-                                          int kk) {
-  const bool und = have && key == kKeyUndecided;
-  if (!queue_push(fc.qc, und, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
-    key = key_exact_slow(st, bg.shell_lo, bg.shell_hi, N, npix, x, y, zc, bg.sh64[0][ii],
-                         bg.sh64[1][jj], bg.sh64[2][kk]);
-    if (key == kKeyInvalid) ++fc.n_invalid;
-    if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o.nblk);
-  }
-  const bool ok = have && key >= 0;
-  if (MODE == kModeKeys) {
-    if (have) o.keys[p] = key;
-  } else if (MODE == kModeDirect) {
-    if (ok) atomicAdd(o.counts + key, 1);
-  } else {
-    if (ok) {
-      const uint32_t bucket = dkey >> kOffBits;
-      if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
-      else atomicAdd(o.hist + bucket, 1u);
-    }
-    dense_append(fc.wc, ok, dkey, o);
-  }
-  fc.n_keyed += ok;
-}
+// Fast stage fed by bulk copies, warp-autonomous.  Persistent blocks; a ring
+// of kWStages chunks of kWChunk particles streams in by cp.async.bulk
+// (16-byte aligned xyz).  Each warp owns a slice of kWPerWarp particles of
+// every chunk and works through it alone, 32 particles at a time:
+//   A: radius, shell (lookup table) and zone; the belt and cap particles are
+//      appended, with their FP32 observer-relative coordinates, to two
+//      circular pending lists of the warp in shared memory (ballots);
+//   B: whenever a list holds 32 entries, the warp computes their pixels
+//      together, so the pixel code always runs on full warps; keys go to the
+//      dense array through the warp's chunk, bucket counts to 16-bit shared
+//      counters (an overflow at 65536 is carried to the global histogram).
+// A stage is free once every warp has finished A on it (the entries hold
+// copies); the last warp to finish issues the copy that refills it, so the
+// steady state has no block-wide barrier.  Without periodic images the
+// lists carry over from chunk to chunk; an entry keeps its offset in its
+// chunk and the chunk's sequence number modulo 4096, and the lists are
+// drained at least every kWAgeFlush chunks.  With periodic images the lists
+// are drained after every (chunk, image) pass.  Particle p of the launch is
+// element p_off + p of the caller's array (chunked launches of ufc_bin_host).
+constexpr int kWThreads = 768;
+constexpr int kWChunk = 1536;                  // particles per chunk (18 KB)
+constexpr int kWStages = 4;
+constexpr int kWWarps = kWThreads / 32;        // 24
+constexpr int kWPerWarp = kWChunk / kWWarps;   // 64
+constexpr int kWGroups = kWPerWarp / 32;
+constexpr int kWList = 64;                     // entries of one pending list
+constexpr int kWAgeFlush = 1024;
+static_assert(kWPerWarp % 32 == 0 && kWChunk <= 4096 && kMaxShells <= 256,
+              "entry metadata: 8-bit shell, 12-bit offset, 12-bit chunk tag");
+static_assert(kWAgeFlush < 4096, "chunk tags are 12-bit");
 
-// Warp-aggregated append to a shared-memory list of `cap` entries.  A round
-// appends at most one entry per particle of the chunk, so idx < cap always
-// holds; the check keeps any violation inside the list.
-__device__ __forceinline__ void list_push(bool want, uint32_t v, uint32_t* list, int* count,
-                                          int cap) {
-  const unsigned m = __ballot_sync(0xFFFFFFFFu, want);
-  if (m == 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(m));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  const int idx = base + __popc(m & ((1u << lane) - 1u));
-  if (want && idx < cap) list[idx] = v;
-}
-
-// Fast stage fed by bulk copies, warp-autonomous.  A ring of kStages chunks
-// of kTChunk particles streams in by cp.async.bulk.  Each warp owns a fixed
-// slice of kPerWarp particles of every chunk and works through it alone:
-//   A: radius, shell and zone of 32 particles at a time; the warp lists its
-//      belt and cap particles in its own shared-memory region (belt from the
-//      front, cap from the back) with ballots;
-//   B: pixels of the listed particles, 32 at a time, keys appended to the
-//      dense array through the warp's chunk, bucket counts in shared memory;
-// then lane 0 counts the warp out of the stage; the last warp to finish a
-// stage issues the bulk copy that refills it.  No block-wide barrier in the
-// steady state.  Bucket counters are 16-bit halves of 32-bit words; an
-// overflow (65536 particles of one bucket in one block) is carried to the
-// global histogram exactly.
-constexpr int kWThreads = 512;
-constexpr int kWChunk = 3072;                  // particles per chunk (36 KB)
-constexpr int kWStages = 3;
-constexpr int kWWarps = kWThreads / 32;
-constexpr int kWPerWarp = kWChunk / kWWarps;  // 192
+constexpr int kWSmemBase = kWStages * kWChunk * 12 + kWWarps * 2 * kWList * 16;   // ring + lists
 
 __device__ __forceinline__ void hist16_inc(uint32_t* h32, uint32_t* ghist, uint32_t bucket) {
   const uint32_t shift = (bucket & 1u) << 4;
@@ -459,12 +430,12 @@ __device__ __forceinline__ void hist16_inc(uint32_t* h32, uint32_t* ghist, uint3
 
 template <int MODE>
 __global__ void __launch_bounds__(kWThreads, 1)
-k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
+k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_id, BoxGeom bg,
            ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
   extern __shared__ __align__(128) uint8_t dyn[];
-  float* ring = reinterpret_cast<float*>(dyn);                        // [kWStages][3 kWChunk]
-  uint32_t* regions = reinterpret_cast<uint32_t*>(dyn + kWStages * kWChunk * 12);  // [warps][kWPerWarp]
-  uint32_t* h32 = regions + kWChunk;                                 // 16-bit bucket counters
+  float* ring = reinterpret_cast<float*>(dyn);                          // [kWStages][3 kWChunk]
+  float4* lists = reinterpret_cast<float4*>(dyn + kWStages * kWChunk * 12);  // [warps][2][kWList]
+  uint32_t* h32 = reinterpret_cast<uint32_t*>(dyn + kWSmemBase);          // 16-bit counters
   __shared__ FastShared fs;
   __shared__ __align__(8) uint64_t bar[kWStages];
   __shared__ int done_s[kWStages];
@@ -485,10 +456,11 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
 
   const int lo = bg.shell_lo, hi = bg.shell_hi;
   const int n1 = 2 * bg.R + 1;
-  const float lo2_first = fs.lo2[lo], hi2_last = fs.hi2[hi];
+  const bool carry = bg.nimg == 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt_mask = (1u << lane) - 1u;
-  uint32_t* region = regions + warp * kWPerWarp;
+  float4* list_eq = lists + (2 * warp) * kWList;
+  float4* list_cap = list_eq + kWList;
   const int64_t nchunks = (n + kWChunk - 1) / kWChunk;
   const int64_t mine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   auto chunk_bytes = [&](int64_t c) -> uint32_t {
@@ -509,113 +481,121 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
 
   FastCtx fc{{-1, 0}, {-1, 0}, 0, 0};
   uint32_t* ghist = o.hist;
-  int64_t k = 0;
+  int he = 0, ne = 0, hc = 0, nc = 0;          // heads and lengths of the two lists
+  int ii = 0, jj = 0, kk = 0;                  // current image
   bool aborted = false;
-  for (; k < mine; ++k) {
-    const int64_t c = blockIdx.x + k * gridDim.x;
+  int64_t k = 0;
+  for (; k <= mine; ++k) {
+    const bool last = k == mine;               // the final pass only drains the lists
     const int s = int(k % kWStages);
-    // every lane waits on the stage's full barrier (bounded)
-    if (!mbar_wait(&bar[s], uint32_t((k / kWStages) & 1))) {
-      aborted = true;
-      abort_s = 1;
-    }
-    if (__any_sync(0xFFFFFFFFu, aborted) || abort_s) { aborted = true; break; }
-    const float* buf = ring + s * 3 * kWChunk;
-    const uint32_t bytes = chunk_bytes(c);
-    const int64_t base = c * kWChunk;
-    auto load = [&](int j, float& x, float& y, float& zc) {
-      if ((uint32_t)(12 * j + 12) <= bytes) {
-        x = buf[3 * j];
-        y = buf[3 * j + 1];
-        zc = buf[3 * j + 2];
-      } else {                                 // ragged tail outside the bulk copy
-        const int64_t p = base + j;
-        x = __ldg(xyz + 3 * p);
-        y = __ldg(xyz + 3 * p + 1);
-        zc = __ldg(xyz + 3 * p + 2);
+    if (!last) {
+      if (!mbar_wait(&bar[s], uint32_t((k / kWStages) & 1))) {   // every lane waits (bounded)
+        aborted = true;
+        abort_s = 1;
       }
-    };
-    int ii = 0, jj = 0, kk = 0;
+      if (__any_sync(0xFFFFFFFFu, aborted) || abort_s) { aborted = true; break; }
+    }
+    const int64_t kq = last ? (k > 0 ? k - 1 : 0) : k;   // chunk of the newest entries
+    const int64_t base = (blockIdx.x + kq * gridDim.x) * kWChunk;
+    const float* buf = ring + s * 3 * kWChunk;
+    const uint32_t bytes = last ? 0u : chunk_bytes(blockIdx.x + k * gridDim.x);
+    const int nimg = last ? 1 : bg.nimg;
+    const bool drain_all = last || !carry || ((k & (kWAgeFlush - 1)) == kWAgeFlush - 1);
+    ii = jj = kk = 0;
 #pragma unroll 1
-    for (int img = 0; img < bg.nimg; ++img) {
+    for (int img = 0; img < nimg; ++img) {
       if (img) {
         if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
       }
       const float sx = fs.shf[0][ii], sy = fs.shf[1][jj], sz = fs.shf[2][kk];
       const float lx = fs.shlo[0][ii], ly = fs.shlo[1][jj], lz = fs.shlo[2][kk];
-      // ---- A: classify this warp's slice
-      int ne = 0, nc = 0;
-#pragma unroll 2
-      for (int h = 0; h < kWPerWarp / 32; ++h) {
-        const int j = warp * kWPerWarp + 32 * h + lane;
-        const int64_t p = base + j;
-        const bool have = p < n;
-        float x = 0.f, y = 0.f, zc = 0.f;
-        if (have) load(j, x, y, zc);
-        const float dx = (x + sx) + lx;
-        const float dy = (y + sy) + ly;
-        const float dz = (zc + sz) + lz;
-        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-        int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap, 4 invalid
-        int32_t b = 0;
-        if (have) {
-          if (!(r2 <= 3.0e38f)) {              // NaN or overflow: inspect the coordinates
-            if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) cls = 4;
-          } else if (!(r2 >= bd.r2_min)) {     // near the observer (r == 0 is invalid)
-            cls = 1;
-          } else if (r2 >= lo2_first && r2 < hi2_last) {
-            b = shell_lut(fs, lo, hi, lp.scale, r2);
-            if (b == -2) cls = 1;
-            else if (b >= 0) {
-              const float za = fabsf(dz * rsqrtf(r2));
-              cls = za <= bd.z_eq ? 2 : (za > bd.z_cap ? 3 : 1);
-            }
-          }
-        }
-        if (cls == 4 && img == 0) ++fc.n_invalid;
-        const uint32_t entry = uint32_t(j) | (uint32_t(b & 255) << 12);
-        const unsigned meq = __ballot_sync(0xFFFFFFFFu, cls == 2);
-        const unsigned mcap = __ballot_sync(0xFFFFFFFFu, cls == 3);
-        if (cls == 2) region[ne + __popc(meq & lt_mask)] = entry;
-        if (cls == 3) region[kWPerWarp - 1 - (nc + __popc(mcap & lt_mask))] = entry;
-        ne += __popc(meq);
-        nc += __popc(mcap);
-        // undecided images wait in queue 1; outside/invalid are final
-        if (!queue_push(fc.qc, cls == 1, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
-          const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
-                                            bg.sh64[1][jj], bg.sh64[2][kk]);
-          if (kx == kKeyInvalid) ++fc.n_invalid;
-          if (kx >= 0) {
-            ++fc.n_keyed;
-            if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
-            if (MODE == kModeDense) {            // rare: straight to the global histogram
-              const uint32_t dk = dense_key(kx, npix, o.nblk);
-              atomicAdd(ghist + (dk >> kOffBits), 1u);
-              const unsigned long long at = atomicAdd(o.dense_count, 1ull);
-              if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
-            }
-          }
-          if (MODE == kModeKeys && have) o.keys[p] = kx;
-        } else if (MODE == kModeKeys && have && cls != 2 && cls != 3) {
-          o.keys[p] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
-        }
-      }
-      __syncwarp();
-      // ---- B: pixels of this warp's list, 32 at a time (belt, then cap)
 #pragma unroll 1
-      for (int pass = 0; pass < 2; ++pass) {
-        const int cnt = pass == 0 ? ne : nc;
-#pragma unroll 1
-        for (int r0 = 0; r0 < cnt; r0 += 32) {
-          const int i = r0 + lane;
-          const bool have = i < cnt;
-          const uint32_t e = have ? (pass == 0 ? region[i] : region[kWPerWarp - 1 - i]) : 0u;
-          const int j = int(e & 4095u), b = int((e >> 12) & 255u);
+      for (int h = 0; h <= (last ? 0 : kWGroups); ++h) {
+        if (h < kWGroups && !last) {
+          // ---- A: classify 32 particles of this warp's slice
+          const int j = warp * kWPerWarp + 32 * h + lane;
+          const bool have = base + j < n;
+          const int64_t p = p_off + base + j;     // index in the caller's array
           float x = 0.f, y = 0.f, zc = 0.f;
-          if (have) load(j, x, y, zc);
+          if (have) {
+            if ((uint32_t)(12 * j + 12) <= bytes) {
+              x = buf[3 * j];
+              y = buf[3 * j + 1];
+              zc = buf[3 * j + 2];
+            } else {                             // ragged tail outside the bulk copy
+              x = __ldg(xyz + 3 * (base + j));
+              y = __ldg(xyz + 3 * (base + j) + 1);
+              zc = __ldg(xyz + 3 * (base + j) + 2);
+            }
+          }
           const float dx = (x + sx) + lx;
           const float dy = (y + sy) + ly;
           const float dz = (zc + sz) + lz;
+          const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+          int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap, 4 invalid
+          int32_t b = 0;
+          if (have) {
+            if (!(r2 <= 3.0e38f)) {              // NaN or overflow: inspect the coordinates
+              if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) cls = 4;
+            } else if (!(r2 >= bd.r2_min)) {     // near the observer (r == 0 is invalid)
+              cls = 1;
+            } else {
+              b = shell_lut(fs, lo, hi, lp.scale, r2);
+              if (b == -2) cls = 1;
+              else if (b >= 0) {
+                const float za = fabsf(dz * rsqrtf(r2));
+                cls = za <= bd.z_eq ? 2 : (za > bd.z_cap ? 3 : 1);
+              }
+            }
+          }
+          if (cls == 4 && img == 0) ++fc.n_invalid;
+          const uint32_t meta = uint32_t(b & 255) | (uint32_t(j) << 8) | (uint32_t(kq & 4095) << 20);
+          const float4 ent = make_float4(dx, dy, dz, __uint_as_float(meta));
+          const unsigned meq = __ballot_sync(0xFFFFFFFFu, cls == 2);
+          const unsigned mcap = __ballot_sync(0xFFFFFFFFu, cls == 3);
+          if (cls == 2) list_eq[(he + ne + __popc(meq & lt_mask)) & (kWList - 1)] = ent;
+          if (cls == 3) list_cap[(hc + nc + __popc(mcap & lt_mask)) & (kWList - 1)] = ent;
+          ne += __popc(meq);
+          nc += __popc(mcap);
+          // undecided images wait in queue 1; outside/invalid are final
+          if (!queue_push(fc.qc, cls == 1, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
+            const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
+                                              bg.sh64[1][jj], bg.sh64[2][kk]);
+            if (kx == kKeyInvalid) ++fc.n_invalid;
+            if (kx >= 0) {
+              ++fc.n_keyed;
+              if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
+              if (MODE == kModeDense) {            // rare: straight to the global histogram
+                const uint32_t dk = dense_key(kx, npix, o.nblk);
+                atomicAdd(ghist + (dk >> kOffBits), 1u);
+                const unsigned long long at = atomicAdd(o.dense_count, 1ull);
+                if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
+              }
+            }
+            if (MODE == kModeKeys && have) o.keys[p] = kx;
+          } else if (MODE == kModeKeys && have && cls != 2 && cls != 3) {
+            o.keys[p] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
+          }
+        }
+        __syncwarp();
+        // ---- B: pixels of full groups of 32 pending entries (after the
+        // last group of a pass, also of the partial rest when draining)
+        const bool tail = h == (last ? 0 : kWGroups);
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+          const int cnt = pass == 0 ? ne : nc;
+          const int take = cnt >= 32 ? 32 : ((tail && drain_all) ? cnt : 0);
+          if (take == 0) continue;
+          const float4* L = pass == 0 ? list_eq : list_cap;
+          const int head = pass == 0 ? he : hc;
+          const bool have = lane < take;
+          float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (have) ent = L[(head + lane) & (kWList - 1)];
+          if (pass == 0) { he = (he + take) & (kWList - 1); ne -= take; }
+          else { hc = (hc + take) & (kWList - 1); nc -= take; }
+          const float dx = ent.x, dy = ent.y, dz = ent.z;
+          const uint32_t meta = __float_as_uint(ent.w);
+          const int b = int(meta & 255u);
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
           const float rinv = rsqrtf(r2);
           const float z = dz * rinv;
@@ -623,11 +603,16 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
           if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
                                     : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
           const bool ok = have && pix != kKeyUndecided;
-          const int64_t p = base + j;
+          // the entry's particle: chunk from the 12-bit tag, offset j
+          const int64_t ke = kq - ((kq - int64_t(meta >> 20)) & 4095);
+          const int64_t pl = (blockIdx.x + ke * gridDim.x) * kWChunk + int64_t((meta >> 8) & 4095u);
+          const int64_t p = p_off + pl;
           const int32_t key = b * npix + pix;
-          const bool queued = queue_push(fc.qc, have && !ok, qpack(box_id, img, p), qs.q1,
-                                         qs.cap1, &qs.cnt->q1);
-          if (!queued) {
+          const bool queued = queue_push(fc.qc, have && !ok, qpack(box_id, carry ? 0 : img, p),
+                                         qs.q1, qs.cap1, &qs.cnt->q1);
+          if (!queued) {                         // queue full: the FP64 procedure here
+            const float x = __ldg(xyz + 3 * pl), y = __ldg(xyz + 3 * pl + 1),
+                        zc = __ldg(xyz + 3 * pl + 2);
             const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
                                               bg.sh64[1][jj], bg.sh64[2][kk]);
             if (kx >= 0) {
@@ -659,9 +644,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
           }
           fc.n_keyed += ok;
         }
+        __syncwarp();
       }
-      __syncwarp();
     }
+    if (last) break;
     // this warp is done with stage s; the last warp refills it
     if (lane == 0) {
       __threadfence_block();
@@ -678,8 +664,8 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int32_t box_id, BoxGeom bg,
     // still be in flight into this block's shared memory, and leave
     if (lane == 0) {
       atomicAdd(&qs.cnt->timeouts, 1ull);
-      for (int64_t kk = k; kk < mine && kk < k + kWStages; ++kk)
-        mbar_wait(&bar[kk % kWStages], uint32_t((kk / kWStages) & 1));
+      for (int64_t q = k; q < mine && q < k + kWStages; ++q)
+        mbar_wait(&bar[q % kWStages], uint32_t((q / kWStages) & 1));
     }
     return;
   }
@@ -1167,35 +1153,71 @@ struct BinPlan {
   int nblk, nbuckets, ng, smem_hist;
 };
 
-// Grows the workspace for a binning call of total_img particle images at
-// (nside, nshell) with nbox boxes, so that the call itself allocates nothing.
-ufc_status reserve_bin_workspace(ufc_ctx* c, int nbox, int64_t total_img, int nshell, int nside) {
+// Particles per staged chunk of ufc_bin_host: a multiple of kWChunk, so that
+// every chunk starts 16-byte aligned (377 MB).
+constexpr int64_t kHostChunk = (int64_t)kWChunk * 10240;
+
+// Workspace of one binning call of total_img particle images in
+// fast_launches fast-stage launches.  Every warp of every launch (fast,
+// refine, exact) may leave one partly filled queue chunk and one partly
+// filled dense chunk behind.
+struct BinSizes {
+  int64_t cap1, cap2;   // queue slots
+  int64_t dense_cap;    // dense key slots
+  int64_t nb, ng;       // buckets and bucket groups of the dense path
+};
+
+static BinSizes bin_sizes(const ufc_ctx* c, int64_t fast_launches, int64_t total_img,
+                          int nshell, int nside) {
+  BinSizes z{};
+  const int64_t fast_warps = (int64_t)std::max(2 * kFastThreads / 32, kWWarps) * c->num_sms;
+  const int64_t late_warps = 2ll * 4 * c->num_sms * (256 / 32);
+  const int64_t warps = fast_launches * fast_warps + late_warps + 64;
+  z.cap1 = std::max<int64_t>(1 << 20, total_img / 16) + warps * kQChunk;
+  z.cap2 = std::max<int64_t>(1 << 16, z.cap1 / 64) + warps * kQChunk;
+  z.dense_cap = total_img + z.cap1 + warps * kChunk;
   const int64_t npix = 12ll * nside * nside;
-  const int64_t qwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
-                         4ll * c->num_sms * (256 / 32);
-  const int64_t cap1 = std::max<int64_t>(1 << 20, total_img / 16) + qwarps * kQChunk;
-  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64) + qwarps * kQChunk;
-  if (!ws_get(c, kSlotQueue1, cap1 * 8) || !ws_get(c, kSlotQueue2, cap2 * 8)) return UFC_ERR_ALLOC;
-  if (nside >= 64 && npix * nshell * 4 > (32ll << 20) && nshell * (npix / kBlockPix) < (1ll << 17)) {
-    const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
-                           2ll * 4 * c->num_sms * (256 / 32) + 64;
-    const int64_t dense_cap = total_img + cap1 + nwarps * kChunk;
-    const int64_t nb = nshell * (npix / kBlockPix);
-    const int64_t ng = (nb + (1 << kGroupBits) - 1) >> kGroupBits;
-    if (!ws_get(c, kSlotDense, dense_cap * 4) || !ws_get(c, kSlotGrouped, dense_cap * 4) ||
-        !ws_get(c, kSlotBucket16, dense_cap * 2) || !ws_get(c, kSlotHist, nb * 4) ||
-        !ws_get(c, kSlotOff, (nb + 1) * 8) || !ws_get(c, kSlotCursors, (nb + ng + 1) * 8) ||
-        !ws_get(c, kSlotTiles, (size_t)(dense_cap / kScatTile + ng + 1) * sizeof(Tile)))
+  z.nb = nshell * (npix / kBlockPix);
+  z.ng = (z.nb + (1 << kGroupBits) - 1) >> kGroupBits;
+  return z;
+}
+
+// Grows the workspace for a binning call of total_img particle images at
+// (nside, nshell) in fast_launches fast-stage launches (one per non-empty
+// box for device input), so that the call itself allocates nothing.
+ufc_status reserve_bin_workspace(ufc_ctx* c, int64_t fast_launches, int64_t total_img,
+                                 int nshell, int nside) {
+  const int64_t npix = 12ll * nside * nside;
+  const BinSizes z = bin_sizes(c, fast_launches, total_img, nshell, nside);
+  if (!ws_get(c, kSlotQueue1, z.cap1 * 8) || !ws_get(c, kSlotQueue2, z.cap2 * 8))
+    return UFC_ERR_ALLOC;
+  if (nside >= 64 && npix * nshell * 4 > (32ll << 20) && z.nb < (1ll << 17)) {
+    if (!ws_get(c, kSlotDense, z.dense_cap * 4) || !ws_get(c, kSlotGrouped, z.dense_cap * 4) ||
+        !ws_get(c, kSlotBucket16, z.dense_cap * 2) || !ws_get(c, kSlotHist, z.nb * 4) ||
+        !ws_get(c, kSlotOff, (z.nb + 1) * 8) || !ws_get(c, kSlotCursors, (z.nb + z.ng + 1) * 8) ||
+        !ws_get(c, kSlotTiles, (size_t)(z.dense_cap / kScatTile + z.ng + 1) * sizeof(Tile)))
       return UFC_ERR_ALLOC;
   }
   return UFC_OK;
 }
 
+static cudaEvent_t copy_event(ufc_ctx* c, size_t i) {
+  while (c->copy_events.size() <= i) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    c->copy_events.push_back(e);
+  }
+  return c->copy_events[i];
+}
+
 // Runs the key pipeline for nbox boxes.  counts (DIRECT/DENSE) or keys (KEYS).
+// xyz_host (non-NULL, ufc_bin_host): positions in host memory, copied into
+// the staging slot chunk by chunk on the copy stream while the fast stage of
+// the chunks already copied runs; xyz is then ignored.
 ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
                              const int64_t* n, const ufc_box* boxes, int nbox,
                              const double* chi, int nshell, int nside, int flags,
-                             int32_t* counts, int32_t* keys) {
+                             int32_t* counts, int32_t* keys, const float* const* xyz_host) {
   if (nbox < 1 || nbox > kMaxBoxes)
     return set_err(c, UFC_ERR_ARG, "nbox must be in [1,%d]", kMaxBoxes);
   if (nshell < 1 || nshell > kMaxShells)
@@ -1208,6 +1230,26 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   ShellTable st;
   ufc_status s = make_table(c, chi, nshell, st);
   if (s) return s;
+  const float* staged[kMaxBoxes] = {};
+  int64_t fast_launches = 0;
+  if (xyz_host) {
+    size_t total = 0;
+    size_t offs[kMaxBoxes];
+    for (int k = 0; k < nbox; ++k) {
+      if (n[k] < 0) return set_err(c, UFC_ERR_ARG, "n[%d] < 0", k);
+      if (n[k] > 0 && !xyz_host[k]) return set_err(c, UFC_ERR_ARG, "xyz_host[%d] is NULL", k);
+      if (n[k] >= (1ll << 47)) return set_err(c, UFC_ERR_ARG, "n[%d] too large", k);
+      offs[k] = total;
+      total += ((size_t)n[k] * 12 + 255) & ~(size_t)255;
+      fast_launches += (n[k] + kHostChunk - 1) / kHostChunk;
+    }
+    char* stage = (char*)ws_get(c, kSlotStage, total);
+    if (!stage) return UFC_ERR_ALLOC;
+    for (int k = 0; k < nbox; ++k) staged[k] = reinterpret_cast<const float*>(stage + offs[k]);
+    xyz = staged;
+  } else {
+    for (int k = 0; k < nbox; ++k) fast_launches += n[k] > 0;
+  }
   BoxesParam bp;
   std::memset(&bp, 0, sizeof bp);
   int64_t total_img = 0;
@@ -1250,20 +1292,20 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     plan.nblk = (int)(npix / kBlockPix);
     plan.nbuckets = nshell * plan.nblk;
     plan.ng = (plan.nbuckets + (1 << kGroupBits) - 1) >> kGroupBits;
-    plan.smem_hist = plan.nbuckets <= kSmemHistMax;
+    // bucket counters in shared memory when both fast kernels still fit
+    const size_t fixed = sizeof(FastShared) + 1024;
+    plan.smem_hist = plan.nbuckets <= kSmemHistMax &&
+                     kWSmemBase + ((plan.nbuckets + 1) / 2) * 4 + fixed <= (size_t)c->smem_optin &&
+                     (size_t)plan.nbuckets * 4 + fixed <= (size_t)c->smem_optin;
   }
 
   // workspace
-  // queue slots: expected undecided entries plus one partly used chunk per warp
-  const int64_t qwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
-                         4ll * c->num_sms * (256 / 32);
-  const int64_t cap1 = std::max<int64_t>(1 << 20, total_img / 16) + qwarps * kQChunk;
-  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64) + qwarps * kQChunk;
+  const BinSizes z = bin_sizes(c, fast_launches, total_img, nshell, nside);
   Queues qs;
-  qs.cap1 = cap1;
-  qs.cap2 = cap2;
-  qs.q1 = (uint64_t*)ws_get(c, kSlotQueue1, cap1 * 8);
-  qs.q2 = (uint64_t*)ws_get(c, kSlotQueue2, cap2 * 8);
+  qs.cap1 = z.cap1;
+  qs.cap2 = z.cap2;
+  qs.q1 = (uint64_t*)ws_get(c, kSlotQueue1, z.cap1 * 8);
+  qs.q2 = (uint64_t*)ws_get(c, kSlotQueue2, z.cap2 * 8);
   if (!qs.q1 || !qs.q2) return UFC_ERR_ALLOC;
   qs.cnt = (BinCounters*)c->counters;
   UFC_CUDA(c, cudaMemsetAsync(qs.cnt, 0, sizeof(BinCounters), c->stream));
@@ -1273,12 +1315,9 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   o.keys = keys;
   o.counts = counts;
   o.dense_count = &qs.cnt->dense;
-  int grid = 0, smem = 0;
+  int smem = 0;
   if (plan.mode == kModeDense) {
-    // every warp of every launch may leave one partly filled chunk
-    const int64_t nwarps = (int64_t)nbox * 2 * c->num_sms * (kTThreads / 32) +
-                           2ll * 4 * c->num_sms * (256 / 32) + 64;
-    o.dense_cap = total_img + cap1 + nwarps * kChunk;   // + sentinel slots of undecided images
+    o.dense_cap = z.dense_cap;
     o.dense = (uint32_t*)ws_get(c, kSlotDense, o.dense_cap * 4);
     o.hist = (uint32_t*)ws_get(c, kSlotHist, (size_t)plan.nbuckets * 4);
     if (!o.dense || !o.hist) return UFC_ERR_ALLOC;
@@ -1294,44 +1333,74 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   // shell lookup table over r^2: lut[i] = edges with lo2 <= i / scale
   LutParam lp;
   {
-    const double r2max = (double)st.hi2[nshell] * (1.0 + 1e-6) + 1e-30;
-    lp.scale = (float)(kLut / r2max);
-    int e = 0;
+    // bins 0 .. kLut-2 cover [0, hi2[nshell]]
+    const double top = std::max((double)st.hi2[nshell], 1e-30);
+    lp.scale = (float)std::min((kLut - 2) / top, 1e30);
+    const double sc = (double)lp.scale;
+    int e0 = 0;
     for (int i = 0; i < kLut; ++i) {
-      const double v = (double)i / (double)lp.scale;
-      while (e <= nshell && (double)st.lo2[e] <= v) ++e;
-      lp.v[i] = (uint16_t)e;
+      // r2 whose fminf(r2 * scale, kLut - 1) rounds to i has r2 * scale in
+      // [i - 1/2, i + 1/2] up to the product's rounding (< 2^-11 here);
+      // the range is widened by 2^-10
+      const double rlo = ((double)i - 0.5 - 0x1p-10) / sc;
+      const double rhi = (i == kLut - 1) ? INFINITY : ((double)i + 0.5 + 0x1p-10) / sc;
+      while (e0 <= nshell && (double)st.hi2[e0] <= rlo) ++e0;
+      const bool clean = e0 > nshell || (double)st.lo2[e0] > rhi;
+      lp.v[i] = (uint16_t)(e0 | (clean ? 0 : kLutScan));
     }
   }
-  // fast stage per box
-  const int tma_smem = kWStages * kWChunk * 12 + kWChunk * 4 +
+  // fast stage: one launch per box, or per staged chunk for host input
+  const int tma_smem = kWSmemBase +
                        (plan.mode == kModeDense && plan.smem_hist ? ((plan.nbuckets + 1) / 2) * 4 : 0);
+  if (xyz_host) {
+    if (!c->copy_stream)
+      UFC_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    // the copies overwrite the staging slot only after the work already on
+    // the context stream (which may still read it) has finished
+    cudaEvent_t e0 = copy_event(c, 0);
+    if (!e0) return set_err(c, UFC_ERR_CUDA, "cudaEventCreate failed");
+    UFC_CUDA(c, cudaEventRecord(e0, c->stream));
+    UFC_CUDA(c, cudaStreamWaitEvent(c->copy_stream, e0, 0));
+  }
+  size_t nev = 1;
   for (int k = 0; k < nbox; ++k) {
-    if (n[k] == 0) continue;
-    const bool tma = (reinterpret_cast<uintptr_t>(xyz[k]) & 15) == 0;
-    ProfScope ps_(c, "k_fast");
-    if (tma) {
-#define UFC_LAUNCH_TMA(M)                                                                      \
-  UFC_CUDA(c, cudaFuncSetAttribute(k_fast_tma<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                   tma_smem));                                                  \
-  k_fast_tma<M><<<c->num_sms, kWThreads, tma_smem, c->stream>>>(xyz[k], n[k], k, bp.box[k], st, \
+    const int64_t step = xyz_host ? kHostChunk : std::max<int64_t>(n[k], 1);
+    for (int64_t p0 = 0; p0 < n[k]; p0 += step) {
+      const int64_t cnt = std::min(step, n[k] - p0);
+      const float* src = xyz[k] + 3 * p0;
+      if (xyz_host) {
+        UFC_CUDA(c, cudaMemcpyAsync(const_cast<float*>(src), xyz_host[k] + 3 * p0,
+                                    (size_t)cnt * 12, cudaMemcpyHostToDevice, c->copy_stream));
+        cudaEvent_t e = copy_event(c, nev++);
+        if (!e) return set_err(c, UFC_ERR_CUDA, "cudaEventCreate failed");
+        UFC_CUDA(c, cudaEventRecord(e, c->copy_stream));
+        UFC_CUDA(c, cudaStreamWaitEvent(c->stream, e, 0));
+      }
+      const bool tma = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+      ProfScope ps_(c, "k_fast");
+      if (tma) {
+#define UFC_LAUNCH_TMA(M)                                                                       \
+  UFC_CUDA(c, cudaFuncSetAttribute(k_fast_tma<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                   tma_smem));                                                   \
+  k_fast_tma<M><<<c->num_sms, kWThreads, tma_smem, c->stream>>>(src, cnt, p0, k, bp.box[k], st,  \
                                                                  lp, bd, nside, (int32_t)npix, o, qs)
-      if (plan.mode == kModeDense) { UFC_LAUNCH_TMA(kModeDense); }
-      else if (plan.mode == kModeDirect) { UFC_LAUNCH_TMA(kModeDirect); }
-      else { UFC_LAUNCH_TMA(kModeKeys); }
+        if (plan.mode == kModeDense) { UFC_LAUNCH_TMA(kModeDense); }
+        else if (plan.mode == kModeDirect) { UFC_LAUNCH_TMA(kModeDirect); }
+        else { UFC_LAUNCH_TMA(kModeKeys); }
 #undef UFC_LAUNCH_TMA
-    } else {
-      const int ssm = plan.mode == kModeDense ? smem : 0;
-#define UFC_LAUNCH_PLAIN(M)                                                                     \
+      } else {
+        const int ssm = plan.mode == kModeDense ? smem : 0;
+#define UFC_LAUNCH_PLAIN(M)                                                                      \
   UFC_CUDA(c, cudaFuncSetAttribute(k_fast<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, ssm)); \
-  k_fast<M><<<(ssm > 0 ? 1 : 2) * c->num_sms, kFastThreads, ssm, c->stream>>>(                    \
-      xyz[k], n[k], k, bp.box[k], st, lp, bd, nside, (int32_t)npix, o, qs)
-      if (plan.mode == kModeDense) { UFC_LAUNCH_PLAIN(kModeDense); }
-      else if (plan.mode == kModeDirect) { UFC_LAUNCH_PLAIN(kModeDirect); }
-      else { UFC_LAUNCH_PLAIN(kModeKeys); }
+  k_fast<M><<<(ssm > 0 ? 1 : 2) * c->num_sms, kFastThreads, ssm, c->stream>>>(                     \
+      src, cnt, p0, k, bp.box[k], st, lp, bd, nside, (int32_t)npix, o, qs)
+        if (plan.mode == kModeDense) { UFC_LAUNCH_PLAIN(kModeDense); }
+        else if (plan.mode == kModeDirect) { UFC_LAUNCH_PLAIN(kModeDirect); }
+        else { UFC_LAUNCH_PLAIN(kModeKeys); }
 #undef UFC_LAUNCH_PLAIN
+      }
+      UFC_CUDA(c, cudaGetLastError());
     }
-    UFC_CUDA(c, cudaGetLastError());
   }
   const int lgrid = 4 * c->num_sms;
   if (plan.mode == kModeDense) {

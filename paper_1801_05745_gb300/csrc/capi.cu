@@ -13,7 +13,7 @@ namespace ufc {
 ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
                              const int64_t* n, const ufc_box* boxes, int nbox,
                              const double* chi, int nshell, int nside, int flags,
-                             int32_t* counts, int32_t* keys);
+                             int32_t* counts, int32_t* keys, const float* const* xyz_host);
 ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
                            const double* A, double C, double lo, double hi, int nbins,
                            float* kappa, double* moments, int64_t* pdf);
@@ -29,7 +29,8 @@ ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int
 ufc_status run_welford_merge(ufc_ctx* c, double* a, const double* b, int d);
 ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, double* mean,
                                 double* cov, double* corr);
-ufc_status reserve_bin_workspace(ufc_ctx* c, int nbox, int64_t total_img, int nshell, int nside);
+ufc_status reserve_bin_workspace(ufc_ctx* c, int64_t fast_launches, int64_t total_img,
+                                 int nshell, int nside);
 ufc_status cosmo_chi_edges(const ufc_cosmo& c, const double* z, int n, double* chi);
 ufc_status cosmo_z_of_chi(const ufc_cosmo& c, const double* chi, int n, double* zout);
 ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
@@ -41,6 +42,7 @@ void* ws_get(ufc_ctx* c, int s, size_t bytes) {
   if (c->cap[s] >= bytes) return c->buf[s];
   if (c->buf[s]) {
     cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     cudaFree(c->buf[s]);
     c->buf[s] = nullptr;
     c->cap[s] = 0;
@@ -117,6 +119,7 @@ ufc_status ufc_create(ufc_ctx** out, int32_t device) {
   c->device = device;
   if (cudaSetDevice(device) != cudaSuccess) { delete c; return UFC_ERR_CUDA; }
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc(&c->counters, sizeof(BinCounters)) != cudaSuccess) { delete c; return UFC_ERR_ALLOC; }
   cudaMemset(c->counters, 0, sizeof(BinCounters));
   *out = c;
@@ -131,6 +134,11 @@ ufc_status ufc_destroy(ufc_ctx* c) {
     if (c->buf[s]) cudaFree(c->buf[s]);
   if (c->counters) cudaFree(c->counters);
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (cudaEvent_t e : c->copy_events) cudaEventDestroy(e);
   delete c;
   return UFC_OK;
 }
@@ -152,21 +160,7 @@ const char* ufc_last_error(const ufc_ctx* c) { return c ? c->err.c_str() : "no c
 ufc_status ufc_reserve(ufc_ctx* c, int32_t nside, int32_t nshell, int64_t n_max) {
   if (!c || nside < 1 || nshell < 1 || n_max < 0) return UFC_ERR_ARG;
   cudaSetDevice(c->device);
-  const int64_t npix = 12ll * nside * nside;
-  const int64_t qwarps = 2ll * 2 * c->num_sms * 32 + 4ll * c->num_sms * 8;
-  const int64_t cap1 = std::max<int64_t>(1 << 20, n_max / 16) + qwarps * 256;
-  const int64_t cap2 = std::max<int64_t>(1 << 16, cap1 / 64) + qwarps * 256;
-  if (!ws_get(c, kSlotQueue1, cap1 * 8) || !ws_get(c, kSlotQueue2, cap2 * 8)) return UFC_ERR_ALLOC;
-  if (nside >= 64 && npix * nshell * 4 > (32ll << 20)) {
-    const int64_t nwarps = 2ll * 2 * c->num_sms * 32 + 2ll * 4 * c->num_sms * 8 + 64;
-    const int64_t cap = n_max + nwarps * 2048;
-    const int64_t nb = nshell * (npix / 24576);
-    if (!ws_get(c, kSlotDense, cap * 4) || !ws_get(c, kSlotGrouped, cap * 4) ||
-        !ws_get(c, kSlotBucket16, cap * 2) || !ws_get(c, kSlotHist, nb * 4) ||
-        !ws_get(c, kSlotOff, (nb + 1) * 8))
-      return UFC_ERR_ALLOC;
-  }
-  return UFC_OK;
+  return reserve_bin_workspace(c, 2, n_max, nshell, nside);
 }
 
 ufc_status ufc_profile_enable(ufc_ctx* c, int32_t on) {
@@ -266,7 +260,7 @@ ufc_status ufc_keys(ufc_ctx* c, const float* xyz_dev, int64_t n, const ufc_box* 
   if (box->replicate != 0) return set_err(c, UFC_ERR_ARG, "ufc_keys needs replicate = 0");
   cudaSetDevice(c->device);
   return run_keys_pipeline(c, 0, &xyz_dev, &n, box, 1, chi_edges, nshell, nside, 0, nullptr,
-                           keys_dev);
+                           keys_dev, nullptr);
 }
 
 ufc_status ufc_bin(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
@@ -284,7 +278,29 @@ ufc_status ufc_bin(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 4-byte aligned");
   cudaSetDevice(c->device);
   return run_keys_pipeline(c, 1, xyz_dev, n, boxes, nbox, chi_edges, nshell, nside, flags,
-                           counts_dev, nullptr);
+                           counts_dev, nullptr, nullptr);
+}
+
+ufc_status ufc_bin_host(ufc_ctx* c, const float* const* xyz_host, const int64_t* n,
+                        const ufc_box* boxes, int32_t nbox, const double* chi_edges,
+                        int32_t nshell, int32_t nside, int32_t flags, int32_t* counts_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!xyz_host || !n || !boxes || !chi_edges || !counts_dev)
+    return set_err(c, UFC_ERR_ARG, "NULL argument to ufc_bin_host");
+  if (flags & ~(UFC_BIN_ACCUMULATE | UFC_BIN_FORCE_DIRECT | UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if ((flags & UFC_BIN_FORCE_DIRECT) && (flags & UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "FORCE_DIRECT and FORCE_DENSE exclude each other");
+  if (reinterpret_cast<uintptr_t>(counts_dev) & 3)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 4-byte aligned");
+  cudaSetDevice(c->device);
+  cudaStreamCaptureStatus cs;
+  UFC_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_err(c, UFC_ERR_UNSUPPORTED, "ufc_bin_host cannot be captured into a graph");
+  return run_keys_pipeline(c, 1, nullptr, n, boxes, nbox, chi_edges, nshell, nside, flags,
+                           counts_dev, nullptr, xyz_host);
 }
 
 ufc_status ufc_bin_info(ufc_ctx* c, int64_t info[4]) {
@@ -395,7 +411,7 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
   }
   for (int r = 0; r < nreal && !s; ++r) {
     s = run_keys_pipeline(c, 1, xyz + r * nbox, n + r * nbox, boxes + r * nbox, nbox, chi, nshell,
-                          nside, 0, counts, nullptr);
+                          nside, 0, counts, nullptr, nullptr);
     if (!s)
       s = run_kappa_stats(c, counts, nshell, nside, A + (size_t)r * nshell, C[r], lo, hi, nbins,
                           kappa, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r);

@@ -15,6 +15,7 @@ struct ufc_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   int num_sms = 0;
+  int smem_optin = 0;            // shared memory per block with opt-in (bytes)
   // grow-only device buffers, one per slot
   static constexpr int kSlots = 16;
   void* buf[kSlots] = {};
@@ -26,6 +27,9 @@ struct ufc_ctx {
   std::vector<ProfRec> prof_recs;
   std::vector<cudaEvent_t> prof_pool;
   size_t prof_pool_used = 0;
+  // binning from host memory: a copy stream and one event per staged chunk
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> copy_events;
 };
 
 namespace ufc {
@@ -43,6 +47,7 @@ enum Slot {
   kSlotPartials,
   kSlotCoeffs,
   kSlotMisc,
+  kSlotStage,      // device copy of host particle positions (ufc_bin_host)
 };
 
 inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {
