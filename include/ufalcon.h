@@ -58,11 +58,17 @@ typedef struct ufc_ctx ufc_ctx;
 
 /* Flat LambdaCDM cosmology (the paper uses h = 0.7, Omega_m = 0.276, Table 1).
  * E(z) = sqrt(Omega_m (1+z)^3 + 1 - Omega_m).  units_mpc_over_h = 1: lengths
- * in Mpc/h, c/H0 = 2997.92458 Mpc/h; 0: lengths in Mpc, c/H0 = 2997.92458/h. */
+ * in Mpc/h, c/H0 = 2997.92458 Mpc/h; 0: lengths in Mpc, c/H0 = 2997.92458/h.
+ * density_volume selects the density factor F_b of Eq. 6 and 7: 0 (as
+ * printed) F_b = N_pix V / (4 pi N chi_b^2) at the shell's lower edge;
+ * 1 its average over the shell volume,
+ * F_b = 3 N_pix V Delta chi_b / (4 pi N (chi_{b+1}^3 - chi_b^3)),
+ * for which the expected kappa and delta of a uniform field are exactly 0. */
 typedef struct {
   double omega_m;
   double h;
   int32_t units_mpc_over_h;
+  int32_t density_volume;
 } ufc_cosmo;
 
 /* One simulation box of the nesting scheme (Sec. 2.4).  obs is the observer
@@ -128,10 +134,11 @@ ufc_status ufc_chi_edges(const ufc_cosmo *cosmo, const double *z_edges,
 ufc_status ufc_z_of_chi(const ufc_cosmo *cosmo, const double *chi, int32_t n,
                         double *z_out);
 /* Coefficients of kappa_p = sum_b A_b n_bp - C (Eq. 6):
- *   A_b = 3/2 Omega_m W_b (H0/c) N_pix V_k / (4 pi N_k chi_b^2),
+ *   A_b = 3/2 Omega_m W_b (H0/c) F_b,  F_b = N_pix V_k / (4 pi N_k chi_b^2),
  *   B_b = 3/2 Omega_m W_b (H0/c) Delta chi_b,  C = sum_b B_b,
  * with W_b from Eq. 3 (plane) or its n(z) average, chi_b the shell's lower
- * edge and (V_k = L^3, N_k = n_total) of the box owning shell b.  Every shell
+ * edge (or F_b over the shell volume, ufc_cosmo.density_volume) and
+ * (V_k = L^3, N_k = n_total) of the box owning shell b.  Every shell
  * must be owned by exactly one box and z_edges[0] > 0.
  * Optional dA [5][nshell] and dC [5] receive the derivatives with respect to
  * theta = (Omega_m, h, alpha, beta, z0) (NULL to skip). */
@@ -139,6 +146,20 @@ ufc_status ufc_kappa_coeffs(const ufc_cosmo *cosmo, const ufc_box *boxes,
                             int32_t nbox, const double *z_edges, int32_t nshell,
                             int32_t nside, const ufc_source *src, double *A,
                             double *B, double *C, double *dA, double *dC);
+
+/* Coefficients of the overdensity map of Eq. 7,
+ *   delta_p = sum_b [F_b n_bp - Delta chi_b] / sum_b Delta chi_b
+ *           = sum_b A_b n_bp - C,   A_b = F_b / sum_b Delta chi_b,  C = 1,
+ * with F_b the density factor of Eq. 6 (ufc_kappa_coeffs, including the
+ * density_volume reading; (V_k, N_k) of the owning box).  The map,
+ * its moments and PDF come from ufc_kappa_stats with these coefficients,
+ * gradients from ufc_kappa_backward with dA [5][nshell] and dC [5] (theta as
+ * for kappa; the n(z) parameters do not enter, their columns are 0).
+ * Arguments and errors as for ufc_kappa_coeffs (no source). */
+ufc_status ufc_delta_coeffs(const ufc_cosmo *cosmo, const ufc_box *boxes,
+                            int32_t nbox, const double *z_edges, int32_t nshell,
+                            int32_t nside, double *A, double *C, double *dA,
+                            double *dC);
 
 /* ---- binning (Eq. 5, Eq. 8, HEALPix pixelisation) ------------------------- */
 
@@ -171,7 +192,7 @@ ufc_status ufc_bin(ufc_ctx *ctx, const float *const *xyz_dev, const int64_t *n,
  * particles arrive from the simulation's output on the host).  Box k's
  * xyz_host[k] (n[k] particles, 12 bytes each) is copied into a device
  * staging buffer owned by the context (grown on demand, kept for later
- * calls) in chunks of about 31M particles on a second stream of the
+ * calls) in chunks of 2^25 particles on a second stream of the
  * context; the fast stage of each chunk starts on the context stream as
  * soon as the chunk has landed, so transfer and binning overlap.  Results
  * are identical to ufc_bin's.  Page-locked host memory (cudaHostAlloc,
@@ -260,7 +281,10 @@ ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
  * finally adds all nreal vectors to the Welford state state_dev in order.
  * The workspace is grown once up front; with UFC_BATCH_GRAPH the per-
  * realisation work is captured into one CUDA graph and launched once (the
- * context stream must not be capturing already).  Asynchronous. */
+ * context stream must not be capturing already; on the legacy default
+ * stream the graph is captured and launched on a stream of the context,
+ * ordered after earlier work and before later work by events).
+ * Asynchronous. */
 ufc_status ufc_batched_stats(ufc_ctx *ctx, int32_t nreal, int32_t nbox,
                              const float *const *xyz_dev, const int64_t *n,
                              const ufc_box *boxes, const double *chi_edges,

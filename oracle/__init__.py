@@ -98,7 +98,8 @@ def _declare(L):
         "or_chi_edges": (None, [D, D, ctypes.c_int, P, I32, P]),
         "or_z_of_chi": (D, [D, D, ctypes.c_int, D]),
         "or_shell_weights": (None, [D, P, I32, P, P]),
-        "or_kappa_coeffs": (None, [D, D, ctypes.c_int, P, I32, P, I32, I64, P, P, P, P]),
+        "or_kappa_coeffs": (None, [D, D, ctypes.c_int, ctypes.c_int, P, I32, P, I32, I64, P, P, P, P]),
+        "or_delta_coeffs": (None, [D, D, ctypes.c_int, ctypes.c_int, P, I32, P, I32, I64, P, P]),
         "or_kappa_map": (None, [P, I32, I64, P, D, P]),
         "or_moments": (None, [P, I64, P]),
         "or_pdf": (None, [P, I64, D, D, I32, P]),
@@ -201,14 +202,26 @@ def shell_weights(omega_m, z_edges, src: Source) -> np.ndarray:
     return out
 
 
-def kappa_coeffs(omega_m, h, units_mpc_over_h, boxes, z_edges, nside, src):
+def kappa_coeffs(omega_m, h, units_mpc_over_h, boxes, z_edges, nside, src, dens_volume=0):
     z = np.ascontiguousarray(z_edges, dtype=np.float64)
     ns = len(z) - 1
     A, B, C = np.empty(ns), np.empty(ns), ctypes.c_double()
     arr, bp = _boxes(boxes)
-    lib().or_kappa_coeffs(omega_m, h, units_mpc_over_h, bp, len(boxes), _ptr(z), ns, nside,
-                          ctypes.byref(src), _ptr(A), _ptr(B), ctypes.byref(C))
+    lib().or_kappa_coeffs(omega_m, h, units_mpc_over_h, dens_volume, bp, len(boxes), _ptr(z), ns,
+                          nside, ctypes.byref(src), _ptr(A), _ptr(B), ctypes.byref(C))
     return A, B, C.value
+
+
+def delta_coeffs(omega_m, h, units_mpc_over_h, boxes, z_edges, nside, dens_volume=0):
+    """(A, C) of the overdensity map delta_p = sum_b A_b n_bp - C (Eq. 7);
+    the map itself is kappa_map(counts, A, C)."""
+    z = np.ascontiguousarray(z_edges, dtype=np.float64)
+    ns = len(z) - 1
+    A, C = np.empty(ns), ctypes.c_double()
+    arr, bp = _boxes(boxes)
+    lib().or_delta_coeffs(omega_m, h, units_mpc_over_h, dens_volume, bp, len(boxes), _ptr(z), ns,
+                          nside, _ptr(A), ctypes.byref(C))
+    return A, C.value
 
 
 # ---- statistics --------------------------------------------------------------------

@@ -54,6 +54,7 @@ static void fejer_init(void) {
 typedef struct {
   cx om, h, alpha, beta, z0;
   int units_mpc_over_h;
+  int dens_volume;   /* density factor: 0 at the lower edge, 1 over the shell volume */
 } theta_t;
 
 static cx inv_E(const theta_t *th, double z) {
@@ -157,6 +158,18 @@ static void weights(const theta_t *th, const double *z_edges, int32_t nshell,
   }
 }
 
+/* Density factor of Eq. 6 and 7: the expected count of a pixel on shell b
+ * is rho/m_p times the pixel's share of the shell volume.  Reading 0 (the
+ * printed Eq. 6): F_b = N_pix V / (4 pi N chi_b^2), chi_b the lower edge.
+ * Reading 1: the mean of 1/chi^2 over the shell volume, so that F_b times
+ * the expected count of a uniform field is exactly Delta chi_b:
+ * F_b = 3 N_pix V Delta chi_b / (4 pi N (chi_{b+1}^3 - chi_b^3)). */
+static cx density_factor(double npix, double V, int64_t n_total, cx lo, cx hi, int volume) {
+  const double pi = 3.14159265358979323846264338327950288;
+  if (volume) return 3.0 * npix * V * (hi - lo) / (4.0 * pi * (double)n_total * (hi * hi * hi - lo * lo * lo));
+  return npix * V / (4.0 * pi * (double)n_total * lo * lo);
+}
+
 static void coeffs(const theta_t *th, const or_box *boxes, int32_t nbox,
                    const double *z_edges, int32_t nshell, int64_t nside,
                    const or_source *src, cx *A, cx *B, cx *C) {
@@ -174,7 +187,7 @@ static void coeffs(const theta_t *th, const or_box *boxes, int32_t nbox,
       if (b >= boxes[k].shell_lo && b < boxes[k].shell_hi) bx = &boxes[k];
     if (!bx) { A[b] = NAN; B[b] = NAN; continue; }
     double V = bx->L * bx->L * bx->L;
-    cx F = npix * V / (4.0 * pi * (double)bx->n_total * chi[b] * chi[b]);
+    cx F = density_factor(npix, V, bx->n_total, chi[b], chi[b + 1], th->dens_volume);
     A[b] = 1.5 * th->om * w[b] * F / cH;
     B[b] = 1.5 * th->om * w[b] * (chi[b + 1] - chi[b]) / cH;
     *C += B[b];
@@ -185,7 +198,7 @@ static void coeffs(const theta_t *th, const or_box *boxes, int32_t nbox,
 
 static theta_t make_theta(double om, double h, int units, const or_source *src) {
   theta_t th;
-  th.om = om; th.h = h; th.units_mpc_over_h = units;
+  th.om = om; th.h = h; th.units_mpc_over_h = units; th.dens_volume = 0;
   th.alpha = src ? src->alpha : 0.0;
   th.beta = src ? src->beta : 1.0;
   th.z0 = src ? src->z0 : 1.0;
@@ -223,16 +236,43 @@ void or_shell_weights(double om, const double *z_edges, int32_t nshell,
   free(w);
 }
 
-void or_kappa_coeffs(double om, double h, int units, const or_box *boxes,
+void or_kappa_coeffs(double om, double h, int units, int dens_volume, const or_box *boxes,
                      int32_t nbox, const double *z_edges, int32_t nshell,
                      int64_t nside, const or_source *src, double *A_out,
                      double *B_out, double *C_out) {
   theta_t th = make_theta(om, h, units, src);
+  th.dens_volume = dens_volume;
   cx *A = (cx *)malloc(sizeof(cx) * nshell), *B = (cx *)malloc(sizeof(cx) * nshell), C;
   coeffs(&th, boxes, nbox, z_edges, nshell, nside, src, A, B, &C);
   for (int b = 0; b < nshell; ++b) { A_out[b] = creal(A[b]); B_out[b] = creal(B[b]); }
   *C_out = creal(C);
   free(A); free(B);
+}
+
+/* Overdensity map, Eq. 7: delta_p = sum_b [F_b n_bp - dchi_b] / sum_b dchi_b,
+ * returned as delta_p = sum_b A_b n_bp - C: A_b = F_b / sum_b dchi_b and
+ * C = (sum_b dchi_b) / (sum_b dchi_b) = 1.  F_b is the density factor of
+ * Eq. 6 (density_factor), with V, N of the box owning shell b;
+ * dchi_b = chi_{b+1} - chi_b. */
+void or_delta_coeffs(double om, double h, int units, int dens_volume, const or_box *boxes,
+                     int32_t nbox, const double *z_edges, int32_t nshell,
+                     int64_t nside, double *A_out, double *C_out) {
+  double *chi = (double *)malloc(sizeof(double) * (nshell + 1));
+  for (int b = 0; b <= nshell; ++b) chi[b] = or_comoving_distance(om, h, units, z_edges[b]);
+  double total = 0.0;
+  for (int b = 0; b < nshell; ++b) total += chi[b + 1] - chi[b];
+  const double npix = (double)or_nside2npix(nside);
+  for (int b = 0; b < nshell; ++b) {
+    const or_box *bx = NULL;
+    for (int k = 0; k < nbox; ++k)
+      if (b >= boxes[k].shell_lo && b < boxes[k].shell_hi) bx = &boxes[k];
+    if (!bx) { A_out[b] = NAN; continue; }
+    const double V = bx->L * bx->L * bx->L;
+    const double F = creal(density_factor(npix, V, bx->n_total, chi[b], chi[b + 1], dens_volume));
+    A_out[b] = F / total;
+  }
+  *C_out = total / total;
+  free(chi);
 }
 
 /* ---- statistics of the unrounded map, for gradients ---------------------- */

@@ -77,12 +77,20 @@ double or_z_of_chi(double omega_m, double h, int units_mpc_over_h, double chi);
 /* Per-shell weight W_b (Eq. 3 for a plane, its n(z) average otherwise). */
 void or_shell_weights(double omega_m, const double *z_edges, int32_t nshell,
                       const or_source *src, double *w_out);
-/* A_b, B_b and C of kappa_p = sum_b A_b n_bp - C (Eq. 6). */
-void or_kappa_coeffs(double omega_m, double h, int units_mpc_over_h,
+/* A_b, B_b and C of kappa_p = sum_b A_b n_bp - C (Eq. 6).  dens_volume
+ * selects the density factor: 0 at the shell's lower edge (as printed),
+ * 1 averaged over the shell volume. */
+void or_kappa_coeffs(double omega_m, double h, int units_mpc_over_h, int dens_volume,
                      const or_box *boxes, int32_t nbox,
                      const double *z_edges, int32_t nshell, int64_t nside,
                      const or_source *src, double *A_out, double *B_out,
                      double *C_out);
+
+/* A_b and C of the overdensity map delta_p = sum_b A_b n_bp - C (Eq. 7). */
+void or_delta_coeffs(double omega_m, double h, int units_mpc_over_h, int dens_volume,
+                     const or_box *boxes, int32_t nbox,
+                     const double *z_edges, int32_t nshell, int64_t nside,
+                     double *A_out, double *C_out);
 
 /* ---- Map statistics (Eq. 6, Eq. 12-13, PDF of Sec. 3.3) ------------------ */
 void or_kappa_map(const int32_t *counts, int32_t nshell, int64_t npix,

@@ -40,8 +40,9 @@ MOMENT_NAMES = ("mean", "mu2", "mu3", "mu4", "skew", "kurt", "s2_expect", "var_s
 
 
 class Cosmo(ctypes.Structure):
-    """ufc_cosmo: flat LambdaCDM (omega_m, h), lengths in Mpc/h if units_mpc_over_h."""
-    _fields_ = [("omega_m", D), ("h", D), ("units_mpc_over_h", I32)]
+    """ufc_cosmo: flat LambdaCDM (omega_m, h), lengths in Mpc/h if units_mpc_over_h;
+    density_volume = 1 averages the density factor over the shell volume."""
+    _fields_ = [("omega_m", D), ("h", D), ("units_mpc_over_h", I32), ("density_volume", I32)]
 
 
 class Box(ctypes.Structure):
@@ -55,8 +56,8 @@ class Source(ctypes.Structure):
     _fields_ = [("kind", I32), ("z_s", D), ("alpha", D), ("beta", D), ("z0", D), ("z_max", D)]
 
 
-def make_cosmo(omega_m=0.3, h=0.7, units_mpc_over_h=1) -> Cosmo:
-    return Cosmo(float(omega_m), float(h), int(units_mpc_over_h))
+def make_cosmo(omega_m=0.3, h=0.7, units_mpc_over_h=1, density_volume=0) -> Cosmo:
+    return Cosmo(float(omega_m), float(h), int(units_mpc_over_h), int(density_volume))
 
 
 def make_box(L, obs, n_total, shell_lo, shell_hi, replicate=0) -> Box:
@@ -82,6 +83,7 @@ _SIGS = {
     "ufc_z_of_chi": [ctypes.POINTER(Cosmo), P, I32, P],
     "ufc_kappa_coeffs": [ctypes.POINTER(Cosmo), P, I32, P, I32, I32, ctypes.POINTER(Source),
                          P, P, P, P, P],
+    "ufc_delta_coeffs": [ctypes.POINTER(Cosmo), P, I32, P, I32, I32, P, P, P, P],
     "ufc_keys": [P, P, I64, ctypes.POINTER(Box), P, I32, I32, P],
     "ufc_bin": [P, P, P, P, I32, P, I32, I32, I32, P],
     "ufc_bin_host": [P, P, P, P, I32, P, I32, I32, I32, P],
@@ -135,6 +137,25 @@ def z_of_chi(cosmo: Cosmo, chi) -> np.ndarray:
     _check(_lib.ufc_z_of_chi(ctypes.byref(cosmo), _np_ptr(c), len(c), _np_ptr(out)),
            what="ufc_z_of_chi")
     return out
+
+
+def delta_coeffs(cosmo: Cosmo, boxes, z_edges, nside: int, derivs=False):
+    """(A, C[, dA, dC]) of the overdensity map delta_p = sum_b A_b n_bp - C
+    (Eq. 7); the map and its statistics come from Context.kappa_stats."""
+    z = np.ascontiguousarray(z_edges, dtype=np.float64)
+    S = len(z) - 1
+    arr = (Box * len(boxes))(*boxes)
+    A = np.empty(S)
+    C = ctypes.c_double()
+    dA = np.empty((5, S)) if derivs else None
+    dC = np.empty(5) if derivs else None
+    _check(_lib.ufc_delta_coeffs(ctypes.byref(cosmo), ctypes.cast(arr, P), len(boxes), _np_ptr(z),
+                                 S, nside, _np_ptr(A), ctypes.byref(C),
+                                 _np_ptr(dA) if derivs else None,
+                                 _np_ptr(dC) if derivs else None), what="ufc_delta_coeffs")
+    if derivs:
+        return A, C.value, dA, dC
+    return A, C.value
 
 
 def kappa_coeffs(cosmo: Cosmo, boxes, z_edges, nside: int, source: Source, derivs=False):

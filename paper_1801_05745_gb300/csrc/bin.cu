@@ -120,8 +120,10 @@ struct QChunk {
   int32_t fill;
 };
 
-__device__ __forceinline__ bool queue_push(QChunk& qc, bool want, uint64_t e, uint64_t* q,
-                                           int64_t cap, unsigned long long* count) {
+// `entry()` gives the value; it is evaluated only by lanes that push.
+template <class F>
+__device__ __forceinline__ bool queue_push_f(QChunk& qc, bool want, F entry, uint64_t* q,
+                                             int64_t cap, unsigned long long* count) {
   const unsigned full = 0xFFFFFFFFu;
   const unsigned m = __ballot_sync(full, want);
   if (m == 0) return true;
@@ -152,8 +154,12 @@ __device__ __forceinline__ bool queue_push(QChunk& qc, bool want, uint64_t e, ui
     qc.fill += cnt;
   }
   if (!want) return true;
-  if (idx < cap) { q[idx] = e; return true; }
+  if (idx < cap) { q[idx] = entry(); return true; }
   return false;
+}
+__device__ __forceinline__ bool queue_push(QChunk& qc, bool want, uint64_t e, uint64_t* q,
+                                           int64_t cap, unsigned long long* count) {
+  return queue_push_f(qc, want, [e]() { return e; }, q, cap, count);
 }
 
 // Marks the unused slots of the warp's last queue chunk.
@@ -406,8 +412,8 @@ __device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo,
 // are drained after every (chunk, image) pass.  Particle p of the launch is
 // element p_off + p of the caller's array (chunked launches of ufc_bin_host).
 constexpr int kWThreads = 768;
-constexpr int kWChunk = 1536;                  // particles per chunk (18 KB)
-constexpr int kWStages = 4;
+constexpr int kWChunk = 2304;                  // particles per chunk (27 KB)
+constexpr int kWStages = 3;
 constexpr int kWWarps = kWThreads / 32;        // 24
 constexpr int kWPerWarp = kWChunk / kWWarps;   // 64
 constexpr int kWGroups = kWPerWarp / 32;
@@ -463,6 +469,9 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
   float4* list_cap = list_eq + kWList;
   const int64_t nchunks = (n + kWChunk - 1) / kWChunk;
   const int64_t mine = nchunks > blockIdx.x ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t nfull = n / kWChunk;                   // chunks of kWChunk particles
+  const int tail_n = int(n - nfull * kWChunk);         // particles of the last, partial chunk
+  const int tail_smem = int(((uint32_t(tail_n) * 12u) & ~15u) / 12u);   // of them inside its copy
   auto chunk_bytes = [&](int64_t c) -> uint32_t {
     const int64_t rest = n - c * kWChunk;
     const int64_t cnt = rest < kWChunk ? rest : (int64_t)kWChunk;
@@ -496,11 +505,16 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
       if (__any_sync(0xFFFFFFFFu, aborted) || abort_s) { aborted = true; break; }
     }
     const int64_t kq = last ? (k > 0 ? k - 1 : 0) : k;   // chunk of the newest entries
-    const int64_t base = (blockIdx.x + kq * gridDim.x) * kWChunk;
+    const int64_t cq = blockIdx.x + kq * gridDim.x;
+    const int64_t base = cq * kWChunk;
+    const bool fullc = cq < nfull;
+    const int nvalid = last ? 0 : (fullc ? kWChunk : tail_n);
+    const int nsmem = fullc ? kWChunk : tail_smem;      // particles inside the bulk copy
     const float* buf = ring + s * 3 * kWChunk;
-    const uint32_t bytes = last ? 0u : chunk_bytes(blockIdx.x + k * gridDim.x);
     const int nimg = last ? 1 : bg.nimg;
     const bool drain_all = last || !carry || ((k & (kWAgeFlush - 1)) == kWAgeFlush - 1);
+    const int ng = last ? 0 : kWGroups;                  // groups of 32 particles to classify
+    const int nsteps = ng + (drain_all ? 1 : 0);         // + a drain step
     ii = jj = kk = 0;
 #pragma unroll 1
     for (int img = 0; img < nimg; ++img) {
@@ -509,24 +523,22 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
       }
       const float sx = fs.shf[0][ii], sy = fs.shf[1][jj], sz = fs.shf[2][kk];
       const float lx = fs.shlo[0][ii], ly = fs.shlo[1][jj], lz = fs.shlo[2][kk];
+      const uint64_t qbase = qpack(box_id, img, p_off + base);   // + offset in the chunk
 #pragma unroll 1
-      for (int h = 0; h <= (last ? 0 : kWGroups); ++h) {
-        if (h < kWGroups && !last) {
+      for (int h = 0; h < nsteps; ++h) {
+        if (h < ng) {
           // ---- A: classify 32 particles of this warp's slice
           const int j = warp * kWPerWarp + 32 * h + lane;
-          const bool have = base + j < n;
-          const int64_t p = p_off + base + j;     // index in the caller's array
+          const bool have = j < nvalid;
           float x = 0.f, y = 0.f, zc = 0.f;
-          if (have) {
-            if ((uint32_t)(12 * j + 12) <= bytes) {
-              x = buf[3 * j];
-              y = buf[3 * j + 1];
-              zc = buf[3 * j + 2];
-            } else {                             // ragged tail outside the bulk copy
-              x = __ldg(xyz + 3 * (base + j));
-              y = __ldg(xyz + 3 * (base + j) + 1);
-              zc = __ldg(xyz + 3 * (base + j) + 2);
-            }
+          if (j < nsmem) {
+            x = buf[3 * j];
+            y = buf[3 * j + 1];
+            zc = buf[3 * j + 2];
+          } else if (have) {                     // ragged tail outside the bulk copy
+            x = __ldg(xyz + 3 * (base + j));
+            y = __ldg(xyz + 3 * (base + j) + 1);
+            zc = __ldg(xyz + 3 * (base + j) + 2);
           }
           const float dx = (x + sx) + lx;
           const float dy = (y + sy) + ly;
@@ -543,8 +555,8 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
               b = shell_lut(fs, lo, hi, lp.scale, r2);
               if (b == -2) cls = 1;
               else if (b >= 0) {
-                const float za = fabsf(dz * rsqrtf(r2));
-                cls = za <= bd.z_eq ? 2 : (za > bd.z_cap ? 3 : 1);
+                const float dz2 = dz * dz;
+                cls = dz2 <= bd.z_eq2 * r2 ? 2 : (dz2 > bd.z_cap2 * r2 ? 3 : 1);
               }
             }
           }
@@ -558,7 +570,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           ne += __popc(meq);
           nc += __popc(mcap);
           // undecided images wait in queue 1; outside/invalid are final
-          if (!queue_push(fc.qc, cls == 1, qpack(box_id, img, p), qs.q1, qs.cap1, &qs.cnt->q1)) {
+          if (!queue_push(fc.qc, cls == 1, qbase + uint64_t(j), qs.q1, qs.cap1, &qs.cnt->q1)) {
             const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
                                               bg.sh64[1][jj], bg.sh64[2][kk]);
             if (kx == kKeyInvalid) ++fc.n_invalid;
@@ -572,15 +584,16 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
               }
             }
-            if (MODE == kModeKeys && have) o.keys[p] = kx;
+            if (MODE == kModeKeys && have) o.keys[p_off + base + j] = kx;
           } else if (MODE == kModeKeys && have && cls != 2 && cls != 3) {
-            o.keys[p] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
+            o.keys[p_off + base + j] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
           }
         }
         __syncwarp();
-        // ---- B: pixels of full groups of 32 pending entries (after the
-        // last group of a pass, also of the partial rest when draining)
-        const bool tail = h == (last ? 0 : kWGroups);
+        // ---- B: pixels of full groups of 32 pending entries (in the drain
+        // step, also of the partial rest)
+        const bool tail = h == ng;
+        if (ne < 32 && nc < 32 && !(tail && (ne | nc))) continue;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
           const int cnt = pass == 0 ? ne : nc;
@@ -603,14 +616,18 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
                                     : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
           const bool ok = have && pix != kKeyUndecided;
-          // the entry's particle: chunk from the 12-bit tag, offset j
-          const int64_t ke = kq - ((kq - int64_t(meta >> 20)) & 4095);
-          const int64_t pl = (blockIdx.x + ke * gridDim.x) * kWChunk + int64_t((meta >> 8) & 4095u);
-          const int64_t p = p_off + pl;
+          // the entry's particle (launch-local index pl): chunk from the
+          // 12-bit tag, offset in the chunk; computed only where needed
+          auto local_index = [&]() -> int64_t {
+            const int64_t ke = kq - ((kq - int64_t(meta >> 20)) & 4095);
+            return (blockIdx.x + ke * gridDim.x) * kWChunk + int64_t((meta >> 8) & 4095u);
+          };
           const int32_t key = b * npix + pix;
-          const bool queued = queue_push(fc.qc, have && !ok, qpack(box_id, carry ? 0 : img, p),
-                                         qs.q1, qs.cap1, &qs.cnt->q1);
+          const bool queued = queue_push_f(
+              fc.qc, have && !ok, [&]() { return qpack(box_id, img, p_off + local_index()); },
+              qs.q1, qs.cap1, &qs.cnt->q1);
           if (!queued) {                         // queue full: the FP64 procedure here
+            const int64_t pl = local_index();
             const float x = __ldg(xyz + 3 * pl), y = __ldg(xyz + 3 * pl + 1),
                         zc = __ldg(xyz + 3 * pl + 2);
             const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
@@ -625,10 +642,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
               }
             }
-            if (MODE == kModeKeys) o.keys[p] = kx;
+            if (MODE == kModeKeys) o.keys[p_off + pl] = kx;
           }
           if (MODE == kModeKeys) {
-            if (have && queued) o.keys[p] = ok ? key : kKeyUndecided;
+            if (have && queued) o.keys[p_off + local_index()] = ok ? key : kKeyUndecided;
           } else if (MODE == kModeDirect) {
             if (ok) atomicAdd(o.counts + key, 1);
           } else {
@@ -863,9 +880,9 @@ __device__ __forceinline__ void warp_exclusive_scan(const uint32_t* cnt, uint32_
   for (int i = a; i < b; ++i) { start[i] = run; run += cnt[i]; }
 }
 
-constexpr int kScatThreads = 256;
+constexpr int kScatThreads = 1024;
 constexpr int kScatPer = 16;
-constexpr int kScatTile = kScatThreads * kScatPer;   // 4096 keys
+constexpr int kScatTile = kScatThreads * kScatPer;   // 16384 keys: ~128 B per destination
 
 // Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.  The
 // next tile's keys are loaded into registers while the current tile is
@@ -955,10 +972,12 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
                  const unsigned long long* __restrict__ ntiles_p,
                  unsigned long long* __restrict__ bcur, uint16_t* __restrict__ out) {
   constexpr int NS = 1 << kGroupBits;
-  __shared__ uint32_t cnt[NS], start[NS];
-  __shared__ unsigned long long base[NS];
-  __shared__ uint16_t tile[kScatTile];
-  __shared__ uint8_t tsub[kScatTile];
+  extern __shared__ __align__(16) uint8_t smb[];
+  unsigned long long* base = reinterpret_cast<unsigned long long*>(smb);    // [NS]
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(base + NS);                  // [NS]
+  uint32_t* start = cnt + NS;                                              // [NS]
+  uint16_t* tile = reinterpret_cast<uint16_t*>(start + NS);                // [kScatTile]
+  uint8_t* tsub = reinterpret_cast<uint8_t*>(tile + kScatTile);            // [kScatTile]
   const int64_t ntiles = (int64_t)*ntiles_p;
   uint32_t v[kScatPer], nv[kScatPer];
   Tile T{0, 0, 0}, NT{0, 0, 0};
@@ -1092,7 +1111,10 @@ static void make_bands(int N, float smax, Bands& bd) {
   double g = std::ldexp(1.0, 11) * u * std::max<double>(smax, 1.0);
   bd.r2_min = f_up(g * g);
   bd.axy_min = f_up(g);
-  bd.pad_ = 0.f;
+  // zone by squares: dz^2 (<= 5u), r2 (<= 6u) and z2 r2 (u) give z^2 within
+  // 12u relative of the exact value above r2_min; the band is twice that
+  bd.z_eq2 = f_down(4.0 / 9.0 / (1.0 + 24.0 * u) * (1.0 - 1e-12));
+  bd.z_cap2 = f_up(4.0 / 9.0 / (1.0 - 24.0 * u) * (1.0 + 1e-12));
 }
 
 static ufc_status make_table(ufc_ctx* c, const double* chi, int nshell, ShellTable& st) {
@@ -1153,9 +1175,9 @@ struct BinPlan {
   int nblk, nbuckets, ng, smem_hist;
 };
 
-// Particles per staged chunk of ufc_bin_host: a multiple of kWChunk, so that
-// every chunk starts 16-byte aligned (377 MB).
-constexpr int64_t kHostChunk = (int64_t)kWChunk * 10240;
+// Particles per staged chunk of ufc_bin_host (402 MB); a multiple of 4, so
+// that every chunk starts 16-byte aligned for the bulk copies.
+constexpr int64_t kHostChunk = 1ll << 25;
 
 // Workspace of one binning call of total_img particle images in
 // fast_launches fast-stage launches.  Every warp of every launch (fast,
@@ -1459,17 +1481,20 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
                                    smemA));
   {
     ProfScope ps_(c, "k_scatter_group");
-    k_scatter_group<<<4 * c->num_sms, kScatThreads, smemA, c->stream>>>(
+    k_scatter_group<<<c->num_sms, kScatThreads, smemA, c->stream>>>(
         o.dense, o.dense_count, o.dense_cap, ng, gcur, grouped);
   }
   {
     ProfScope ps_(c, "k_tiles");
     k_tiles<<<1, 1024, 0, c->stream>>>(off, nb, ng, tiles, ntiles);
   }
+  const int smemB = (1 << kGroupBits) * 16 + kScatTile * 3;
+  UFC_CUDA(c, cudaFuncSetAttribute(k_scatter_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smemB));
   {
     ProfScope ps_(c, "k_scatter_bucket");
-    k_scatter_bucket<<<4 * c->num_sms, kScatThreads, 0, c->stream>>>(grouped, tiles, ntiles,
-                                                                     bcur, b16);
+    k_scatter_bucket<<<c->num_sms, kScatThreads, smemB, c->stream>>>(grouped, tiles, ntiles,
+                                                                      bcur, b16);
   }
   const int smemH = kBlockPix * 4;
   UFC_CUDA(c, cudaFuncSetAttribute(k_hist_block, cudaFuncAttributeMaxDynamicSharedMemorySize,

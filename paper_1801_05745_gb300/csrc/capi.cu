@@ -36,6 +36,9 @@ ufc_status cosmo_z_of_chi(const ufc_cosmo& c, const double* chi, int n, double* 
 ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
                               const double* z, int S, int nside, const ufc_source& src,
                               double* A, double* B, double* C, double* dA, double* dC);
+ufc_status cosmo_delta_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
+                              const double* z, int S, int nside, double* A, double* C,
+                              double* dA, double* dC);
 
 void* ws_get(ufc_ctx* c, int s, size_t bytes) {
   if (bytes == 0) bytes = 256;
@@ -87,6 +90,8 @@ static ufc_status check_cosmo(ufc_ctx* c, const ufc_cosmo* cs) {
   if (!(cs->h > 0.0) || !std::isfinite(cs->h)) return set_err(c, UFC_ERR_ARG, "h must be > 0");
   if (cs->units_mpc_over_h != 0 && cs->units_mpc_over_h != 1)
     return set_err(c, UFC_ERR_ARG, "units_mpc_over_h must be 0 or 1");
+  if (cs->density_volume != 0 && cs->density_volume != 1)
+    return set_err(c, UFC_ERR_ARG, "density_volume must be 0 or 1");
   return UFC_OK;
 }
 
@@ -139,6 +144,12 @@ ufc_status ufc_destroy(ufc_ctx* c) {
     cudaStreamDestroy(c->copy_stream);
   }
   for (cudaEvent_t e : c->copy_events) cudaEventDestroy(e);
+  if (c->aux_stream) {
+    cudaStreamSynchronize(c->aux_stream);
+    cudaStreamDestroy(c->aux_stream);
+  }
+  for (cudaEvent_t e : c->aux_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return UFC_OK;
 }
@@ -218,18 +229,16 @@ ufc_status ufc_z_of_chi(const ufc_cosmo* cosmo, const double* chi, int32_t n, do
   return cosmo_z_of_chi(*cosmo, chi, n, z_out);
 }
 
-ufc_status ufc_kappa_coeffs(const ufc_cosmo* cosmo, const ufc_box* boxes, int32_t nbox,
-                            const double* z_edges, int32_t nshell, int32_t nside,
-                            const ufc_source* src, double* A, double* B, double* C,
-                            double* dA, double* dC) {
+// Arguments shared by the kappa and delta coefficient calls.
+static ufc_status check_map_geometry(const ufc_cosmo* cosmo, const ufc_box* boxes, int32_t nbox,
+                                     const double* z_edges, int32_t nshell, int32_t nside) {
   ufc_status s = check_cosmo(nullptr, cosmo);
   if (s) return s;
-  if (!boxes || nbox < 1 || nshell < 1 || nshell > UFC_MAX_SHELLS || !src || !A || !C)
-    return UFC_ERR_ARG;
+  if (!boxes || nbox < 1 || nshell < 1 || nshell > UFC_MAX_SHELLS) return UFC_ERR_ARG;
   if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1))) return UFC_ERR_ARG;
   s = check_z(nullptr, z_edges, nshell + 1);
   if (s) return s;
-  if (!(z_edges[0] > 0.0)) return UFC_ERR_ARG;   // Eq. 6 divides by chi(z_0)^2
+  if (!(z_edges[0] > 0.0)) return UFC_ERR_ARG;   // Eq. 6 and 7 divide by chi(z_0)^2
   for (int b = 0; b < nshell; ++b) {
     int owners = 0;
     for (int k = 0; k < nbox; ++k)
@@ -238,6 +247,25 @@ ufc_status ufc_kappa_coeffs(const ufc_cosmo* cosmo, const ufc_box* boxes, int32_
   }
   for (int k = 0; k < nbox; ++k)
     if (!(boxes[k].L > 0.0) || boxes[k].n_total < 1) return UFC_ERR_ARG;
+  return UFC_OK;
+}
+
+ufc_status ufc_delta_coeffs(const ufc_cosmo* cosmo, const ufc_box* boxes, int32_t nbox,
+                            const double* z_edges, int32_t nshell, int32_t nside, double* A,
+                            double* C, double* dA, double* dC) {
+  ufc_status s = check_map_geometry(cosmo, boxes, nbox, z_edges, nshell, nside);
+  if (s) return s;
+  if (!A || !C) return UFC_ERR_ARG;
+  return cosmo_delta_coeffs(*cosmo, boxes, nbox, z_edges, nshell, nside, A, C, dA, dC);
+}
+
+ufc_status ufc_kappa_coeffs(const ufc_cosmo* cosmo, const ufc_box* boxes, int32_t nbox,
+                            const double* z_edges, int32_t nshell, int32_t nside,
+                            const ufc_source* src, double* A, double* B, double* C,
+                            double* dA, double* dC) {
+  ufc_status s = check_map_geometry(cosmo, boxes, nbox, z_edges, nshell, nside);
+  if (s) return s;
+  if (!src || !A || !C) return UFC_ERR_ARG;
   if (src->kind == 0) {
     if (!(src->z_s > 0.0) || src->z_s > 20.0) return UFC_ERR_ARG;
   } else if (src->kind == 1) {
@@ -395,19 +423,30 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
   const bool graph = (flags & UFC_BATCH_GRAPH) != 0;
   const bool prof = c->prof;
   cudaGraph_t g = nullptr;
+  cudaStream_t user = c->stream;
   if (graph) {
-    c->prof = false;   // event records would become graph nodes
     cudaStreamCaptureStatus cs;
-    UFC_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
-    if (cs != cudaStreamCaptureStatusNone) {
-      c->prof = prof;
+    UFC_CUDA(c, cudaStreamIsCapturing(user, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
       return set_err(c, UFC_ERR_ARG, "the context stream is already capturing");
+    if (user == nullptr) {
+      // the legacy default stream cannot be captured: capture on the
+      // context's own stream, ordered after the work already enqueued
+      if (!c->aux_stream)
+        UFC_CUDA(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : c->aux_ev)
+        if (!e) UFC_CUDA(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      UFC_CUDA(c, cudaEventRecord(c->aux_ev[0], user));
+      UFC_CUDA(c, cudaStreamWaitEvent(c->aux_stream, c->aux_ev[0], 0));
+      c->stream = c->aux_stream;
     }
-    if (c->stream == nullptr) {
+    c->prof = false;   // event records would become graph nodes
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      c->stream = user;
       c->prof = prof;
-      return set_err(c, UFC_ERR_ARG, "UFC_BATCH_GRAPH needs a non-default stream");
+      return set_err(c, UFC_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
     }
-    UFC_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
   }
   for (int r = 0; r < nreal && !s; ++r) {
     s = run_keys_pipeline(c, 1, xyz + r * nbox, n + r * nbox, boxes + r * nbox, nbox, chi, nshell,
@@ -420,15 +459,21 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
   }
   if (!s) s = run_welford_update(c, stats, nreal, d, state);
   if (graph) {
-    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    cudaStream_t cap = c->stream;
+    c->stream = user;
     c->prof = prof;
+    cudaError_t e = cudaStreamEndCapture(cap, &g);
     if (s) { if (g) cudaGraphDestroy(g); return s; }
     if (e != cudaSuccess) return set_err(c, UFC_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     cudaGraphExec_t ge = nullptr;
     e = cudaGraphInstantiate(&ge, g, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(ge, c->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ge, cap);
     if (ge) cudaGraphExecDestroy(ge);
     cudaGraphDestroy(g);
+    if (e == cudaSuccess && cap != user) {      // join: later work on the caller's stream waits
+      e = cudaEventRecord(c->aux_ev[1], cap);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(user, c->aux_ev[1], 0);
+    }
     if (e != cudaSuccess) return set_err(c, UFC_ERR_CUDA, "graph launch failed: %s", cudaGetErrorString(e));
   }
   return s;

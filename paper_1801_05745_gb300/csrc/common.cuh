@@ -55,7 +55,8 @@ struct Bands {
   float ip_per_ir;  // band of the in-ring coordinate t*ir, per unit of ir
   float r2_min;     // below this squared radius: undecided
   float axy_min;    // max(|dx|,|dy|) below this: undecided
-  float pad_;
+  float z_eq2;      // dz^2 <= z_eq2 r2  => equatorial belt for certain
+  float z_cap2;     // dz^2 >  z_cap2 r2 => polar cap for certain
 };
 
 struct GeomAll {

@@ -99,6 +99,7 @@ static Dual integrate(F f, double a, double b) {
 struct Theta {
   Dual om, h, alpha, beta, z0;
   int units;
+  int vol;   // density factor over the shell volume (ufc_cosmo.density_volume)
 };
 
 static Dual invE(const Theta& t, double z) {
@@ -119,6 +120,7 @@ static Dual nz(const Theta& t, double z) {
 static Theta theta(const ufc_cosmo& c, const ufc_source* s, bool derivs) {
   Theta t;
   t.units = c.units_mpc_over_h;
+  t.vol = c.density_volume;
   t.om = derivs ? Dual::var(c.omega_m, 0) : Dual(c.omega_m);
   t.h = derivs ? Dual::var(c.h, 1) : Dual(c.h);
   const double a = s ? s->alpha : 0.0, b = s ? s->beta : 1.0, z0 = s ? s->z0 : 1.0;
@@ -126,6 +128,14 @@ static Theta theta(const ufc_cosmo& c, const ufc_source* s, bool derivs) {
   t.beta = derivs ? Dual::var(b, 3) : Dual(b);
   t.z0 = derivs ? Dual::var(z0, 4) : Dual(z0);
   return t;
+}
+
+// Density factor of Eq. 6 and 7 with k = N_pix V / (4 pi N): k / chi_lo^2
+// (lower edge, as printed), or its mean over the shell volume,
+// 3 k (chi_hi - chi_lo) / (chi_hi^3 - chi_lo^3).
+static Dual density_factor(double k, const Dual& lo, const Dual& hi, int volume) {
+  if (volume) return Dual(3.0 * k) * (hi - lo) / (hi * hi * hi - lo * lo * lo);
+  return Dual(k) / (lo * lo);
 }
 
 // Shell weights W_b (Eq. 3 or its n(z) average).
@@ -227,7 +237,8 @@ ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox
     for (int k = 0; k < nbox; ++k)
       if (b >= boxes[k].shell_lo && b < boxes[k].shell_hi) bx = &boxes[k];
     const double V = bx->L * bx->L * bx->L;
-    Dual F = Dual(npix * V / (4.0 * pi * (double)bx->n_total)) / (chi[b] * chi[b]);
+    const Dual F = density_factor(npix * V / (4.0 * pi * (double)bx->n_total), chi[b], chi[b + 1],
+                                  t.vol);
     Dual Ab = Dual(1.5) * t.om * W[b] * F / ch;
     Dual Bb = Dual(1.5) * t.om * W[b] * (chi[b + 1] - chi[b]) / ch;
     A[b] = Ab.v;
@@ -239,6 +250,40 @@ ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox
   *C = Ct.v;
   if (dC)
     for (int j = 0; j < kNP; ++j) dC[j] = Ct.d[j];
+  return UFC_OK;
+}
+
+// Overdensity map, Eq. 7: delta_p = sum_b [F_b n_bp - Delta chi_b] / sum_b Delta chi_b
+// = sum_b A_b n_bp - C with A_b = F_b / sum_b Delta chi_b and C = 1; F_b is
+// the density factor of Eq. 6 (N_pix V_k / (4 pi N_k chi_b^2), chi_b the
+// shell's lower edge).  Derivatives with respect to theta as for kappa
+// (only Omega_m and, in Mpc units, h enter, through chi).
+ufc_status cosmo_delta_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
+                              const double* z, int S, int nside, double* A, double* C,
+                              double* dA, double* dC) {
+  const bool derivs = dA || dC;
+  Theta t = theta(c, nullptr, derivs);
+  const Dual ch = cH0(t);
+  std::vector<Dual> chi(S + 1);
+  for (int b = 0; b <= S; ++b) chi[b] = ch * Dist(t, z[b]);
+  Dual thick(0.0);
+  for (int b = 0; b < S; ++b) thick += chi[b + 1] - chi[b];
+  const double pi = 3.14159265358979323846;
+  const double npix = 12.0 * nside * nside;
+  for (int b = 0; b < S; ++b) {
+    const ufc_box* bx = nullptr;
+    for (int k = 0; k < nbox; ++k)
+      if (b >= boxes[k].shell_lo && b < boxes[k].shell_hi) bx = &boxes[k];
+    const double V = bx->L * bx->L * bx->L;
+    const Dual Ab = density_factor(npix * V / (4.0 * pi * (double)bx->n_total), chi[b],
+                                   chi[b + 1], t.vol) / thick;
+    A[b] = Ab.v;
+    if (dA)
+      for (int j = 0; j < kNP; ++j) dA[j * S + b] = Ab.d[j];
+  }
+  *C = 1.0;
+  if (dC)
+    for (int j = 0; j < kNP; ++j) dC[j] = 0.0;
   return UFC_OK;
 }
 

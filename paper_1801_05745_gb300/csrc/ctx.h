@@ -30,6 +30,10 @@ struct ufc_ctx {
   // binning from host memory: a copy stream and one event per staged chunk
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> copy_events;
+  // graph capture when the caller's stream is the legacy default stream:
+  // captured on aux_stream, forked and joined by aux_ev
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
 };
 
 namespace ufc {

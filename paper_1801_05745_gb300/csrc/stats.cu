@@ -401,8 +401,8 @@ k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
   }
 }
 
-// Forward pass without staging, for maps with more shells than the staged
-// tile holds (nshell > 96).
+// Forward pass with scalar loads, for a kappa buffer that is not 16-byte
+// aligned.
 __global__ void __launch_bounds__(kKT)
 k_kappa_plain(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
               double* __restrict__ ksum_part) {
@@ -423,6 +423,47 @@ k_kappa_plain(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ k
     ks = f2_add(ks, f2{kf, 0.f});
   }
   const double t = block_sum_d<kKT>(f2_to_d(ks), red);
+  if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
+}
+
+// Forward pass with vector loads: each thread owns 4 adjacent pixels and
+// reads every shell row of them as one 16-byte streaming load, 8 rows in
+// flight; no staging and no barriers, several blocks per SM.  Needs 16-byte
+// aligned counts and kappa (12 nside^2 is a multiple of 4).
+constexpr int kKV = 256;
+__device__ __forceinline__ float kappa_round(f2 a, f2 mc) {
+  const f2 e = f2_add(f2_norm(a.h, a.l), mc);   // e = acc - C (unrounded)
+  return __fadd_rn(e.h, e.l);
+}
+__global__ void __launch_bounds__(kKV)
+k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
+            double* __restrict__ ksum_part) {
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ double red[kKV / 32];
+  const int S = cf.nshell;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+  __syncthreads();
+  const int ng = cf.npix >> 2;
+  const int4* c4 = reinterpret_cast<const int4*>(counts);
+  const f2 mc{-cf.ch, -cf.cl};
+  f2 ks{0.f, 0.f};
+  for (int g = blockIdx.x * kKV + threadIdx.x; g < ng; g += gridDim.x * kKV) {
+    f2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+#pragma unroll 8
+    for (int b = 0; b < S; ++b) {
+      const int4 n = __ldcs(c4 + (size_t)b * ng + g);
+      const float h = ah_s[b], l = al_s[b];
+      f2_mac(a0, h, l, float(n.x));
+      f2_mac(a1, h, l, float(n.y));
+      f2_mac(a2, h, l, float(n.z));
+      f2_mac(a3, h, l, float(n.w));
+    }
+    const float4 kv = make_float4(kappa_round(a0, mc), kappa_round(a1, mc), kappa_round(a2, mc),
+                                  kappa_round(a3, mc));
+    reinterpret_cast<float4*>(kappa)[g] = kv;
+    ks = f2_add(ks, f2_add(f2_two_sum(kv.x, kv.y), f2_two_sum(kv.z, kv.w)));
+  }
+  const double t = block_sum_d<kKV>(f2_to_d(ks), red);
   if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
 }
 
@@ -632,7 +673,7 @@ static ufc_status check_kappa_args(ufc_ctx* c, const int32_t* counts, int S, int
   return UFC_OK;
 }
 
-constexpr int kStagedMaxShells = 96;
+constexpr int kStagedMaxShells = 96;   // shells of one staged adjoint tile
 
 static int kappa_grid(ufc_ctx* c, int npix) {
   const int ntile = (npix + kKT - 1) / kKT;
@@ -643,6 +684,20 @@ static int kappa_stages(int S) { return std::max(2, std::min(kKMaxStages, (200 *
 static size_t kappa_smem(int S, bool adj) {
   return (size_t)kappa_stages(S) * S * kKT * 4 + (adj ? (size_t)S * sizeof(AdjRow) : 0);
 }
+// Forward kappa pass shared by ufc_kappa_stats and its allocation-free
+// variant (identical results): grid blocks, one partial sum each in ksum.
+static int kappa_fwd_grid(ufc_ctx* c) { return 8 * c->num_sms; }
+static ufc_status launch_kappa_fwd(ufc_ctx* c, const int32_t* counts, const Coef& cf,
+                                   float* kappa, double* ksum, int grid) {
+  if ((reinterpret_cast<uintptr_t>(kappa) & 15) == 0) {
+    k_kappa_vec<<<grid, kKV, 0, c->stream>>>(counts, cf, kappa, ksum);
+  } else {
+    k_kappa_plain<<<grid, kKT, 0, c->stream>>>(counts, cf, kappa, ksum);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
 static unsigned long long* timeout_counter(ufc_ctx* c) {
   return &reinterpret_cast<BinCounters*>(c->counters)->timeouts;
 }
@@ -666,8 +721,7 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
   make_coef(A, C, S, npix, cf);
   if (reinterpret_cast<uintptr_t>(counts) & 15)
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
-  const bool staged = S <= kStagedMaxShells;
-  const int grid = staged ? kappa_grid(c, npix) : 8 * c->num_sms;
+  const int grid = kappa_fwd_grid(c);
   const int mgrid = 2 * c->num_sms;
   double* ksum = (double*)ws_get(c, kSlotPartials, (size_t)(grid + 3 * mgrid) * 8);
   if (!ksum) return UFC_ERR_ALLOC;
@@ -678,18 +732,11 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
     if (!kmap) return UFC_ERR_ALLOC;
   }
   if (!kmap) return UFC_OK;   // nothing requested
-  if (staged) {
-    const size_t sm = kappa_smem(S, false);
-    UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<true, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  {
     ProfScope ps_(c, "k_kappa");
-    k_kappa<true, false><<<grid, kKT, sm, c->stream>>>(counts, cf, kmap, ksum,
-                                                      AdjOut{nullptr, nullptr, nullptr}, timeout_counter(c));
-  } else {
-    ProfScope ps_(c, "k_kappa");
-    k_kappa_plain<<<grid, kKT, 0, c->stream>>>(counts, cf, kmap, ksum);
+    s = launch_kappa_fwd(c, counts, cf, kmap, ksum, grid);
+    if (s) return s;
   }
-  UFC_CUDA(c, cudaGetLastError());
   if (!want_stats) return UFC_OK;
   PdfParam pp;
   pp.lo = lo;
@@ -732,7 +779,8 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
   if (s) return s;
   if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
   if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
-  if (S > 96) return set_err(c, UFC_ERR_UNSUPPORTED, "the adjoint supports nshell <= 96");
+  if (S > kStagedMaxShells)
+    return set_err(c, UFC_ERR_UNSUPPORTED, "the adjoint supports nshell <= %d", kStagedMaxShells);
   const int npix = 12 * nside * nside;
   Coef cf;
   make_coef(A, C, S, npix, cf);
@@ -849,8 +897,7 @@ ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int
   if (reinterpret_cast<uintptr_t>(counts) & 15)
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
   const int npix = 12 * nside * nside;
-  const bool staged = S <= kStagedMaxShells;
-  const int grid = staged ? kappa_grid(c, npix) : 8 * c->num_sms;
+  const int grid = kappa_fwd_grid(c);
   const int mgrid = 2 * c->num_sms;
   if (grid + 3 * mgrid > kNoAllocScratch)
     return set_err(c, UFC_ERR_CAPACITY,
@@ -862,17 +909,8 @@ ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int
   double* mpart = ksum + grid;   // every slot is written before it is read
   Coef cf;
   make_coef(A, C, S, npix, cf);
-  if (staged) {
-    const size_t sm = kappa_smem(S, false);
-    UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<true, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_kappa<true, false><<<grid, kKT, sm, c->stream>>>(counts, cf, kappa, ksum,
-                                                      AdjOut{nullptr, nullptr, nullptr},
-                                                      timeout_counter(c));
-  } else {
-    k_kappa_plain<<<grid, kKT, 0, c->stream>>>(counts, cf, kappa, ksum);
-  }
-  UFC_CUDA(c, cudaGetLastError());
+  s = launch_kappa_fwd(c, counts, cf, kappa, ksum, grid);
+  if (s) return s;
   PdfParam pp;
   pp.lo = lo;
   pp.hi = hi;

@@ -81,3 +81,52 @@ def test_coefficient_derivatives_vs_oracle_complex_step(api, orc, kind, units):
         G = orc.kappa_stat_grads(counts, nside, 0.3, 0.7, units, boxes_o, z, orc.make_source(**kw), g)
         # <g, kappa> = A_b - C  ->  d/dtheta = dA_b - dC
         assert np.allclose(G[2], dA[:, b] - dC, rtol=1e-11, atol=1e-14 * np.abs(dA).max())
+
+
+@pytest.mark.parametrize("units", [1, 0])
+def test_delta_coeffs_vs_oracle(api, orc, units):
+    """Overdensity coefficients (Eq. 7) of the host library against the
+    oracle, and their dual-number derivatives against 4th-order central
+    differences of the oracle in (Omega_m, h)."""
+    z = np.linspace(0.1, 1.5, 21)
+    boxes_a = [api.make_box(2000.0, [1000.0] * 3, 512 ** 3, 0, 8),
+               api.make_box(6400.0, [3200.0] * 3, 512 ** 3, 8, 20)]
+    boxes_o = [orc.make_box(2000.0, [1000.0] * 3, 512 ** 3, 0, 8),
+               orc.make_box(6400.0, [3200.0] * 3, 512 ** 3, 8, 20)]
+    A, C, dA, dC = api.delta_coeffs(api.make_cosmo(0.3, 0.7, units), boxes_a, z, 256, derivs=True)
+    Ao, Co = orc.delta_coeffs(0.3, 0.7, units, boxes_o, z, 256)
+    assert np.allclose(A, Ao, rtol=1e-12, atol=0)
+    assert C == Co == 1.0
+    assert np.all(dC == 0.0) and np.all(dA[2:] == 0.0)     # n(z) parameters do not enter
+    for j, (om, h) in enumerate([(1, 0), (0, 1)]):
+        e = 1e-3
+        f = lambda t: orc.delta_coeffs(0.3 + om * t, 0.7 + h * t, units, boxes_o, z, 256)[0]
+        fd = (-f(2 * e) + 8 * f(e) - 8 * f(-e) + f(-2 * e)) / (12 * e)
+        assert np.allclose(dA[j], fd, rtol=2e-8, atol=1e-10 * np.abs(A).max())
+
+
+def test_volume_reading_coeffs_vs_oracle(api, orc):
+    """density_volume = 1: kappa and delta coefficients of the host library
+    against the oracle, derivatives against central differences."""
+    z = np.linspace(0.1, 1.5, 21)
+    boxes_a = [api.make_box(2000.0, [1000.0] * 3, 512 ** 3, 0, 8),
+               api.make_box(6400.0, [3200.0] * 3, 512 ** 3, 8, 20)]
+    boxes_o = [orc.make_box(2000.0, [1000.0] * 3, 512 ** 3, 0, 8),
+               orc.make_box(6400.0, [3200.0] * 3, 512 ** 3, 8, 20)]
+    kw = dict(kind=1, z_s=1.5, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    cosmo = api.make_cosmo(0.3, 0.7, 1, density_volume=1)
+    A, B, C, dA, dC = api.kappa_coeffs(cosmo, boxes_a, z, 512, api.make_source(**kw), derivs=True)
+    Ao, Bo, Co = orc.kappa_coeffs(0.3, 0.7, 1, boxes_o, z, 512, orc.make_source(**kw), dens_volume=1)
+    assert np.allclose(A, Ao, rtol=1e-12, atol=0) and np.allclose(B, Bo, rtol=1e-12, atol=0)
+    assert C == pytest.approx(Co, rel=1e-12)
+    e = 1e-3
+    f = lambda t: orc.kappa_coeffs(0.3 + t, 0.7, 1, boxes_o, z, 512, orc.make_source(**kw),
+                                   dens_volume=1)[0]
+    fd = (-f(2 * e) + 8 * f(e) - 8 * f(-e) + f(-2 * e)) / (12 * e)
+    assert np.allclose(dA[0], fd, rtol=2e-7, atol=1e-10 * np.abs(A).max())
+    Ad, Cd = api.delta_coeffs(cosmo, boxes_a, z, 512)
+    Ado, Cdo = orc.delta_coeffs(0.3, 0.7, 1, boxes_o, z, 512, dens_volume=1)
+    assert np.allclose(Ad, Ado, rtol=1e-12, atol=0) and Cd == Cdo == 1.0
+    with pytest.raises(api.UfcError):
+        api.kappa_coeffs(api.make_cosmo(0.3, 0.7, 1, density_volume=2), boxes_a, z, 512,
+                         api.make_source(**kw))

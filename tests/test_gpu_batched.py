@@ -34,8 +34,11 @@ def _realisations(orc, api, nreal, nside, nshell, nbase):
     return z, chi, xs, bxs, np.array(As), np.array(Cs)
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batched_equals_serial(orc, graph):
+@pytest.mark.parametrize("graph,side_stream", [(False, True), (True, True), (True, False)])
+def test_batched_equals_serial(orc, graph, side_stream):
+    """Batched call = the same maps one at a time, bit for bit; with the
+    graph on a side stream and on the legacy default stream (captured on
+    the context's own stream, joined by events)."""
     api, ctx = api_ctx()
     nreal, nside, nshell, nb = 5, 64, 12, 100_000
     z, chi, xs, bxs, A, C = _realisations(orc, api, nreal, nside, nshell, nb)
@@ -52,11 +55,19 @@ def test_batched_equals_serial(orc, graph):
         torch.cuda.synchronize()
         serial.append((mom.clone(), pdf.clone(), v.clone()))
     st_b = api.welford_state(d)
-    stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
+    torch.cuda.synchronize()
+    if side_stream:
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            mom, pdf, stats = ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, st_b,
+                                                graph=graph)
+        stream.synchronize()
+    else:
         mom, pdf, stats = ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, st_b,
                                             graph=graph)
-    stream.synchronize()
+        # ordered on the default stream: no explicit synchronisation before use
+        mom, pdf, stats = mom.clone(), pdf.clone(), stats.clone()
+        torch.cuda.synchronize()
     for r in range(nreal):
         assert torch.equal(mom[r], serial[r][0])
         assert torch.equal(pdf[r], serial[r][1])

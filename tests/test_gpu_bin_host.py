@@ -12,7 +12,7 @@ from tests.gpu_common import api_ctx, both_boxes, to_dev
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-HOST_CHUNK = 3072 * 10240     # particles per staged chunk in the library
+HOST_CHUNK = 1 << 25          # particles per staged chunk in the library
 
 
 def _nested(orc, nshell):

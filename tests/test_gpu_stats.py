@@ -106,3 +106,40 @@ def test_welford_vs_oracle_covariance(orc):
         assert np.allclose(mean.cpu().numpy(), m_o, rtol=1e-12, atol=1e-12)
         assert np.allclose(cov.cpu().numpy(), c_o, rtol=1e-9, atol=1e-12)
         assert np.allclose(corr.cpu().numpy(), r_o, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("nside,nshell", [(64, 20), (256, 40)])
+def test_delta_map_stats_and_gradient(orc, nside, nshell):
+    """Overdensity map of Eq. 7 through ufc_kappa_stats with the library's
+    delta coefficients: map against the oracle's definition, moments and
+    PDF on the GPU's map, and d var / d(Omega_m, h) from ufc_kappa_backward
+    against 4th-order central differences of the FP64 map (Mpc units, where
+    both parameters enter through chi)."""
+    api, ctx = api_ctx()
+    counts, z, ba, bo, kw = _map(orc, api, ctx, nside, nshell, 400_000, 777 + nside)
+    cosmo = api.make_cosmo(0.3, 0.7, 0)
+    A, C, dA, dC = api.delta_coeffs(cosmo, list(ba), z, nside, derivs=True)
+    Ao, Co = orc.delta_coeffs(0.3, 0.7, 0, list(bo), z, nside)
+    assert np.allclose(A, Ao, rtol=1e-12) and C == Co == 1.0
+    cn = counts.cpu().numpy()
+    d_or = orc.kappa_map(cn, Ao, Co)
+    lo, hi = -1.0, float(d_or.max()) * 0.5
+    dmap, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, 100)
+    dg = dmap.cpu().numpy()
+    assert kappa_gate(dg, d_or, Ao, cn).all()
+    m_or = orc.moments(dg)
+    mg = mom.cpu().numpy()
+    for i in (1, 2, 3, 4, 5):
+        assert mg[i] == pytest.approx(m_or[i], rel=1e-9), i
+    assert np.array_equal(pdf.cpu().numpy(), orc.pdf(dg, lo, hi, 100))
+    grad, _, _ = ctx.kappa_backward(counts, A, C, dA, dC, 1.0, 0.0)
+
+    def var(om, h):
+        a, c = orc.delta_coeffs(om, h, 0, list(bo), z, nside)
+        d = a @ cn.astype(np.float64) - c
+        return float(np.mean((d - d.mean()) ** 2))
+    for j, (om, h) in enumerate([(1, 0), (0, 1)]):
+        e = 1e-4
+        f = lambda t: var(0.3 + om * t, 0.7 + h * t)
+        fd = (-f(2 * e) + 8 * f(e) - 8 * f(-e) + f(-2 * e)) / (12 * e)
+        assert grad[j] == pytest.approx(fd, rel=1e-6), j
