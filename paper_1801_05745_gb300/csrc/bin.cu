@@ -18,6 +18,7 @@
 //            once.  No global atomics on the count map.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <vector>
 
@@ -593,18 +594,16 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
         // ---- B: pixels of full groups of 32 pending entries (in the drain
         // step, also of the partial rest)
         const bool tail = h == ng;
-        if (ne < 32 && nc < 32 && !(tail && (ne | nc))) continue;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-          const int cnt = pass == 0 ? ne : nc;
-          const int take = cnt >= 32 ? 32 : ((tail && drain_all) ? cnt : 0);
-          if (take == 0) continue;
-          const float4* L = pass == 0 ? list_eq : list_cap;
-          const int head = pass == 0 ? he : hc;
+        // one instantiation per zone, so that a group runs only its zone's
+        // pixel code
+        auto group_b = [&](auto zone_tag, int take) {
+          constexpr int ZONE = decltype(zone_tag)::value;
+          const float4* L = ZONE == 0 ? list_eq : list_cap;
+          const int head = ZONE == 0 ? he : hc;
           const bool have = lane < take;
           float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
           if (have) ent = L[(head + lane) & (kWList - 1)];
-          if (pass == 0) { he = (he + take) & (kWList - 1); ne -= take; }
+          if constexpr (ZONE == 0) { he = (he + take) & (kWList - 1); ne -= take; }
           else { hc = (hc + take) & (kWList - 1); nc -= take; }
           const float dx = ent.x, dy = ent.y, dz = ent.z;
           const uint32_t meta = __float_as_uint(ent.w);
@@ -613,8 +612,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           const float rinv = rsqrtf(r2);
           const float z = dz * rinv;
           int32_t pix = kKeyUndecided;
-          if (have) pix = pass == 0 ? pixel_fast_eq(N, bd, dx, dy, z)
-                                    : pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
+          if (have) {
+            if constexpr (ZONE == 0) pix = pixel_fast_eq(N, bd, dx, dy, z);
+            else pix = pixel_fast_cap(N, bd, dx, dy, dz, r2, rinv, z);
+          }
           const bool ok = have && pix != kKeyUndecided;
           // the entry's particle (launch-local index pl): chunk from the
           // 12-bit tag, offset in the chunk; computed only where needed
@@ -660,7 +661,11 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
             dense_append(fc.wc, ok, dk, o);
           }
           fc.n_keyed += ok;
-        }
+        };
+        const int take_e = ne >= 32 ? 32 : ((tail && drain_all) ? ne : 0);
+        if (take_e) group_b(std::integral_constant<int, 0>{}, take_e);
+        const int take_c = nc >= 32 ? 32 : ((tail && drain_all) ? nc : 0);
+        if (take_c) group_b(std::integral_constant<int, 1>{}, take_c);
         __syncwarp();
       }
     }

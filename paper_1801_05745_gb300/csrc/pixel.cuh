@@ -186,7 +186,7 @@ __device__ __forceinline__ Azim azimuth_fast(float dx, float dy, const Bands& bd
   const float ax = fabsf(dx), ay = fabsf(dy);
   open |= fmaxf(ax, ay) < bd.axy_min;
   const bool sw = ay > ax;
-  const float q = sw ? __fdividef(ax, ay) : __fdividef(ay, ax);
+  const float q = __fdividef(fminf(ax, ay), fmaxf(ax, ay));   // one division, either octant
   Azim r;
   r.a = atanq_poly(q);                         // quarter turns, [0, 1/2]
   const bool xp = dx >= 0.0f, yp = dy >= 0.0f;
