@@ -33,6 +33,11 @@ METRIC = ("G particles/s binned and kappa maps/s at Nside 1024 (% HBM roofline);
           "batched vs serial")
 UNIT = "Gparticles/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) per particle of the fast stage, from the ncu
+# capture in profiles/k_fast_tma_2x512cubed_nside512.md (two launches of
+# 134.2M particles: 1.868 and 1.839 GB); scaled to a launch by its particle
+# count.  Retake it whenever k_fast_tma changes.
+FAST_TRAFFIC_PER_PARTICLE = (1.868076e9 + 1.838689e9) / 2 / 134217728
 
 
 def hbm_peak():
@@ -420,7 +425,8 @@ def main():
         "bound": "hbm", "kernel": "k_fast",
         "achieved": fast_bytes / (fast_ms * 1e-3) / 1e9 if fast_ms else None,
         "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs",
-        "traffic": None,
+        "traffic": FAST_TRAFFIC_PER_PARTICLE * n_total / 2,
+        "traffic_source": "ncu dram__bytes_read+write of a 2 x 512^3 capture, scaled per particle",
         "per_launch_bytes": 12.0 * n_total / 2, "launches": fast_n,
         "avg_launch_ms": fast_ms / max(fast_n, 1),
     }

@@ -75,27 +75,16 @@ struct Coef {
   float ch, cl;        // C as double-float
   int32_t nshell;
   int32_t npix;
-  int32_t nst;         // stages of the staged kernels
-  int32_t pad_;
 };
 
 // ------------------------------------------------- kappa + adjoint sums ---
-// One pass over the counts.  Each thread owns one pixel of a 256-pixel
-// tile; kappa_p = sum_b A_b n_bp - C is accumulated in double-float.
-//   KAPPA  : writes FP32 kappa and per-block partial sums of kappa.
-//   ADJ    : per-shell sums S1_b = sum_p e_p n_bp, S2_b = sum_p e_p^2 n_bp,
-//            T_b = sum_p g_p n_bp, N_b = sum_p n_bp and global sums
-//            P_k = sum_p e_p^k (k = 1..3), Q = sum_p g_p, e_p = unrounded kappa_p.
-//            The per-pixel factors are quantised per tile to 31-bit integers
-//            (scale 2^s from the tile maximum) and multiplied by the counts
-//            in exact 64-bit integer arithmetic.
-constexpr int kKT = 256;   // threads (pixels) per tile
-
-struct AdjOut {
-  double* part;   // [grid][4*nshell + 4]: S1, S2, T, N per shell, then P1, P2, P3, Q
-  const float* g; // may be null
-  unsigned long long* range_flag;   // set when |e| or |g| exceeds 2^14
-};
+// kappa_p = sum_b A_b n_bp - C is accumulated in double-float over the
+// shells in order.  The adjoint needs per-shell sums S1_b = sum_p e_p n_bp,
+// S2_b = sum_p e_p^2 n_bp, T_b = sum_p g_p n_bp, N_b = sum_p n_bp and global
+// sums P_k = sum_p e_p^k (k = 1..3), Q = sum_p g_p of the unrounded map e;
+// e, e^2 and g are quantised to pairs of integers and multiplied by the
+// counts in exact integer arithmetic.
+constexpr int kKT = 256;   // threads of the scalar-load kappa kernel
 
 // Exact FP32 helpers that avoid the conversion instructions (float->int,
 // round-to-integral), which GB300 executes on its narrow FP64 pipe.
@@ -159,247 +148,6 @@ __device__ __forceinline__ double i128_to_d(I128 a, int frac_bits) {
 // |e|, |g| < 2^14 and |e|^2 < 2^28 every sum fits the 128-bit range.
 constexpr int kFrac1 = 72, kFrac2 = 56, kFrac3 = 72;
 struct AdjRow { I128 s[3]; long long n; long long pad_; };
-
-// --- bulk-copy helpers (TMA, 1-D) ---
-__device__ __forceinline__ uint32_t s_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(n));
-}
-__device__ __forceinline__ void bar_expect(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool bar_try(uint64_t* b, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(s_u32(b)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-constexpr long long kPollLimit = 1ll << 28;
-__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
-  for (long long i = 0; i < kPollLimit; ++i)
-    if (bar_try(b, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          s_u32(dst)),
-      "l"(src), "r"(bytes), "r"(s_u32(b))
-      : "memory");
-}
-
-constexpr int kKMaxStages = 4;
-
-// Tiles of kKT pixels x nshell counts arrive by nshell row copies of
-// kKT*4 bytes into a two-stage ring; counts must be 16-byte aligned and
-// 12 nside^2 is a multiple of 4, so every row copy is a multiple of 16 bytes.
-template <bool KAPPA, bool ADJ>
-__global__ void __launch_bounds__(kKT)
-k_kappa(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
-        double* __restrict__ ksum_part, AdjOut ao, unsigned long long* timeouts) {
-  extern __shared__ __align__(128) int32_t ring_s[];   // [kKStages][nshell][kKT], then 4 doubles/shell
-  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
-  __shared__ double red[kKT / 32];
-  __shared__ int q_s[6][kKT];                   // hi/lo of e, e^2, g
-  __shared__ float fmax_s[4][kKT / 32];
-  __shared__ __align__(8) uint64_t kbar[kKMaxStages];
-  __shared__ int abort_s;
-  const int S = cf.nshell;
-  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
-  AdjRow* rows = reinterpret_cast<AdjRow*>(ring_s + cf.nst * S * kKT);
-  if (ADJ)
-    for (int i = threadIdx.x; i < S; i += blockDim.x) rows[i] = AdjRow{};
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < cf.nst; ++st) bar_init(&kbar[st], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    abort_s = 0;
-  }
-  f2 ks{0.f, 0.f}, p1{0.f, 0.f}, p2{0.f, 0.f}, p3{0.f, 0.f}, qg{0.f, 0.f};
-  __syncthreads();
-  const bool use_g = ADJ && ao.g != nullptr;
-  const int ntile = (cf.npix + kKT - 1) / kKT;
-  const int mine = ntile > (int)blockIdx.x ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  auto issue = [&](int k) {
-    const int tile = blockIdx.x + k * gridDim.x;
-    const int st = k % cf.nst;
-    const int cnt = min(kKT, cf.npix - tile * kKT);
-    const uint32_t rb = uint32_t(cnt) * 4u;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    bar_expect(&kbar[st], rb * uint32_t(S));
-    for (int b = 0; b < S; ++b)
-      bulk_copy(ring_s + (st * S + b) * kKT, counts + (size_t)b * cf.npix + (size_t)tile * kKT, rb,
-                &kbar[st]);
-  };
-  int issued = 0;
-  if (threadIdx.x == 0)
-    for (; issued < mine && issued < cf.nst; ++issued) issue(issued);
-  int k = 0;
-  for (; k < mine; ++k) {
-    const int tile = blockIdx.x + k * gridDim.x;
-    const int st = k % cf.nst;
-    if (!bar_wait(&kbar[st], uint32_t((k / cf.nst) & 1))) abort_s = 1;
-    __syncthreads();
-    if (abort_s) break;
-    const int32_t* cnt_s = ring_s + st * S * kKT;
-    const int p = tile * kKT + threadIdx.x;
-    const bool have = p < cf.npix;
-    f2 acc{0.f, 0.f}, acc2{0.f, 0.f};
-    int nmax = 0;
-    int b = 0;
-    for (; b + 1 < S; b += 2) {                 // two chains for latency
-      const int n0 = have ? cnt_s[b * kKT + threadIdx.x] : 0;
-      const int n1 = have ? cnt_s[(b + 1) * kKT + threadIdx.x] : 0;
-      nmax = max(nmax, max(n0, n1));
-      f2_mac(acc, ah_s[b], al_s[b], float(n0));
-      f2_mac(acc2, ah_s[b + 1], al_s[b + 1], float(n1));
-    }
-    if (b < S) {
-      const int n0 = have ? cnt_s[b * kKT + threadIdx.x] : 0;
-      nmax = max(nmax, n0);
-      f2_mac(acc, ah_s[b], al_s[b], float(n0));
-    }
-    acc = f2_add(f2_norm(acc.h, acc.l), f2_norm(acc2.h, acc2.l));
-    // e = acc - C (unrounded), kappa = round(e)
-    f2 e = f2_add(f2_norm(acc.h, acc.l), f2{-cf.ch, -cf.cl});
-    if (KAPPA && have) {
-      float kf = __fadd_rn(e.h, e.l);
-      kappa[p] = kf;
-      ks = f2_add(ks, f2{kf, 0.f});
-    }
-    if (ADJ) {
-      f2 e2 = f2_mul(e, e);
-      float gv = (use_g && have) ? ao.g[p] : 0.f;
-      if (have) {
-        p1 = f2_add(p1, e);
-        p2 = f2_add(p2, e2);
-        p3 = f2_add(p3, f2_mul(e2, e));
-        qg = f2_add(qg, f2{gv, 0.f});
-      } else {
-        e = {0.f, 0.f};
-        e2 = {0.f, 0.f};
-      }
-      // tile maxima -> power-of-two scales with max 2^s < 2^29
-      float m1 = fabsf(e.h), m2 = fabsf(e2.h), m3 = fabsf(gv), mn = float(nmax);
-      for (int o = 16; o > 0; o >>= 1) {
-        m1 = fmaxf(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
-        m2 = fmaxf(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
-        m3 = fmaxf(m3, __shfl_xor_sync(0xFFFFFFFFu, m3, o));
-        mn = fmaxf(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
-      }
-      if ((threadIdx.x & 31) == 0) {
-        fmax_s[0][threadIdx.x >> 5] = m1;
-        fmax_s[1][threadIdx.x >> 5] = m2;
-        fmax_s[2][threadIdx.x >> 5] = m3;
-        fmax_s[3][threadIdx.x >> 5] = mn;
-      }
-      __syncthreads();
-      float M1 = 0.f, M2 = 0.f, M3 = 0.f, MN = 0.f;
-      for (int i = 0; i < kKT / 32; ++i) {
-        M1 = fmaxf(M1, fmax_s[0][i]);
-        M2 = fmaxf(M2, fmax_s[1][i]);
-        M3 = fmaxf(M3, fmax_s[2][i]);
-        MN = fmaxf(MN, fmax_s[3][i]);
-      }
-      if (threadIdx.x == 0 && (M1 >= 16384.0f || M3 >= 16384.0f || M2 >= 268435456.0f))
-        atomicAdd(ao.range_flag, 1ull);
-      const int s1 = M1 > 0.f ? min(120, 21 - ilog2f(M1)) : 0;
-      const int s2 = M2 > 0.f ? min(120, 21 - ilog2f(M2)) : 0;
-      const int s3 = M3 > 0.f ? min(120, 21 - ilog2f(M3)) : 0;
-      int h, l;
-      quant2(e, s1, h, l);
-      q_s[0][threadIdx.x] = h;
-      q_s[1][threadIdx.x] = l;
-      quant2(e2, s2, h, l);
-      q_s[2][threadIdx.x] = h;
-      q_s[3][threadIdx.x] = l;
-      quant2(f2{gv, 0.f}, s3, h, l);
-      q_s[4][threadIdx.x] = h;
-      q_s[5][threadIdx.x] = l;
-      __syncthreads();
-      // phase 2: warp w owns shells w, w+8, ...; lane l pixels l, l+32, ...
-      // |q| < 2^22 and counts < 2^31 keep the 8-term lane sums below 2^56
-      // and the warp sums below 2^61; the owner lane folds them into the
-      // block's 128-bit fixed-point sums with integer operations only.
-      const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
-      int qv[6][kKT / 32];
-#pragma unroll
-      for (int q = 0; q < kKT / 32; ++q)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) qv[j][q] = q_s[j][ln + 32 * q];
-      for (int b = w; b < S; b += kKT / 32) {
-        long long a[6] = {0, 0, 0, 0, 0, 0};
-        long long an = 0;
-        const int valid = cf.npix - tile * kKT;     // pixels of this tile (last tile may be short)
-#pragma unroll
-        for (int q = 0; q < kKT / 32; ++q) {
-          const int t = ln + 32 * q;
-          const int n = t < valid ? cnt_s[b * kKT + t] : 0;
-          an += n;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) a[j] += (long long)qv[j][q] * n;
-          if (use_g) {
-            a[4] += (long long)qv[4][q] * n;
-            a[5] += (long long)qv[5][q] * n;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 6; ++j) a[j] = warp_sum_ll(a[j]);
-        an = warp_sum_ll(an);
-        if (ln == 0) {
-          AdjRow& row = rows[b];
-          i128_add(row.s[0], a[0], kFrac1 - s1);
-          i128_add(row.s[0], a[1], kFrac1 - s1 - 22);
-          i128_add(row.s[1], a[2], kFrac2 - s2);
-          i128_add(row.s[1], a[3], kFrac2 - s2 - 22);
-          if (use_g) {
-            i128_add(row.s[2], a[4], kFrac3 - s3);
-            i128_add(row.s[2], a[5], kFrac3 - s3 - 22);
-          }
-          row.n += an;
-        }
-      }
-      __syncthreads();
-    }
-    __syncthreads();                           // stage st fully consumed
-    if (threadIdx.x == 0 && issued < mine) issue(issued++);
-  }
-  if (abort_s) {
-    if (threadIdx.x == 0) {
-      atomicAdd(timeouts, 1ull);
-      for (int kk = k; kk < issued; ++kk) bar_wait(&kbar[kk % cf.nst], uint32_t((kk / cf.nst) & 1));
-    }
-    return;
-  }
-  if (KAPPA) {
-    double t = block_sum_d<kKT>(f2_to_d(ks), red);
-    if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
-  }
-  if (ADJ) {
-    double* dst = ao.part + (size_t)blockIdx.x * (4 * S + 4);
-    __syncthreads();
-    for (int b = threadIdx.x; b < S; b += blockDim.x) {
-      dst[4 * b + 0] = i128_to_d(rows[b].s[0], kFrac1);
-      dst[4 * b + 1] = i128_to_d(rows[b].s[1], kFrac2);
-      dst[4 * b + 2] = i128_to_d(rows[b].s[2], kFrac3);
-      dst[4 * b + 3] = (double)rows[b].n;
-    }
-    double v1 = block_sum_d<kKT>(f2_to_d(p1), red);
-    if (threadIdx.x == 0) dst[4 * S + 0] = v1;
-    double v2 = block_sum_d<kKT>(f2_to_d(p2), red);
-    if (threadIdx.x == 0) dst[4 * S + 1] = v2;
-    double v3 = block_sum_d<kKT>(f2_to_d(p3), red);
-    if (threadIdx.x == 0) dst[4 * S + 2] = v3;
-    double v4 = block_sum_d<kKT>(f2_to_d(qg), red);
-    if (threadIdx.x == 0) dst[4 * S + 3] = v4;
-  }
-}
 
 // Forward pass with scalar loads, for a kappa buffer that is not 16-byte
 // aligned.
@@ -465,6 +213,241 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
   }
   const double t = block_sum_d<kKV>(f2_to_d(ks), red);
   if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
+}
+
+// --------------------------------------------- adjoint, two passes -----
+// Pass 1 (k_adj_pre): e_p = sum_b A_b n_bp - C unrounded (double-float, the
+// shells in order), per block the maxima of |e|, e^2, |g| and the sums
+// P1..P3 = sum_p e_p^k, Q = sum_p g_p.
+// Pass 2 (k_adj_main): one quantisation scale per quantity from the global
+// maxima; e_p is recomputed exactly as in pass 1 and split into two integers
+// (quant2); warp w owns shells w, w + 32, w + 64 and each lane a column of
+// the tile's pixels, accumulating q n in 64-bit integers across tiles.  The tile's counts are read a second time from L2.  A bound
+// on the accumulated magnitudes (pixels per lane x tile maximum count x 2^22
+// per tile) triggers a flush into the block's 128-bit fixed-point rows before
+// any 64-bit sum could overflow.
+constexpr int kAdjThreads = 1024;         // pass 2 block: 32 warps, 4096-pixel tiles
+constexpr int kAdjSpw = 3;                // shells per warp in pass 2 (nshell <= 96)
+
+__global__ void __launch_bounds__(kKV)
+k_adj_pre(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
+          float* __restrict__ maxpart, double* __restrict__ sumpart) {
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ double red[kKV / 32];
+  __shared__ float mred[3][kKV / 32];
+  const int S = cf.nshell;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+  __syncthreads();
+  const int ng = cf.npix >> 2;
+  const int4* c4 = reinterpret_cast<const int4*>(counts);
+  const f2 mc{-cf.ch, -cf.cl};
+  f2 p1{0.f, 0.f}, p2{0.f, 0.f}, p3{0.f, 0.f}, qg{0.f, 0.f};
+  float m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  for (int gi = blockIdx.x * kKV + threadIdx.x; gi < ng; gi += gridDim.x * kKV) {
+    f2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+    for (int b = 0; b < S; ++b) {
+      const int4 n = __ldcs(c4 + (size_t)b * ng + gi);
+      const float h = ah_s[b], l = al_s[b];
+      f2_mac(a[0], h, l, float(n.x));
+      f2_mac(a[1], h, l, float(n.y));
+      f2_mac(a[2], h, l, float(n.z));
+      f2_mac(a[3], h, l, float(n.w));
+    }
+    const float4 gv = g ? reinterpret_cast<const float4*>(g)[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float gs[4] = {gv.x, gv.y, gv.z, gv.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const f2 e = f2_add(f2_norm(a[i].h, a[i].l), mc);
+      const f2 e2 = f2_mul(e, e);
+      p1 = f2_add(p1, e);
+      p2 = f2_add(p2, e2);
+      p3 = f2_add(p3, f2_mul(e2, e));
+      qg = f2_add(qg, f2{gs[i], 0.f});
+      m1 = fmaxf(m1, fabsf(e.h));
+      m2 = fmaxf(m2, fabsf(e2.h));
+      m3 = fmaxf(m3, fabsf(gs[i]));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m1 = fmaxf(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
+    m2 = fmaxf(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
+    m3 = fmaxf(m3, __shfl_xor_sync(0xFFFFFFFFu, m3, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    mred[0][threadIdx.x >> 5] = m1;
+    mred[1][threadIdx.x >> 5] = m2;
+    mred[2][threadIdx.x >> 5] = m3;
+  }
+  const double v1 = block_sum_d<kKV>(f2_to_d(p1), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 0] = v1;
+  const double v2 = block_sum_d<kKV>(f2_to_d(p2), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 1] = v2;
+  const double v3 = block_sum_d<kKV>(f2_to_d(p3), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 2] = v3;
+  const double v4 = block_sum_d<kKV>(f2_to_d(qg), red);
+  if (threadIdx.x == 0) {
+    sumpart[4 * blockIdx.x + 3] = v4;
+    float M[3] = {0.f, 0.f, 0.f};
+    for (int w = 0; w < kKV / 32; ++w)
+      for (int j = 0; j < 3; ++j) M[j] = fmaxf(M[j], mred[j][w]);
+    for (int j = 0; j < 3; ++j) maxpart[3 * blockIdx.x + j] = M[j];
+  }
+}
+
+template <bool USE_G>
+__global__ void __launch_bounds__(kAdjThreads, 1)
+k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
+           const float* __restrict__ maxpart, int npre, double* __restrict__ rows_out,
+           unsigned long long* range_flag) {
+  extern __shared__ __align__(16) uint8_t adj_sm[];
+  constexpr int T = kAdjThreads, NW = T / 32, TP = 4 * T;   // TP pixels per tile
+  int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP]
+  AdjRow* rows = reinterpret_cast<AdjRow*>(adj_sm + 24 * TP);  // [nshell]
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ float mred[3][NW];
+  __shared__ int nred[NW];
+  const int S = cf.nshell, npix = cf.npix, ng = npix >> 2;
+  const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < S; i += T) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; rows[i] = AdjRow{}; }
+  // global maxima of pass 1
+  float m1 = 0.f, m2 = 0.f, m3 = 0.f;
+  for (int i = threadIdx.x; i < npre; i += T) {
+    m1 = fmaxf(m1, maxpart[3 * i]);
+    m2 = fmaxf(m2, maxpart[3 * i + 1]);
+    m3 = fmaxf(m3, maxpart[3 * i + 2]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m1 = fmaxf(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
+    m2 = fmaxf(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
+    m3 = fmaxf(m3, __shfl_xor_sync(0xFFFFFFFFu, m3, o));
+  }
+  if (ln == 0) { mred[0][w] = m1; mred[1][w] = m2; mred[2][w] = m3; }
+  __syncthreads();
+  float M1 = 0.f, M2 = 0.f, M3 = 0.f;
+  for (int i = 0; i < NW; ++i) {
+    M1 = fmaxf(M1, mred[0][i]);
+    M2 = fmaxf(M2, mred[1][i]);
+    M3 = fmaxf(M3, mred[2][i]);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (M1 >= 16384.0f || M3 >= 16384.0f || M2 >= 268435456.0f))
+    atomicAdd(range_flag, 1ull);
+  const int s1 = M1 > 0.f ? min(120, 21 - ilog2f(M1)) : 0;
+  const int s2 = M2 > 0.f ? min(120, 21 - ilog2f(M2)) : 0;
+  const int s3 = M3 > 0.f ? min(120, 21 - ilog2f(M3)) : 0;
+  constexpr int NQ = USE_G ? 6 : 4;
+  long long acc[kAdjSpw][NQ + 1];
+#pragma unroll
+  for (int k = 0; k < kAdjSpw; ++k)
+#pragma unroll
+    for (int j = 0; j <= NQ; ++j) acc[k][j] = 0;
+  // shells of this warp: w, w + NW, w + 2 NW
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < kAdjSpw; ++k) {
+      const int b = w + NW * k;
+      long long a[NQ + 1];
+#pragma unroll
+      for (int j = 0; j <= NQ; ++j) { a[j] = warp_sum_ll(acc[k][j]); acc[k][j] = 0; }
+      if (ln == 0 && b < S) {
+        AdjRow& row = rows[b];
+        i128_add(row.s[0], a[0], kFrac1 - s1);
+        i128_add(row.s[0], a[1], kFrac1 - s1 - 22);
+        i128_add(row.s[1], a[2], kFrac2 - s2);
+        i128_add(row.s[1], a[3], kFrac2 - s2 - 22);
+        if (USE_G) {
+          i128_add(row.s[2], a[4], kFrac3 - s3);
+          i128_add(row.s[2], a[5], kFrac3 - s3 - 22);
+        }
+        row.n += a[NQ];
+      }
+    }
+  };
+  const int4* c4 = reinterpret_cast<const int4*>(counts);
+  const f2 mc{-cf.ch, -cf.cl};
+  const int ntile = (npix + TP - 1) / TP;
+  double bound = 0.0;                      // bound on |any 64-bit sum|, uniform
+  for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    // phase 1: e of 4 adjacent pixels per thread, as in pass 1
+    const int gi = tile * T + threadIdx.x;   // group of 4 pixels
+    const bool have = gi < ng;
+    f2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    int nmx = 0;
+    if (have) {
+#pragma unroll 4
+      for (int b = 0; b < S; ++b) {
+        const int4 n = c4[(size_t)b * ng + gi];
+        const float h = ah_s[b], l = al_s[b];
+        nmx = max(nmx, max(max(n.x, n.y), max(n.z, n.w)));
+        f2_mac(a[0], h, l, float(n.x));
+        f2_mac(a[1], h, l, float(n.y));
+        f2_mac(a[2], h, l, float(n.z));
+        f2_mac(a[3], h, l, float(n.w));
+      }
+    }
+    const float4 gv4 = (USE_G && have) ? reinterpret_cast<const float4*>(g)[gi]
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float gs[4] = {gv4.x, gv4.y, gv4.z, gv4.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f2 e = f2_add(f2_norm(a[i].h, a[i].l), mc);
+      f2 e2 = f2_mul(e, e);
+      if (!have) { e = f2{0.f, 0.f}; e2 = f2{0.f, 0.f}; }
+      const int px = 4 * threadIdx.x + i;
+      int h, l;
+      quant2(e, s1, h, l);
+      q_s[px] = h;
+      q_s[TP + px] = l;
+      quant2(e2, s2, h, l);
+      q_s[2 * TP + px] = h;
+      q_s[3 * TP + px] = l;
+      if (USE_G) {
+        quant2(f2{gs[i], 0.f}, s3, h, l);
+        q_s[4 * TP + px] = h;
+        q_s[5 * TP + px] = l;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) nmx = max(nmx, __shfl_xor_sync(0xFFFFFFFFu, nmx, o));
+    if (ln == 0) nred[w] = nmx;
+    __syncthreads();
+    int NMX = 0;
+    for (int i = 0; i < NW; ++i) NMX = max(NMX, nred[i]);
+    const double inc = double(TP / 32) * double(NMX) * 4194304.0;   // per lane, this tile
+    if (bound + inc > 2305843009213693952.0) {                     // 2^61
+      flush();
+      bound = 0.0;
+    }
+    bound += inc;
+    // phase 2: lane ln takes pixels ln, ln + 32, ... of the tile (L2 re-reads)
+    const int base = tile * TP;
+    const int valid = min(TP, npix - base);
+#pragma unroll 4
+    for (int pi = ln; pi < valid; pi += 32) {
+      int qv[NQ];
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) qv[j] = q_s[j * TP + pi];
+#pragma unroll
+      for (int k = 0; k < kAdjSpw; ++k) {
+        const int b = w + NW * k;
+        if (b < S) {
+          const long long n = counts[(size_t)b * npix + base + pi];
+#pragma unroll
+          for (int j = 0; j < NQ; ++j) acc[k][j] += (long long)qv[j] * n;
+          acc[k][NQ] += n;
+        }
+      }
+    }
+    __syncthreads();                       // q_s and nred are rewritten by the next tile
+  }
+  flush();
+  __syncthreads();
+  double* dst = rows_out + (size_t)blockIdx.x * 4 * S;
+  for (int b = threadIdx.x; b < S; b += T) {
+    dst[4 * b + 0] = i128_to_d(rows[b].s[0], kFrac1);
+    dst[4 * b + 1] = i128_to_d(rows[b].s[1], kFrac2);
+    dst[4 * b + 2] = USE_G ? i128_to_d(rows[b].s[2], kFrac3) : 0.0;
+    dst[4 * b + 3] = (double)rows[b].n;
+  }
 }
 
 // ------------------------------------------------ moments + PDF pass -----
@@ -644,10 +627,8 @@ k_welford_final(const double* __restrict__ st, int d, int ddof, double* __restri
 
 // ============================================================== host =====
 
-static int kappa_stages(int S);
 static void make_coef(const double* A, double C, int S, int npix, Coef& cf) {
   std::memset(&cf, 0, sizeof cf);
-  cf.nst = kappa_stages(S);
   for (int b = 0; b < S; ++b) {
     cf.ah[b] = (float)A[b];
     cf.al[b] = (float)(A[b] - (double)cf.ah[b]);
@@ -673,17 +654,8 @@ static ufc_status check_kappa_args(ufc_ctx* c, const int32_t* counts, int S, int
   return UFC_OK;
 }
 
-constexpr int kStagedMaxShells = 96;   // shells of one staged adjoint tile
+constexpr int kAdjMaxShells = kAdjSpw * (kAdjThreads / 32);
 
-static int kappa_grid(ufc_ctx* c, int npix) {
-  const int ntile = (npix + kKT - 1) / kKT;
-  return std::max(1, std::min(ntile, c->num_sms));
-}
-// Stages that fit 200 KB of shared memory (at most 4).
-static int kappa_stages(int S) { return std::max(2, std::min(kKMaxStages, (200 * 1024) / (S * kKT * 4))); }
-static size_t kappa_smem(int S, bool adj) {
-  return (size_t)kappa_stages(S) * S * kKT * 4 + (adj ? (size_t)S * sizeof(AdjRow) : 0);
-}
 // Forward kappa pass shared by ufc_kappa_stats and its allocation-free
 // variant (identical results): grid blocks, one partial sum each in ksum.
 static int kappa_fwd_grid(ufc_ctx* c) { return 8 * c->num_sms; }
@@ -698,9 +670,6 @@ static ufc_status launch_kappa_fwd(ufc_ctx* c, const int32_t* counts, const Coef
   return UFC_OK;
 }
 
-static unsigned long long* timeout_counter(ufc_ctx* c) {
-  return &reinterpret_cast<BinCounters*>(c->counters)->timeouts;
-}
 
 ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
                            const double* A, double C, double lo, double hi, int nbins,
@@ -779,29 +748,46 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
   if (s) return s;
   if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
   if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
-  if (S > kStagedMaxShells)
-    return set_err(c, UFC_ERR_UNSUPPORTED, "the adjoint supports nshell <= %d", kStagedMaxShells);
+  if (S > kAdjMaxShells)
+    return set_err(c, UFC_ERR_UNSUPPORTED, "the adjoint supports nshell <= %d", kAdjMaxShells);
   const int npix = 12 * nside * nside;
   Coef cf;
   make_coef(A, C, S, npix, cf);
   if (reinterpret_cast<uintptr_t>(counts) & 15)
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
-  const int grid = kappa_grid(c, npix);
-  const size_t prow = 4 * S + 4;
-  double* part = (double*)ws_get(c, kSlotPartials, (size_t)grid * prow * 8);
+  if (g && (reinterpret_cast<uintptr_t>(g) & 15))
+    return set_err(c, UFC_ERR_ARG, "g_dev must be 16-byte aligned");
+  const int grid1 = kappa_fwd_grid(c);                    // pass 1 blocks
+  const int grid2 = c->num_sms;                            // pass 2 blocks
+  const size_t nrow = (size_t)grid2 * 4 * S, nsum = (size_t)grid1 * 4;
+  double* part = (double*)ws_get(c, kSlotPartials, (nrow + nsum) * 8 + (size_t)grid1 * 3 * 4);
   if (!part) return UFC_ERR_ALLOC;
-  const size_t smem = kappa_smem(S, true);
-  UFC_CUDA(c, cudaFuncSetAttribute(k_kappa<false, true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  double* rows = part;
+  double* sums = part + nrow;
+  float* maxp = reinterpret_cast<float*>(sums + nsum);
   BinCounters* bc = reinterpret_cast<BinCounters*>(c->counters);
   UFC_CUDA(c, cudaMemsetAsync(&bc->range, 0, sizeof(unsigned long long), c->stream));
   {
-    ProfScope ps_(c, "k_kappa_adjoint");
-    k_kappa<false, true><<<grid, kKT, smem, c->stream>>>(counts, cf, nullptr, nullptr,
-                                                        AdjOut{part, g, &bc->range}, timeout_counter(c));
+    ProfScope ps_(c, "k_adj_pre");
+    k_adj_pre<<<grid1, kKV, 0, c->stream>>>(counts, cf, g, maxp, sums);
   }
   UFC_CUDA(c, cudaGetLastError());
-  std::vector<double> hp((size_t)grid * prow);
+  const size_t smem2 = (size_t)24 * 4 * kAdjThreads + (size_t)S * sizeof(AdjRow);
+  {
+    ProfScope ps_(c, "k_adj_main");
+    if (g) {
+      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem2));
+      k_adj_main<true><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, g, maxp, grid1, rows, &bc->range);
+    } else {
+      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem2));
+      k_adj_main<false><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, nullptr, maxp, grid1, rows,
+                                                         &bc->range);
+    }
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  std::vector<double> hp(nrow + nsum);
   unsigned long long range_hits = 0;
   UFC_CUDA(c, cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
   UFC_CUDA(c, cudaMemcpyAsync(&range_hits, &bc->range, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -811,18 +797,21 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
                    "adjoint needs |kappa_p| < 2^14 and |g_p| < 2^14 (fixed-point range)");
   std::vector<double> S1(S, 0.0), S2(S, 0.0), T(S, 0.0), Nb(S, 0.0);
   double P1 = 0, P2 = 0, P3 = 0, Q = 0;
-  for (int i = 0; i < grid; ++i) {
-    const double* r = hp.data() + (size_t)i * prow;
+  for (int i = 0; i < grid2; ++i) {
+    const double* r = hp.data() + (size_t)i * 4 * S;
     for (int b = 0; b < S; ++b) {
       S1[b] += r[4 * b];
       S2[b] += r[4 * b + 1];
       T[b] += r[4 * b + 2];
       Nb[b] += r[4 * b + 3];
     }
-    P1 += r[4 * S];
-    P2 += r[4 * S + 1];
-    P3 += r[4 * S + 2];
-    Q += r[4 * S + 3];
+  }
+  for (int i = 0; i < grid1; ++i) {
+    const double* r = hp.data() + nrow + 4 * (size_t)i;
+    P1 += r[0];
+    P2 += r[1];
+    P3 += r[2];
+    Q += r[3];
   }
   // central moments of the unrounded map from the raw sums about 0
   const double N = npix;
