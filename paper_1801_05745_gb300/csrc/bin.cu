@@ -413,8 +413,8 @@ __device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo,
 // are drained after every (chunk, image) pass.  Particle p of the launch is
 // element p_off + p of the caller's array (chunked launches of ufc_bin_host).
 constexpr int kWThreads = 768;
-constexpr int kWChunk = 2304;                  // particles per chunk (27 KB)
-constexpr int kWStages = 3;
+constexpr int kWChunk = 3072;                  // particles per chunk (36 KB)
+constexpr int kWStages = 2;
 constexpr int kWWarps = kWThreads / 32;        // 24
 constexpr int kWPerWarp = kWChunk / kWWarps;   // 64
 constexpr int kWGroups = kWPerWarp / 32;
@@ -750,8 +750,11 @@ k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues
       const int b = qbox(e), img = qimg(e);
       p = qidx(e);
       const BoxGeom& g = bp.box[b];
-      const int n1 = 2 * g.R + 1;
-      const int ii = img / (n1 * n1), jj = (img / n1) % n1, kk = img % n1;
+      int ii = 0, jj = 0, kk = 0;
+      if (g.R) {                                   // periodic images only
+        const int n1 = 2 * g.R + 1;
+        ii = img / (n1 * n1); jj = (img / n1) % n1; kk = img % n1;
+      }
       const float* xp = bp.xyz[b] + 3 * p;
       float x = xp[0], y = xp[1], zc = xp[2];
       key = key_refine(st, g.shell_lo, g.shell_hi, N, npix, x, y, zc, g.shf[0][ii],

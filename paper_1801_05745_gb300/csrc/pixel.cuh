@@ -388,9 +388,18 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
   df r2 = df_add(s2, df_mul(dz, dz));
   df r = df_sqrt(r2);
   if (!(r.h > 0.0f)) return kKeyUndecided;
-  // shell: compare r with the FP64 edges (linear scan; this stage is rare)
-  int32_t b = -1;
-  for (int32_t e = lo; e <= hi; ++e) {
+  // shell: the last edge whose FP32 part is <= r.h by binary search, then the
+  // double-float rule from the edge below it.  Edges are >= 3e-6 apart
+  // (relative), far more than an FP32 ulp plus the band, so every edge two
+  // or more below the candidate is below r beyond the band.
+  int32_t cand = lo - 1;
+  for (int32_t L = lo, H = hi; L <= H;) {
+    const int32_t mid = (L + H) >> 1;
+    if (st.chih[mid] <= r.h) { cand = mid; L = mid + 1; } else { H = mid - 1; }
+  }
+  const int32_t e0 = cand - 1 > lo ? cand - 1 : lo;
+  int32_t b = e0 - 1;                                // lo - 1: below the first edge
+  for (int32_t e = e0; e <= hi; ++e) {
     df c = {st.chih[e], st.chil[e]};
     df dd = df_sub(r, c);
     float tol = 4.0f * kRefineRel * r.h;
@@ -449,9 +458,9 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
     open |= ir > N;
     ir = ir > N ? N : ir;
     int32_t fl = floor_df_certain(df_mulf(sa, i2f_fast(ir)), kRefineRel * 8.0f * i2f_fast(ir + 1), open);
-    int32_t ip = base * ir + fl;
-    int32_t m = 4 * ir;
-    ip = ((ip % m) + m) % m;
+    int32_t ip = base * ir + fl;                    // in [-1.5 ir, 4.5 ir]
+    const int32_t m = 4 * ir;
+    ip = ip < 0 ? ip + m : (ip >= m ? ip - m : ip);
     pix = (z.h > 0.0f) ? 2 * ir * (ir - 1) + ip : 12 * N * N - 2 * ir * (ir + 1) + ip;
   }
   if (open) return kKeyUndecided;
