@@ -75,3 +75,19 @@ def test_host_input_rejects_bad_arguments(orc):
         ctx.bin_host([to_dev(np.zeros((10, 3), np.float32))], [b], chi, 64)
     with pytest.raises(api.UfcError):
         ctx.bin_host([np.zeros((10, 3), np.float32)], [b], chi, 63)
+
+
+def test_host_input_periodic_images(orc):
+    """64^3 particles of a 500 Mpc/h box with 4 image layers (729 images per
+    particle: the pending lists drain after every pass) from host memory."""
+    api, ctx = api_ctx()
+    from paper_1801_05745_gb300 import synth as sy
+    L = 500.0
+    xyz = sy.particles_numpy(64 ** 3, L, 5.0, sy.seed_for(1, 1, 0))
+    c0, c1 = orc.comoving_distance(0.3, 0.7, 1, 0.1), orc.comoving_distance(0.3, 0.7, 1, 0.5)
+    chi = np.linspace(c0, c1, 11)
+    ba, bo = both_boxes(api, orc, L, [L / 2] * 3, len(xyz), 0, 10, R=4)
+    got = ctx.bin_host([xyz], [ba], chi, 64)
+    ctx.synchronize()
+    ref, inv = orc.bin_counts(xyz, bo, chi, 64)
+    assert np.array_equal(got.cpu().numpy(), ref)
