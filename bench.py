@@ -165,7 +165,8 @@ def cpu_baseline(w, parts_host, counts_host, A, C, dAC, seconds_budget=20.0):
 
 
 # ------------------------------------------------- batched vs serial leg ----
-def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8):
+def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8,
+                nside: int | None = None):
     """Covariance of n_real realisations of the nested Nside-512 map, each box
     holding Poisson(f n_side^3) particles, f ~ U(0.5, 1.5): one graph-captured
     ufc_batched_stats call against the same maps one at a time through
@@ -178,6 +179,9 @@ def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8):
     import torch
     from paper_1801_05745_gb300 import workloads
     wb = workloads.batched(n_real, n_side)
+    if nside is not None:
+        wb.nside = nside
+        wb.name = f"batched_nside{nside}"
     z, chi, split = shells(wb, api=api)
     cosmo = api.make_cosmo(wb.omega_m, wb.h, 1)
     src = api.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
@@ -456,6 +460,9 @@ def main():
     if not args.no_batched:
         line["batched_vs_serial"] = batched_leg(ctx, api, synth, dev, args.batched_real,
                                                 args.batched_side)
+        # small maps, where launch overheads matter: 2 x 64^3 particles, Nside 64
+        line["batched_vs_serial_small"] = batched_leg(ctx, api, synth, dev, args.batched_real,
+                                                      64, nside=64)
 
     # end to end: particles from pinned host memory through the C ABI each
     # step (ufc_bin_host copies them in chunks, overlapped with the binning),

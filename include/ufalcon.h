@@ -287,7 +287,11 @@ ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
  * realisation work is captured into one CUDA graph and launched once (the
  * context stream must not be capturing already; on the legacy default
  * stream the graph is captured and launched on a stream of the context,
- * ordered after earlier work and before later work by events).
+ * ordered after earlier work and before later work by events).  The
+ * executable graph stays in the context: a call whose host arguments
+ * (pointers, sizes, boxes, shell edges, coefficients, PDF range) equal the
+ * previous graph call's relaunches it without capture, reading the particle
+ * buffers' current contents; other calls update or rebuild it.
  * Asynchronous. */
 ufc_status ufc_batched_stats(ufc_ctx *ctx, int32_t nreal, int32_t nbox,
                              const float *const *xyz_dev, const int64_t *n,

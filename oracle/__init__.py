@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SOURCES = ["healpix.c", "lightcone.c", "cosmo.c", "stats.c"]
+_SOURCES = ["healpix.c", "lightcone.c", "cosmo.c", "stats.c", "sht.c"]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -100,6 +100,10 @@ def _declare(L):
         "or_shell_weights": (None, [D, P, I32, P, P]),
         "or_kappa_coeffs": (None, [D, D, ctypes.c_int, ctypes.c_int, P, I32, P, I32, I64, P, P, P, P]),
         "or_delta_coeffs": (None, [D, D, ctypes.c_int, ctypes.c_int, P, I32, P, I32, I64, P, P]),
+        "or_alm_index": (I64, [I32, I32, I32]),
+        "or_lambda_lm": (None, [D, D, I32, P]),
+        "or_map2alm": (None, [P, I64, I32, P, P]),
+        "or_alm2cl": (None, [P, P, I32, P]),
         "or_kappa_map": (None, [P, I32, I64, P, D, P]),
         "or_moments": (None, [P, I64, P]),
         "or_pdf": (None, [P, I64, D, D, I32, P]),
@@ -222,6 +226,39 @@ def delta_coeffs(omega_m, h, units_mpc_over_h, boxes, z_edges, nside, dens_volum
     lib().or_delta_coeffs(omega_m, h, units_mpc_over_h, dens_volume, bp, len(boxes), _ptr(z), ns,
                           nside, _ptr(A), ctypes.byref(C))
     return A, C.value
+
+
+# ---- spherical-harmonic analysis --------------------------------------------------
+def alm_size(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def alm_index(lmax: int, l: int, m: int) -> int:
+    """m-major index of a_lm: m (2 lmax + 1 - m) / 2 + l."""
+    return int(lib().or_alm_index(lmax, l, m))
+
+
+def lambda_lm(z: float, lmax: int) -> np.ndarray:
+    """Orthonormal associated Legendre functions lambda_lm(z) (m-major)."""
+    out = np.empty(alm_size(lmax))
+    lib().or_lambda_lm(float(z), float(np.sqrt((1.0 - z) * (1.0 + z))), lmax, _ptr(out))
+    return out
+
+
+def map2alm(m: np.ndarray, nside: int, lmax: int) -> np.ndarray:
+    """complex128 a_lm (m-major) of a RING map by the direct sum over pixels."""
+    mp = np.ascontiguousarray(m, dtype=np.float32)
+    re, im = np.empty(alm_size(lmax)), np.empty(alm_size(lmax))
+    lib().or_map2alm(_ptr(mp), nside, lmax, _ptr(re), _ptr(im))
+    return re + 1j * im
+
+
+def alm2cl(alm: np.ndarray, lmax: int) -> np.ndarray:
+    re = np.ascontiguousarray(alm.real, dtype=np.float64)
+    im = np.ascontiguousarray(alm.imag, dtype=np.float64)
+    out = np.empty(lmax + 1)
+    lib().or_alm2cl(_ptr(re), _ptr(im), lmax, _ptr(out))
+    return out
 
 
 # ---- statistics --------------------------------------------------------------------

@@ -120,6 +120,16 @@ void or_kappa_stats_f64(const int32_t *counts, int32_t nshell, int64_t nside,
                         const double *z_edges, const or_source *src,
                         const float *g, double *out);
 
+/* ---- Spherical-harmonic analysis (full-sky C_l of Sec. 3.2) ----------------- */
+/* a_lm index m (2 lmax + 1 - m) / 2 + l, 0 <= m <= l <= lmax. */
+int64_t or_alm_index(int32_t lmax, int32_t l, int32_t m);
+/* Orthonormal associated Legendre functions lambda_lm(z), s = sqrt(1 - z^2). */
+void or_lambda_lm(double z, double s, int32_t lmax, double *lam);
+/* a_lm = (4 pi / N_pix) sum_p map_p Y*_lm at the RING pixel centres. */
+void or_map2alm(const float *map, int64_t nside, int32_t lmax, double *alm_re, double *alm_im);
+/* C_l = (|a_l0|^2 + 2 sum_{m>0} |a_lm|^2) / (2l + 1). */
+void or_alm2cl(const double *alm_re, const double *alm_im, int32_t lmax, double *cl);
+
 #ifdef __cplusplus
 }
 #endif

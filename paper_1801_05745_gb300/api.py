@@ -331,6 +331,8 @@ class Context:
         gp = None
         if g_kappa is not None:
             g_kappa = _dev_f32(g_kappa, self.device)
+            if g_kappa.data_ptr() % 16:          # the adjoint reads g with 16-byte loads
+                g_kappa = g_kappa.clone()
             gp = P(g_kappa.data_ptr())
         self._stream()
         self._ck(_lib.ufc_kappa_backward(self.h, P(counts.data_ptr()), S, nside, _np_ptr(A),

@@ -34,6 +34,11 @@ struct ufc_ctx {
   // captured on aux_stream, forked and joined by aux_ev
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t aux_ev[2] = {nullptr, nullptr};
+  // executable graph of the last ufc_batched_stats call with UFC_BATCH_GRAPH
+  // and that call's host arguments, byte for byte; dropped whenever a
+  // workspace buffer it refers to is reallocated
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
 };
 
 namespace ufc {
