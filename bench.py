@@ -320,6 +320,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cl", action="store_true")
     ap.add_argument("--batched-real", type=int, default=150)
     ap.add_argument("--batched-side", type=int, default=512)
     args = ap.parse_args()
@@ -456,6 +457,34 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+
+    if not args.no_cl:
+        # full-sky C_l of the step's kappa map: a_lm, C_l
+        # and band powers at lmax = 3 nside - 1
+        lmax = 3 * w.nside - 1
+        alm = ctx.map2alm(kap, w.nside, lmax)
+        cl = ctx.alm2cl(alm, lmax)
+        bp = ctx.cl_bin(cl, lmax, 10, 10, (lmax - 9) // 10)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        e0.record(stream)
+        for _ in range(3):
+            ctx.map2alm(kap, w.nside, lmax, out=alm)
+            ctx.alm2cl(alm, lmax, out=cl)
+            ctx.cl_bin(cl, lmax, 10, 10, (lmax - 9) // 10, out=bp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        cprof = ctx.profile_read()
+        ctx.profile(False)
+        ms_cl = e0.elapsed_time(e1) / 3
+        npairs = 2 * w.nside
+        nalm = (lmax + 1) * (lmax + 2) // 2
+        fp64 = 6.0 * npairs * nalm          # recurrence + accumulation per (l, m, ring pair)
+        leg = cprof.get("k_legendre", (0.0, 1))
+        line["cl"] = {"nside": w.nside, "lmax": lmax, "ms_per_map": ms_cl,
+                      "maps_per_s": 1e3 / ms_cl,
+                      "kernels_ms_per_map": {k: round(v[0] / 3, 3) for k, v in cprof.items()},
+                      "k_legendre_fp64_tflops": fp64 / (leg[0] / 3 * 1e-3) / 1e12 if leg[0] else None}
 
     if not args.no_batched:
         line["batched_vs_serial"] = batched_leg(ctx, api, synth, dev, args.batched_real,

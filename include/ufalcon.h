@@ -270,6 +270,31 @@ ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
                               const double *dC, double *grad_theta, double *G,
                               double *H);
 
+/* ---- full-sky power spectrum (Sec. 3.2) ------------------ */
+
+/* Spherical-harmonic coefficients of a RING map (FP32 [12 nside^2], e.g.
+ * kappa or delta from ufc_kappa_stats):
+ *   a_lm = (4 pi / N_pix) sum_p map_p Y*_lm(theta_p, phi_p),  0 <= m <= l <= lmax,
+ * at the pixel centres, Y_lm orthonormal with the Condon-Shortley phase.
+ * alm_dev: FP64 (re, im) pairs, m-major (index m (2 lmax + 1 - m)/2 + l),
+ * (lmax+1)(lmax+2)/2 of them, 16-byte aligned.  nside a power of two
+ * <= 1024 (UFC_ERR_UNSUPPORTED above), 0 <= lmax <= 4 nside (the usual
+ * choice is 3 nside - 1).  Workspace about 16 (lmax+1)(4 nside) + 12 (lmax+1)
+ * (2 nside) + 16 (lmax+1)(lmax+2)/2 ceil(nside/512) bytes.  Asynchronous. */
+ufc_status ufc_map2alm(ufc_ctx *ctx, const float *map_dev, int32_t nside,
+                       int32_t lmax, double *alm_dev);
+/* Angular power spectrum of a real map from its a_lm (layout as above):
+ * cl_dev[l] = (|a_l0|^2 + 2 sum_{m=1..l} |a_lm|^2) / (2l + 1), l = 0..lmax.
+ * Its covariance over realisations: ufc_welford_update on (binned) C_l. */
+ufc_status ufc_alm2cl(ufc_ctx *ctx, const double *alm_dev, int32_t lmax,
+                      double *cl_dev);
+/* Band powers for the binned C_l covariance (the paper bins with
+ * Delta l = 4, 10, 24): out_dev[b] = mean of cl_dev[l] over
+ * l in [lmin + b dl, lmin + (b+1) dl), b < nbins; the bins must lie in
+ * [0, lmax].  Feed them to ufc_welford_update for their covariance. */
+ufc_status ufc_cl_bin(ufc_ctx *ctx, const double *cl_dev, int32_t lmax,
+                      int32_t lmin, int32_t dl, int32_t nbins, double *out_dev);
+
 /* ---- covariance over realisations (Eq. 10-11) ------------------------------ */
 
 #define UFC_BATCH_GRAPH 1      /* capture the whole batch into one CUDA graph */

@@ -96,6 +96,9 @@ _SIGS = {
     "ufc_stats_vector": [P, P, P, I32, P],
     "ufc_batched_stats": [P, I32, I32, P, P, P, P, I32, I32, P, P, D, D, I32, P, P, P, P, P, P, I32],
     "ufc_kappa_stats_noalloc": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
+    "ufc_map2alm": [P, P, I32, I32, P],
+    "ufc_alm2cl": [P, P, I32, P],
+    "ufc_cl_bin": [P, P, I32, I32, I32, I32, P],
     "ufc_profile_enable": [P, I32],
     "ufc_profile_read": [P, I32, P, P, P, P],
 }
@@ -375,6 +378,37 @@ class Context:
                                         P(pdf.data_ptr()), P(stats.data_ptr()), P(state.data_ptr()),
                                         UFC_BATCH_GRAPH if graph else 0), "ufc_batched_stats")
         return mom, pdf, stats
+
+    # -- full-sky power spectrum --
+    def map2alm(self, m, nside: int, lmax: int, out=None):
+        """complex128 a_lm [(lmax+1)(lmax+2)/2], m-major, of a FP32 RING map."""
+        import torch
+        m = _dev_f32(m, self.device)
+        nalm = (lmax + 1) * (lmax + 2) // 2
+        if out is None:
+            out = torch.empty(nalm, dtype=torch.complex128, device=m.device)
+        self._stream()
+        self._ck(_lib.ufc_map2alm(self.h, P(m.data_ptr()), nside, lmax, P(out.data_ptr())),
+                 "ufc_map2alm")
+        return out
+
+    def alm2cl(self, alm, lmax: int, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(lmax + 1, dtype=torch.float64, device=alm.device)
+        self._stream()
+        self._ck(_lib.ufc_alm2cl(self.h, P(alm.data_ptr()), lmax, P(out.data_ptr())), "ufc_alm2cl")
+        return out
+
+    def cl_bin(self, cl, lmax: int, lmin: int, dl: int, nbins: int, out=None):
+        """Band powers: means of C_l over [lmin + b dl, lmin + (b+1) dl)."""
+        import torch
+        if out is None:
+            out = torch.empty(nbins, dtype=torch.float64, device=cl.device)
+        self._stream()
+        self._ck(_lib.ufc_cl_bin(self.h, P(cl.data_ptr()), lmax, lmin, dl, nbins,
+                                 P(out.data_ptr())), "ufc_cl_bin")
+        return out
 
     # -- covariance --
     def stats_vector(self, moments, pdf, out=None):

@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libufalcon_gb300.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["bin.cu", "stats.cu", "capi.cu"]
+CU = ["bin.cu", "stats.cu", "sht.cu", "capi.cu"]
 CPP = ["cosmo.cpp"]
 HEADERS = ["common.cuh", "pixel.cuh", "ctx.h"]
 

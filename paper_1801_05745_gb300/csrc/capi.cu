@@ -31,6 +31,10 @@ ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, d
                                 double* cov, double* corr);
 ufc_status reserve_bin_workspace(ufc_ctx* c, int64_t fast_launches, int64_t total_img,
                                  int nshell, int nside);
+ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double* alm_out);
+ufc_status run_alm2cl(ufc_ctx* c, const double* alm, int lmax, double* cl);
+ufc_status run_cl_bin(ufc_ctx* c, const double* cl, int lmax, int lmin, int dl, int nbins,
+                      double* out);
 ufc_status cosmo_chi_edges(const ufc_cosmo& c, const double* z, int n, double* chi);
 ufc_status cosmo_z_of_chi(const ufc_cosmo& c, const double* chi, int n, double* zout);
 ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
@@ -336,6 +340,29 @@ ufc_status ufc_bin_host(ufc_ctx* c, const float* const* xyz_host, const int64_t*
     return set_err(c, UFC_ERR_UNSUPPORTED, "ufc_bin_host cannot be captured into a graph");
   return run_keys_pipeline(c, 1, nullptr, n, boxes, nbox, chi_edges, nshell, nside, flags,
                            counts_dev, nullptr, xyz_host);
+}
+
+ufc_status ufc_map2alm(ufc_ctx* c, const float* map_dev, int32_t nside, int32_t lmax,
+                       double* alm_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_map2alm(c, map_dev, nside, lmax, alm_dev);
+}
+
+ufc_status ufc_alm2cl(ufc_ctx* c, const double* alm_dev, int32_t lmax, double* cl_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_alm2cl(c, alm_dev, lmax, cl_dev);
+}
+
+ufc_status ufc_cl_bin(ufc_ctx* c, const double* cl_dev, int32_t lmax, int32_t lmin, int32_t dl,
+                      int32_t nbins, double* out_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_cl_bin(c, cl_dev, lmax, lmin, dl, nbins, out_dev);
 }
 
 ufc_status ufc_bin_info(ufc_ctx* c, int64_t info[4]) {

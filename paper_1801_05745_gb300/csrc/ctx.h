@@ -57,6 +57,7 @@ enum Slot {
   kSlotCoeffs,
   kSlotMisc,
   kSlotStage,      // device copy of host particle positions (ufc_bin_host)
+  kSlotSht,        // ring transforms, Legendre seeds, partial a_lm (ufc_map2alm)
 };
 
 inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {
