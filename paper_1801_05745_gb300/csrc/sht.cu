@@ -226,7 +226,11 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
         v1[q] = mu[(size_t)m * npairs + p];
         e[q] = ex[(size_t)m * npairs + p];
       }
-      scale[q] = e[q] > -1070 ? ldexp(1.0, e[q]) : 0.0;
+      // 2^e folded into F while it is a normal number far from underflow;
+      // below 2^-960 the pair's terms (< 2^-460 |F|) are dropped
+      scale[q] = e[q] > -960 ? ldexp(1.0, e[q]) : 0.0;
+      E[q] = make_double2(E[q].x * scale[q], E[q].y * scale[q]);
+      O[q] = make_double2(O[q].x * scale[q], O[q].y * scale[q]);
     }
     const double c1 = sqrt(2.0 * m + 3.0);
     const size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;   // index of (l = 0, m)
@@ -264,21 +268,37 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
             v2[q] = v1[q];
             v1[q] = v;
           }
-          if (fabs(v1[q]) > 0x1p500) {        // keep the mantissas in range
-            v1[q] *= 0x1p-500;
-            v2[q] *= 0x1p-500;
-            v = v1[q];
-            e[q] += 500;
-            scale[q] = e[q] > -1070 ? ldexp(1.0, e[q]) : 0.0;
-          }
-          const double lam = v * scale[q];
           const double2 f = odd ? O[q] : E[q];
-          cr = fma(lam, f.x, cr);
-          ci = fma(lam, f.y, ci);
+          cr = fma(v, f.x, cr);
+          ci = fma(v, f.y, ci);
         }
         cr = warp_sum_dd(cr);
         ci = warp_sum_dd(ci);
         if (lane == 0) red[warp][t] = make_double2(cr, ci);
+      }
+      // keep the mantissas in range: one step grows them by less than
+      // a (1 + b) < 2 sqrt(2 l) <= 2^8, so after a check every kLegChunkL
+      // (32) steps they stay below 2^(500 + 256)
+#pragma unroll
+      for (int q = 0; q < kLegPPT; ++q) {
+        while (fabs(v1[q]) > 0x1p500 || fabs(v2[q]) > 0x1p500) {
+          v1[q] *= 0x1p-500;
+          v2[q] *= 0x1p-500;
+          e[q] += 500;
+          if (scale[q] > 0.0) {            // exact: powers of two on normal numbers
+            E[q] = make_double2(E[q].x * 0x1p500, E[q].y * 0x1p500);
+            O[q] = make_double2(O[q].x * 0x1p500, O[q].y * 0x1p500);
+            scale[q] = ldexp(1.0, e[q]);
+          } else if (e[q] > -960) {        // the factor becomes representable
+            scale[q] = ldexp(1.0, e[q]);
+            const int p = pp[q];
+            const double2 fn = F[(size_t)m * nrings + p];
+            const int ps = nrings - 1 - p;
+            const double2 fs = ps != p ? F[(size_t)m * nrings + ps] : make_double2(0.0, 0.0);
+            E[q] = make_double2((fn.x + fs.x) * scale[q], (fn.y + fs.y) * scale[q]);
+            O[q] = make_double2((fn.x - fs.x) * scale[q], (fn.y - fs.y) * scale[q]);
+          }
+        }
       }
       __syncthreads();
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
