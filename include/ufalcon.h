@@ -205,6 +205,22 @@ ufc_status ufc_bin_host(ufc_ctx *ctx, const float *const *xyz_host, const int64_
                         const ufc_box *boxes, int32_t nbox, const double *chi_edges,
                         int32_t nshell, int32_t nside, int32_t flags,
                         int32_t *counts_dev);
+/* ufc_bin from host memory for particle sets of any size (beyond device
+ * memory): each box's particles are cut into chunks of at most `chunk`
+ * particles, copied into one of two device buffers owned by the context
+ * while the previous chunk is binned from the other, and every chunk is
+ * binned into counts_dev like a ufc_bin call (accumulating after the
+ * first; UFC_BIN_ACCUMULATE adds the first chunk too).  Device memory held:
+ * 2 x 12 chunk bytes plus one chunk's binning workspace.  Counts equal
+ * ufc_bin's.  Larger chunks amortise the per-chunk work (at large maps each
+ * chunk's histogram pass touches the whole map).  ufc_bin_info then
+ * describes the last chunk.  Host buffers as for ufc_bin_host.
+ * UFC_ERR_UNSUPPORTED while the context stream is capturing. */
+ufc_status ufc_bin_host_stream(ufc_ctx *ctx, const float *const *xyz_host,
+                               const int64_t *n, const ufc_box *boxes,
+                               int32_t nbox, const double *chi_edges,
+                               int32_t nshell, int32_t nside, int32_t flags,
+                               int64_t chunk, int32_t *counts_dev);
 /* Diagnostics of the last ufc_bin/ufc_keys call (synchronises):
  * info[0] invalid particles, info[1] particle-images with a key,
  * info[2] decisions refined past the FP32 stage, info[3] past the
@@ -294,6 +310,25 @@ ufc_status ufc_alm2cl(ufc_ctx *ctx, const double *alm_dev, int32_t lmax,
  * [0, lmax].  Feed them to ufc_welford_update for their covariance. */
 ufc_status ufc_cl_bin(ufc_ctx *ctx, const double *cl_dev, int32_t lmax,
                       int32_t lmin, int32_t dl, int32_t nbins, double *out_dev);
+
+/* ---- smoothed maps (Sec. 3.3) ----------------------------- */
+
+/* Gaussian beam in harmonic space: alm_out[l, m] = alm_in[l, m] b_l,
+ * b_l = exp(-l(l+1) sigma^2 / 2), sigma the beam's r.m.s. radius in
+ * radians (the paper smooths with 10.8 arcmin).  In place allowed. */
+ufc_status ufc_alm_beam(ufc_ctx *ctx, const double *alm_in_dev, int32_t lmax,
+                        double sigma, double *alm_out_dev);
+/* The real field with coefficients a_lm (layout of ufc_map2alm) at the RING
+ * pixel centres: map_p = sum_l sum_{m>=0} (2 - delta_m0) Re(a_lm Y_lm(p)),
+ * written as FP32 [12 nside^2].  Same nside and lmax limits as ufc_map2alm. */
+ufc_status ufc_alm2map(ufc_ctx *ctx, const double *alm_dev, int32_t nside,
+                       int32_t lmax, float *map_dev);
+/* Moments (the 10 of ufc_kappa_stats, including s^2 and sigma^2_{s^2} of
+ * Eq. 12-13) and PDF of any FP32 RING map (16-byte aligned), e.g. a map
+ * smoothed with ufc_alm_beam + ufc_alm2map. */
+ufc_status ufc_map_stats(ufc_ctx *ctx, const float *map_dev, int32_t nside,
+                         double pdf_lo, double pdf_hi, int32_t nbins,
+                         double *moments_dev, int64_t *pdf_dev);
 
 /* ---- covariance over realisations (Eq. 10-11) ------------------------------ */
 

@@ -104,6 +104,8 @@ def _declare(L):
         "or_lambda_lm": (None, [D, D, I32, P]),
         "or_map2alm": (None, [P, I64, I32, P, P]),
         "or_alm2cl": (None, [P, P, I32, P]),
+        "or_alm2map": (None, [P, P, I64, I32, P]),
+        "or_gauss_beam": (None, [D, I32, P]),
         "or_kappa_map": (None, [P, I32, I64, P, D, P]),
         "or_moments": (None, [P, I64, P]),
         "or_pdf": (None, [P, I64, D, D, I32, P]),
@@ -251,6 +253,21 @@ def map2alm(m: np.ndarray, nside: int, lmax: int) -> np.ndarray:
     re, im = np.empty(alm_size(lmax)), np.empty(alm_size(lmax))
     lib().or_map2alm(_ptr(mp), nside, lmax, _ptr(re), _ptr(im))
     return re + 1j * im
+
+
+def alm2map(alm: np.ndarray, nside: int, lmax: int) -> np.ndarray:
+    """FP64 RING map of the real field with coefficients a_lm (m >= 0)."""
+    re = np.ascontiguousarray(alm.real, dtype=np.float64)
+    im = np.ascontiguousarray(alm.imag, dtype=np.float64)
+    out = np.empty(12 * nside * nside)
+    lib().or_alm2map(_ptr(re), _ptr(im), nside, lmax, _ptr(out))
+    return out
+
+
+def gauss_beam(sigma: float, lmax: int) -> np.ndarray:
+    out = np.empty(lmax + 1)
+    lib().or_gauss_beam(float(sigma), lmax, _ptr(out))
+    return out
 
 
 def alm2cl(alm: np.ndarray, lmax: int) -> np.ndarray:

@@ -129,6 +129,11 @@ void or_lambda_lm(double z, double s, int32_t lmax, double *lam);
 void or_map2alm(const float *map, int64_t nside, int32_t lmax, double *alm_re, double *alm_im);
 /* C_l = (|a_l0|^2 + 2 sum_{m>0} |a_lm|^2) / (2l + 1). */
 void or_alm2cl(const double *alm_re, const double *alm_im, int32_t lmax, double *cl);
+/* map_p = sum_l sum_{m>=0} (2 - delta_m0) Re(a_lm Y_lm) at the RING pixel centres. */
+void or_alm2map(const double *alm_re, const double *alm_im, int64_t nside, int32_t lmax,
+                double *map);
+/* Gaussian beam b_l = exp(-l(l+1) sigma^2 / 2), sigma the r.m.s. radius (radians). */
+void or_gauss_beam(double sigma, int32_t lmax, double *b);
 
 #ifdef __cplusplus
 }

@@ -16,6 +16,11 @@
  *   lambda_lm = sqrt((4l^2-1)/(l^2-m^2)) (cos(theta) lambda_{l-1,m}
  *               - sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)) lambda_{l-2,m}).
  * a_lm is stored m-major: index m (2 lmax + 1 - m) / 2 + l.
+ *
+ * Synthesis (the inverse direction, for maps smoothed in harmonic space,
+ * Sec. 3.3): map_p = sum_l sum_{m>=0} (2 - delta_m0) Re(a_lm Y_lm(theta_p, phi_p)),
+ * the real field whose a_l,-m = (-1)^m conj(a_lm); the Gaussian beam of
+ * r.m.s. radius sigma multiplies a_lm by b_l = exp(-l(l+1) sigma^2 / 2).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -86,4 +91,33 @@ void or_alm2cl(const double *alm_re, const double *alm_im, int32_t lmax, double 
     }
     cl[l] = s / (2.0 * l + 1.0);
   }
+}
+
+void or_alm2map(const double *alm_re, const double *alm_im, int64_t nside, int32_t lmax,
+                double *map) {
+  const int64_t npix = or_nside2npix(nside);
+  const int64_t nalm = (int64_t)(lmax + 1) * (lmax + 2) / 2;
+  double *lam = (double *)malloc(sizeof(double) * nalm);
+  for (int64_t p = 0; p < npix; ++p) {
+    double z, phi;
+    or_pix2ang_ring(nside, p, &z, &phi);
+    const double s = sqrt((1.0 - z) * (1.0 + z));
+    or_lambda_lm(z, s, lmax, lam);
+    double v = 0.0;
+    for (int32_t m = 0; m <= lmax; ++m) {
+      const double c = cos(m * phi), sn = sin(m * phi);   /* e^{i m phi} = c + i sn */
+      double acc = 0.0;
+      for (int32_t l = m; l <= lmax; ++l) {
+        const int64_t k = or_alm_index(lmax, l, m);
+        acc += lam[k] * (alm_re[k] * c - alm_im[k] * sn);
+      }
+      v += (m == 0) ? acc : 2.0 * acc;
+    }
+    map[p] = v;
+  }
+  free(lam);
+}
+
+void or_gauss_beam(double sigma, int32_t lmax, double *b) {
+  for (int32_t l = 0; l <= lmax; ++l) b[l] = exp(-0.5 * (double)l * (l + 1) * sigma * sigma);
 }

@@ -87,6 +87,7 @@ _SIGS = {
     "ufc_keys": [P, P, I64, ctypes.POINTER(Box), P, I32, I32, P],
     "ufc_bin": [P, P, P, P, I32, P, I32, I32, I32, P],
     "ufc_bin_host": [P, P, P, P, I32, P, I32, I32, I32, P],
+    "ufc_bin_host_stream": [P, P, P, P, I32, P, I32, I32, I32, I64, P],
     "ufc_bin_info": [P, P],
     "ufc_kappa_stats": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_kappa_backward": [P, P, I32, I32, P, D, D, D, P, P, P, P, P, P],
@@ -99,6 +100,9 @@ _SIGS = {
     "ufc_map2alm": [P, P, I32, I32, P],
     "ufc_alm2cl": [P, P, I32, P],
     "ufc_cl_bin": [P, P, I32, I32, I32, I32, P],
+    "ufc_alm2map": [P, P, I32, I32, P],
+    "ufc_alm_beam": [P, P, I32, D, P],
+    "ufc_map_stats": [P, P, I32, D, D, I32, P, P],
     "ufc_profile_enable": [P, I32],
     "ufc_profile_read": [P, I32, P, P, P, P],
 }
@@ -295,6 +299,28 @@ class Context:
                  "ufc_bin_host")
         return counts
 
+    def bin_host_stream(self, xyz_list, boxes, chi_edges, nside: int, chunk: int, counts=None,
+                        accumulate=False, path: str | None = None):
+        """bin_host through two device buffers of `chunk` particles
+        (ufc_bin_host_stream): particle sets beyond device memory."""
+        import torch
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        S = len(chi) - 1
+        npix = 12 * nside * nside
+        xs = [_host_f32(x) for x in xyz_list]
+        if counts is None:
+            counts = torch.empty((S, npix), dtype=torch.int32, device=f"cuda:{self.device}")
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.numel() == S * npix
+        ptrs = (P * len(xs))(*[P(a) for a, _ in xs])
+        ns = (I64 * len(xs))(*[m // 3 for _, m in xs])
+        arr = (Box * len(boxes))(*boxes)
+        self._stream()
+        self._ck(_lib.ufc_bin_host_stream(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P),
+                                          ctypes.cast(arr, P), len(boxes), _np_ptr(chi), S, nside,
+                                          _bin_flags(accumulate, path), int(chunk),
+                                          P(counts.data_ptr())), "ufc_bin_host_stream")
+        return counts
+
     def bin_info(self):
         out = np.zeros(4, dtype=np.int64)
         self._stream()
@@ -398,6 +424,52 @@ class Context:
             out = torch.empty(lmax + 1, dtype=torch.float64, device=alm.device)
         self._stream()
         self._ck(_lib.ufc_alm2cl(self.h, P(alm.data_ptr()), lmax, P(out.data_ptr())), "ufc_alm2cl")
+        return out
+
+    def alm2map(self, alm, nside: int, lmax: int, out=None):
+        """FP32 RING map of the real field with coefficients a_lm."""
+        import torch
+        if out is None:
+            out = torch.empty(12 * nside * nside, dtype=torch.float32, device=alm.device)
+        self._stream()
+        self._ck(_lib.ufc_alm2map(self.h, P(alm.data_ptr()), nside, lmax, P(out.data_ptr())),
+                 "ufc_alm2map")
+        return out
+
+    def alm_beam(self, alm, lmax: int, sigma: float, out=None):
+        """a_lm times the Gaussian beam of r.m.s. radius sigma (radians)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(alm)
+        self._stream()
+        self._ck(_lib.ufc_alm_beam(self.h, P(alm.data_ptr()), lmax, float(sigma), P(out.data_ptr())),
+                 "ufc_alm_beam")
+        return out
+
+    def map_stats(self, m, nside: int, lo: float, hi: float, nbins: int):
+        """(moments [10], pdf [nbins + 3]) of an FP32 map."""
+        import torch
+        m = _dev_f32(m, self.device)
+        mom = torch.empty(NMOMENTS, dtype=torch.float64, device=m.device)
+        pdf = torch.empty(nbins + 3, dtype=torch.int64, device=m.device)
+        self._stream()
+        self._ck(_lib.ufc_map_stats(self.h, P(m.data_ptr()), nside, float(lo), float(hi), nbins,
+                                    P(mom.data_ptr()), P(pdf.data_ptr())), "ufc_map_stats")
+        return mom, pdf
+
+    def smoothed_moments(self, m, nside: int, lmax: int, sigmas, lo: float, hi: float,
+                         nbins: int):
+        """Moments and PDF of the map smoothed by Gaussian beams of r.m.s.
+        radii sigmas (radians): one analysis, then per scale beam + synthesis
+        + statistics, all on the device."""
+        alm = self.map2alm(m, nside, lmax)
+        work = alm.clone()
+        sm = None
+        out = []
+        for s in sigmas:
+            self.alm_beam(alm, lmax, s, out=work)
+            sm = self.alm2map(work, nside, lmax, out=sm)
+            out.append(self.map_stats(sm, nside, lo, hi, nbins))
         return out
 
     def cl_bin(self, cl, lmax: int, lmin: int, dl: int, nbins: int, out=None):

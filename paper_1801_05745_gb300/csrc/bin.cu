@@ -1517,3 +1517,62 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
 }
 
 }  // namespace ufc
+
+namespace ufc {
+
+// Binning from host memory through a bounded device buffer: the boxes'
+// particles are cut into chunks of at most `chunk` particles; chunk i+1 is
+// copied into one of two device buffers on the copy stream while chunk i is
+// binned from the other on the context stream.  Every chunk is a complete
+// binning call into counts (accumulating after the first), so the device
+// memory held is two chunks plus one chunk's workspace whatever the
+// particle count.
+ufc_status run_bin_stream(ufc_ctx* c, const float* const* xyz_host, const int64_t* n,
+                          const ufc_box* boxes, int nbox, const double* chi, int nshell,
+                          int nside, int flags, int64_t chunk, int32_t* counts) {
+  if (nbox < 1 || nbox > kMaxBoxes) return set_err(c, UFC_ERR_ARG, "nbox must be in [1,%d]", kMaxBoxes);
+  if (chunk < 1) return set_err(c, UFC_ERR_ARG, "chunk must be >= 1");
+  int64_t largest = 0;
+  for (int k = 0; k < nbox; ++k) {
+    if (n[k] < 0) return set_err(c, UFC_ERR_ARG, "n[%d] < 0", k);
+    if (n[k] > 0 && !xyz_host[k]) return set_err(c, UFC_ERR_ARG, "xyz_host[%d] is NULL", k);
+    largest = std::max(largest, std::min(n[k], chunk));
+  }
+  const size_t bufb = ((size_t)largest * 12 + 255) & ~(size_t)255;
+  char* stage = (char*)ws_get(c, kSlotStage, 2 * std::max<size_t>(bufb, 256));
+  if (!stage) return UFC_ERR_ALLOC;
+  float* buf[2] = {reinterpret_cast<float*>(stage), reinterpret_cast<float*>(stage + bufb)};
+  if (!c->copy_stream)
+    UFC_CUDA(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  // events: 0, 1 = buffer free; 2, 3 = buffer filled
+  for (int i = 0; i < 4; ++i)
+    if (!copy_event(c, i)) return set_err(c, UFC_ERR_CUDA, "cudaEventCreate failed");
+  for (int b = 0; b < 2; ++b) UFC_CUDA(c, cudaEventRecord(c->copy_events[b], c->stream));
+  bool first = !(flags & UFC_BIN_ACCUMULATE);
+  int it = 0;
+  for (int k = 0; k < nbox; ++k) {
+    for (int64_t p0 = 0; p0 < n[k]; p0 += chunk, ++it) {
+      const int64_t cnt = std::min(chunk, n[k] - p0);
+      const int b = it & 1;
+      UFC_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->copy_events[b], 0));
+      UFC_CUDA(c, cudaMemcpyAsync(buf[b], xyz_host[k] + 3 * p0, (size_t)cnt * 12,
+                                  cudaMemcpyHostToDevice, c->copy_stream));
+      UFC_CUDA(c, cudaEventRecord(c->copy_events[2 + b], c->copy_stream));
+      UFC_CUDA(c, cudaStreamWaitEvent(c->stream, c->copy_events[2 + b], 0));
+      const float* xs[1] = {buf[b]};
+      const int fl = (flags & (UFC_BIN_FORCE_DIRECT | UFC_BIN_FORCE_DENSE)) |
+                     (first ? 0 : UFC_BIN_ACCUMULATE);
+      ufc_status s = run_keys_pipeline(c, 1, xs, &cnt, &boxes[k], 1, chi, nshell, nside, fl,
+                                       counts, nullptr, nullptr);
+      if (s) return s;
+      UFC_CUDA(c, cudaEventRecord(c->copy_events[b], c->stream));
+      first = false;
+    }
+  }
+  if (first && !(flags & UFC_BIN_ACCUMULATE)) {      // no particles at all: zero counts
+    UFC_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)nshell * 12 * nside * nside * 4, c->stream));
+  }
+  return UFC_OK;
+}
+
+}  // namespace ufc

@@ -35,6 +35,13 @@ ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double
 ufc_status run_alm2cl(ufc_ctx* c, const double* alm, int lmax, double* cl);
 ufc_status run_cl_bin(ufc_ctx* c, const double* cl, int lmax, int lmin, int dl, int nbins,
                       double* out);
+ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float* map);
+ufc_status run_bin_stream(ufc_ctx* c, const float* const* xyz_host, const int64_t* n,
+                          const ufc_box* boxes, int nbox, const double* chi, int nshell,
+                          int nside, int flags, int64_t chunk, int32_t* counts);
+ufc_status run_alm_beam(ufc_ctx* c, const double* in, int lmax, double sigma, double* out);
+ufc_status run_map_stats(ufc_ctx* c, const float* map, int nside, double lo, double hi,
+                         int nbins, double* moments, int64_t* pdf);
 ufc_status cosmo_chi_edges(const ufc_cosmo& c, const double* z, int n, double* chi);
 ufc_status cosmo_z_of_chi(const ufc_cosmo& c, const double* chi, int n, double* zout);
 ufc_status cosmo_kappa_coeffs(const ufc_cosmo& c, const ufc_box* boxes, int nbox,
@@ -81,7 +88,7 @@ static cudaEvent_t prof_event(ufc_ctx* c) {
 }
 
 void prof_begin(ufc_ctx* c, const char* name) {
-  if (!c->prof) return;
+  if (!c || !c->prof) return;
   cudaEvent_t a = prof_event(c), b = prof_event(c);
   if (!a || !b) return;
   cudaEventRecord(a, c->stream);
@@ -89,7 +96,7 @@ void prof_begin(ufc_ctx* c, const char* name) {
 }
 
 void prof_end(ufc_ctx* c) {
-  if (!c->prof || c->prof_recs.empty()) return;
+  if (!c || !c->prof || c->prof_recs.empty()) return;
   cudaEventRecord(c->prof_recs.back().b, c->stream);
 }
 
@@ -363,6 +370,53 @@ ufc_status ufc_cl_bin(ufc_ctx* c, const double* cl_dev, int32_t lmax, int32_t lm
   c->err.clear();
   cudaSetDevice(c->device);
   return run_cl_bin(c, cl_dev, lmax, lmin, dl, nbins, out_dev);
+}
+
+ufc_status ufc_alm2map(ufc_ctx* c, const double* alm_dev, int32_t nside, int32_t lmax,
+                       float* map_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_alm2map(c, alm_dev, nside, lmax, map_dev);
+}
+
+ufc_status ufc_alm_beam(ufc_ctx* c, const double* alm_in_dev, int32_t lmax, double sigma,
+                        double* alm_out_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_alm_beam(c, alm_in_dev, lmax, sigma, alm_out_dev);
+}
+
+ufc_status ufc_map_stats(ufc_ctx* c, const float* map_dev, int32_t nside, double pdf_lo,
+                         double pdf_hi, int32_t nbins, double* moments_dev, int64_t* pdf_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_map_stats(c, map_dev, nside, pdf_lo, pdf_hi, nbins, moments_dev, pdf_dev);
+}
+
+ufc_status ufc_bin_host_stream(ufc_ctx* c, const float* const* xyz_host, const int64_t* n,
+                               const ufc_box* boxes, int32_t nbox, const double* chi_edges,
+                               int32_t nshell, int32_t nside, int32_t flags, int64_t chunk,
+                               int32_t* counts_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!xyz_host || !n || !boxes || !chi_edges || !counts_dev)
+    return set_err(c, UFC_ERR_ARG, "NULL argument to ufc_bin_host_stream");
+  if (flags & ~(UFC_BIN_ACCUMULATE | UFC_BIN_FORCE_DIRECT | UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if ((flags & UFC_BIN_FORCE_DIRECT) && (flags & UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "FORCE_DIRECT and FORCE_DENSE exclude each other");
+  if (reinterpret_cast<uintptr_t>(counts_dev) & 3)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 4-byte aligned");
+  cudaSetDevice(c->device);
+  cudaStreamCaptureStatus cs;
+  UFC_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone)
+    return set_err(c, UFC_ERR_UNSUPPORTED, "ufc_bin_host_stream cannot be captured into a graph");
+  return run_bin_stream(c, xyz_host, n, boxes, nbox, chi_edges, nshell, nside, flags, chunk,
+                        counts_dev);
 }
 
 ufc_status ufc_bin_info(ufc_ctx* c, int64_t info[4]) {

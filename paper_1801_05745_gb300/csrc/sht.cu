@@ -336,6 +336,205 @@ __global__ void k_alm2cl(const double2* __restrict__ alm, int32_t lmax, double* 
   cl[l] = s / (2.0 * l + 1.0);
 }
 
+// ------------------------------------------------------------ synthesis --
+// map_p = sum_l sum_{m>=0} (2 - delta_m0) Re(a_lm Y_lm(theta_p, phi_p)), the
+// real field with a_l,-m = (-1)^m conj(a_lm), ring by ring:
+//   k_legendre_synth : G_m(ring) = sum_l a_lm lambda_lm(z_ring), per (m, ring
+//                      pair) with the even/odd split of the mirror rings;
+//   k_ring_synth     : map_j = sum_{|m| <= lmax} G_m e^{i m phi_j}, folding
+//                      m onto the ring's n frequencies and an inverse DFT.
+__global__ void __launch_bounds__(kLegThreads)
+k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
+                 const int32_t* __restrict__ ex, int32_t N, int32_t lmax, int32_t nrings,
+                 int32_t npairs, double2* __restrict__ G) {
+  __shared__ double ra[kLegChunkL], rb[kLegChunkL];
+  __shared__ double2 as[kLegChunkL];
+  const int chunk = blockIdx.x;
+  int pp[kLegPPT];
+  bool have[kLegPPT];
+  double z[kLegPPT];
+#pragma unroll
+  for (int q = 0; q < kLegPPT; ++q) {
+    pp[q] = chunk * kLegThreads * kLegPPT + q * kLegThreads + threadIdx.x;
+    have[q] = pp[q] < npairs;
+    z[q] = have[q] ? ring_geom(N, pp[q]).z : 0.0;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    const int m = pass == 0 ? (int)blockIdx.y : lmax - (int)blockIdx.y;
+    if (pass == 1 && m <= (int)blockIdx.y) break;
+    double v1[kLegPPT], v2[kLegPPT];
+    int e[kLegPPT];
+    double2 ge[kLegPPT], go[kLegPPT];     // sums over l + m even / odd, in units of 2^e
+#pragma unroll
+    for (int q = 0; q < kLegPPT; ++q) {
+      v1[q] = have[q] ? mu[(size_t)m * npairs + pp[q]] : 0.0;
+      v2[q] = 0.0;
+      e[q] = have[q] ? ex[(size_t)m * npairs + pp[q]] : 0;
+      ge[q] = make_double2(0.0, 0.0);
+      go[q] = ge[q];
+    }
+    const double c1 = sqrt(2.0 * m + 3.0);
+    const size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;
+    for (int l0 = m; l0 <= lmax; l0 += kLegChunkL) {
+      const int cnt = min(kLegChunkL, lmax + 1 - l0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int l = l0 + t;
+        as[t] = alm[base + l];
+        if (l >= m + 2) {
+          const double ll = (double)l, mm = (double)m, l1 = (double)(l - 1);
+          ra[t] = sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm));
+          rb[t] = sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0));
+        } else {
+          ra[t] = 0.0;
+          rb[t] = 0.0;
+        }
+      }
+      __syncthreads();
+      for (int t = 0; t < cnt; ++t) {
+        const int l = l0 + t;
+        const double at = ra[t], bt = rb[t];
+        const double2 a = as[t];
+        const bool odd = (l + m) & 1;
+#pragma unroll
+        for (int q = 0; q < kLegPPT; ++q) {
+          double v;
+          if (l == m) {
+            v = v1[q];
+          } else if (l == m + 1) {
+            v = c1 * z[q] * v1[q];
+            v2[q] = v1[q];
+            v1[q] = v;
+          } else {
+            v = at * (z[q] * v1[q] - bt * v2[q]);
+            v2[q] = v1[q];
+            v1[q] = v;
+          }
+          double2& g = odd ? go[q] : ge[q];
+          g.x = fma(v, a.x, g.x);
+          g.y = fma(v, a.y, g.y);
+        }
+      }
+      // mantissas back in range (growth per step < 2^8, see k_legendre); the
+      // sums so far are rescaled with them (terms 2^-500 below the current
+      // scale may underflow: they are negligible)
+#pragma unroll
+      for (int q = 0; q < kLegPPT; ++q) {
+        while (fabs(v1[q]) > 0x1p500 || fabs(v2[q]) > 0x1p500) {
+          v1[q] *= 0x1p-500;
+          v2[q] *= 0x1p-500;
+          ge[q] = make_double2(ge[q].x * 0x1p-500, ge[q].y * 0x1p-500);
+          go[q] = make_double2(go[q].x * 0x1p-500, go[q].y * 0x1p-500);
+          e[q] += 500;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kLegPPT; ++q) {
+      if (!have[q]) continue;
+      const double sc = e[q] > -1070 ? ldexp(1.0, e[q]) : 0.0;
+      const int p = pp[q], ps = nrings - 1 - p;
+      G[(size_t)m * nrings + p] = make_double2((ge[q].x + go[q].x) * sc, (ge[q].y + go[q].y) * sc);
+      if (ps != p)
+        G[(size_t)m * nrings + ps] = make_double2((ge[q].x - go[q].x) * sc, (ge[q].y - go[q].y) * sc);
+    }
+  }
+}
+
+// One block per ring: H_k = sum over m = k mod n (0 <= m <= lmax) of
+// G_m e^{i m phi_0} plus, for the negative frequencies, the conjugates of
+// the terms with m = -k mod n (1 <= m <= lmax); then map_j = sum_k H_k
+// e^{2 pi i k j / n} (inverse radix-2 FFT for power-of-two rings, direct
+// sum otherwise).  Each H_k is summed by one thread in increasing m.
+__global__ void __launch_bounds__(512)
+k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nrings,
+             float* __restrict__ map) {
+  extern __shared__ __align__(16) double2 sh[];
+  const int r = blockIdx.x;
+  const Ring g = ring_geom(N, r);
+  const int n = g.n;
+  double2* w = sh;            // [n]: e^{+2 pi i k / n}
+  double2* H = sh + n;        // [n]
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * (double)k / (double)n, &sn, &cs);
+    w[k] = make_double2(cs, sn);
+  }
+  const bool fft = is_pow2(n);
+  int bits = 0;
+  while ((1 << bits) < n) ++bits;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double hx = 0.0, hy = 0.0;
+    for (int m = k; m <= lmax; m += n) {              // m = k mod n
+      const double2 gm = G[(size_t)m * nrings + r];
+      double sn, cs;
+      sincospi((double)m * g.phi0_pi, &sn, &cs);
+      hx += cs * gm.x - sn * gm.y;
+      hy += cs * gm.y + sn * gm.x;
+    }
+    for (int m = (n - k) % n; m <= lmax; m += n) {    // -m = k mod n
+      if (m == 0) continue;
+      const double2 gm = G[(size_t)m * nrings + r];
+      double sn, cs;
+      sincospi((double)m * g.phi0_pi, &sn, &cs);
+      hx += cs * gm.x - sn * gm.y;                    // conj(G_m e^{i m phi_0})
+      hy -= cs * gm.y + sn * gm.x;
+    }
+    const int dst = fft ? (int)(__brev(k) >> (32 - bits)) : k;
+    H[dst] = make_double2(hx, hy);
+  }
+  __syncthreads();
+  if (fft) {
+    for (int len = 2; len <= n; len <<= 1) {
+      const int half = len >> 1, step = n / len;
+      for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+        const int grp = t / half, pos = t - grp * half;
+        const int a = grp * len + pos, b = a + half;
+        const double2 tw = w[pos * step];
+        const double2 xb = H[b];
+        const double2 p = make_double2(tw.x * xb.x - tw.y * xb.y, tw.x * xb.y + tw.y * xb.x);
+        const double2 xa = H[a];
+        H[a] = make_double2(xa.x + p.x, xa.y + p.y);
+        H[b] = make_double2(xa.x - p.x, xa.y - p.y);
+      }
+      __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = (float)H[j].x;
+  } else {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double s = 0.0;
+      int idx = 0;
+      for (int k = 0; k < n; ++k) {
+        const double2 h = H[k], tw = w[idx];
+        s = fma(h.x, tw.x, fma(-h.y, tw.y, s));
+        idx += j;
+        idx -= idx >= n ? n : 0;
+      }
+      map[g.start + j] = (float)s;
+    }
+  }
+}
+
+// a_lm b_l with the Gaussian beam b_l = exp(-l(l+1) sigma^2 / 2).
+__global__ void k_alm_beam(const double2* __restrict__ in, int32_t lmax, double sigma,
+                           double2* __restrict__ out) {
+  const int64_t nalm = (int64_t)(lmax + 1) * (lmax + 2) / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    // m from the m-major index: block m starts at s(m) = m (2 lmax + 3 - m) / 2
+    // (the entry l = m); take the largest m with s(m) <= i
+    const double q = 2.0 * lmax + 3.0;
+    int m = (int)((q - sqrt(fmax(q * q - 8.0 * (double)i, 0.0))) / 2.0);
+    m = m < 0 ? 0 : (m > lmax ? lmax : m);
+    while (m > 0 && (int64_t)m * (2 * lmax + 3 - m) / 2 > i) --m;
+    while (m < lmax && (int64_t)(m + 1) * (2 * lmax + 2 - m) / 2 <= i) ++m;
+    const int l = (int)(i - (int64_t)m * (2 * lmax + 1 - m) / 2);
+    const double b = exp(-0.5 * (double)l * (l + 1) * sigma * sigma);
+    const double2 a = in[i];
+    out[i] = make_double2(a.x * b, a.y * b);
+  }
+}
+
 // Band powers: out[b] = mean of C_l over l in [lmin + b dl, lmin + (b+1) dl).
 __global__ void k_cl_bin(const double* __restrict__ cl, int32_t lmin, int32_t dl, int32_t nbins,
                          double* __restrict__ out) {
@@ -404,6 +603,55 @@ ufc_status run_cl_bin(ufc_ctx* c, const double* cl, int lmax, int lmin, int dl, 
     return set_err(c, UFC_ERR_ARG, "bins [lmin, lmin + nbins dl) must lie in [0, lmax]");
   ProfScope ps_(c, "k_cl_bin");
   k_cl_bin<<<(nbins + 255) / 256, 256, 0, c->stream>>>(cl, lmin, dl, nbins, out);
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float* map) {
+  if (!alm || !map) return set_err(c, UFC_ERR_ARG, "alm_dev and map_dev are required");
+  if (nside < 1 || nside > kShtMaxNside || (nside & (nside - 1)))
+    return set_err(c, UFC_ERR_UNSUPPORTED, "alm2map needs a power-of-two nside <= %d", kShtMaxNside);
+  if (lmax < 0 || lmax > 4 * nside) return set_err(c, UFC_ERR_ARG, "lmax must be in [0, 4 nside]");
+  if ((reinterpret_cast<uintptr_t>(alm) & 15))
+    return set_err(c, UFC_ERR_ARG, "alm_dev must be 16-byte aligned");
+  const int nrings = 4 * nside - 1, npairs = 2 * nside;
+  const int nchunk = (npairs + kLegThreads * kLegPPT - 1) / (kLegThreads * kLegPPT);
+  const size_t gbytes = (size_t)(lmax + 1) * nrings * sizeof(double2);
+  const size_t lbytes = (size_t)(lmax + 1) * npairs * (sizeof(double) + sizeof(int32_t));
+  char* ws = (char*)ws_get(c, kSlotSht, gbytes + lbytes + 512);
+  if (!ws) return UFC_ERR_ALLOC;
+  double2* Gm = reinterpret_cast<double2*>(ws);
+  double* mu = reinterpret_cast<double*>(ws + gbytes);
+  int32_t* ex = reinterpret_cast<int32_t*>(ws + gbytes + (size_t)(lmax + 1) * npairs * 8);
+  {
+    ProfScope ps_(c, "k_lmm");
+    k_lmm<<<(npairs + 127) / 128, 128, 0, c->stream>>>(nside, lmax, npairs, mu, ex);
+  }
+  {
+    ProfScope ps_(c, "k_legendre_synth");
+    dim3 grid(nchunk, lmax / 2 + 1);
+    k_legendre_synth<<<grid, kLegThreads, 0, c->stream>>>(reinterpret_cast<const double2*>(alm), mu,
+                                                          ex, nside, lmax, nrings, npairs, Gm);
+  }
+  const int smem = 2 * 4 * nside * (int)sizeof(double2);
+  UFC_CUDA(c, cudaFuncSetAttribute(k_ring_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  {
+    ProfScope ps_(c, "k_ring_synth");
+    k_ring_synth<<<nrings, 512, smem, c->stream>>>(Gm, nside, lmax, nrings, map);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+ufc_status run_alm_beam(ufc_ctx* c, const double* in, int lmax, double sigma, double* out) {
+  if (!in || !out) return set_err(c, UFC_ERR_ARG, "alm_in_dev and alm_out_dev are required");
+  if (lmax < 0 || !(sigma >= 0.0) || !std::isfinite(sigma))
+    return set_err(c, UFC_ERR_ARG, "lmax >= 0 and a finite sigma >= 0 are required");
+  if ((reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+    return set_err(c, UFC_ERR_ARG, "a_lm buffers must be 16-byte aligned");
+  ProfScope ps_(c, "k_alm_beam");
+  k_alm_beam<<<2 * c->num_sms, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(in), lmax,
+                                                    sigma, reinterpret_cast<double2*>(out));
   UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;
 }

@@ -450,6 +450,22 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
   }
 }
 
+// Per-block sums of an FP32 map (double-float per thread), the first pass of
+// the moments of an arbitrary map (ufc_map_stats).  Needs a 16-byte aligned
+// map of a multiple of 4 values.
+__global__ void __launch_bounds__(kKV)
+k_map_sum(const float* __restrict__ map, int npix, double* __restrict__ ksum_part) {
+  __shared__ double red[kKV / 32];
+  const int ng = npix >> 2;
+  f2 ks{0.f, 0.f};
+  for (int g = blockIdx.x * kKV + threadIdx.x; g < ng; g += gridDim.x * kKV) {
+    const float4 v = reinterpret_cast<const float4*>(map)[g];
+    ks = f2_add(ks, f2_add(f2_two_sum(v.x, v.y), f2_two_sum(v.z, v.w)));
+  }
+  const double t = block_sum_d<kKV>(f2_to_d(ks), red);
+  if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
+}
+
 // ------------------------------------------------ moments + PDF pass -----
 // Second pass over the FP32 map (L2-resident at these sizes): central
 // power sums about the exact FP64 mean in double-float, and the PDF.
@@ -671,6 +687,66 @@ static ufc_status launch_kappa_fwd(ufc_ctx* c, const int32_t* counts, const Coef
 }
 
 
+// Moments and PDF of an FP32 map whose per-block sums (grid of them) are in
+// ksum: the second pass over the map and the final reduction.
+static ufc_status launch_moments(ufc_ctx* c, const float* kmap, int npix, const double* ksum,
+                                 int grid, double lo, double hi, int nbins, double* mpart,
+                                 int mgrid, double* moments, int64_t* pdf, bool timed) {
+  PdfParam pp;
+  pp.lo = lo;
+  pp.hi = hi;
+  pp.scale = (double)nbins / (hi - lo);
+  pp.lo_f = (float)lo;
+  pp.scale_f = (float)pp.scale;
+  pp.nbins = nbins;
+  // |x_f - x_64| <= 3u |x| + u |lo| s + 2^-52 |x| (u = 2^-24); when
+  // |lo| s < 16 that is below 68u (|x| + 1) < 2^-16 (|x| + 1), the band
+  // used; other ranges send every value through the FP64 expression.
+  pp.band_rel = std::fabs(lo) * pp.scale < 16.0 ? std::ldexp(1.0f, -16) : 2.0f;
+  auto fdn = [](double v) { float f = (float)v; return (double)f > v ? nextafterf(f, -INFINITY) : f; };
+  auto fup = [](double v) { float f = (float)v; return (double)f < v ? nextafterf(f, INFINITY) : f; };
+  pp.lo_dn = fdn(lo);
+  pp.lo_up = fup(lo);
+  pp.hi_dn = fdn(hi);
+  pp.hi_up = fup(hi);
+  UFC_CUDA(c, cudaMemsetAsync(pdf, 0, (size_t)(nbins + 3) * 8, c->stream));
+  const int smem = (nbins + 3) * 4;
+  {
+    ProfScope ps_(timed ? c : nullptr, "k_moments");
+    k_moments<<<mgrid, kMT, smem, c->stream>>>(kmap, npix, ksum, grid, pp, mpart,
+                                               (unsigned long long*)pdf);
+  }
+  {
+    ProfScope ps_(timed ? c : nullptr, "k_moments_final");
+    k_moments_final<<<1, 32, 0, c->stream>>>(ksum, grid, mpart, mgrid, npix, moments);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+// Moments and PDF of any FP32 RING map (smoothed maps of Sec. 3.3).
+ufc_status run_map_stats(ufc_ctx* c, const float* map, int nside, double lo, double hi,
+                         int nbins, double* moments, int64_t* pdf) {
+  if (!map || !moments || !pdf) return set_err(c, UFC_ERR_ARG, "map, moments and pdf are required");
+  if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1)))
+    return set_err(c, UFC_ERR_ARG, "nside must be a power of two in [1,%d]", UFC_MAX_NSIDE);
+  if (nbins < 1 || nbins > kMaxBins) return set_err(c, UFC_ERR_ARG, "nbins must be in [1,%d]", kMaxBins);
+  if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+    return set_err(c, UFC_ERR_ARG, "PDF range needs finite lo < hi");
+  if (reinterpret_cast<uintptr_t>(map) & 15) return set_err(c, UFC_ERR_ARG, "map_dev must be 16-byte aligned");
+  const int npix = 12 * nside * nside;
+  const int grid = kappa_fwd_grid(c), mgrid = 2 * c->num_sms;
+  double* ksum = (double*)ws_get(c, kSlotPartials, (size_t)(grid + 3 * mgrid) * 8);
+  if (!ksum) return UFC_ERR_ALLOC;
+  {
+    ProfScope ps_(c, "k_map_sum");
+    k_map_sum<<<grid, kKV, 0, c->stream>>>(map, npix, ksum);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return launch_moments(c, map, npix, ksum, grid, lo, hi, nbins, ksum + grid, mgrid, moments, pdf,
+                        true);
+}
+
 ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
                            const double* A, double C, double lo, double hi, int nbins,
                            float* kappa, double* moments, int64_t* pdf) {
@@ -707,36 +783,8 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
     if (s) return s;
   }
   if (!want_stats) return UFC_OK;
-  PdfParam pp;
-  pp.lo = lo;
-  pp.hi = hi;
-  pp.scale = (double)nbins / (hi - lo);
-  pp.lo_f = (float)lo;
-  pp.scale_f = (float)pp.scale;
-  pp.nbins = nbins;
-  // |x_f - x_64| <= 3u |x| + u |lo| s + 2^-52 |x| (u = 2^-24); when
-  // |lo| s < 16 that is below 68u (|x| + 1) < 2^-16 (|x| + 1), the band
-  // used; other ranges send every value through the FP64 expression.
-  pp.band_rel = std::fabs(lo) * pp.scale < 16.0 ? std::ldexp(1.0f, -16) : 2.0f;
-  auto fdn = [](double v) { float f = (float)v; return (double)f > v ? nextafterf(f, -INFINITY) : f; };
-  auto fup = [](double v) { float f = (float)v; return (double)f < v ? nextafterf(f, INFINITY) : f; };
-  pp.lo_dn = fdn(lo);
-  pp.lo_up = fup(lo);
-  pp.hi_dn = fdn(hi);
-  pp.hi_up = fup(hi);
-  UFC_CUDA(c, cudaMemsetAsync(pdf, 0, (size_t)(nbins + 3) * 8, c->stream));
-  const int smem = (nbins + 3) * 4;
-  {
-    ProfScope ps_(c, "k_moments");
-    k_moments<<<mgrid, kMT, smem, c->stream>>>(kmap, npix, ksum, grid, pp, mpart,
-                                               (unsigned long long*)pdf);
-  }
-  {
-    ProfScope ps_(c, "k_moments_final");
-    k_moments_final<<<1, 32, 0, c->stream>>>(ksum, grid, mpart, mgrid, npix, moments);
-  }
-  UFC_CUDA(c, cudaGetLastError());
-  return UFC_OK;
+  return launch_moments(c, kmap, npix, ksum, grid, lo, hi, nbins, mpart, mgrid, moments, pdf,
+                        true);
 }
 
 // Adjoint sums -> gradients (host FP64 assembly).  Synchronises.
@@ -900,27 +948,9 @@ ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int
   make_coef(A, C, S, npix, cf);
   s = launch_kappa_fwd(c, counts, cf, kappa, ksum, grid);
   if (s) return s;
-  PdfParam pp;
-  pp.lo = lo;
-  pp.hi = hi;
-  pp.scale = (double)nbins / (hi - lo);
-  pp.lo_f = (float)lo;
-  pp.scale_f = (float)pp.scale;
-  pp.nbins = nbins;
-  pp.band_rel = std::fabs(lo) * pp.scale < 16.0 ? std::ldexp(1.0f, -16) : 2.0f;
-  auto fdn = [](double v) { float f = (float)v; return (double)f > v ? nextafterf(f, -INFINITY) : f; };
-  auto fup = [](double v) { float f = (float)v; return (double)f < v ? nextafterf(f, INFINITY) : f; };
-  pp.lo_dn = fdn(lo);
-  pp.lo_up = fup(lo);
-  pp.hi_dn = fdn(hi);
-  pp.hi_up = fup(hi);
-  UFC_CUDA(c, cudaMemsetAsync(pdf, 0, (size_t)(nbins + 3) * 8, c->stream));
   // (no kernel-timing records here: recording them may allocate)
-  k_moments<<<mgrid, kMT, (nbins + 3) * 4, c->stream>>>(kappa, npix, ksum, grid, pp, mpart,
-                                                        (unsigned long long*)pdf);
-  k_moments_final<<<1, 32, 0, c->stream>>>(ksum, grid, mpart, mgrid, npix, moments);
-  UFC_CUDA(c, cudaGetLastError());
-  return UFC_OK;
+  return launch_moments(c, kappa, npix, ksum, grid, lo, hi, nbins, mpart, mgrid, moments, pdf,
+                        false);
 }
 
 ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins,

@@ -90,3 +90,55 @@ def test_band_powers_and_their_covariance(orc):
     assert np.allclose(cov.cpu().numpy(), c_o, rtol=1e-8, atol=1e-12 * np.abs(c_o).max())
     with pytest.raises(api.UfcError):
         ctx.cl_bin(cl, lmax, 40, 10, 1)
+
+
+@pytest.mark.parametrize("nside,lmax", [(4, 11), (4, 16), (16, 47), (32, 95)])
+def test_alm2map_matches_oracle(orc, nside, lmax):
+    """Synthesis of random a_lm (the real field; a_l0 real) against the
+    oracle's pixel-by-pixel sum; the GPU map is FP32."""
+    api, ctx = api_ctx()
+    rng = np.random.default_rng(100 + nside + lmax)
+    n = orc.alm_size(lmax)
+    a = rng.normal(size=n) + 1j * rng.normal(size=n)
+    for l in range(lmax + 1):
+        a[orc.alm_index(lmax, l, 0)] = a[orc.alm_index(lmax, l, 0)].real
+    got = ctx.alm2map(torch.from_numpy(a).cuda(), nside, lmax).cpu().numpy()
+    ref = orc.alm2map(a, nside, lmax)
+    assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_smoothing_chain_matches_oracle(orc):
+    """Map -> a_lm -> Gaussian beam (r.m.s. radius 2 pixels) -> map -> moments
+    and PDF, against the oracle's chain; moments at 1e-9 on the GPU's map."""
+    api, ctx = api_ctx()
+    nside, lmax = 32, 95
+    rng = np.random.default_rng(77)
+    mp = (rng.normal(size=12 * nside ** 2) + 5.0 * (rng.random(12 * nside ** 2) < 0.01)).astype(np.float32)
+    sigma = 2 * np.sqrt(4 * np.pi / (12 * nside ** 2))
+    a = ctx.map2alm(torch.from_numpy(mp).cuda(), nside, lmax)
+    sm = ctx.alm2map(ctx.alm_beam(a, lmax, sigma), nside, lmax)
+    a_o = orc.map2alm(mp, nside, lmax) * np.repeat(
+        [orc.gauss_beam(sigma, lmax)], 1, axis=0)[0][[l for m in range(lmax + 1) for l in range(m, lmax + 1)]]
+    ref = orc.alm2map(a_o, nside, lmax)
+    smh = sm.cpu().numpy()
+    assert np.abs(smh - ref).max() <= 2e-6 * np.abs(ref).max()
+    lo, hi = float(smh.min()), float(smh.max()) * 0.9
+    mom, pdf = ctx.map_stats(sm, nside, lo, hi, 50)
+    m_or = orc.moments(smh)
+    mg = mom.cpu().numpy()
+    for i in (1, 2, 3, 4, 5, 6, 7, 8):
+        assert mg[i] == pytest.approx(m_or[i], rel=1e-9), i
+    assert np.array_equal(pdf.cpu().numpy(), orc.pdf(smh, lo, hi, 50))
+
+
+def test_map_stats_equals_kappa_stats(orc):
+    """ufc_map_stats on the kappa map gives ufc_kappa_stats's moments and PDF
+    bit for bit (same per-block sums, same second pass)."""
+    api, ctx = api_ctx()
+    nside, S = 64, 8
+    rng = np.random.default_rng(3)
+    counts = torch.from_numpy(rng.poisson(4.0, size=(S, 12 * nside ** 2)).astype(np.int32)).cuda()
+    A = rng.uniform(0.001, 0.01, size=S)
+    kap, mom, pdf = ctx.kappa_stats(counts, A, 0.1, -0.1, 0.4, 40)
+    mom2, pdf2 = ctx.map_stats(kap, nside, -0.1, 0.4, 40)
+    assert torch.equal(mom, mom2) and torch.equal(pdf, pdf2)

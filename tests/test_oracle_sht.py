@@ -110,3 +110,66 @@ def test_cl_against_all_m_bruteforce(orc):
         cl_ref[l] /= 2 * l + 1
     cl = orc.alm2cl(orc.map2alm(mp, nside, lmax), lmax)
     assert np.allclose(cl, cl_ref, rtol=1e-10, atol=1e-14 * cl_ref.max())
+
+
+def test_synthesis_single_modes(orc):
+    """a_l0 = 1 gives lambda_l0 = sqrt((2l+1)/4pi) P_l(z) (numpy Legendre);
+    a_lm = c (m > 0) gives 2 Re(c Y_lm) (scipy)."""
+    nside, lmax = 8, 12
+    npix = 12 * nside ** 2
+    z = np.array([orc.pix2ang(nside, p)[0] for p in range(npix)])
+    ph = np.array([orc.pix2ang(nside, p)[1] for p in range(npix)])
+    for l in (0, 1, 5, 12):
+        a = np.zeros(orc.alm_size(lmax), complex)
+        a[orc.alm_index(lmax, l, 0)] = 1.0
+        ref = np.sqrt((2 * l + 1) / (4 * np.pi)) * np.polynomial.legendre.Legendre.basis(l)(z)
+        assert np.allclose(orc.alm2map(a, nside, lmax), ref, rtol=1e-12, atol=1e-13)
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    c = 0.7 - 1.3j
+    for l, m in ((3, 2), (12, 7), (9, 9)):
+        a = np.zeros(orc.alm_size(lmax), complex)
+        a[orc.alm_index(lmax, l, m)] = c
+        ref = 2 * np.real(c * sp.sph_harm_y(l, m, np.arccos(z), ph))
+        assert np.allclose(orc.alm2map(a, nside, lmax), ref, rtol=1e-11, atol=1e-13)
+
+
+def test_synthesis_real_field_all_m(orc):
+    """Random a_lm (m >= 0): the map equals the sum over -l <= m <= l with
+    a_l,-m = (-1)^m conj(a_lm), every Y_lm from scipy."""
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    nside, lmax = 4, 10
+    npix = 12 * nside ** 2
+    rng = np.random.default_rng(6)
+    a = rng.normal(size=orc.alm_size(lmax)) + 1j * rng.normal(size=orc.alm_size(lmax))
+    for l in range(lmax + 1):
+        a[orc.alm_index(lmax, l, 0)] = a[orc.alm_index(lmax, l, 0)].real   # real field: a_l0 real
+    th = np.array([np.arccos(orc.pix2ang(nside, p)[0]) for p in range(npix)])
+    ph = np.array([orc.pix2ang(nside, p)[1] for p in range(npix)])
+    ref = np.zeros(npix, complex)
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            alm = a[orc.alm_index(lmax, l, abs(m))]
+            if m < 0:
+                alm = (-1) ** m * np.conj(alm)
+            ref += alm * sp.sph_harm_y(l, m, th, ph)
+    assert np.abs(ref.imag).max() < 1e-12 * np.abs(ref).max()
+    assert np.allclose(orc.alm2map(a, nside, lmax), ref.real, rtol=1e-11, atol=1e-12)
+
+
+def test_gaussian_beam_is_the_gaussian_kernel(orc):
+    """b_l of r.m.s. radius sigma against the Legendre transform of the
+    normalised kernel K(g) = exp(-g^2 / 2 sigma^2) / (2 pi sigma^2):
+    2 pi int K(g) P_l(cos g) sin g dg, equal to first order in sigma^2."""
+    integrate = pytest.importorskip("scipy.integrate")
+    sp = pytest.importorskip("scipy.special")
+    sigma = 10.8 / 60 * np.pi / 180
+    b = orc.gauss_beam(sigma, 1000)
+    for l in (0, 10, 100, 500, 1000):
+        f = lambda g: (np.exp(-g * g / (2 * sigma ** 2)) / (2 * np.pi * sigma ** 2)
+                       * sp.eval_legendre(l, np.cos(g)) * np.sin(g))
+        ref = 2 * np.pi * integrate.quad(f, 0.0, 12 * sigma, limit=400, epsabs=1e-14)[0]
+        assert b[l] == pytest.approx(ref, rel=2e-3, abs=1e-6)
