@@ -481,6 +481,23 @@ def main():
         nalm = (lmax + 1) * (lmax + 2) // 2
         fp64 = 6.0 * npairs * nalm          # recurrence + accumulation per (l, m, ring pair)
         leg = cprof.get("k_legendre", (0.0, 1))
+        # smoothing at the paper's 10.8 arcmin: beam, synthesis, moments, PDF
+        sig = 10.8 / 60.0 * np.pi / 180.0
+        work = ctx.alm_beam(alm, lmax, sig)
+        sm = ctx.alm2map(work, w.nside, lmax)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            ctx.alm_beam(alm, lmax, sig, out=work)
+            ctx.alm2map(work, w.nside, lmax, out=sm)
+            smom, _ = ctx.map_stats(sm, w.nside, lo, hi, w.pdf_bins)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sm = e0.elapsed_time(e1) / 3
+        smh = smom.cpu().numpy()
+        line["smoothed"] = {"sigma_arcmin": 10.8, "ms_per_scale": ms_sm,
+                            "s2": float(smh[1]), "sigma2_s2": float(smh[7]),
+                            "s2_over_sigma2_s2": float(smh[8])}
         line["cl"] = {"nside": w.nside, "lmax": lmax, "ms_per_map": ms_cl,
                       "maps_per_s": 1e3 / ms_cl,
                       "kernels_ms_per_map": {k: round(v[0] / 3, 3) for k, v in cprof.items()},
