@@ -33,11 +33,11 @@ METRIC = ("G particles/s binned and kappa maps/s at Nside 1024 (% HBM roofline);
           "batched vs serial")
 UNIT = "Gparticles/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per particle of the fast stage, from the ncu
-# capture in profiles/k_fast_tma_2x512cubed_nside512.md (two launches of
-# 134.2M particles: 1.868 and 1.839 GB); scaled to a launch by its particle
-# count.  Retake it whenever k_fast_tma changes.
-FAST_TRAFFIC_PER_PARTICLE = (1.868076e9 + 1.838689e9) / 2 / 134217728
+# DRAM bytes (read + write) per particle of the fast stage, from an ncu
+# capture of k_fast_tma on two boxes of 512^3 particles at Nside 512 (two
+# launches of 134.2M particles: 1.869 and 1.838 GB); scaled to a launch by
+# its particle count.  Retake it whenever k_fast_tma changes.
+FAST_TRAFFIC_PER_PARTICLE = (1.611092e9 + 257.53856e6 + 1.611049e9 + 227.421696e6) / 2 / 134217728
 
 
 def hbm_peak():
@@ -259,6 +259,51 @@ def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8,
     return out
 
 
+def snapshot_leg(ctx, api, synth, dev, w, z, chi, n_per: int = 1 << 25):
+    """Snapshot-mode lightcone (ufc_bin_snapshots): one snapshot at every
+    second shell edge (30 for 60 shells, each filling two shells), each of
+    n_per particles in a 6400 Mpc/h box around the observer, Nside of the
+    workload.  Every snapshot is read once per call; the rate counts all of
+    their particles."""
+    import torch
+    z_snap = z[:-1:2]
+    sos = api.snapshot_assign(z, z_snap)
+    xs = [synth.particles_torch(n_per, 6400.0, w.boxes[1].sigma, synth.seed_for(5, s, 1),
+                                device=dev) for s in range(len(z_snap))]
+    geoms = [api.make_box(6400.0, [3200.0] * 3, n_per, 0, 1) for _ in xs]
+    counts = torch.empty((w.nshell, 12 * w.nside ** 2), dtype=torch.int32, device=dev)
+    ctx.bin_snapshots(xs, geoms, sos, chi, w.nside, counts=counts)      # warm-up
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.bin_snapshots(xs, geoms, sos, chi, w.nside, counts=counts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = e0.elapsed_time(e1) / reps
+    n_tot = n_per * len(xs)
+    info = ctx.bin_info()
+    fast_ms = prof.get("k_fast", (0.0, 1))[0] / reps
+    out = {"ms": ms, "gparticles_per_s": n_tot / (ms * 1e-3) / 1e9,
+           "k_fast_ms": fast_ms,
+           "k_fast_frac_of_peak": (12.0 * n_tot / (fast_ms * 1e-3) / 1e9) / hbm_peak()[0]
+           if fast_ms else None,
+           "kernels_ms": {k: round(v[0] / reps, 3) for k, v in prof.items()},
+           "in_shells_last_pass": info["keyed"],
+           "config": {"workload": "snapshots_nside%d" % w.nside, "snapshots": len(xs),
+                      "particles_per_snapshot": n_per, "box": "6400 Mpc/h",
+                      "nshell": w.nshell, "nside": w.nside,
+                      "shells_per_snapshot": 2}}
+    del xs
+    return out
+
+
 # ---------------------------------------------------------- reference arm ----
 def run_reference(args):
     """The oracle as the reference arm: each step bins a bounded particle
@@ -321,6 +366,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cl", action="store_true")
+    ap.add_argument("--no-snapshots", action="store_true")
     ap.add_argument("--batched-real", type=int, default=150)
     ap.add_argument("--batched-side", type=int, default=512)
     args = ap.parse_args()
@@ -459,7 +505,7 @@ def main():
     }
 
     if not args.no_cl:
-        # full-sky C_l of the step's kappa map: a_lm, C_l
+        # full-sky C_l of the step's kappa map (Sec. 3.2): a_lm, C_l
         # and band powers at lmax = 3 nside - 1
         lmax = 3 * w.nside - 1
         alm = ctx.map2alm(kap, w.nside, lmax)
@@ -509,6 +555,9 @@ def main():
         # small maps, where launch overheads matter: 2 x 64^3 particles, Nside 64
         line["batched_vs_serial_small"] = batched_leg(ctx, api, synth, dev, args.batched_real,
                                                       64, nside=64)
+
+    if not args.no_snapshots:
+        line["snapshots"] = snapshot_leg(ctx, api, synth, dev, w, z, chi)
 
     # end to end: particles from pinned host memory through the C ABI each
     # step (ufc_bin_host copies them in chunks, overlapped with the binning),

@@ -221,6 +221,35 @@ ufc_status ufc_bin_host_stream(ufc_ctx *ctx, const float *const *xyz_host,
                                int32_t nbox, const double *chi_edges,
                                int32_t nshell, int32_t nside, int32_t flags,
                                int64_t chunk, int32_t *counts_dev);
+
+/* ---- snapshot-mode lightcone (Sec. 2.1, Sec. 2.4) -------------------------- */
+
+/* Which snapshot fills each shell when the simulation wrote snapshots (all
+ * particles at one redshift) instead of a lightcone output.  Shell b is
+ * filled from the snapshot at its redshift z_b, the lower edge (Sec. 2.4);
+ * with snapshots sparser than shells (the paper's snapshots are spaced
+ * dz = 0.02, its shells 0.01) shell b takes the last snapshot at or below
+ * z_b: snap_of_shell[b] = max{s : z_snap[s] <= z_b + 1e-9 (1 + |z_b|)}, or
+ * -1 when every snapshot lies above z_b.  The 1e-9 slack absorbs the last-bit
+ * differences of redshift grids generated in different ways.
+ * z_edges: nshell+1 finite, increasing; z_snap: nsnap finite, strictly
+ * increasing (host arrays).  UFC_ERR_ARG otherwise.  Host only. */
+ufc_status ufc_snapshot_assign(const double *z_edges, int32_t nshell,
+                               const double *z_snap, int32_t nsnap,
+                               int32_t *snap_of_shell);
+/* Count maps of a snapshot-mode lightcone: shell b counts the particles of
+ * snapshot s = snap_of_shell[b] (xyz_dev[s], n[s] of them, in the box
+ * snap_geom[s]: L, obs, n_total and replicate are used, the shell range is
+ * ignored) whose radius lies in shell b; a shell with s = -1 stays empty.
+ * Each run of consecutive shells taken from one snapshot is one box of a
+ * ufc_bin pass; a pass takes up to 16 runs and the later passes accumulate.
+ * The dense path's histogram covers only the shells of the pass.  Flags and
+ * output as for ufc_bin; ufc_bin_info describes the last pass. */
+ufc_status ufc_bin_snapshots(ufc_ctx *ctx, const float *const *xyz_dev,
+                             const int64_t *n, const ufc_box *snap_geom,
+                             int32_t nsnap, const int32_t *snap_of_shell,
+                             const double *chi_edges, int32_t nshell,
+                             int32_t nside, int32_t flags, int32_t *counts_dev);
 /* Diagnostics of the last ufc_bin/ufc_keys call (synchronises):
  * info[0] invalid particles, info[1] particle-images with a key,
  * info[2] decisions refined past the FP32 stage, info[3] past the
@@ -286,7 +315,7 @@ ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
                               const double *dC, double *grad_theta, double *G,
                               double *H);
 
-/* ---- full-sky power spectrum (Sec. 3.2) ------------------ */
+/* ---- full-sky power spectrum (Sec. 3.2, Eq. 10-11) ------------------------- */
 
 /* Spherical-harmonic coefficients of a RING map (FP32 [12 nside^2], e.g.
  * kappa or delta from ufc_kappa_stats):
@@ -311,7 +340,7 @@ ufc_status ufc_alm2cl(ufc_ctx *ctx, const double *alm_dev, int32_t lmax,
 ufc_status ufc_cl_bin(ufc_ctx *ctx, const double *cl_dev, int32_t lmax,
                       int32_t lmin, int32_t dl, int32_t nbins, double *out_dev);
 
-/* ---- smoothed maps (Sec. 3.3) ----------------------------- */
+/* ---- smoothed maps (Sec. 3.3, Eq. 12-13) ----------------------------------- */
 
 /* Gaussian beam in harmonic space: alm_out[l, m] = alm_in[l, m] b_l,
  * b_l = exp(-l(l+1) sigma^2 / 2), sigma the beam's r.m.s. radius in

@@ -94,6 +94,8 @@ def _declare(L):
         "or_pix2ang_ring": (None, [I64, I64, P, P]),
         "or_keys": (None, [P, I64, P, P, I32, I64, P]),
         "or_bin": (I64, [P, I64, P, P, I32, I64, P]),
+        "or_snapshot_assign": (None, [P, I32, P, I32, P]),
+        "or_bin_snapshots": (I64, [P, P, P, P, P, I32, I64, P]),
         "or_comoving_distance": (D, [D, D, ctypes.c_int, D]),
         "or_chi_edges": (None, [D, D, ctypes.c_int, P, I32, P]),
         "or_z_of_chi": (D, [D, D, ctypes.c_int, D]),
@@ -182,6 +184,33 @@ def bin_counts(xyz: np.ndarray, box: Box, chi_edges: np.ndarray, nside: int,
         counts = np.zeros((nshell, nside2npix(nside)), dtype=np.int32)
     assert counts.dtype == np.int32 and counts.flags.c_contiguous
     inv = lib().or_bin(_ptr(xyz), len(xyz), ctypes.byref(box), _ptr(chi), nshell, nside, _ptr(counts))
+    return counts, int(inv)
+
+
+def snapshot_assign(z_edges, z_snap) -> np.ndarray:
+    """Snapshot of each shell in snapshot mode (Sec. 2.1, 2.4), -1 if none."""
+    z = np.ascontiguousarray(z_edges, dtype=np.float64)
+    zs = np.ascontiguousarray(z_snap, dtype=np.float64)
+    out = np.empty(len(z) - 1, dtype=np.int32)
+    lib().or_snapshot_assign(_ptr(z), len(z) - 1, _ptr(zs), len(zs), _ptr(out))
+    return out
+
+
+def bin_snapshots(xyz_list, geoms, snap_of_shell, chi_edges, nside: int):
+    """Count maps int32[nshell, npix] of a snapshot-mode lightcone: shell b
+    from the particles of snapshot snap_of_shell[b]; returns (counts, n_invalid)."""
+    xs = [np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 3) for x in xyz_list]
+    chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+    nshell = len(chi) - 1
+    sos = np.ascontiguousarray(snap_of_shell, dtype=np.int32)
+    assert len(sos) == nshell and len(geoms) == len(xs)
+    counts = np.zeros((nshell, nside2npix(nside)), dtype=np.int32)
+    ptrs = (ctypes.c_void_p * len(xs))(*[x.ctypes.data for x in xs])
+    ns = np.array([len(x) for x in xs], dtype=np.int64)
+    arr = (Box * len(geoms))(*geoms)
+    inv = lib().or_bin_snapshots(ctypes.cast(ptrs, ctypes.c_void_p), _ptr(ns),
+                                 ctypes.cast(arr, ctypes.c_void_p), _ptr(sos), _ptr(chi), nshell,
+                                 nside, _ptr(counts))
     return counts, int(inv)
 
 

@@ -60,6 +60,14 @@ void or_keys(const float *xyz, int64_t n, const or_box *box,
 int64_t or_bin(const float *xyz, int64_t n, const or_box *box,
                const double *chi_edges, int32_t nshell, int64_t nside,
                int32_t *counts);
+/* Snapshot mode: the snapshot of each shell (last one at or below the
+ * shell's lower-edge redshift, -1 if none), and the count maps with shell b
+ * taken from snapshot snap_of_shell[b] (added to counts). */
+void or_snapshot_assign(const double *z_edges, int32_t nshell, const double *z_snap,
+                        int32_t nsnap, int32_t *snap_of_shell);
+int64_t or_bin_snapshots(const float *const *xyz, const int64_t *n, const or_box *geom,
+                         const int32_t *snap_of_shell, const double *chi_edges,
+                         int32_t nshell, int64_t nside, int32_t *counts);
 
 /* ---- Cosmology and shell weights (Eq. 1-3, Eq. 6) ------------------------ */
 /* Source: kind 0 = single plane at z_s (Eq. 3); kind 1 = n(z) proportional to

@@ -89,6 +89,8 @@ _SIGS = {
     "ufc_bin_host": [P, P, P, P, I32, P, I32, I32, I32, P],
     "ufc_bin_host_stream": [P, P, P, P, I32, P, I32, I32, I32, I64, P],
     "ufc_bin_info": [P, P],
+    "ufc_snapshot_assign": [P, I32, P, I32, P],
+    "ufc_bin_snapshots": [P, P, P, P, I32, P, P, I32, I32, I32, P],
     "ufc_kappa_stats": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_kappa_backward": [P, P, I32, I32, P, D, D, D, P, P, P, P, P, P],
     "ufc_welford_update": [P, P, I32, I32, P],
@@ -143,6 +145,17 @@ def z_of_chi(cosmo: Cosmo, chi) -> np.ndarray:
     out = np.empty_like(c)
     _check(_lib.ufc_z_of_chi(ctypes.byref(cosmo), _np_ptr(c), len(c), _np_ptr(out)),
            what="ufc_z_of_chi")
+    return out
+
+
+def snapshot_assign(z_edges, z_snap) -> np.ndarray:
+    """int32 snapshot index of every shell in snapshot mode (the last snapshot
+    at or below the shell's lower-edge redshift, -1 if none)."""
+    z = np.ascontiguousarray(z_edges, dtype=np.float64)
+    zs = np.ascontiguousarray(z_snap, dtype=np.float64)
+    out = np.empty(len(z) - 1, dtype=np.int32)
+    _check(_lib.ufc_snapshot_assign(_np_ptr(z), len(z) - 1, _np_ptr(zs), len(zs), _np_ptr(out)),
+           what="ufc_snapshot_assign")
     return out
 
 
@@ -319,6 +332,31 @@ class Context:
                                           ctypes.cast(arr, P), len(boxes), _np_ptr(chi), S, nside,
                                           _bin_flags(accumulate, path), int(chunk),
                                           P(counts.data_ptr())), "ufc_bin_host_stream")
+        return counts
+
+    def bin_snapshots(self, xyz_list, geoms, snap_of_shell, chi_edges, nside: int, counts=None,
+                      accumulate=False, path: str | None = None):
+        """Count maps of a snapshot-mode lightcone (ufc_bin_snapshots): shell b
+        from the particles xyz_list[s] of snapshot s = snap_of_shell[b], in the
+        box geoms[s] (its shell range is ignored)."""
+        import torch
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        S = len(chi) - 1
+        npix = 12 * nside * nside
+        sos = np.ascontiguousarray(snap_of_shell, dtype=np.int32)
+        assert len(sos) == S and len(geoms) == len(xyz_list)
+        xs = [_dev_f32(x, self.device) for x in xyz_list]
+        if counts is None:
+            counts = torch.empty((S, npix), dtype=torch.int32, device=f"cuda:{self.device}")
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.numel() == S * npix
+        ptrs = (P * len(xs))(*[P(x.data_ptr()) for x in xs])
+        ns = (I64 * len(xs))(*[x.numel() // 3 for x in xs])
+        arr = (Box * len(geoms))(*geoms)
+        self._stream()
+        self._ck(_lib.ufc_bin_snapshots(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P),
+                                        ctypes.cast(arr, P), len(geoms), _np_ptr(sos),
+                                        _np_ptr(chi), S, nside, _bin_flags(accumulate, path),
+                                        P(counts.data_ptr())), "ufc_bin_snapshots")
         return counts
 
     def bin_info(self):

@@ -47,6 +47,8 @@ struct KeyOut {
   int64_t dense_cap;
   int32_t nblk;                // blocks per shell (DENSE)
   int32_t nbuckets;
+  int32_t shell0;              // DENSE: first shell of the call's window; buckets
+                               // count blocks from shell0 * nblk
   int32_t smem_hist;           // 1: histogram in shared memory
 };
 
@@ -63,11 +65,11 @@ struct WarpChunk {
   int32_t fill;
 };
 
-__device__ __forceinline__ uint32_t dense_key(int32_t key, int32_t npix, int32_t nblk) {
+__device__ __forceinline__ uint32_t dense_key(int32_t key, int32_t npix, const KeyOut& o) {
   int32_t b = key / npix;
   int32_t pix = key - b * npix;
   int32_t blk = pix / kBlockPix;
-  return (uint32_t(b * nblk + blk) << kOffBits) | uint32_t(pix - blk * kBlockPix);
+  return (uint32_t((b - o.shell0) * o.nblk + blk) << kOffBits) | uint32_t(pix - blk * kBlockPix);
 }
 
 // Appends the keys of lanes with `want` to the warp's chunk of the dense
@@ -252,7 +254,7 @@ __device__ __forceinline__ void fast_particle(bool have, float x, float y, float
           key = (pix == kKeyUndecided) ? kKeyUndecided : b * npix + pix;
           if (MODE == kModeDense && pix != kKeyUndecided) {
             const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
-            dkey = ((uint32_t(b) * uint32_t(o.nblk) + blk) << kOffBits) |
+            dkey = ((uint32_t(b - o.shell0) * uint32_t(o.nblk) + blk) << kOffBits) |
                    (uint32_t(pix) - blk * uint32_t(kBlockPix));
           }
         }
@@ -264,7 +266,7 @@ __device__ __forceinline__ void fast_particle(bool have, float x, float y, float
       key = key_exact(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii], bg.sh64[1][jj],
                       bg.sh64[2][kk]);
       if (key == kKeyInvalid) ++fc.n_invalid;
-      if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o.nblk);
+      if (MODE == kModeDense && key >= 0) dkey = dense_key(key, npix, o);
     }
     if (MODE == kModeKeys) {
       if (have) o.keys[p] = finite ? key : kKeyInvalid;
@@ -579,7 +581,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
               ++fc.n_keyed;
               if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
               if (MODE == kModeDense) {            // rare: straight to the global histogram
-                const uint32_t dk = dense_key(kx, npix, o.nblk);
+                const uint32_t dk = dense_key(kx, npix, o);
                 atomicAdd(ghist + (dk >> kOffBits), 1u);
                 const unsigned long long at = atomicAdd(o.dense_count, 1ull);
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
@@ -637,7 +639,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
               ++fc.n_keyed;
               if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
               if (MODE == kModeDense) {
-                const uint32_t dk = dense_key(kx, npix, o.nblk);
+                const uint32_t dk = dense_key(kx, npix, o);
                 atomicAdd(ghist + (dk >> kOffBits), 1u);
                 const unsigned long long at = atomicAdd(o.dense_count, 1ull);
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
@@ -653,7 +655,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
             uint32_t dk = 0u;
             if (ok) {
               const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
-              const uint32_t bucket = uint32_t(b) * uint32_t(o.nblk) + blk;
+              const uint32_t bucket = uint32_t(b - o.shell0) * uint32_t(o.nblk) + blk;
               dk = (bucket << kOffBits) | (uint32_t(pix) - blk * uint32_t(kBlockPix));
               if (o.smem_hist) hist16_inc(h32, ghist, bucket);
               else atomicAdd(ghist + bucket, 1u);
@@ -717,7 +719,7 @@ __device__ __forceinline__ void emit_late(int32_t key, int64_t p, int32_t npix,
   } else if (MODE == kModeDirect) {
     if (key >= 0) atomicAdd(o.counts + key, 1);
   } else {
-    uint32_t dk = key >= 0 ? dense_key(key, npix, o.nblk) : 0u;
+    uint32_t dk = key >= 0 ? dense_key(key, npix, o) : 0u;
     if (key >= 0) atomicAdd(o.hist + (dk >> kOffBits), 1u);
     dense_append(wc, key >= 0, dk, o);
   }
@@ -1035,17 +1037,19 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
 
 // Count map of each bucket from its u16 offsets, in shared memory.  The
 // bucket's offsets are read with 16-byte loads (8 offsets each), two per
-// thread in flight, plus scalar head and tail.
+// thread in flight, plus scalar head and tail.  When accumulating, a bucket
+// without particles leaves its block of the map untouched.
 constexpr int kHistThreads = 512;
 __global__ void __launch_bounds__(kHistThreads)
 k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off, int nb,
              int32_t* __restrict__ counts, int accumulate) {
   extern __shared__ uint32_t h[];   // [kBlockPix]
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t a = off[b], e = off[b + 1];
+    if (accumulate && a == e) continue;          // nothing to add (uniform over the block)
     uint4* h4 = reinterpret_cast<uint4*>(h);
     for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) h4[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    const int64_t a = off[b], e = off[b + 1];
     const int64_t a8r = (a + 7) & ~7ll, e8r = e & ~7ll;
     const int64_t a8 = a8r < e ? a8r : e;                  // first 16-byte boundary
     const int64_t e8 = e8r > a8 ? e8r : a8;                // last one
@@ -1180,6 +1184,7 @@ static ufc_status make_box(ufc_ctx* c, const ufc_box& b, int nshell, BoxGeom& g)
 
 struct BinPlan {
   int mode;
+  int shell0, shell1;            // shells any box of the call owns: [shell0, shell1)
   int nblk, nbuckets, ng, smem_hist;
 };
 
@@ -1303,10 +1308,17 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
 
   BinPlan plan{};
   plan.mode = mode_req;
+  plan.shell0 = nshell;
+  plan.shell1 = 0;
+  for (int k = 0; k < nbox; ++k) {
+    plan.shell0 = std::min(plan.shell0, (int)boxes[k].shell_lo);
+    plan.shell1 = std::max(plan.shell1, (int)boxes[k].shell_hi);
+  }
+  const int nwin = plan.shell1 - plan.shell0;   // the dense path covers these shells only
   if (mode_req != kModeKeys) {
-    const int64_t map_bytes = (int64_t)nshell * npix * 4;
+    const int64_t map_bytes = (int64_t)nwin * npix * 4;
     const bool dense_ok = nside >= 64 && maxR == 0 &&
-                          (int64_t)nshell * (npix / kBlockPix) < (1ll << 17);
+                          (int64_t)nwin * (npix / kBlockPix) < (1ll << 17);
     const bool aligned = (reinterpret_cast<uintptr_t>(counts) & 15) == 0;
     plan.mode = (dense_ok && aligned && map_bytes > (32ll << 20)) ? kModeDense : kModeDirect;
     if (flags & UFC_BIN_FORCE_DIRECT) plan.mode = kModeDirect;
@@ -1314,13 +1326,13 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
       if (!(dense_ok && aligned))
         return set_err(c, UFC_ERR_UNSUPPORTED,
                        "the dense path needs nside >= 64, no replication, 16-byte aligned counts "
-                       "and nshell * 12 nside^2 / 24576 < 2^17");
+                       "and (shells of the boxes) * 12 nside^2 / 24576 < 2^17");
       plan.mode = kModeDense;
     }
   }
   if (plan.mode == kModeDense) {
     plan.nblk = (int)(npix / kBlockPix);
-    plan.nbuckets = nshell * plan.nblk;
+    plan.nbuckets = nwin * plan.nblk;
     plan.ng = (plan.nbuckets + (1 << kGroupBits) - 1) >> kGroupBits;
     // bucket counters in shared memory when both fast kernels still fit
     const size_t fixed = sizeof(FastShared) + 1024;
@@ -1354,7 +1366,15 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     o.nblk = plan.nblk;
     o.nbuckets = plan.nbuckets;
     o.smem_hist = plan.smem_hist;
+    o.shell0 = plan.shell0;
     UFC_CUDA(c, cudaMemsetAsync(o.hist, 0, (size_t)plan.nbuckets * 4, c->stream));
+    if (!(flags & UFC_BIN_ACCUMULATE)) {   // shells outside the window hold no particle
+      if (plan.shell0 > 0)
+        UFC_CUDA(c, cudaMemsetAsync(counts, 0, (size_t)plan.shell0 * npix * 4, c->stream));
+      if (plan.shell1 < nshell)
+        UFC_CUDA(c, cudaMemsetAsync(counts + (int64_t)plan.shell1 * npix, 0,
+                                    (size_t)(nshell - plan.shell1) * npix * 4, c->stream));
+    }
     smem = plan.smem_hist ? plan.nbuckets * 4 : 0;
   } else if (plan.mode == kModeDirect) {
     if (!(flags & UFC_BIN_ACCUMULATE))
@@ -1510,7 +1530,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   {
     ProfScope ps_(c, "k_hist_block");
     k_hist_block<<<2 * c->num_sms, kHistThreads, smemH, c->stream>>>(
-        b16, off, nb, counts, (flags & UFC_BIN_ACCUMULATE) ? 1 : 0);
+        b16, off, nb, counts + (int64_t)plan.shell0 * npix, (flags & UFC_BIN_ACCUMULATE) ? 1 : 0);
   }
   UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;

@@ -419,6 +419,83 @@ ufc_status ufc_bin_host_stream(ufc_ctx* c, const float* const* xyz_host, const i
                         counts_dev);
 }
 
+ufc_status ufc_snapshot_assign(const double* z_edges, int32_t nshell, const double* z_snap,
+                               int32_t nsnap, int32_t* snap_of_shell) {
+  if (!z_edges || !z_snap || !snap_of_shell || nshell < 1 || nshell > UFC_MAX_SHELLS || nsnap < 1)
+    return UFC_ERR_ARG;
+  for (int b = 0; b <= nshell; ++b)
+    if (!std::isfinite(z_edges[b]) || (b > 0 && !(z_edges[b] > z_edges[b - 1]))) return UFC_ERR_ARG;
+  for (int s = 0; s < nsnap; ++s)
+    if (!std::isfinite(z_snap[s]) || (s > 0 && !(z_snap[s] > z_snap[s - 1]))) return UFC_ERR_ARG;
+  // both lists ascend: one merge pass
+  int s = -1;
+  for (int b = 0; b < nshell; ++b) {
+    const double lim = z_edges[b] + 1e-9 * (1.0 + std::fabs(z_edges[b]));
+    while (s + 1 < nsnap && z_snap[s + 1] <= lim) ++s;
+    snap_of_shell[b] = s;
+  }
+  return UFC_OK;
+}
+
+ufc_status ufc_bin_snapshots(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
+                             const ufc_box* snap_geom, int32_t nsnap, const int32_t* snap_of_shell,
+                             const double* chi_edges, int32_t nshell, int32_t nside, int32_t flags,
+                             int32_t* counts_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!xyz_dev || !n || !snap_geom || !snap_of_shell || !chi_edges || !counts_dev)
+    return set_err(c, UFC_ERR_ARG, "NULL argument to ufc_bin_snapshots");
+  if (nsnap < 1) return set_err(c, UFC_ERR_ARG, "nsnap must be >= 1");
+  if (nshell < 1 || nshell > UFC_MAX_SHELLS)
+    return set_err(c, UFC_ERR_ARG, "nshell must be in [1,%d]", UFC_MAX_SHELLS);
+  if (flags & ~(UFC_BIN_ACCUMULATE | UFC_BIN_FORCE_DIRECT | UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if ((flags & UFC_BIN_FORCE_DIRECT) && (flags & UFC_BIN_FORCE_DENSE))
+    return set_err(c, UFC_ERR_ARG, "FORCE_DIRECT and FORCE_DENSE exclude each other");
+  if (reinterpret_cast<uintptr_t>(counts_dev) & 3)
+    return set_err(c, UFC_ERR_ARG, "counts_dev must be 4-byte aligned");
+  for (int b = 0; b < nshell; ++b)
+    if (snap_of_shell[b] < -1 || snap_of_shell[b] >= nsnap)
+      return set_err(c, UFC_ERR_ARG, "snap_of_shell[%d] = %d outside [-1,%d)", b,
+                     snap_of_shell[b], nsnap);
+  cudaSetDevice(c->device);
+  // runs of consecutive shells from one snapshot, kMaxBoxes per pass
+  ufc_box rb[kMaxBoxes];
+  const float* rx[kMaxBoxes];
+  int64_t rn[kMaxBoxes];
+  int nrun = 0, passes = 0;
+  auto pass = [&]() -> ufc_status {
+    const int32_t f = flags | (passes > 0 ? UFC_BIN_ACCUMULATE : 0);
+    const ufc_status st = run_keys_pipeline(c, 1, rx, rn, rb, nrun, chi_edges, nshell, nside, f,
+                                            counts_dev, nullptr, nullptr);
+    ++passes;
+    nrun = 0;
+    return st;
+  };
+  for (int b = 0; b < nshell;) {
+    const int s = snap_of_shell[b];
+    int e = b + 1;
+    while (e < nshell && snap_of_shell[e] == s) ++e;
+    if (s >= 0) {
+      if (nrun == kMaxBoxes) {
+        const ufc_status st = pass();
+        if (st) return st;
+      }
+      rb[nrun] = snap_geom[s];
+      rb[nrun].shell_lo = b;
+      rb[nrun].shell_hi = e;
+      rx[nrun] = xyz_dev[s];
+      rn[nrun] = n[s];
+      ++nrun;
+    }
+    b = e;
+  }
+  if (nrun > 0) return pass();
+  if (passes == 0 && !(flags & UFC_BIN_ACCUMULATE))   // no shell has a snapshot
+    UFC_CUDA(c, cudaMemsetAsync(counts_dev, 0, (size_t)nshell * 12 * nside * nside * 4, c->stream));
+  return UFC_OK;
+}
+
 ufc_status ufc_bin_info(ufc_ctx* c, int64_t info[4]) {
   if (!c || !info) return UFC_ERR_ARG;
   BinCounters h;
