@@ -57,6 +57,8 @@ struct Queues {
   uint64_t* q2;
   int64_t cap1, cap2;
   BinCounters* cnt;
+  uint32_t* ovf;        // one bit per particle of the boxes without images
+  int64_t ovf_base;     // first bit of the launch's box
 };
 
 // ---------------------------------------------------------------- emission --
@@ -163,6 +165,48 @@ __device__ __forceinline__ bool queue_push_f(QChunk& qc, bool want, F entry, uin
 __device__ __forceinline__ bool queue_push(QChunk& qc, bool want, uint64_t e, uint64_t* q,
                                            int64_t cap, unsigned long long* count) {
   return queue_push_f(qc, want, [e]() { return e; }, q, cap, count);
+}
+
+// queue_push_f whose entries that find the queue full set their particle's
+// bit (base + particle index) in the overflow bitmap instead.
+template <class F>
+__device__ __forceinline__ void queue_push_mark(QChunk& qc, bool want, F entry, uint64_t* q,
+                                                int64_t cap, unsigned long long* count,
+                                                uint32_t* ovf, int64_t ovf_base,
+                                                unsigned long long* flag) {
+  const unsigned full = 0xFFFFFFFFu;
+  const unsigned m = __ballot_sync(full, want);
+  if (m == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int cnt = __popc(m);
+  const int rank = __popc(m & ((1u << lane) - 1u));
+  if (qc.base < 0) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(count, (unsigned long long)kQChunk);
+    qc.base = (int64_t)__shfl_sync(full, b, 0);
+    qc.fill = 0;
+  }
+  const int room = kQChunk - qc.fill;
+  int64_t idx = rank < room ? qc.base + qc.fill + rank : -1;
+  if (cnt >= room) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(count, (unsigned long long)kQChunk);
+    const int64_t nb = (int64_t)__shfl_sync(full, b, 0);
+    if (rank >= room) idx = nb + (rank - room);
+    qc.base = nb;
+    qc.fill = cnt - room;
+  } else {
+    qc.fill += cnt;
+  }
+  if (!want) return;
+  const uint64_t e = entry();
+  if (idx < cap) {
+    q[idx] = e;
+  } else {
+    const uint64_t bit = uint64_t(ovf_base) + uint64_t(qidx(e));
+    atomicOr(ovf + (bit >> 5), 1u << (bit & 31u));
+    *flag = 1ull;
+  }
 }
 
 // Marks the unused slots of the warp's last queue chunk.
@@ -437,7 +481,7 @@ __device__ __forceinline__ void hist16_inc(uint32_t* h32, uint32_t* ghist, uint3
   }
 }
 
-template <int MODE>
+template <int MODE, bool IMAGES>
 __global__ void __launch_bounds__(kWThreads, 1)
 k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_id, BoxGeom bg,
            ShellTable st, LutParam lp, Bands bd, int32_t N, int32_t npix, KeyOut o, Queues qs) {
@@ -626,9 +670,16 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
             return (blockIdx.x + ke * gridDim.x) * kWChunk + int64_t((meta >> 8) & 4095u);
           };
           const int32_t key = b * npix + pix;
-          const bool queued = queue_push_f(
-              fc.qc, have && !ok, [&]() { return qpack(box_id, img, p_off + local_index()); },
-              qs.q1, qs.cap1, &qs.cnt->q1);
+          bool queued = true;
+          if constexpr (IMAGES) {
+            queued = queue_push_f(
+                fc.qc, have && !ok, [&]() { return qpack(box_id, img, p_off + local_index()); },
+                qs.q1, qs.cap1, &qs.cnt->q1);
+          } else {                               // queue full: left to the exact pass
+            queue_push_mark(
+                fc.qc, have && !ok, [&]() { return qpack(box_id, 0, p_off + local_index()); },
+                qs.q1, qs.cap1, &qs.cnt->q1, qs.ovf, qs.ovf_base, &qs.cnt->ovf);
+          }
           if (!queued) {                         // queue full: the FP64 procedure here
             const int64_t pl = local_index();
             const float x = __ldg(xyz + 3 * pl), y = __ldg(xyz + 3 * pl + 1),
@@ -728,6 +779,8 @@ __device__ __forceinline__ void emit_late(int32_t key, int64_t p, int32_t npix,
 struct BoxesParam {
   BoxGeom box[kMaxBoxes];
   const float* xyz[kMaxBoxes];
+  int64_t n[kMaxBoxes];          // particles of each box in this call
+  int64_t bit_base[kMaxBoxes];   // first overflow bit of each box (boxes without images)
 };
 
 template <int MODE>
@@ -839,6 +892,49 @@ k_exact(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues 
   }
 }
 
+// Exact pass over the images the fast stage could neither decide nor queue
+// (queue 1 full; boxes without periodic images): one bit per particle of
+// those boxes.  Returns at once unless the fast stage marked any.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+k_overflow(BoxesParam bp, int nbox, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues qs,
+           int64_t nwords) {
+  if (qs.cnt->ovf == 0ull) return;
+  unsigned long long n_ex = 0, n_invalid = 0, n_keyed = 0;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t m = qs.ovf[w];
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1u;
+      const int64_t idx = w * 32 + bit;
+      int k = 0;
+      while (k + 1 < nbox && bp.bit_base[k + 1] <= idx) ++k;
+      const int64_t p = idx - bp.bit_base[k];
+      const BoxGeom& g = bp.box[k];
+      const float* xp = bp.xyz[k] + 3 * p;
+      const int32_t key = key_exact(st, g.shell_lo, g.shell_hi, N, npix, xp[0], xp[1], xp[2],
+                                    g.sh64[0][0], g.sh64[1][0], g.sh64[2][0]);
+      ++n_ex;
+      if (key == kKeyInvalid) ++n_invalid;
+      if (MODE == kModeKeys) o.keys[p] = key;
+      if (key >= 0) {
+        ++n_keyed;
+        if (MODE == kModeDirect) atomicAdd(o.counts + key, 1);
+        if (MODE == kModeDense) {
+          const uint32_t dk = dense_key(key, npix, o);
+          atomicAdd(o.hist + (dk >> kOffBits), 1u);
+          const unsigned long long at = atomicAdd(o.dense_count, 1ull);
+          if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
+        }
+      }
+    }
+  }
+  if (n_ex) atomicAdd(&qs.cnt->exact, n_ex);
+  if (n_invalid) atomicAdd(&qs.cnt->invalid, n_invalid);
+  if (n_keyed) atomicAdd(&qs.cnt->keyed, n_keyed);
+}
+
 // ------------------------------------------------------ dense pipeline -----
 // Exclusive scan of hist[nb] into off[nb+1] (one block of 1024 threads).
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ hist, int nb,
@@ -890,14 +986,15 @@ __device__ __forceinline__ void warp_exclusive_scan(const uint32_t* cnt, uint32_
   for (int i = a; i < b; ++i) { start[i] = run; run += cnt[i]; }
 }
 
-constexpr int kScatThreads = 1024;
+constexpr int kScatThreads = 512;
 constexpr int kScatPer = 16;
-constexpr int kScatTile = kScatThreads * kScatPer;   // 16384 keys: ~128 B per destination
+constexpr int kScatTile = kScatThreads * kScatPer;   // 8192 keys: ~64 B per destination
 
-// Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.  The
-// next tile's keys are loaded into registers while the current tile is
-// sorted in shared memory and written out.
-__global__ void __launch_bounds__(kScatThreads)
+// Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.  Two
+// blocks per SM: one block's loads overlap the other's counting, scan and
+// write-out phases.  Each destination's offset is kept as (global base -
+// tile start), one 64-bit shared load per key at write-out.
+__global__ void __launch_bounds__(kScatThreads, 2)
 k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* dense_count,
                 int64_t dense_cap, int ng, unsigned long long* __restrict__ gcur, uint32_t* __restrict__ out) {
   extern __shared__ uint32_t sm[];
@@ -908,7 +1005,7 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
   const int64_t total = (int64_t)min(*dense_count, (unsigned long long)dense_cap);
   const int64_t ntiles = (total + kScatTile - 1) / kScatTile;
   const int shift = kOffBits + kGroupBits;
-  uint32_t v[kScatPer], nv[kScatPer];
+  uint32_t v[kScatPer];
   auto fetch = [&](int64_t t, uint32_t* dst) {
     const int64_t t0 = t * kScatTile;
 #pragma unroll
@@ -918,9 +1015,8 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
     }
   };
   int64_t tIdx = blockIdx.x;
-  fetch(tIdx, v);
   for (; tIdx < ntiles; tIdx += gridDim.x) {
-    fetch(tIdx + gridDim.x, nv);           // prefetch the next tile
+    fetch(tIdx, v);
     for (int i = threadIdx.x; i < ng; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     uint32_t slot[kScatPer];
@@ -931,7 +1027,7 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
     if (threadIdx.x < 32) warp_exclusive_scan(cnt, start, ng);
     __syncthreads();
     for (int g = threadIdx.x; g < ng; g += blockDim.x)
-      base[g] = cnt[g] ? atomicAdd(gcur + g, (unsigned long long)cnt[g]) : 0ull;
+      base[g] = (cnt[g] ? atomicAdd(gcur + g, (unsigned long long)cnt[g]) : 0ull) - start[g];
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k)
       if (v[k] != kSentinel) tile[start[v[k] >> shift] + slot[k]] = v[k];
@@ -940,44 +1036,53 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
     for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) {
       const uint32_t val = tile[i];
       const uint32_t g = val >> shift;
-      out[base[g] + (i - start[g])] = val;
+      out[base[g] + i] = val;
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kScatPer; ++k) v[k] = nv[k];
   }
 }
 
 struct Tile { int32_t group; int32_t len; int64_t start; };
 
 // Tile list of pass B: every group's range split into kScatTile pieces.
-__global__ void __launch_bounds__(1024) k_tiles(const int64_t* __restrict__ off, int nb, int ng,
-                                                Tile* __restrict__ tiles,
-                                                unsigned long long* __restrict__ ntiles) {
-  __shared__ int64_t pre[1025];
-  const int t = threadIdx.x;
-  int64_t mine = 0;
-  for (int g = t; g < ng; g += 1024) {
-    int64_t a = off[min(nb, g << kGroupBits)], b = off[min(nb, (g + 1) << kGroupBits)];
-    mine += (b - a + kScatTile - 1) / kScatTile;
-  }
-  pre[t + 1] = mine;
-  if (t == 0) pre[0] = 0;
+// Every block scans the per-group tile counts in shared memory (ng + 1
+// entries), then the grid writes the tiles, each thread finding its tile's
+// group by binary search over the scan.
+constexpr int kTilesThreads = 256;
+__global__ void __launch_bounds__(kTilesThreads) k_tiles(const int64_t* __restrict__ off, int nb,
+                                                         int ng, Tile* __restrict__ tiles,
+                                                         unsigned long long* __restrict__ ntiles) {
+  extern __shared__ int64_t tsm[];
+  int64_t* gs = tsm;                 // [ng + 1] first key of each group, then the end
+  int64_t* pre = tsm + ng + 1;       // [ng + 1] first tile of each group, then the total
+  for (int g = threadIdx.x; g <= ng; g += blockDim.x) gs[g] = off[min(nb, g << kGroupBits)];
   __syncthreads();
-  if (t == 0)
-    for (int i = 1; i <= 1024; ++i) pre[i] += pre[i - 1];
-  __syncthreads();
-  int64_t w = pre[t];
-  for (int g = t; g < ng; g += 1024) {
-    int64_t a = off[min(nb, g << kGroupBits)], b = off[min(nb, (g + 1) << kGroupBits)];
-    for (int64_t s = a; s < b; s += kScatTile)
-      tiles[w++] = Tile{g, (int32_t)((b - s) < kScatTile ? (b - s) : kScatTile), s};
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int g = 0; g < ng; ++g) {
+      pre[g] = run;
+      run += (gs[g + 1] - gs[g] + kScatTile - 1) / kScatTile;
+    }
+    pre[ng] = run;
   }
-  if (t == 0) *ntiles = (unsigned long long)pre[1024];
+  __syncthreads();
+  const int64_t total = pre[ng];
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ng;                           // pre[lo] <= w < pre[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pre[mid] <= w) lo = mid; else hi = mid;
+    }
+    const int64_t st = gs[lo] + (w - pre[lo]) * kScatTile;
+    const int64_t len = gs[lo + 1] - st;
+    tiles[w] = Tile{lo, (int32_t)(len < kScatTile ? len : kScatTile), st};
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *ntiles = (unsigned long long)total;
 }
 
-// Pass B: grouped keys -> per-bucket u16 offsets (next tile prefetched).
-__global__ void __launch_bounds__(kScatThreads)
+// Pass B: grouped keys -> per-bucket u16 offsets (two blocks per SM, as pass A).
+__global__ void __launch_bounds__(kScatThreads, 2)
 k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ tiles,
                  const unsigned long long* __restrict__ ntiles_p,
                  unsigned long long* __restrict__ bcur, uint16_t* __restrict__ out) {
@@ -989,8 +1094,8 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
   uint16_t* tile = reinterpret_cast<uint16_t*>(start + NS);                // [kScatTile]
   uint8_t* tsub = reinterpret_cast<uint8_t*>(tile + kScatTile);            // [kScatTile]
   const int64_t ntiles = (int64_t)*ntiles_p;
-  uint32_t v[kScatPer], nv[kScatPer];
-  Tile T{0, 0, 0}, NT{0, 0, 0};
+  uint32_t v[kScatPer];
+  Tile T{0, 0, 0};
   auto fetch = [&](int64_t ti, Tile& tt, uint32_t* dst) {
     if (ti < ntiles) tt = tiles[ti]; else tt = Tile{0, 0, 0};
 #pragma unroll
@@ -1000,9 +1105,8 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
     }
   };
   int64_t ti = blockIdx.x;
-  fetch(ti, T, v);
   for (; ti < ntiles; ti += gridDim.x) {
-    fetch(ti + gridDim.x, NT, nv);
+    fetch(ti, T, v);
     for (int i = threadIdx.x; i < NS; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     uint32_t slot[kScatPer];
@@ -1013,8 +1117,8 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
     if (threadIdx.x < 32) warp_exclusive_scan(cnt, start, NS);
     __syncthreads();
     for (int sIdx = threadIdx.x; sIdx < NS; sIdx += blockDim.x)
-      base[sIdx] = cnt[sIdx] ? atomicAdd(bcur + ((int64_t)T.group << kGroupBits) + sIdx,
-                                         (unsigned long long)cnt[sIdx]) : 0ull;
+      base[sIdx] = (cnt[sIdx] ? atomicAdd(bcur + ((int64_t)T.group << kGroupBits) + sIdx,
+                                          (unsigned long long)cnt[sIdx]) : 0ull) - start[sIdx];
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k)
       if (v[k] != kSentinel) {
@@ -1026,30 +1130,30 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
     __syncthreads();
     for (int i = threadIdx.x; i < T.len; i += blockDim.x) {
       const uint32_t sub = tsub[i];
-      out[base[sub] + (i - start[sub])] = tile[i];
+      out[base[sub] + i] = tile[i];
     }
     __syncthreads();
-    T = NT;
-#pragma unroll
-    for (int k = 0; k < kScatPer; ++k) v[k] = nv[k];
   }
 }
 
 // Count map of each bucket from its u16 offsets, in shared memory.  The
-// bucket's offsets are read with 16-byte loads (8 offsets each), two per
-// thread in flight, plus scalar head and tail.  When accumulating, a bucket
-// without particles leaves its block of the map untouched.
+// bucket's offsets are read with 16-byte loads (8 offsets each), up to
+// kHistVec per thread in flight, plus scalar head and tail.  The write-out
+// of a bucket also clears its shared counters for the next one.  When
+// accumulating, a bucket without particles leaves its block of the map
+// untouched.
 constexpr int kHistThreads = 512;
+constexpr int kHistVec = 8;
 __global__ void __launch_bounds__(kHistThreads)
 k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off, int nb,
              int32_t* __restrict__ counts, int accumulate) {
   extern __shared__ uint32_t h[];   // [kBlockPix]
+  uint4* h4 = reinterpret_cast<uint4*>(h);
+  for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) h4[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     const int64_t a = off[b], e = off[b + 1];
     if (accumulate && a == e) continue;          // nothing to add (uniform over the block)
-    uint4* h4 = reinterpret_cast<uint4*>(h);
-    for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) h4[i] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
     const int64_t a8r = (a + 7) & ~7ll, e8r = e & ~7ll;
     const int64_t a8 = a8r < e ? a8r : e;                  // first 16-byte boundary
     const int64_t e8 = e8r > a8 ? e8r : a8;                // last one
@@ -1057,30 +1161,30 @@ k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off,
     if (threadIdx.x < e - e8) atomicAdd(h + offs[e8 + threadIdx.x], 1u);
     const uint4* body = reinterpret_cast<const uint4*>(offs + a8);
     const int64_t nvec = (e8 - a8) >> 3;
-    for (int64_t i = threadIdx.x; i < nvec; i += 2 * kHistThreads) {
-      const uint4 p = __ldcs(body + i);
-      const bool two = i + kHistThreads < nvec;
-      const uint4 q = two ? __ldcs(body + i + kHistThreads) : make_uint4(0, 0, 0, 0);
-      const uint32_t w[4] = {p.x, p.y, p.z, p.w};
+    for (int64_t i0 = threadIdx.x; i0 < nvec; i0 += kHistVec * kHistThreads) {
+      uint4 q[kHistVec];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        atomicAdd(h + (w[k] & 0xFFFFu), 1u);
-        atomicAdd(h + (w[k] >> 16), 1u);
+      for (int k = 0; k < kHistVec; ++k) {
+        const int64_t i = i0 + k * kHistThreads;
+        q[k] = i < nvec ? __ldcs(body + i) : make_uint4(0, 0, 0, 0);
       }
-      if (two) {
-        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          atomicAdd(h + (u[k] & 0xFFFFu), 1u);
-          atomicAdd(h + (u[k] >> 16), 1u);
+      for (int k = 0; k < kHistVec; ++k) {
+        if (i0 + k * kHistThreads < nvec) {
+          const uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            atomicAdd(h + (w[j] & 0xFFFFu), 1u);
+            atomicAdd(h + (w[j] >> 16), 1u);
+          }
         }
       }
     }
     __syncthreads();
     int4* dst = reinterpret_cast<int4*>(counts + (int64_t)b * kBlockPix);
-    const uint4* src = reinterpret_cast<const uint4*>(h);
     for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) {
-      const uint4 sv = src[i];
+      const uint4 sv = h4[i];
+      h4[i] = make_uint4(0, 0, 0, 0);
       int4 d = make_int4(int(sv.x), int(sv.y), int(sv.z), int(sv.w));
       if (accumulate) {
         const int4 o = dst[i];
@@ -1299,6 +1403,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     s = make_box(c, boxes[k], nshell, bp.box[k]);
     if (s) return s;
     bp.xyz[k] = xyz[k];
+    bp.n[k] = n[k];
     total_img += n[k] * bp.box[k].nimg;
     smax = std::max(smax, bp.box[k].smax);
     maxR = std::max(maxR, (int)boxes[k].replicate);
@@ -1351,6 +1456,17 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   if (!qs.q1 || !qs.q2) return UFC_ERR_ALLOC;
   qs.cnt = (BinCounters*)c->counters;
   UFC_CUDA(c, cudaMemsetAsync(qs.cnt, 0, sizeof(BinCounters), c->stream));
+  // overflow bits: one per particle of the boxes without periodic images
+  int64_t nbits = 0;
+  for (int k = 0; k < nbox; ++k) {
+    bp.bit_base[k] = nbits;
+    if (bp.box[k].nimg == 1) nbits += n[k];
+  }
+  const int64_t ovf_words = (nbits + 31) / 32;
+  qs.ovf = (uint32_t*)ws_get(c, kSlotOvf, (size_t)ovf_words * 4);
+  if (!qs.ovf) return UFC_ERR_ALLOC;
+  qs.ovf_base = 0;
+  if (ovf_words) UFC_CUDA(c, cudaMemsetAsync(qs.ovf, 0, (size_t)ovf_words * 4, c->stream));
 
   KeyOut o;
   std::memset(&o, 0, sizeof o);
@@ -1429,14 +1545,20 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
       const bool tma = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
       ProfScope ps_(c, "k_fast");
       if (tma) {
-#define UFC_LAUNCH_TMA(M)                                                                       \
-  UFC_CUDA(c, cudaFuncSetAttribute(k_fast_tma<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+        qs.ovf_base = bp.bit_base[k];
+        const bool images = bp.box[k].nimg > 1;
+#define UFC_LAUNCH_TMA(M, I)                                                                    \
+  UFC_CUDA(c, cudaFuncSetAttribute(k_fast_tma<M, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                    tma_smem));                                                   \
-  k_fast_tma<M><<<c->num_sms, kWThreads, tma_smem, c->stream>>>(src, cnt, p0, k, bp.box[k], st,  \
-                                                                 lp, bd, nside, (int32_t)npix, o, qs)
-        if (plan.mode == kModeDense) { UFC_LAUNCH_TMA(kModeDense); }
-        else if (plan.mode == kModeDirect) { UFC_LAUNCH_TMA(kModeDirect); }
-        else { UFC_LAUNCH_TMA(kModeKeys); }
+  k_fast_tma<M, I><<<c->num_sms, kWThreads, tma_smem, c->stream>>>(                              \
+      src, cnt, p0, k, bp.box[k], st, lp, bd, nside, (int32_t)npix, o, qs)
+        if (plan.mode == kModeDense) {
+          if (images) { UFC_LAUNCH_TMA(kModeDense, true); } else { UFC_LAUNCH_TMA(kModeDense, false); }
+        } else if (plan.mode == kModeDirect) {
+          if (images) { UFC_LAUNCH_TMA(kModeDirect, true); } else { UFC_LAUNCH_TMA(kModeDirect, false); }
+        } else {
+          if (images) { UFC_LAUNCH_TMA(kModeKeys, true); } else { UFC_LAUNCH_TMA(kModeKeys, false); }
+        }
 #undef UFC_LAUNCH_TMA
       } else {
         const int ssm = plan.mode == kModeDense ? smem : 0;
@@ -1462,6 +1584,11 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
       ProfScope ps_(c, "k_exact");
       k_exact<kModeDense><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
     }
+    if (ovf_words) {
+      ProfScope ps_(c, "k_overflow");
+      k_overflow<kModeDense><<<lgrid, 256, 0, c->stream>>>(bp, nbox, st, nside, (int32_t)npix, o, qs,
+                                                      ovf_words);
+    }
   } else if (plan.mode == kModeDirect) {
     {
       ProfScope ps_(c, "k_refine");
@@ -1471,6 +1598,11 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
       ProfScope ps_(c, "k_exact");
       k_exact<kModeDirect><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
     }
+    if (ovf_words) {
+      ProfScope ps_(c, "k_overflow");
+      k_overflow<kModeDirect><<<lgrid, 256, 0, c->stream>>>(bp, nbox, st, nside, (int32_t)npix, o, qs,
+                                                      ovf_words);
+    }
   } else {
     {
       ProfScope ps_(c, "k_refine");
@@ -1479,6 +1611,11 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     {
       ProfScope ps_(c, "k_exact");
       k_exact<kModeKeys><<<lgrid, 256, 0, c->stream>>>(bp, st, nside, (int32_t)npix, o, qs);
+    }
+    if (ovf_words) {
+      ProfScope ps_(c, "k_overflow");
+      k_overflow<kModeKeys><<<lgrid, 256, 0, c->stream>>>(bp, nbox, st, nside, (int32_t)npix, o, qs,
+                                                      ovf_words);
     }
   }
   UFC_CUDA(c, cudaGetLastError());
@@ -1509,19 +1646,20 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
                                    smemA));
   {
     ProfScope ps_(c, "k_scatter_group");
-    k_scatter_group<<<c->num_sms, kScatThreads, smemA, c->stream>>>(
+    k_scatter_group<<<2 * c->num_sms, kScatThreads, smemA, c->stream>>>(
         o.dense, o.dense_count, o.dense_cap, ng, gcur, grouped);
   }
   {
     ProfScope ps_(c, "k_tiles");
-    k_tiles<<<1, 1024, 0, c->stream>>>(off, nb, ng, tiles, ntiles);
+    k_tiles<<<c->num_sms, kTilesThreads, (size_t)(2 * ng + 2) * 8, c->stream>>>(off, nb, ng, tiles,
+                                                                              ntiles);
   }
   const int smemB = (1 << kGroupBits) * 16 + kScatTile * 3;
   UFC_CUDA(c, cudaFuncSetAttribute(k_scatter_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    smemB));
   {
     ProfScope ps_(c, "k_scatter_bucket");
-    k_scatter_bucket<<<c->num_sms, kScatThreads, smemB, c->stream>>>(grouped, tiles, ntiles,
+    k_scatter_bucket<<<2 * c->num_sms, kScatThreads, smemB, c->stream>>>(grouped, tiles, ntiles,
                                                                       bcur, b16);
   }
   const int smemH = kBlockPix * 4;

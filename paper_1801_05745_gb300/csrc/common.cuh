@@ -79,6 +79,7 @@ struct BinCounters {
   unsigned long long ntiles;    // tiles of the second scatter pass
   unsigned long long timeouts;  // bounded device waits that ran out
   unsigned long long range;     // adjoint inputs outside the fixed-point range
+  unsigned long long ovf;       // images marked for the exact pass (queue 1 was full)
 };
 
 // Queue entry of an undecided particle image: box (4 bits), image (13 bits),

@@ -58,6 +58,7 @@ enum Slot {
   kSlotMisc,
   kSlotStage,      // device copy of host particle positions (ufc_bin_host)
   kSlotSht,        // ring transforms, Legendre seeds, partial a_lm (ufc_map2alm)
+  kSlotOvf,        // one bit per particle image: left undecided when queue 1 was full
 };
 
 inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {

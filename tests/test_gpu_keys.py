@@ -83,3 +83,37 @@ def test_keys_observer_not_representable_in_fp32(orc):
     got = ctx.keys(to_dev(xyz), ba, chi, 128).cpu().numpy()
     ref = orc.keys(xyz, bo, chi, 128)
     assert np.array_equal(got, ref.astype(np.int32))
+
+
+@pytest.mark.parametrize("path", ["keys", "dense", "direct"])
+def test_refine_queue_overflow(orc, path):
+    """More undecided particles than the refine stage's queue holds (about
+    1/16 of the particles plus one chunk per warp): the overflow takes the
+    FP64 procedure inside the fast stage.  25k particles on pixel and shell
+    edges, repeated 1000 times: keys and counts equal the oracle's."""
+    api, ctx = api_ctx()
+    nside, L = 1024, 6400.0
+    obs = np.array([3200.0, 3200.0, 3200.0])
+    chi = orc.chi_edges(0.3, 0.7, 1, np.linspace(0.1, 0.9, 9))
+    d = boundary_points(orc, nside, 20_000, chi[0], chi[-1], seed=77)
+    rng = np.random.default_rng(78)
+    u = rng.normal(size=(5000, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    d = np.concatenate([d, u * chi[rng.integers(0, len(chi), 5000)][:, None]])
+    uniq = (d + obs).astype(np.float32)
+    reps = 1000
+    xyz = np.tile(uniq, (reps, 1))
+    n = len(xyz)
+    ba, bo = both_boxes(api, orc, L, obs, n, 0, 8)
+    ref = orc.keys(uniq, bo, chi, nside)
+    if path == "keys":
+        got = ctx.keys(to_dev(xyz), ba, chi, nside).cpu().numpy()
+        bad = np.nonzero(got != np.tile(ref, reps))[0]
+        assert len(bad) == 0, (len(bad), bad[:5])
+    else:
+        counts = ctx.bin([to_dev(xyz)], [ba], chi, nside, path=path).cpu().numpy().ravel()
+        exp = np.bincount(ref[ref >= 0], minlength=counts.size).astype(np.int64) * reps
+        assert np.array_equal(counts.astype(np.int64), exp)
+    info = ctx.bin_info()
+    cap1 = max(1 << 20, n // 16)
+    assert info["refined"] > cap1 // 2, info          # the queue was (nearly) full
