@@ -35,9 +35,9 @@ UNIT = "Gparticles/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per particle of the fast stage, from an ncu
 # capture of k_fast_tma on two boxes of 512^3 particles at Nside 512 (two
-# launches of 134.2M particles: 1.869 and 1.838 GB); scaled to a launch by
+# launches of 134.2M particles: 1.868 and 1.838 GB); scaled to a launch by
 # its particle count.  Retake it whenever k_fast_tma changes.
-FAST_TRAFFIC_PER_PARTICLE = (1.611092e9 + 257.53856e6 + 1.611049e9 + 227.421696e6) / 2 / 134217728
+FAST_TRAFFIC_PER_PARTICLE = (1.611103e9 + 257.357312e6 + 1.610991e9 + 227.349504e6) / 2 / 134217728
 
 
 def hbm_peak():
