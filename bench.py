@@ -155,12 +155,31 @@ def cpu_baseline(w, parts_host, counts_host, A, C, dAC, seconds_budget=20.0):
     oracle.kappa_stat_grads(np.ascontiguousarray(sub), nside_sub, w.omega_m, w.h, 1, boxes, z, src)
     t_grad = (time.perf_counter() - t0) * 16
     t_step = per_particle * n_total + t_kappa + t_stats + t_grad
+    # the oracle's OpenMP binning (all host cores, atomic increments) on the
+    # same sample, the rest of the step as above
+    counts_omp = np.zeros((w.nshell, 12 * w.nside ** 2), dtype=np.int32)
+    t0 = time.perf_counter()
+    threads = 1
+    for k in range(2):
+        _, _, threads = oracle.bin_counts_omp(parts_host[k][:m], boxes[k], chi, w.nside, counts_omp)
+    per_particle_omp = (time.perf_counter() - t0) / done
+    del counts_omp
+    t_step_omp = per_particle_omp * n_total + t_kappa + t_stats + t_grad
     return {
         "value": n_total / t_step / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
         "sample": (f"oracle keys of {done} particles ({per_particle * 1e9:.0f} ns each, scaled to "
                    f"{n_total}); one full Nside {w.nside} kappa map {t_kappa:.2f} s; moments+PDF "
                    f"{t_stats:.2f} s; complex-step gradient on 1/16 of the pixels x16 = "
                    f"{t_grad:.1f} s; estimated {t_step:.1f} s per step, single thread"),
+        "all_cores": {
+            "value": n_total / t_step_omp / 1e9, "unit": UNIT, "cores": threads,
+            "kind": "oracle (OpenMP binning)",
+            "sample": (f"oracle OpenMP binning of the same {done} particles on {threads} threads "
+                       f"({per_particle_omp * 1e9:.1f} ns each, scaled to {n_total}); kappa map, "
+                       f"moments, PDF and gradient single-threaded as above; estimated "
+                       f"{t_step_omp:.1f} s per step"),
+            "binning_gparticles_per_s": 1e-9 / per_particle_omp,
+        },
     }
 
 

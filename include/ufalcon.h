@@ -372,6 +372,11 @@ ufc_status ufc_map_stats(ufc_ctx *ctx, const float *map_dev, int32_t nside,
  * counts_dev (scratch, [nshell][npix]), writes moments_dev[r][10],
  * pdf_dev[r][nbins+3] and stats_dev[r][6 + nbins] (ufc_stats_vector), and
  * finally adds all nreal vectors to the Welford state state_dev in order.
+ * Count maps of up to 64 MB run on up to 8 concurrent lanes: realisation r
+ * on lane r mod 8, lane 0 being this context with counts_dev and kappa_dev,
+ * the others extra contexts owned by this one, each with its own count and
+ * kappa maps, workspace and stream (forked from and joined back to the
+ * context stream by events); results do not depend on the lanes.
  * The workspace is grown once up front; with UFC_BATCH_GRAPH the per-
  * realisation work is captured into one CUDA graph and launched once (the
  * context stream must not be capturing already; on the legacy default

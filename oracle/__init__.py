@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-std=c11", "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+           "-fopenmp", "-std=c11", "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -94,6 +94,7 @@ def _declare(L):
         "or_pix2ang_ring": (None, [I64, I64, P, P]),
         "or_keys": (None, [P, I64, P, P, I32, I64, P]),
         "or_bin": (I64, [P, I64, P, P, I32, I64, P]),
+        "or_bin_omp": (I64, [P, I64, P, P, I32, I64, P, P]),
         "or_snapshot_assign": (None, [P, I32, P, I32, P]),
         "or_bin_snapshots": (I64, [P, P, P, P, P, I32, I64, P]),
         "or_comoving_distance": (D, [D, D, ctypes.c_int, D]),
@@ -185,6 +186,21 @@ def bin_counts(xyz: np.ndarray, box: Box, chi_edges: np.ndarray, nside: int,
     assert counts.dtype == np.int32 and counts.flags.c_contiguous
     inv = lib().or_bin(_ptr(xyz), len(xyz), ctypes.byref(box), _ptr(chi), nshell, nside, _ptr(counts))
     return counts, int(inv)
+
+
+def bin_counts_omp(xyz: np.ndarray, box: Box, chi_edges: np.ndarray, nside: int,
+                   counts: np.ndarray | None = None):
+    """bin_counts on all host cores (OpenMP); returns (counts, n_invalid, threads)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+    nshell = len(chi) - 1
+    if counts is None:
+        counts = np.zeros((nshell, nside2npix(nside)), dtype=np.int32)
+    assert counts.dtype == np.int32 and counts.flags.c_contiguous
+    th = np.zeros(1, dtype=np.int32)
+    inv = lib().or_bin_omp(_ptr(xyz), len(xyz), ctypes.byref(box), _ptr(chi), nshell, nside,
+                           _ptr(counts), _ptr(th))
+    return counts, int(inv), int(th[0])
 
 
 def snapshot_assign(z_edges, z_snap) -> np.ndarray:

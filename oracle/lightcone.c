@@ -12,6 +12,7 @@
  * with a non-finite coordinate, or an image with r == 0, is invalid.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include "oracle.h"
 
@@ -105,5 +106,48 @@ int64_t or_bin_snapshots(const float *const *xyz, const int64_t *n, const or_box
     box.shell_hi = b + 1;
     invalid += or_bin(xyz[s], n[s], &box, chi_edges, nshell, nside, counts);
   }
+  return invalid;
+}
+
+/*
+ * The same binning spread over the host's cores with OpenMP (used to time
+ * the CPU baseline on all cores): particles are independent, each adds its
+ * images to the shared count maps with atomic increments, so the counts
+ * equal or_bin's.  Returns the invalid particles; *threads_out is the
+ * number of threads that ran.
+ */
+int64_t or_bin_omp(const float *xyz, int64_t n, const or_box *box,
+                   const double *chi_edges, int32_t nshell, int64_t nside,
+                   int32_t *counts, int32_t *threads_out) {
+  (void)nshell;
+  const int R = box->replicate;
+  int64_t invalid = 0;
+  int threads = 1;
+#pragma omp parallel reduction(+ : invalid)
+  {
+#pragma omp single
+    threads = omp_get_num_threads();
+#pragma omp for schedule(static)
+    for (int64_t p = 0; p < n; ++p) {
+      const float x = xyz[3 * p], y = xyz[3 * p + 1], z = xyz[3 * p + 2];
+      if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { ++invalid; continue; }
+      for (int i = -R; i <= R; ++i)
+        for (int j = -R; j <= R; ++j)
+          for (int k = -R; k <= R; ++k) {
+            const double sx = (double)i * box->L - box->obs[0];
+            const double sy = (double)j * box->L - box->obs[1];
+            const double sz = (double)k * box->L - box->obs[2];
+            const int64_t key = key_of((double)x + sx, (double)y + sy, (double)z + sz,
+                                       box, chi_edges, nside);
+            if (key >= 0) {
+#pragma omp atomic
+              counts[key] += 1;
+            } else if (key == -2) {
+              ++invalid;
+            }
+          }
+    }
+  }
+  if (threads_out) *threads_out = threads;
   return invalid;
 }

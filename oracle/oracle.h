@@ -60,6 +60,10 @@ void or_keys(const float *xyz, int64_t n, const or_box *box,
 int64_t or_bin(const float *xyz, int64_t n, const or_box *box,
                const double *chi_edges, int32_t nshell, int64_t nside,
                int32_t *counts);
+/* or_bin on all host cores (OpenMP, atomic increments): same counts. */
+int64_t or_bin_omp(const float *xyz, int64_t n, const or_box *box,
+                   const double *chi_edges, int32_t nshell, int64_t nside,
+                   int32_t *counts, int32_t *threads_out);
 /* Snapshot mode: the snapshot of each shell (last one at or below the
  * shell's lower-edge redshift, -1 if none), and the count maps with shell b
  * taken from snapshot snap_of_shell[b] (added to counts). */

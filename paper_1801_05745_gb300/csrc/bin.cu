@@ -1328,7 +1328,8 @@ ufc_status reserve_bin_workspace(ufc_ctx* c, int64_t fast_launches, int64_t tota
                                  int nshell, int nside) {
   const int64_t npix = 12ll * nside * nside;
   const BinSizes z = bin_sizes(c, fast_launches, total_img, nshell, nside);
-  if (!ws_get(c, kSlotQueue1, z.cap1 * 8) || !ws_get(c, kSlotQueue2, z.cap2 * 8))
+  if (!ws_get(c, kSlotQueue1, z.cap1 * 8) || !ws_get(c, kSlotQueue2, z.cap2 * 8) ||
+      !ws_get(c, kSlotOvf, (size_t)((total_img + 31) / 32) * 4))   // overflow bits (bound)
     return UFC_ERR_ALLOC;
   if (nside >= 64 && npix * nshell * 4 > (32ll << 20) && z.nb < (1ll << 17)) {
     if (!ws_get(c, kSlotDense, z.dense_cap * 4) || !ws_get(c, kSlotGrouped, z.dense_cap * 4) ||

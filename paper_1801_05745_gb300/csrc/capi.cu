@@ -58,10 +58,13 @@ void* ws_get(ufc_ctx* c, int s, size_t bytes) {
     cudaStreamSynchronize(c->stream);
     if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
     if (c->aux_stream) cudaStreamSynchronize(c->aux_stream);
-    if (c->graph_exec) {                  // the cached graph refers to this buffer
-      cudaGraphExecDestroy(c->graph_exec);
-      c->graph_exec = nullptr;
-      c->graph_key.clear();
+    ufc_ctx* gc = c->owner ? c->owner : c;   // the context whose graph may use this buffer
+    if (gc->graph_exec) {                 // the cached graph refers to this buffer
+      cudaStreamSynchronize(gc->stream);
+      if (gc->aux_stream) cudaStreamSynchronize(gc->aux_stream);
+      cudaGraphExecDestroy(gc->graph_exec);
+      gc->graph_exec = nullptr;
+      gc->graph_key.clear();
     }
     cudaFree(c->buf[s]);
     c->buf[s] = nullptr;
@@ -168,6 +171,13 @@ ufc_status ufc_destroy(ufc_ctx* c) {
   for (cudaEvent_t e : c->aux_ev)
     if (e) cudaEventDestroy(e);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  for (int k = 0; k < ufc_ctx::kMaxLanes; ++k) {
+    if (c->lane_stream[k]) cudaStreamSynchronize(c->lane_stream[k]);
+    if (c->lanes[k]) { c->lanes[k]->stream = c->lane_stream[k]; ufc_destroy(c->lanes[k]); }
+    if (c->lane_stream[k]) cudaStreamDestroy(c->lane_stream[k]);
+  }
+  for (cudaEvent_t e : c->lane_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return UFC_OK;
 }
@@ -555,6 +565,34 @@ ufc_status ufc_stats_vector(ufc_ctx* c, const double* moments_dev, const int64_t
   return run_stats_vector(c, moments_dev, pdf_dev, nbins, v_dev);
 }
 
+// Lane k of c (k >= 1) for ufc_batched_stats: a context on c's device with
+// its own workspace, counters and stream.
+static ufc_ctx* lane_of(ufc_ctx* c, int k) {
+  if (!c->lane_stream[k] &&
+      cudaStreamCreateWithFlags(&c->lane_stream[k], cudaStreamNonBlocking) != cudaSuccess)
+    return nullptr;
+  if (!c->lanes[k]) {
+    ufc_ctx* l = new (std::nothrow) ufc_ctx();
+    if (!l) return nullptr;
+    l->device = c->device;
+    l->num_sms = c->num_sms;
+    l->smem_optin = c->smem_optin;
+    l->owner = c;
+    if (cudaMalloc(&l->counters, sizeof(BinCounters)) != cudaSuccess) {
+      cudaGetLastError();
+      delete l;
+      return nullptr;
+    }
+    cudaMemsetAsync(l->counters, 0, sizeof(BinCounters), c->lane_stream[k]);
+    c->lanes[k] = l;
+  }
+  c->lanes[k]->stream = c->lane_stream[k];
+  return c->lanes[k];
+}
+
+// Count maps up to this size run ufc_batched_stats on concurrent lanes.
+constexpr size_t kLaneMapMax = 64ull << 20;
+
 ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const float* const* xyz,
                              const int64_t* n, const ufc_box* boxes, const double* chi,
                              int32_t nshell, int32_t nside, const double* A, const double* C,
@@ -585,6 +623,32 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
   // per-block partial sums of the kappa and moment kernels
   if (!ws_get(c, kSlotPartials, (size_t)16 * c->num_sms * 8)) return UFC_ERR_ALLOC;
   const int d = 6 + nbins;
+  // small maps: realisation r runs on lane r mod nlane, the lanes concurrently
+  // (lane 0 is this context with the caller's scratch maps; the others have
+  // their own count and kappa maps, workspace and stream)
+  const int64_t npix = 12ll * nside * nside;
+  const size_t map_bytes = (size_t)nshell * npix * 4;
+  // (and a bound of 8 GB on the lanes' binning workspace, ~16 B per image)
+  const int64_t ws_lanes = std::max<int64_t>(1, (8ll << 30) / std::max<int64_t>(1, 16 * max_img));
+  const int nlane = map_bytes <= kLaneMapMax
+                        ? (int)std::min<int64_t>({ufc_ctx::kMaxLanes, nreal, ws_lanes})
+                        : 1;
+  ufc_ctx* lane[ufc_ctx::kMaxLanes] = {c};
+  int32_t* lane_counts[ufc_ctx::kMaxLanes] = {counts};
+  float* lane_kappa[ufc_ctx::kMaxLanes] = {kappa};
+  for (int k = 1; k < nlane; ++k) {
+    lane[k] = lane_of(c, k);
+    if (!lane[k]) return set_err(c, UFC_ERR_ALLOC, "could not create a batch lane");
+    s = reserve_bin_workspace(lane[k], nbox, max_img, nshell, nside);
+    if (s) return set_err(c, s, "%s", lane[k]->err.c_str());
+    char* m = (char*)ws_get(lane[k], kSlotLaneMap, map_bytes + (size_t)npix * 4 + 256);
+    if (!m || !ws_get(lane[k], kSlotPartials, (size_t)16 * c->num_sms * 8))
+      return set_err(c, UFC_ERR_ALLOC, "%s", lane[k]->err.c_str());
+    lane_counts[k] = reinterpret_cast<int32_t*>(m);
+    lane_kappa[k] = reinterpret_cast<float*>(m + ((map_bytes + 255) & ~(size_t)255));
+  }
+  for (int k = 0; k <= nlane; ++k)
+    if (!c->lane_ev[k]) UFC_CUDA(c, cudaEventCreateWithFlags(&c->lane_ev[k], cudaEventDisableTiming));
   const bool graph = (flags & UFC_BATCH_GRAPH) != 0;
   const bool prof = c->prof;
   cudaGraph_t g = nullptr;
@@ -641,14 +705,29 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
       return set_err(c, UFC_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
     }
   }
+  // fork: the lanes start after the work already on this context's stream
+  if (nlane > 1) {
+    UFC_CUDA(c, cudaEventRecord(c->lane_ev[0], c->stream));
+    for (int k = 1; k < nlane; ++k) UFC_CUDA(c, cudaStreamWaitEvent(lane[k]->stream, c->lane_ev[0], 0));
+  }
   for (int r = 0; r < nreal && !s; ++r) {
-    s = run_keys_pipeline(c, 1, xyz + r * nbox, n + r * nbox, boxes + r * nbox, nbox, chi, nshell,
-                          nside, 0, counts, nullptr, nullptr);
+    ufc_ctx* lc = lane[r % nlane];
+    int32_t* cnt = lane_counts[r % nlane];
+    float* kap = lane_kappa[r % nlane];
+    s = run_keys_pipeline(lc, 1, xyz + r * nbox, n + r * nbox, boxes + r * nbox, nbox, chi, nshell,
+                          nside, 0, cnt, nullptr, nullptr);
     if (!s)
-      s = run_kappa_stats(c, counts, nshell, nside, A + (size_t)r * nshell, C[r], lo, hi, nbins,
-                          kappa, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r);
-    if (!s) s = run_stats_vector(c, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r, nbins,
+      s = run_kappa_stats(lc, cnt, nshell, nside, A + (size_t)r * nshell, C[r], lo, hi, nbins,
+                          kap, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r);
+    if (!s) s = run_stats_vector(lc, moments + 10 * (size_t)r, pdf + (size_t)(nbins + 3) * r, nbins,
                                  stats + (size_t)d * r);
+    if (s && lc != c) set_err(c, s, "%s", lc->err.c_str());
+  }
+  // join: the Welford update (in realisation order) waits for every lane
+  for (int k = 1; k < nlane; ++k) {
+    const cudaError_t e = cudaEventRecord(c->lane_ev[k], lane[k]->stream);
+    if (e == cudaSuccess) cudaStreamWaitEvent(c->stream, c->lane_ev[k], 0);
+    else if (!s) s = set_err(c, UFC_ERR_CUDA, "lane join: %s", cudaGetErrorString(e));
   }
   if (!s) s = run_welford_update(c, stats, nreal, d, state);
   if (graph) {

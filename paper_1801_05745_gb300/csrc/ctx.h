@@ -39,6 +39,15 @@ struct ufc_ctx {
   // workspace buffer it refers to is reallocated
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<unsigned char> graph_key;
+  // ufc_batched_stats on small maps: extra contexts ("lanes") with their
+  // own workspace, counters and stream, each binning a share of the
+  // realisations concurrently; a lane's owner drops its graph whenever the
+  // lane's workspace is reallocated
+  static constexpr int kMaxLanes = 8;
+  ufc_ctx* lanes[kMaxLanes] = {};
+  cudaStream_t lane_stream[kMaxLanes] = {};
+  cudaEvent_t lane_ev[kMaxLanes + 1] = {};
+  ufc_ctx* owner = nullptr;
 };
 
 namespace ufc {
@@ -59,6 +68,7 @@ enum Slot {
   kSlotStage,      // device copy of host particle positions (ufc_bin_host)
   kSlotSht,        // ring transforms, Legendre seeds, partial a_lm (ufc_map2alm)
   kSlotOvf,        // one bit per particle image: left undecided when queue 1 was full
+  kSlotLaneMap,    // a lane's count map and kappa map (ufc_batched_stats)
 };
 
 inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {

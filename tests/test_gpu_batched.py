@@ -34,13 +34,16 @@ def _realisations(orc, api, nreal, nside, nshell, nbase):
     return z, chi, xs, bxs, np.array(As), np.array(Cs)
 
 
-@pytest.mark.parametrize("graph,side_stream", [(False, True), (True, True), (True, False)])
-def test_batched_equals_serial(orc, graph, side_stream):
+@pytest.mark.parametrize("graph,side_stream,nreal", [(False, True, 5), (True, True, 5),
+                                                    (True, False, 5), (True, True, 19),
+                                                    (False, False, 19)])
+def test_batched_equals_serial(orc, graph, side_stream, nreal):
     """Batched call = the same maps one at a time, bit for bit; with the
     graph on a side stream and on the legacy default stream (captured on
-    the context's own stream, joined by events)."""
+    the context's own stream, joined by events).  Small maps run on up to 8
+    concurrent lanes: 19 realisations use every lane more than once."""
     api, ctx = api_ctx()
-    nreal, nside, nshell, nb = 5, 64, 12, 100_000
+    nside, nshell, nb = 64, 12, 100_000
     z, chi, xs, bxs, A, C = _realisations(orc, api, nreal, nside, nshell, nb)
     nbins, lo, hi = 40, -0.05, 0.2
     d = 6 + nbins

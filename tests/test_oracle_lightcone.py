@@ -82,3 +82,19 @@ def test_half_open_edges_and_invalid(orc):
     assert k[7] // npix == 1 and k[7] % npix == 5    # (0, 2.5, 0): phi = pi/2 -> pixel 5
     c, inv = orc.bin_counts(xyz, box, chi, 1)
     assert inv == 3 and c.sum() == 3
+
+
+def test_openmp_binning_equals_serial(orc):
+    """The oracle's all-cores binning (OpenMP, atomic increments) gives the
+    serial oracle's counts and invalid count, with and without periodic
+    images, non-finite particles included."""
+    from paper_1801_05745_gb300 import synth
+    x = synth.particles_numpy(120_000, 2000.0, 5.0, synth.seed_for(13, 0, 0))
+    x[::997] = np.nan
+    chi = orc.chi_edges(0.3, 0.7, 1, np.linspace(0.05, 0.35, 13))
+    for R, L in ((0, 2000.0), (1, 500.0)):
+        xx = (x % L).astype(np.float32) if R else x
+        b = orc.make_box(L, [L / 2] * 3, len(xx), 0, 12, R)
+        ref, inv = orc.bin_counts(xx, b, chi, 32)
+        got, inv2, threads = orc.bin_counts_omp(xx, b, chi, 32)
+        assert np.array_equal(got, ref) and inv == inv2 and threads >= 1
