@@ -523,6 +523,39 @@ def main():
         "clocks": clk,
     }
 
+    # end to end: particles from pinned host memory through the C ABI each
+    # step (ufc_bin_host copies them in chunks, overlapped with the binning),
+    # moments and PDF back to pinned host memory
+    if not args.no_e2e:
+        host = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True) for p in parts]
+        for h_, p_ in zip(host, parts):
+            h_.copy_(p_)
+        out_h = torch.empty(10 + w.pdf_bins + 3, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        ke = max(2, min(args.steps, 4))
+
+        def e2e_step():
+            mom, pdf, grad = step(host)
+            out_h[:10].copy_(mom, non_blocking=True)
+            out_h[10:].copy_(pdf.to(torch.float64), non_blocking=True)
+        e2e_step()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_e = e0.elapsed_time(e1) / ke
+        if dist:
+            t = torch.tensor([ms_e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e = float(t.item())
+        line["e2e"] = {"value": world * n_total / (ms_e * 1e-3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in parts)),
+                       "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8 + w.nshell * 8),
+                       "ms_per_step": ms_e}
+        del host
+
     if not args.no_cl:
         # full-sky C_l of the step's kappa map (Sec. 3.2): a_lm, C_l
         # and band powers at lmax = 3 nside - 1
@@ -577,39 +610,6 @@ def main():
 
     if not args.no_snapshots:
         line["snapshots"] = snapshot_leg(ctx, api, synth, dev, w, z, chi)
-
-    # end to end: particles from pinned host memory through the C ABI each
-    # step (ufc_bin_host copies them in chunks, overlapped with the binning),
-    # moments and PDF back to pinned host memory
-    if not args.no_e2e:
-        host = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True) for p in parts]
-        for h_, p_ in zip(host, parts):
-            h_.copy_(p_)
-        out_h = torch.empty(10 + w.pdf_bins + 3, dtype=torch.float64, pin_memory=True)
-        torch.cuda.synchronize()
-        ke = max(2, min(args.steps, 4))
-
-        def e2e_step():
-            mom, pdf, grad = step(host)
-            out_h[:10].copy_(mom, non_blocking=True)
-            out_h[10:].copy_(pdf.to(torch.float64), non_blocking=True)
-        e2e_step()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(ke):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_e = e0.elapsed_time(e1) / ke
-        if dist:
-            t = torch.tensor([ms_e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e = float(t.item())
-        line["e2e"] = {"value": world * n_total / (ms_e * 1e-3) / 1e9, "unit": UNIT,
-                       "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in parts)),
-                       "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8 + w.nshell * 8),
-                       "ms_per_step": ms_e}
-        del host
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         parts_h = [p[: 1 << 24].cpu().numpy() for p in parts]

@@ -215,134 +215,58 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
   if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
 }
 
-// --------------------------------------------- adjoint, two passes -----
-// Pass 1 (k_adj_pre): e_p = sum_b A_b n_bp - C unrounded (double-float, the
-// shells in order), per block the maxima of |e|, e^2, |g| and the sums
-// P1..P3 = sum_p e_p^k, Q = sum_p g_p.
-// Pass 2 (k_adj_main): one quantisation scale per quantity from the global
-// maxima; e_p is recomputed exactly as in pass 1 and split into two integers
-// (quant2); warp w owns shells w, w + 32, w + 64 and each lane a column of
-// the tile's pixels, accumulating q n in 64-bit integers across tiles.  The tile's counts are read a second time from L2.  A bound
-// on the accumulated magnitudes (pixels per lane x tile maximum count x 2^22
-// per tile) triggers a flush into the block's 128-bit fixed-point rows before
-// any 64-bit sum could overflow.
-constexpr int kAdjThreads = 1024;         // pass 2 block: 32 warps, 4096-pixel tiles
-constexpr int kAdjSpw = 3;                // shells per warp in pass 2 (nshell <= 96)
-
-__global__ void __launch_bounds__(kKV)
-k_adj_pre(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
-          float* __restrict__ maxpart, double* __restrict__ sumpart) {
-  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
-  __shared__ double red[kKV / 32];
-  __shared__ float mred[3][kKV / 32];
-  const int S = cf.nshell;
-  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
-  __syncthreads();
-  const int ng = cf.npix >> 2;
-  const int4* c4 = reinterpret_cast<const int4*>(counts);
-  const f2 mc{-cf.ch, -cf.cl};
-  f2 p1{0.f, 0.f}, p2{0.f, 0.f}, p3{0.f, 0.f}, qg{0.f, 0.f};
-  float m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  for (int gi = blockIdx.x * kKV + threadIdx.x; gi < ng; gi += gridDim.x * kKV) {
-    f2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 8
-    for (int b = 0; b < S; ++b) {
-      const int4 n = __ldcs(c4 + (size_t)b * ng + gi);
-      const float h = ah_s[b], l = al_s[b];
-      f2_mac(a[0], h, l, float(n.x));
-      f2_mac(a[1], h, l, float(n.y));
-      f2_mac(a[2], h, l, float(n.z));
-      f2_mac(a[3], h, l, float(n.w));
-    }
-    const float4 gv = g ? reinterpret_cast<const float4*>(g)[gi] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float gs[4] = {gv.x, gv.y, gv.z, gv.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const f2 e = f2_add(f2_norm(a[i].h, a[i].l), mc);
-      const f2 e2 = f2_mul(e, e);
-      p1 = f2_add(p1, e);
-      p2 = f2_add(p2, e2);
-      p3 = f2_add(p3, f2_mul(e2, e));
-      qg = f2_add(qg, f2{gs[i], 0.f});
-      m1 = fmaxf(m1, fabsf(e.h));
-      m2 = fmaxf(m2, fabsf(e2.h));
-      m3 = fmaxf(m3, fabsf(gs[i]));
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    m1 = fmaxf(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
-    m2 = fmaxf(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
-    m3 = fmaxf(m3, __shfl_xor_sync(0xFFFFFFFFu, m3, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    mred[0][threadIdx.x >> 5] = m1;
-    mred[1][threadIdx.x >> 5] = m2;
-    mred[2][threadIdx.x >> 5] = m3;
-  }
-  const double v1 = block_sum_d<kKV>(f2_to_d(p1), red);
-  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 0] = v1;
-  const double v2 = block_sum_d<kKV>(f2_to_d(p2), red);
-  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 1] = v2;
-  const double v3 = block_sum_d<kKV>(f2_to_d(p3), red);
-  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 2] = v3;
-  const double v4 = block_sum_d<kKV>(f2_to_d(qg), red);
-  if (threadIdx.x == 0) {
-    sumpart[4 * blockIdx.x + 3] = v4;
-    float M[3] = {0.f, 0.f, 0.f};
-    for (int w = 0; w < kKV / 32; ++w)
-      for (int j = 0; j < 3; ++j) M[j] = fmaxf(M[j], mred[j][w]);
-    for (int j = 0; j < 3; ++j) maxpart[3 * blockIdx.x + j] = M[j];
-  }
-}
+// --------------------------------------------------------- adjoint -----
+// One pass (k_adj_main) over 4096-pixel tiles, one block per SM.  Phase 1:
+// e_p = sum_b A_b n_bp - C unrounded (double-float, the shells in order, as
+// the forward pass), e_p^2, the power sums P1..P3 = sum_p e_p^k and
+// Q = sum_p g_p, and the tile's maxima of |e|, e^2, |g|.  Each quantity is
+// quantised (quant2: two integers, 43 bits relative to the scale) with a
+// power-of-two scale from the block's running maximum over the tiles it has
+// seen; when a tile raises a maximum, the 64-bit accumulators are first
+// flushed at the old scale into the block's 128-bit fixed-point rows, which
+// take every flush at its own scale exactly.  Every pixel is therefore
+// quantised at least as finely as a single scale from the global maxima
+// would.  Phase 2: warp w owns shells w, w + 32, w + 64 and each lane a
+// column of the tile's pixels, accumulating q n in 64-bit integers (the
+// tile's counts read a second time, mostly from L2).  A bound on the
+// accumulated magnitudes (pixels per lane x tile maximum count x 2^22 per
+// tile) triggers a flush before any 64-bit sum could overflow.
+constexpr int kAdjThreads = 1024;         // 32 warps, 4096-pixel tiles
+constexpr int kAdjSpw = 3;                // shells per warp in phase 2 (nshell <= 96)
 
 template <bool USE_G>
 __global__ void __launch_bounds__(kAdjThreads, 1)
 k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
-           const float* __restrict__ maxpart, int npre, double* __restrict__ rows_out,
+           double* __restrict__ rows_out, double* __restrict__ sumpart,
            unsigned long long* range_flag) {
   extern __shared__ __align__(16) uint8_t adj_sm[];
-  constexpr int T = kAdjThreads, NW = T / 32, TP = 4 * T;   // TP pixels per tile
-  int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP]
-  AdjRow* rows = reinterpret_cast<AdjRow*>(adj_sm + 24 * TP);  // [nshell]
+  constexpr int T = kAdjThreads, NW = T / 32, TP = 4 * T;
+  int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP] quantised e, e^2, g
+  float* ef_s = reinterpret_cast<float*>(adj_sm);            // the same memory: e, e^2 as floats
+  float* ps_s = reinterpret_cast<float*>(adj_sm + 24 * TP);   // [8][T] this thread's power sums
+  AdjRow* rows = reinterpret_cast<AdjRow*>(adj_sm + 24 * TP + 32 * T);  // [nshell]
   __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
   __shared__ float mred[3][NW];
   __shared__ int nred[NW];
+  __shared__ double red[NW];
   const int S = cf.nshell, npix = cf.npix, ng = npix >> 2;
   const int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
   for (int i = threadIdx.x; i < S; i += T) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; rows[i] = AdjRow{}; }
-  // global maxima of pass 1
-  float m1 = 0.f, m2 = 0.f, m3 = 0.f;
-  for (int i = threadIdx.x; i < npre; i += T) {
-    m1 = fmaxf(m1, maxpart[3 * i]);
-    m2 = fmaxf(m2, maxpart[3 * i + 1]);
-    m3 = fmaxf(m3, maxpart[3 * i + 2]);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    m1 = fmaxf(m1, __shfl_xor_sync(0xFFFFFFFFu, m1, o));
-    m2 = fmaxf(m2, __shfl_xor_sync(0xFFFFFFFFu, m2, o));
-    m3 = fmaxf(m3, __shfl_xor_sync(0xFFFFFFFFu, m3, o));
-  }
-  if (ln == 0) { mred[0][w] = m1; mred[1][w] = m2; mred[2][w] = m3; }
-  __syncthreads();
-  float M1 = 0.f, M2 = 0.f, M3 = 0.f;
-  for (int i = 0; i < NW; ++i) {
-    M1 = fmaxf(M1, mred[0][i]);
-    M2 = fmaxf(M2, mred[1][i]);
-    M3 = fmaxf(M3, mred[2][i]);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && (M1 >= 16384.0f || M3 >= 16384.0f || M2 >= 268435456.0f))
-    atomicAdd(range_flag, 1ull);
-  const int s1 = M1 > 0.f ? min(120, 21 - ilog2f(M1)) : 0;
-  const int s2 = M2 > 0.f ? min(120, 21 - ilog2f(M2)) : 0;
-  const int s3 = M3 > 0.f ? min(120, 21 - ilog2f(M3)) : 0;
+  // running maxima of |e|, e^2, |g| over this block's tiles, in shared
+  // memory: thread 0 updates them after a barrier that every thread's read
+  // of them for the tile has passed
+  __shared__ float Ms[3];
+  if (threadIdx.x == 0) Ms[0] = Ms[1] = Ms[2] = 0.f;
+  auto scale = [](float M) { return M > 0.f ? min(120, 21 - ilog2f(M)) : 0; };
+  for (int k = 0; k < 8; ++k) ps_s[k * T + threadIdx.x] = 0.f;
+  __syncthreads();                         // ah_s, al_s, rows and Ms before any use
   constexpr int NQ = USE_G ? 6 : 4;
   long long acc[kAdjSpw][NQ + 1];
 #pragma unroll
   for (int k = 0; k < kAdjSpw; ++k)
 #pragma unroll
     for (int j = 0; j <= NQ; ++j) acc[k][j] = 0;
-  // shells of this warp: w, w + NW, w + 2 NW
-  auto flush = [&]() {
+  auto flush = [&](int s1, int s2, int s3) {
 #pragma unroll
     for (int k = 0; k < kAdjSpw; ++k) {
       const int b = w + NW * k;
@@ -368,7 +292,9 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
   const int ntile = (npix + TP - 1) / TP;
   double bound = 0.0;                      // bound on |any 64-bit sum|, uniform
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    // phase 1: e of 4 adjacent pixels per thread, as in pass 1
+    // phase 1: e of 4 adjacent pixels per thread (the shells in order, as in
+    // the forward pass), the power sums and the tile's maxima; e and e^2
+    // wait in shared memory until the tile's scale is known
     const int gi = tile * T + threadIdx.x;   // group of 4 pixels
     const bool have = gi < ng;
     f2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
@@ -388,12 +314,74 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     const float4 gv4 = (USE_G && have) ? reinterpret_cast<const float4*>(g)[gi]
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
     const float gs[4] = {gv4.x, gv4.y, gv4.z, gv4.w};
+    float t1 = 0.f, t2 = 0.f, t3 = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       f2 e = f2_add(f2_norm(a[i].h, a[i].l), mc);
       f2 e2 = f2_mul(e, e);
       if (!have) { e = f2{0.f, 0.f}; e2 = f2{0.f, 0.f}; }
+      t1 = fmaxf(t1, fabsf(e.h));
+      t2 = fmaxf(t2, fabsf(e2.h));
+      t3 = fmaxf(t3, fabsf(gs[i]));
       const int px = 4 * threadIdx.x + i;
+      ef_s[px] = e.h;
+      ef_s[TP + px] = e.l;
+      ef_s[2 * TP + px] = e2.h;
+      ef_s[3 * TP + px] = e2.l;
+    }
+    if (have) {
+      f2 p1{ps_s[threadIdx.x], ps_s[T + threadIdx.x]};
+      f2 p2{ps_s[2 * T + threadIdx.x], ps_s[3 * T + threadIdx.x]};
+      f2 p3{ps_s[4 * T + threadIdx.x], ps_s[5 * T + threadIdx.x]};
+      f2 qg{ps_s[6 * T + threadIdx.x], ps_s[7 * T + threadIdx.x]};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int px = 4 * threadIdx.x + i;
+        const f2 e{ef_s[px], ef_s[TP + px]};
+        const f2 e2{ef_s[2 * TP + px], ef_s[3 * TP + px]};
+        p1 = f2_add(p1, e);
+        p2 = f2_add(p2, e2);
+        p3 = f2_add(p3, f2_mul(e2, e));
+        qg = f2_add(qg, f2{gs[i], 0.f});
+      }
+      ps_s[threadIdx.x] = p1.h; ps_s[T + threadIdx.x] = p1.l;
+      ps_s[2 * T + threadIdx.x] = p2.h; ps_s[3 * T + threadIdx.x] = p2.l;
+      ps_s[4 * T + threadIdx.x] = p3.h; ps_s[5 * T + threadIdx.x] = p3.l;
+      ps_s[6 * T + threadIdx.x] = qg.h; ps_s[7 * T + threadIdx.x] = qg.l;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      nmx = max(nmx, __shfl_xor_sync(0xFFFFFFFFu, nmx, o));
+      t1 = fmaxf(t1, __shfl_xor_sync(0xFFFFFFFFu, t1, o));
+      t2 = fmaxf(t2, __shfl_xor_sync(0xFFFFFFFFu, t2, o));
+      t3 = fmaxf(t3, __shfl_xor_sync(0xFFFFFFFFu, t3, o));
+    }
+    if (ln == 0) { nred[w] = nmx; mred[0][w] = t1; mred[1][w] = t2; mred[2][w] = t3; }
+    __syncthreads();
+    int NMX = 0;
+    float T1 = 0.f, T2 = 0.f, T3 = 0.f;
+    for (int i = 0; i < NW; ++i) {
+      NMX = max(NMX, nred[i]);
+      T1 = fmaxf(T1, mred[0][i]);
+      T2 = fmaxf(T2, mred[1][i]);
+      T3 = fmaxf(T3, mred[2][i]);
+    }
+    const float M1 = Ms[0], M2 = Ms[1], M3 = Ms[2];
+    const bool grow = T1 > M1 || T2 > M2 || T3 > M3;   // (uniform) a coarser scale
+    const double inc = double(TP / 32) * double(NMX) * 4194304.0;   // per lane, this tile
+    if (grow || bound + inc > 2305843009213693952.0) {              // 2^61
+      flush(scale(M1), scale(M2), scale(M3));                       // at the old scale
+      bound = 0.0;
+    }
+    bound += inc;
+    const float N1 = fmaxf(M1, T1), N2 = fmaxf(M2, T2), N3 = fmaxf(M3, T3);
+    if (grow && threadIdx.x == 0 && (N1 >= 16384.0f || N3 >= 16384.0f || N2 >= 268435456.0f))
+      atomicAdd(range_flag, 1ull);
+    const int s1 = scale(N1), s2 = scale(N2), s3 = scale(N3);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int px = 4 * threadIdx.x + i;
+      const f2 e{ef_s[px], ef_s[TP + px]};
+      const f2 e2{ef_s[2 * TP + px], ef_s[3 * TP + px]};
       int h, l;
       quant2(e, s1, h, l);
       q_s[px] = h;
@@ -407,17 +395,8 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
         q_s[5 * TP + px] = l;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) nmx = max(nmx, __shfl_xor_sync(0xFFFFFFFFu, nmx, o));
-    if (ln == 0) nred[w] = nmx;
-    __syncthreads();
-    int NMX = 0;
-    for (int i = 0; i < NW; ++i) NMX = max(NMX, nred[i]);
-    const double inc = double(TP / 32) * double(NMX) * 4194304.0;   // per lane, this tile
-    if (bound + inc > 2305843009213693952.0) {                     // 2^61
-      flush();
-      bound = 0.0;
-    }
-    bound += inc;
+    __syncthreads();                       // q_s complete; every thread has read Ms
+    if (grow && threadIdx.x == 0) { Ms[0] = N1; Ms[1] = N2; Ms[2] = N3; }
     // phase 2: lane ln takes pixels ln, ln + 32, ... of the tile (L2 re-reads)
     const int base = tile * TP;
     const int valid = min(TP, npix - base);
@@ -439,7 +418,8 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     }
     __syncthreads();                       // q_s and nred are rewritten by the next tile
   }
-  flush();
+  __syncthreads();
+  flush(scale(Ms[0]), scale(Ms[1]), scale(Ms[2]));
   __syncthreads();
   double* dst = rows_out + (size_t)blockIdx.x * 4 * S;
   for (int b = threadIdx.x; b < S; b += T) {
@@ -448,6 +428,16 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     dst[4 * b + 2] = USE_G ? i128_to_d(rows[b].s[2], kFrac3) : 0.0;
     dst[4 * b + 3] = (double)rows[b].n;
   }
+  const f2 p1{ps_s[threadIdx.x], ps_s[T + threadIdx.x]}, p2{ps_s[2 * T + threadIdx.x], ps_s[3 * T + threadIdx.x]};
+  const f2 p3{ps_s[4 * T + threadIdx.x], ps_s[5 * T + threadIdx.x]}, qg{ps_s[6 * T + threadIdx.x], ps_s[7 * T + threadIdx.x]};
+  const double v1 = block_sum_d<T>(f2_to_d(p1), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 0] = v1;
+  const double v2 = block_sum_d<T>(f2_to_d(p2), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 1] = v2;
+  const double v3 = block_sum_d<T>(f2_to_d(p3), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 2] = v3;
+  const double v4 = block_sum_d<T>(f2_to_d(qg), red);
+  if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 3] = v4;
 }
 
 // Per-block sums of an FP32 map (double-float per thread), the first pass of
@@ -805,33 +795,29 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
   if (g && (reinterpret_cast<uintptr_t>(g) & 15))
     return set_err(c, UFC_ERR_ARG, "g_dev must be 16-byte aligned");
-  const int grid1 = kappa_fwd_grid(c);                    // pass 1 blocks
-  const int grid2 = c->num_sms;                            // pass 2 blocks
-  const size_t nrow = (size_t)grid2 * 4 * S, nsum = (size_t)grid1 * 4;
-  double* part = (double*)ws_get(c, kSlotPartials, (nrow + nsum) * 8 + (size_t)grid1 * 3 * 4);
+  const int grid2 = c->num_sms;                            // one block per SM
+  const size_t nrow = (size_t)grid2 * 4 * S, nsum = (size_t)grid2 * 4;
+  double* part = (double*)ws_get(c, kSlotPartials, (nrow + nsum) * 8);
   if (!part) return UFC_ERR_ALLOC;
   double* rows = part;
   double* sums = part + nrow;
-  float* maxp = reinterpret_cast<float*>(sums + nsum);
   BinCounters* bc = reinterpret_cast<BinCounters*>(c->counters);
   UFC_CUDA(c, cudaMemsetAsync(&bc->range, 0, sizeof(unsigned long long), c->stream));
-  {
-    ProfScope ps_(c, "k_adj_pre");
-    k_adj_pre<<<grid1, kKV, 0, c->stream>>>(counts, cf, g, maxp, sums);
-  }
-  UFC_CUDA(c, cudaGetLastError());
-  const size_t smem2 = (size_t)24 * 4 * kAdjThreads + (size_t)S * sizeof(AdjRow);
+  // q_s, the threads' power sums, rows
+  const size_t smem2 = (size_t)24 * 4 * kAdjThreads + (size_t)32 * kAdjThreads +
+                       (size_t)S * sizeof(AdjRow);
   {
     ProfScope ps_(c, "k_adj_main");
     if (g) {
-      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem2));
-      k_adj_main<true><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, g, maxp, grid1, rows, &bc->range);
+      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      k_adj_main<true><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, g, rows, sums,
+                                                                  &bc->range);
     } else {
-      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem2));
-      k_adj_main<false><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, nullptr, maxp, grid1, rows,
-                                                         &bc->range);
+      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
+      k_adj_main<false><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, nullptr, rows, sums,
+                                                                   &bc->range);
     }
   }
   UFC_CUDA(c, cudaGetLastError());
@@ -854,7 +840,7 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
       Nb[b] += r[4 * b + 3];
     }
   }
-  for (int i = 0; i < grid1; ++i) {
+  for (int i = 0; i < grid2; ++i) {
     const double* r = hp.data() + nrow + 4 * (size_t)i;
     P1 += r[0];
     P2 += r[1];
