@@ -3,7 +3,8 @@
 // Eq. 10-11 estimates):
 //   a_lm = (4 pi / N_pix) sum_p map_p Y*_lm(theta_p, phi_p),  0 <= m <= l <= lmax,
 //   C_l  = (|a_l0|^2 + 2 sum_{m>0} |a_lm|^2) / (2l + 1),
-// evaluated ring by ring, FP64 throughout:
+// evaluated ring by ring in FP64, with the long sums and recurrences in
+// double-float (pairs of FP32, about 48 bits) on the FP32 pipe:
 //   k_ring_transform : per ring, F_m = sum_j map_j e^{-i m phi_j}
 //                      = e^{-i m phi_0} X_{m mod n}, X the ring's DFT (radix-2
 //                      FFT in shared memory for power-of-two rings, direct
@@ -69,6 +70,58 @@ __host__ __device__ inline Ring ring_geom(int32_t N, int32_t r) {
 
 __device__ __forceinline__ bool is_pow2(int v) { return (v & (v - 1)) == 0; }
 
+// Double-float arithmetic on the FP32 pipe (GB300 runs FP64 at 1/64 of the
+// FP32 rate): a value is h + l with |l| <= ulp(h)/2, about 48 bits.  Every
+// step is a correctly rounded FP32 intrinsic, so that no contraction changes
+// the error-free transformations (Dekker/Knuth two-sum, FMA two-product).
+struct dfl { float h, l; };
+__device__ __forceinline__ dfl df_from_d(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_d(dfl a) { return (double)a.h + (double)a.l; }
+// h + l with |h| >= |l| renormalised (fast two-sum)
+__device__ __forceinline__ dfl df_norm(float h, float l) {
+  const float s = __fadd_rn(h, l);
+  return {s, __fadd_rn(l, __fsub_rn(h, s))};
+}
+// a * b: the exact product of the high parts plus the cross terms
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  return df_norm(p, e);
+}
+// a + b (two-sum of the high parts)
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  return df_norm(s, __fadd_rn(err, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_scale(dfl a, float p2) { return {a.h * p2, a.l * p2}; }  // exact
+// acc += a * b, the low part left unnormalised (renormalised by df_add)
+__device__ __forceinline__ void df_mac(dfl& acc, dfl a, dfl b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float pe = __fmaf_rn(a.h, b.h, -p);
+  const float s = __fadd_rn(acc.h, p);
+  const float bb = __fsub_rn(s, acc.h);
+  const float se = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  const float cross = __fmaf_rn(a.h, b.l, __fmul_rn(a.l, b.h));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(se, __fadd_rn(pe, cross)));
+}
+__device__ __forceinline__ dfl warp_sum_df(dfl v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfl w{__shfl_down_sync(0xFFFFFFFFu, v.h, o), __shfl_down_sync(0xFFFFFFFFu, v.l, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+
 // One block per ring.  Shared memory: twiddles w_k = e^{-2 pi i k / n} and the
 // ring's values (real, or complex for the FFT).
 __global__ void __launch_bounds__(512)
@@ -110,23 +163,36 @@ k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t
       __syncthreads();
     }
   } else {
-    double* xr = reinterpret_cast<double*>(x + n / 2 + 1);   // real input after X[0..n/2]
-    for (int j = threadIdx.x; j < n; j += blockDim.x) xr[j] = (double)map[g.start + j];
+    // direct DFT of the real ring (non power-of-two length), accumulated in
+    // double-float on the FP32 pipe: the map values are FP32, the twiddles
+    // are split into double-float pairs
+    // twiddles converted in place (each thread its own, as computed above)
+    float4* wf = reinterpret_cast<float4*>(w);          // [n] (re.h, re.l, im.h, im.l)
+    float* xr = reinterpret_cast<float*>(x + n / 2 + 1);   // real input after X[0..n/2]
+    for (int j = threadIdx.x; j < n; j += blockDim.x) xr[j] = map[g.start + j];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const double2 t = w[k];
+      const dfl re = df_from_d(t.x), im = df_from_d(t.y);
+      wf[k] = make_float4(re.h, re.l, im.h, im.l);
+    }
     __syncthreads();
     const int kmax = min(n / 2, lmax);       // X_{n-k} = conj X_k for real input
-    double2 acc[4];
     for (int k0 = 0; k0 <= kmax; k0 += 4 * blockDim.x) {
       int kk[4];
+      dfl ar[4], ai[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { kk[u] = k0 + u * blockDim.x + threadIdx.x; acc[u] = make_double2(0.0, 0.0); }
+      for (int u = 0; u < 4; ++u) {
+        kk[u] = k0 + u * blockDim.x + threadIdx.x;
+        ar[u] = ai[u] = dfl{0.f, 0.f};
+      }
       int idx[4] = {0, 0, 0, 0};
       for (int j = 0; j < n; ++j) {
-        const double v = xr[j];
+        const dfl v{xr[j], 0.f};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const double2 tw = w[idx[u]];
-          acc[u].x = fma(v, tw.x, acc[u].x);
-          acc[u].y = fma(v, tw.y, acc[u].y);
+          const float4 tw = wf[idx[u]];
+          df_mac(ar[u], v, dfl{tw.x, tw.y});
+          df_mac(ai[u], v, dfl{tw.z, tw.w});
           idx[u] += kk[u] <= kmax ? kk[u] : 0;
           idx[u] -= idx[u] >= n ? n : 0;
         }
@@ -134,7 +200,10 @@ k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t
       __syncthreads();                        // all reads of xr done before X is written
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (kk[u] <= kmax) x[kk[u]] = acc[u];
+        if (kk[u] <= kmax) {
+          const dfl rr = df_add(ar[u], dfl{0.f, 0.f}), ii = df_add(ai[u], dfl{0.f, 0.f});
+          x[kk[u]] = make_double2(df_to_d(rr), df_to_d(ii));
+        }
       __syncthreads();
     }
   }
@@ -180,15 +249,19 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
 // p = chunk * kLegThreads * kLegPPT + q * kLegThreads + t.  Pair p is the
 // north ring p and the south ring 4N - 2 - p (the equator ring, p = 2N - 1,
 // is its own mirror); lambda_lm(-z) = (-1)^(l+m) lambda_lm(z), so the pair
-// contributes lambda_lm(z_p) (F_north +- F_south).  A thread adds its pairs'
-// contributions before the warp reduction, so the FP64 additions of the
-// reduction are spread over kLegPPT pairs.  Output: partial sums (without
-// the 4 pi / N_pix factor) part[chunk][idx(l, m)].
+// contributes lambda_lm(z_p) (F_north +- F_south).  The recurrence over l
+// and the pair sums run in double-float: lambda_lm = v 2^e with the
+// mantissa v brought below 2^30 every 4 steps (a step grows it by less
+// than a (1 + b) < 2 sqrt(2 l) <= 2^8, so |v| < 2^62 throughout), the
+// factor 2^e folded into the pair's F while e > -120 (below, the pair's
+// terms are under 2^-58 |F| and are left out until e grows).  The block reduction
+// over warps is in FP64.  Output: partial sums (without the 4 pi / N_pix
+// factor) part[chunk][idx(l, m)].
 __global__ void __launch_bounds__(kLegThreads)
 k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
            const int32_t* __restrict__ ex, int32_t N, int32_t lmax, int32_t nrings,
            int32_t npairs, int64_t nalm, double2* __restrict__ part) {
-  __shared__ double ra[kLegChunkL], rb[kLegChunkL];
+  __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
   __shared__ double2 red[kLegThreads / 32][kLegChunkL];
   // blockIdx.y in [0, lmax/2] handles m = y and (if distinct) m = lmax - y,
   // which balances the work per block
@@ -196,43 +269,46 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int pp[kLegPPT];
   bool have[kLegPPT];
-  double z[kLegPPT];
+  dfl z[kLegPPT];
 #pragma unroll
   for (int q = 0; q < kLegPPT; ++q) {
     pp[q] = chunk * kLegThreads * kLegPPT + q * kLegThreads + threadIdx.x;
     have[q] = pp[q] < npairs;
-    z[q] = have[q] ? ring_geom(N, pp[q]).z : 0.0;
+    z[q] = df_from_d(have[q] ? ring_geom(N, pp[q]).z : 0.0);
   }
+  // the pair's (F_north +- F_south) 2^e in double-float, or 0 below 2^-120
+  auto fold = [&](int q, int m, int e, dfl* Eo, dfl* Oo) {
+    if (!have[q] || e <= -120) {
+      Eo[0] = Eo[1] = Oo[0] = Oo[1] = dfl{0.f, 0.f};
+      return;
+    }
+    const int p = pp[q];
+    const double2 fn = F[(size_t)m * nrings + p];
+    const int ps = nrings - 1 - p;
+    const double2 fs = ps != p ? F[(size_t)m * nrings + ps] : make_double2(0.0, 0.0);
+    const double sc = ldexp(1.0, e);
+    Eo[0] = df_from_d((fn.x + fs.x) * sc);
+    Eo[1] = df_from_d((fn.y + fs.y) * sc);
+    Oo[0] = df_from_d((fn.x - fs.x) * sc);
+    Oo[1] = df_from_d((fn.y - fs.y) * sc);
+  };
   for (int pass = 0; pass < 2; ++pass) {
     const int m = pass == 0 ? (int)blockIdx.y : lmax - (int)blockIdx.y;
     if (pass == 1 && m <= (int)blockIdx.y) break;
-    double2 E[kLegPPT], O[kLegPPT];
-    double v1[kLegPPT], v2[kLegPPT], scale[kLegPPT];   // lambda_{l-1}, lambda_{l-2} mantissas
+    dfl E[kLegPPT][2], O[kLegPPT][2];
+    dfl v1[kLegPPT], v2[kLegPPT];                 // lambda_{l-1}, lambda_{l-2} mantissas
     int e[kLegPPT];
 #pragma unroll
     for (int q = 0; q < kLegPPT; ++q) {
-      E[q] = make_double2(0.0, 0.0);
-      O[q] = E[q];
-      v1[q] = 0.0;
-      v2[q] = 0.0;
-      e[q] = -100000;
-      if (have[q]) {
-        const int p = pp[q];
-        const double2 fn = F[(size_t)m * nrings + p];
-        const int ps = nrings - 1 - p;
-        const double2 fs = ps != p ? F[(size_t)m * nrings + ps] : make_double2(0.0, 0.0);
-        E[q] = make_double2(fn.x + fs.x, fn.y + fs.y);
-        O[q] = make_double2(fn.x - fs.x, fn.y - fs.y);
-        v1[q] = mu[(size_t)m * npairs + p];
-        e[q] = ex[(size_t)m * npairs + p];
-      }
-      // 2^e folded into F while it is a normal number far from underflow;
-      // below 2^-960 the pair's terms (< 2^-460 |F|) are dropped
-      scale[q] = e[q] > -960 ? ldexp(1.0, e[q]) : 0.0;
-      E[q] = make_double2(E[q].x * scale[q], E[q].y * scale[q]);
-      O[q] = make_double2(O[q].x * scale[q], O[q].y * scale[q]);
+      double mant = 0.0;
+      int ee = 0;
+      if (have[q]) mant = frexp(mu[(size_t)m * npairs + pp[q]], &ee);   // [0.5, 1) 2^ee
+      e[q] = have[q] ? ex[(size_t)m * npairs + pp[q]] + ee : -100000;
+      v1[q] = df_from_d(mant);
+      v2[q] = dfl{0.f, 0.f};
+      fold(q, m, e[q], E[q], O[q]);
     }
-    const double c1 = sqrt(2.0 * m + 3.0);
+    const dfl c1 = df_from_d(sqrt(2.0 * m + 3.0));
     const size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;   // index of (l = 0, m)
     for (int l0 = m; l0 <= lmax; l0 += kLegChunkL) {
       const int cnt = min(kLegChunkL, lmax + 1 - l0);
@@ -241,62 +317,58 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
         const int l = l0 + t;
         if (l >= m + 2) {
           const double ll = (double)l, mm = (double)m, l1 = (double)(l - 1);
-          ra[t] = sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm));
-          rb[t] = sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0));
+          ra[t] = df_from_d(sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm)));
+          rb[t] = df_from_d(sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0)));
         } else {
-          ra[t] = 0.0;
-          rb[t] = 0.0;
+          ra[t] = dfl{0.f, 0.f};
+          rb[t] = dfl{0.f, 0.f};
         }
       }
       __syncthreads();
       for (int t = 0; t < cnt; ++t) {
         const int l = l0 + t;
-        const double at = ra[t], bt = rb[t];
+        const dfl at = ra[t], bt = rb[t];
         const bool odd = (l + m) & 1;
-        double cr = 0.0, ci = 0.0;
+        dfl cr{0.f, 0.f}, ci{0.f, 0.f};
 #pragma unroll
         for (int q = 0; q < kLegPPT; ++q) {
-          double v;
+          dfl v;
           if (l == m) {
             v = v1[q];
           } else if (l == m + 1) {
-            v = c1 * z[q] * v1[q];
+            v = df_mul(df_mul(c1, z[q]), v1[q]);
             v2[q] = v1[q];
             v1[q] = v;
           } else {
-            v = at * (z[q] * v1[q] - bt * v2[q]);
+            v = df_mul(at, df_add(df_mul(z[q], v1[q]), df_neg(df_mul(bt, v2[q]))));
             v2[q] = v1[q];
             v1[q] = v;
           }
-          const double2 f = odd ? O[q] : E[q];
-          cr = fma(v, f.x, cr);
-          ci = fma(v, f.y, ci);
+          const dfl* f = odd ? O[q] : E[q];
+          df_mac(cr, v, f[0]);
+          df_mac(ci, v, f[1]);
         }
-        cr = warp_sum_dd(cr);
-        ci = warp_sum_dd(ci);
-        if (lane == 0) red[warp][t] = make_double2(cr, ci);
-      }
-      // keep the mantissas in range: one step grows them by less than
-      // a (1 + b) < 2 sqrt(2 l) <= 2^8, so after a check every kLegChunkL
-      // (32) steps they stay below 2^(500 + 256)
+        cr = warp_sum_df(cr);
+        ci = warp_sum_df(ci);
+        if (lane == 0) red[warp][t] = make_double2(df_to_d(cr), df_to_d(ci));
+        // keep the mantissas below 2^30 (checked every 4 steps)
+        if ((t & 3) == 3) {
 #pragma unroll
-      for (int q = 0; q < kLegPPT; ++q) {
-        while (fabs(v1[q]) > 0x1p500 || fabs(v2[q]) > 0x1p500) {
-          v1[q] *= 0x1p-500;
-          v2[q] *= 0x1p-500;
-          e[q] += 500;
-          if (scale[q] > 0.0) {            // exact: powers of two on normal numbers
-            E[q] = make_double2(E[q].x * 0x1p500, E[q].y * 0x1p500);
-            O[q] = make_double2(O[q].x * 0x1p500, O[q].y * 0x1p500);
-            scale[q] = ldexp(1.0, e[q]);
-          } else if (e[q] > -960) {        // the factor becomes representable
-            scale[q] = ldexp(1.0, e[q]);
-            const int p = pp[q];
-            const double2 fn = F[(size_t)m * nrings + p];
-            const int ps = nrings - 1 - p;
-            const double2 fs = ps != p ? F[(size_t)m * nrings + ps] : make_double2(0.0, 0.0);
-            E[q] = make_double2((fn.x + fs.x) * scale[q], (fn.y + fs.y) * scale[q]);
-            O[q] = make_double2((fn.x - fs.x) * scale[q], (fn.y - fs.y) * scale[q]);
+          for (int q = 0; q < kLegPPT; ++q) {
+            while (fabsf(v1[q].h) > 0x1p30f || fabsf(v2[q].h) > 0x1p30f) {
+              v1[q] = df_scale(v1[q], 0x1p-30f);
+              v2[q] = df_scale(v2[q], 0x1p-30f);
+              const bool folded = e[q] > -120;
+              e[q] += 30;
+              if (folded) {              // exact: powers of two on normal numbers
+                E[q][0] = df_scale(E[q][0], 0x1p30f);
+                E[q][1] = df_scale(E[q][1], 0x1p30f);
+                O[q][0] = df_scale(O[q][0], 0x1p30f);
+                O[q][1] = df_scale(O[q][1], 0x1p30f);
+              } else {
+                fold(q, m, e[q], E[q], O[q]);
+              }
+            }
           }
         }
       }
@@ -347,85 +419,94 @@ __global__ void __launch_bounds__(kLegThreads)
 k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
                  const int32_t* __restrict__ ex, int32_t N, int32_t lmax, int32_t nrings,
                  int32_t npairs, double2* __restrict__ G) {
-  __shared__ double ra[kLegChunkL], rb[kLegChunkL];
-  __shared__ double2 as[kLegChunkL];
+  __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
+  __shared__ dfl as[kLegChunkL][2];
   const int chunk = blockIdx.x;
   int pp[kLegPPT];
   bool have[kLegPPT];
-  double z[kLegPPT];
+  dfl z[kLegPPT];
 #pragma unroll
   for (int q = 0; q < kLegPPT; ++q) {
     pp[q] = chunk * kLegThreads * kLegPPT + q * kLegThreads + threadIdx.x;
     have[q] = pp[q] < npairs;
-    z[q] = have[q] ? ring_geom(N, pp[q]).z : 0.0;
+    z[q] = df_from_d(have[q] ? ring_geom(N, pp[q]).z : 0.0);
   }
   for (int pass = 0; pass < 2; ++pass) {
     const int m = pass == 0 ? (int)blockIdx.y : lmax - (int)blockIdx.y;
     if (pass == 1 && m <= (int)blockIdx.y) break;
-    double v1[kLegPPT], v2[kLegPPT];
+    dfl v1[kLegPPT], v2[kLegPPT];
     int e[kLegPPT];
-    double2 ge[kLegPPT], go[kLegPPT];     // sums over l + m even / odd, in units of 2^e
+    dfl ge[kLegPPT][2], go[kLegPPT][2];   // sums over l + m even / odd, in units of 2^e
 #pragma unroll
     for (int q = 0; q < kLegPPT; ++q) {
-      v1[q] = have[q] ? mu[(size_t)m * npairs + pp[q]] : 0.0;
-      v2[q] = 0.0;
-      e[q] = have[q] ? ex[(size_t)m * npairs + pp[q]] : 0;
-      ge[q] = make_double2(0.0, 0.0);
-      go[q] = ge[q];
+      double mant = 0.0;
+      int ee = 0;
+      if (have[q]) mant = frexp(mu[(size_t)m * npairs + pp[q]], &ee);   // [0.5, 1) 2^ee
+      v1[q] = df_from_d(mant);
+      v2[q] = dfl{0.f, 0.f};
+      e[q] = have[q] ? ex[(size_t)m * npairs + pp[q]] + ee : 0;
+      ge[q][0] = ge[q][1] = go[q][0] = go[q][1] = dfl{0.f, 0.f};
     }
-    const double c1 = sqrt(2.0 * m + 3.0);
+    const dfl c1 = df_from_d(sqrt(2.0 * m + 3.0));
     const size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;
     for (int l0 = m; l0 <= lmax; l0 += kLegChunkL) {
       const int cnt = min(kLegChunkL, lmax + 1 - l0);
       __syncthreads();
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         const int l = l0 + t;
-        as[t] = alm[base + l];
+        const double2 a = alm[base + l];
+        as[t][0] = df_from_d(a.x);
+        as[t][1] = df_from_d(a.y);
         if (l >= m + 2) {
           const double ll = (double)l, mm = (double)m, l1 = (double)(l - 1);
-          ra[t] = sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm));
-          rb[t] = sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0));
+          ra[t] = df_from_d(sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm)));
+          rb[t] = df_from_d(sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0)));
         } else {
-          ra[t] = 0.0;
-          rb[t] = 0.0;
+          ra[t] = dfl{0.f, 0.f};
+          rb[t] = dfl{0.f, 0.f};
         }
       }
       __syncthreads();
       for (int t = 0; t < cnt; ++t) {
         const int l = l0 + t;
-        const double at = ra[t], bt = rb[t];
-        const double2 a = as[t];
+        const dfl at = ra[t], bt = rb[t];
+        const dfl ax = as[t][0], ay = as[t][1];
         const bool odd = (l + m) & 1;
 #pragma unroll
         for (int q = 0; q < kLegPPT; ++q) {
-          double v;
+          dfl v;
           if (l == m) {
             v = v1[q];
           } else if (l == m + 1) {
-            v = c1 * z[q] * v1[q];
+            v = df_mul(df_mul(c1, z[q]), v1[q]);
             v2[q] = v1[q];
             v1[q] = v;
           } else {
-            v = at * (z[q] * v1[q] - bt * v2[q]);
+            v = df_mul(at, df_add(df_mul(z[q], v1[q]), df_neg(df_mul(bt, v2[q]))));
             v2[q] = v1[q];
             v1[q] = v;
           }
-          double2& g = odd ? go[q] : ge[q];
-          g.x = fma(v, a.x, g.x);
-          g.y = fma(v, a.y, g.y);
+          dfl* g = odd ? go[q] : ge[q];
+          df_mac(g[0], v, ax);
+          df_mac(g[1], v, ay);
         }
-      }
-      // mantissas back in range (growth per step < 2^8, see k_legendre); the
-      // sums so far are rescaled with them (terms 2^-500 below the current
-      // scale may underflow: they are negligible)
+        // mantissas back below 2^30 every 4 steps (growth per step < 2^8,
+        // see k_legendre), so that |v| < 2^62 and the sums stay far from
+        // the FP32 range; the sums so far are rescaled with them (terms
+        // 2^-30 below the current scale may lose bits: they are negligible)
+        if ((t & 3) == 3 || t == cnt - 1) {
 #pragma unroll
-      for (int q = 0; q < kLegPPT; ++q) {
-        while (fabs(v1[q]) > 0x1p500 || fabs(v2[q]) > 0x1p500) {
-          v1[q] *= 0x1p-500;
-          v2[q] *= 0x1p-500;
-          ge[q] = make_double2(ge[q].x * 0x1p-500, ge[q].y * 0x1p-500);
-          go[q] = make_double2(go[q].x * 0x1p-500, go[q].y * 0x1p-500);
-          e[q] += 500;
+          for (int q = 0; q < kLegPPT; ++q) {
+            while (fabsf(v1[q].h) > 0x1p30f || fabsf(v2[q].h) > 0x1p30f) {
+              v1[q] = df_scale(v1[q], 0x1p-30f);
+              v2[q] = df_scale(v2[q], 0x1p-30f);
+              ge[q][0] = df_scale(ge[q][0], 0x1p-30f);
+              ge[q][1] = df_scale(ge[q][1], 0x1p-30f);
+              go[q][0] = df_scale(go[q][0], 0x1p-30f);
+              go[q][1] = df_scale(go[q][1], 0x1p-30f);
+              e[q] += 30;
+            }
+          }
         }
       }
     }
@@ -433,10 +514,11 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
     for (int q = 0; q < kLegPPT; ++q) {
       if (!have[q]) continue;
       const double sc = e[q] > -1070 ? ldexp(1.0, e[q]) : 0.0;
+      const double er = df_to_d(ge[q][0]), ei = df_to_d(ge[q][1]);
+      const double orr = df_to_d(go[q][0]), oi = df_to_d(go[q][1]);
       const int p = pp[q], ps = nrings - 1 - p;
-      G[(size_t)m * nrings + p] = make_double2((ge[q].x + go[q].x) * sc, (ge[q].y + go[q].y) * sc);
-      if (ps != p)
-        G[(size_t)m * nrings + ps] = make_double2((ge[q].x - go[q].x) * sc, (ge[q].y - go[q].y) * sc);
+      G[(size_t)m * nrings + p] = make_double2((er + orr) * sc, (ei + oi) * sc);
+      if (ps != p) G[(size_t)m * nrings + ps] = make_double2((er - orr) * sc, (ei - oi) * sc);
     }
   }
 }
@@ -501,16 +583,41 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
     }
     for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = (float)H[j].x;
   } else {
+    // direct inverse DFT (non power-of-two ring) in double-float on the FP32
+    // pipe; H and the twiddles are converted in place, each element by one
+    // thread (the twiddles by the thread that computed them)
+    float4* wf = reinterpret_cast<float4*>(w);   // (re.h, re.l, im.h, im.l)
+    float4* hf = reinterpret_cast<float4*>(H);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const double2 t = w[k], h = H[k];
+      const dfl tr = df_from_d(t.x), ti = df_from_d(t.y), hr = df_from_d(h.x), hi = df_from_d(h.y);
+      wf[k] = make_float4(tr.h, tr.l, ti.h, ti.l);
+      hf[k] = make_float4(hr.h, hr.l, hi.h, hi.l);
+    }
+    __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double s = 0.0;
-      int idx = 0;
-      for (int k = 0; k < n; ++k) {
-        const double2 h = H[k], tw = w[idx];
-        s = fma(h.x, tw.x, fma(-h.y, tw.y, s));
-        idx += j;
+      dfl acc0{0.f, 0.f}, acc1{0.f, 0.f};        // k even / odd: two dependency chains
+      int idx = 0;                               // j k mod n
+      int j2 = 2 * j;
+      j2 -= j2 >= n ? n : 0;
+      int k = 0;
+      for (; k + 1 < n; k += 2) {
+        int idx1 = idx + j;
+        idx1 -= idx1 >= n ? n : 0;
+        const float4 h0 = hf[k], t0 = wf[idx], h1 = hf[k + 1], t1 = wf[idx1];
+        df_mac(acc0, dfl{h0.x, h0.y}, dfl{t0.x, t0.y});       // Re(H_k w^{jk})
+        df_mac(acc0, dfl{-h0.z, -h0.w}, dfl{t0.z, t0.w});
+        df_mac(acc1, dfl{h1.x, h1.y}, dfl{t1.x, t1.y});
+        df_mac(acc1, dfl{-h1.z, -h1.w}, dfl{t1.z, t1.w});
+        idx += j2;
         idx -= idx >= n ? n : 0;
       }
-      map[g.start + j] = (float)s;
+      if (k < n) {
+        const float4 h0 = hf[k], t0 = wf[idx];
+        df_mac(acc0, dfl{h0.x, h0.y}, dfl{t0.x, t0.y});
+        df_mac(acc0, dfl{-h0.z, -h0.w}, dfl{t0.z, t0.w});
+      }
+      map[g.start + j] = (float)df_to_d(df_add(acc0, acc1));
     }
   }
 }
