@@ -158,6 +158,7 @@ def cpu_baseline(w, parts_host, counts_host, A, C, dAC, seconds_budget=20.0):
     # the oracle's OpenMP binning (all host cores, atomic increments) on the
     # same sample, the rest of the step as above
     counts_omp = np.zeros((w.nshell, 12 * w.nside ** 2), dtype=np.int32)
+    counts_omp.fill(0)              # touch every page before the timed region
     t0 = time.perf_counter()
     threads = 1
     for k in range(2):

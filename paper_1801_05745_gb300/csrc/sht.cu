@@ -245,6 +245,27 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
   return v;
 }
 
+// Recurrence coefficients of every (l, m), m-major like a_lm, as
+// double-float pairs (a.h, a.l, b.h, b.l):
+//   a_lm = sqrt((4 l^2 - 1) / (l^2 - m^2)),
+//   b_lm = sqrt(((l-1)^2 - m^2) / (4 (l-1)^2 - 1))   for l >= m + 2, else 0.
+// Computed once per call in FP64 (block y = m), so that the Legendre kernels
+// read them instead of evaluating FP64 divisions and square roots per block.
+__global__ void k_leg_coef(int32_t lmax, float4* __restrict__ coef) {
+  const int m = blockIdx.y;
+  const size_t base = (size_t)m * (2 * lmax + 1 - m) / 2;
+  for (int l = m + blockIdx.x * blockDim.x + threadIdx.x; l <= lmax; l += gridDim.x * blockDim.x) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l >= m + 2) {
+      const double ll = (double)l, mm = (double)m, l1 = (double)(l - 1);
+      const dfl a = df_from_d(sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm)));
+      const dfl b = df_from_d(sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0)));
+      v = make_float4(a.h, a.l, b.h, b.l);
+    }
+    coef[base + l] = v;
+  }
+}
+
 // Block (m, chunk): each thread owns kLegPPT ring pairs
 // p = chunk * kLegThreads * kLegPPT + q * kLegThreads + t.  Pair p is the
 // north ring p and the south ring 4N - 2 - p (the equator ring, p = 2N - 1,
@@ -255,14 +276,16 @@ __device__ __forceinline__ double warp_sum_dd(double v) {
 // than a (1 + b) < 2 sqrt(2 l) <= 2^8, so |v| < 2^62 throughout), the
 // factor 2^e folded into the pair's F while e > -120 (below, the pair's
 // terms are under 2^-58 |F| and are left out until e grows).  The block reduction
-// over warps is in FP64.  Output: partial sums (without the 4 pi / N_pix
-// factor) part[chunk][idx(l, m)].
+// over warps is in double-float too (FP64 only for the block's result:
+// an FP64 instruction costs the FP32 pipe's time for about 64).  Output:
+// partial sums (without the 4 pi / N_pix factor) part[chunk][idx(l, m)].
 __global__ void __launch_bounds__(kLegThreads)
 k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
-           const int32_t* __restrict__ ex, int32_t N, int32_t lmax, int32_t nrings,
-           int32_t npairs, int64_t nalm, double2* __restrict__ part) {
+           const int32_t* __restrict__ ex, const float4* __restrict__ coef, int32_t N,
+           int32_t lmax, int32_t nrings, int32_t npairs, int64_t nalm,
+           double2* __restrict__ part) {
   __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
-  __shared__ double2 red[kLegThreads / 32][kLegChunkL];
+  __shared__ float4 red[kLegThreads / 32][kLegChunkL];   // warp sums (re.h, re.l, im.h, im.l)
   // blockIdx.y in [0, lmax/2] handles m = y and (if distinct) m = lmax - y,
   // which balances the work per block
   const int chunk = blockIdx.x;
@@ -314,15 +337,9 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
       const int cnt = min(kLegChunkL, lmax + 1 - l0);
       __syncthreads();
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        const int l = l0 + t;
-        if (l >= m + 2) {
-          const double ll = (double)l, mm = (double)m, l1 = (double)(l - 1);
-          ra[t] = df_from_d(sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm)));
-          rb[t] = df_from_d(sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0)));
-        } else {
-          ra[t] = dfl{0.f, 0.f};
-          rb[t] = dfl{0.f, 0.f};
-        }
+        const float4 cv = coef[base + l0 + t];
+        ra[t] = dfl{cv.x, cv.y};
+        rb[t] = dfl{cv.z, cv.w};
       }
       __syncthreads();
       for (int t = 0; t < cnt; ++t) {
@@ -350,7 +367,7 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
         }
         cr = warp_sum_df(cr);
         ci = warp_sum_df(ci);
-        if (lane == 0) red[warp][t] = make_double2(df_to_d(cr), df_to_d(ci));
+        if (lane == 0) red[warp][t] = make_float4(cr.h, cr.l, ci.h, ci.l);
         // keep the mantissas below 2^30 (checked every 4 steps)
         if ((t & 3) == 3) {
 #pragma unroll
@@ -374,9 +391,13 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
       }
       __syncthreads();
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        double sr = 0.0, si = 0.0;
-        for (int w = 0; w < kLegThreads / 32; ++w) { sr += red[w][t].x; si += red[w][t].y; }
-        part[(size_t)chunk * nalm + base + l0 + t] = make_double2(sr, si);
+        dfl sr{0.f, 0.f}, si{0.f, 0.f};
+        for (int w = 0; w < kLegThreads / 32; ++w) {
+          const float4 v = red[w][t];
+          sr = df_add(sr, dfl{v.x, v.y});
+          si = df_add(si, dfl{v.z, v.w});
+        }
+        part[(size_t)chunk * nalm + base + l0 + t] = make_double2(df_to_d(sr), df_to_d(si));
       }
     }
   }
@@ -417,8 +438,8 @@ __global__ void k_alm2cl(const double2* __restrict__ alm, int32_t lmax, double* 
 //                      m onto the ring's n frequencies and an inverse DFT.
 __global__ void __launch_bounds__(kLegThreads)
 k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
-                 const int32_t* __restrict__ ex, int32_t N, int32_t lmax, int32_t nrings,
-                 int32_t npairs, double2* __restrict__ G) {
+                 const int32_t* __restrict__ ex, const float4* __restrict__ coef, int32_t N,
+                 int32_t lmax, int32_t nrings, int32_t npairs, double2* __restrict__ G) {
   __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
   __shared__ dfl as[kLegChunkL][2];
   const int chunk = blockIdx.x;
@@ -457,14 +478,9 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
         const double2 a = alm[base + l];
         as[t][0] = df_from_d(a.x);
         as[t][1] = df_from_d(a.y);
-        if (l >= m + 2) {
-          const double ll = (double)l, mm = (double)m, l1 = (double)(l - 1);
-          ra[t] = df_from_d(sqrt((4.0 * ll * ll - 1.0) / (ll * ll - mm * mm)));
-          rb[t] = df_from_d(sqrt((l1 * l1 - mm * mm) / (4.0 * l1 * l1 - 1.0)));
-        } else {
-          ra[t] = dfl{0.f, 0.f};
-          rb[t] = dfl{0.f, 0.f};
-        }
+        const float4 cv = coef[base + l];
+        ra[t] = dfl{cv.x, cv.y};
+        rb[t] = dfl{cv.z, cv.w};
       }
       __syncthreads();
       for (int t = 0; t < cnt; ++t) {
@@ -545,7 +561,10 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
   const bool fft = is_pow2(n);
   int bits = 0;
   while ((1 << bits) < n) ++bits;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  // the map is real, so H_{n-k} = conj(H_k): the direct transform below
+  // needs H_k for k <= n/2 only
+  const int kend = fft ? n : n / 2 + 1;
+  for (int k = threadIdx.x; k < kend; k += blockDim.x) {
     double hx = 0.0, hy = 0.0;
     for (int m = k; m <= lmax; m += n) {              // m = k mod n
       const double2 gm = G[(size_t)m * nrings + r];
@@ -583,25 +602,32 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
     }
     for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = (float)H[j].x;
   } else {
-    // direct inverse DFT (non power-of-two ring) in double-float on the FP32
-    // pipe; H and the twiddles are converted in place, each element by one
-    // thread (the twiddles by the thread that computed them)
+    // direct inverse DFT (non power-of-two ring, n = 4i even) in double-float
+    // on the FP32 pipe, from the Hermitian half: map_j = Re H_0
+    // + 2 sum_{k=1}^{n/2-1} Re(H_k w^{jk}) + (-1)^j Re H_{n/2}.  H and the
+    // twiddles are converted in place, each element by one thread (the
+    // twiddles by the thread that computed them)
     float4* wf = reinterpret_cast<float4*>(w);   // (re.h, re.l, im.h, im.l)
     float4* hf = reinterpret_cast<float4*>(H);
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const double2 t = w[k], h = H[k];
-      const dfl tr = df_from_d(t.x), ti = df_from_d(t.y), hr = df_from_d(h.x), hi = df_from_d(h.y);
+      const double2 t = w[k];
+      const dfl tr = df_from_d(t.x), ti = df_from_d(t.y);
       wf[k] = make_float4(tr.h, tr.l, ti.h, ti.l);
-      hf[k] = make_float4(hr.h, hr.l, hi.h, hi.l);
+      if (k <= n / 2) {
+        const double2 h = H[k];
+        const dfl hr = df_from_d(h.x), hi = df_from_d(h.y);
+        hf[k] = make_float4(hr.h, hr.l, hi.h, hi.l);
+      }
     }
     __syncthreads();
+    const int half = n / 2;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      dfl acc0{0.f, 0.f}, acc1{0.f, 0.f};        // k even / odd: two dependency chains
-      int idx = 0;                               // j k mod n
+      dfl acc0{0.f, 0.f}, acc1{0.f, 0.f};        // k odd / even: two dependency chains
+      int idx = j;                               // j k mod n, from k = 1
       int j2 = 2 * j;
       j2 -= j2 >= n ? n : 0;
-      int k = 0;
-      for (; k + 1 < n; k += 2) {
+      int k = 1;
+      for (; k + 1 < half; k += 2) {
         int idx1 = idx + j;
         idx1 -= idx1 >= n ? n : 0;
         const float4 h0 = hf[k], t0 = wf[idx], h1 = hf[k + 1], t1 = wf[idx1];
@@ -612,12 +638,17 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
         idx += j2;
         idx -= idx >= n ? n : 0;
       }
-      if (k < n) {
+      if (k < half) {
         const float4 h0 = hf[k], t0 = wf[idx];
         df_mac(acc0, dfl{h0.x, h0.y}, dfl{t0.x, t0.y});
         df_mac(acc0, dfl{-h0.z, -h0.w}, dfl{t0.z, t0.w});
       }
-      map[g.start + j] = (float)df_to_d(df_add(acc0, acc1));
+      dfl sum = df_add(acc0, acc1);
+      sum = df_add(sum, sum);                    // the conjugate half
+      const float4 h0 = hf[0], hn = hf[half];
+      sum = df_add(sum, dfl{h0.x, h0.y});
+      sum = df_add(sum, (j & 1) ? dfl{-hn.x, -hn.y} : dfl{hn.x, hn.y});
+      map[g.start + j] = (float)df_to_d(sum);
     }
   }
 }
@@ -668,7 +699,8 @@ ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double
   const size_t fbytes = (size_t)(lmax + 1) * nrings * sizeof(double2);
   const size_t lbytes = (size_t)(lmax + 1) * npairs * (sizeof(double) + sizeof(int32_t));
   const size_t pbytes = (size_t)nchunk * nalm * sizeof(double2);
-  char* ws = (char*)ws_get(c, kSlotSht, fbytes + lbytes + pbytes + 512);
+  const size_t cbytes = (size_t)nalm * sizeof(float4);
+  char* ws = (char*)ws_get(c, kSlotSht, fbytes + lbytes + pbytes + cbytes + 512);
   if (!ws) return UFC_ERR_ALLOC;
   double2* F = reinterpret_cast<double2*>(ws);
   double* mu = reinterpret_cast<double*>(ws + fbytes);
@@ -676,6 +708,7 @@ ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double
   char* pp = ws + fbytes + lbytes;
   pp += (16 - (reinterpret_cast<uintptr_t>(pp) & 15)) & 15;
   double2* part = reinterpret_cast<double2*>(pp);
+  float4* coef = reinterpret_cast<float4*>(pp + pbytes);
   const int smem = 2 * 4 * nside * (int)sizeof(double2);
   UFC_CUDA(c, cudaFuncSetAttribute(k_ring_transform, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    smem));
@@ -688,10 +721,14 @@ ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double
     k_lmm<<<(npairs + 127) / 128, 128, 0, c->stream>>>(nside, lmax, npairs, mu, ex);
   }
   {
+    ProfScope ps_(c, "k_leg_coef");
+    k_leg_coef<<<dim3(4, lmax + 1), 256, 0, c->stream>>>(lmax, coef);
+  }
+  {
     ProfScope ps_(c, "k_legendre");
     dim3 grid(nchunk, lmax / 2 + 1);
-    k_legendre<<<grid, kLegThreads, 0, c->stream>>>(F, mu, ex, nside, lmax, nrings, npairs, nalm,
-                                                    part);
+    k_legendre<<<grid, kLegThreads, 0, c->stream>>>(F, mu, ex, coef, nside, lmax, nrings, npairs,
+                                                    nalm, part);
   }
   {
     ProfScope ps_(c, "k_alm_sum");
@@ -725,11 +762,20 @@ ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float
   const int nchunk = (npairs + kLegThreads * kLegPPT - 1) / (kLegThreads * kLegPPT);
   const size_t gbytes = (size_t)(lmax + 1) * nrings * sizeof(double2);
   const size_t lbytes = (size_t)(lmax + 1) * npairs * (sizeof(double) + sizeof(int32_t));
-  char* ws = (char*)ws_get(c, kSlotSht, gbytes + lbytes + 512);
+  const int64_t nalm = (int64_t)(lmax + 1) * (lmax + 2) / 2;
+  const size_t cbytes = (size_t)nalm * sizeof(float4);
+  char* ws = (char*)ws_get(c, kSlotSht, gbytes + lbytes + cbytes + 512);
   if (!ws) return UFC_ERR_ALLOC;
   double2* Gm = reinterpret_cast<double2*>(ws);
   double* mu = reinterpret_cast<double*>(ws + gbytes);
   int32_t* ex = reinterpret_cast<int32_t*>(ws + gbytes + (size_t)(lmax + 1) * npairs * 8);
+  char* cp = ws + gbytes + lbytes;
+  cp += (16 - (reinterpret_cast<uintptr_t>(cp) & 15)) & 15;
+  float4* coef = reinterpret_cast<float4*>(cp);
+  {
+    ProfScope ps_(c, "k_leg_coef");
+    k_leg_coef<<<dim3(4, lmax + 1), 256, 0, c->stream>>>(lmax, coef);
+  }
   {
     ProfScope ps_(c, "k_lmm");
     k_lmm<<<(npairs + 127) / 128, 128, 0, c->stream>>>(nside, lmax, npairs, mu, ex);
@@ -738,7 +784,7 @@ ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float
     ProfScope ps_(c, "k_legendre_synth");
     dim3 grid(nchunk, lmax / 2 + 1);
     k_legendre_synth<<<grid, kLegThreads, 0, c->stream>>>(reinterpret_cast<const double2*>(alm), mu,
-                                                          ex, nside, lmax, nrings, npairs, Gm);
+                                                          ex, coef, nside, lmax, nrings, npairs, Gm);
   }
   const int smem = 2 * 4 * nside * (int)sizeof(double2);
   UFC_CUDA(c, cudaFuncSetAttribute(k_ring_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));

@@ -187,3 +187,24 @@ def test_adjoint_vs_central_difference_step_1e4(orc):
         fd = (var_at(tp) - var_at(tm)) / (2 * h)
         assert grad[j] == pytest.approx(fd, rel=1e-6, abs=1e-12)
     assert grad[1] == 0.0
+
+
+def test_batched_lanes_grow_between_graph_calls(orc):
+    """Graph calls on small maps (concurrent lanes): a first call with small
+    realisations, then one with ten times the particles, which grows every
+    lane's workspace and so drops the cached graph that referred to it; the
+    second call rebuilds it and equals the maps computed one at a time."""
+    api, ctx = api_ctx()
+    nside, nshell, nreal = 64, 12, 11
+    nbins, lo, hi = 30, -0.05, 0.2
+    d = 6 + nbins
+    for nb in (20_000, 200_000):
+        z, chi, xs, bxs, A, C = _realisations(orc, api, nreal, nside, nshell, nb)
+        st = api.welford_state(d)
+        mom, pdf, stats = ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, st,
+                                            graph=True)
+        torch.cuda.synchronize()
+        for r in range(nreal):
+            counts = ctx.bin(xs[r], bxs[r], chi, nside)
+            _, m1, p1 = ctx.kappa_stats(counts, A[r], C[r], lo, hi, nbins)
+            assert torch.equal(mom[r], m1) and torch.equal(pdf[r], p1)
