@@ -113,14 +113,6 @@ __device__ __forceinline__ void df_mac(dfl& acc, dfl a, dfl b) {
   acc.h = s;
   acc.l = __fadd_rn(acc.l, __fadd_rn(se, __fadd_rn(pe, cross)));
 }
-__device__ __forceinline__ dfl warp_sum_df(dfl v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    const dfl w{__shfl_down_sync(0xFFFFFFFFu, v.h, o), __shfl_down_sync(0xFFFFFFFFu, v.l, o)};
-    v = df_add(v, w);
-  }
-  return v;
-}
-
 
 // One block per ring.  Shared memory: twiddles w_k = e^{-2 pi i k / n} and the
 // ring's values (real, or complex for the FFT).
@@ -275,8 +267,10 @@ __global__ void k_leg_coef(int32_t lmax, float4* __restrict__ coef) {
 // mantissa v brought below 2^30 every 4 steps (a step grows it by less
 // than a (1 + b) < 2 sqrt(2 l) <= 2^8, so |v| < 2^62 throughout), the
 // factor 2^e folded into the pair's F while e > -120 (below, the pair's
-// terms are under 2^-58 |F| and are left out until e grows).  The block reduction
-// over warps is in double-float too (FP64 only for the block's result:
+// terms are under 2^-58 |F| and are left out until e grows).  Each degree's
+// sum over the pairs: a thread's pairs, then groups of 4 lanes (shuffles),
+// then the block's 64 group sums in shared memory, all in double-float
+// (FP64 only for the block's result:
 // an FP64 instruction costs the FP32 pipe's time for about 64).  Output:
 // partial sums (without the 4 pi / N_pix factor) part[chunk][idx(l, m)].
 __global__ void __launch_bounds__(kLegThreads)
@@ -285,7 +279,8 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
            int32_t lmax, int32_t nrings, int32_t npairs, int64_t nalm,
            double2* __restrict__ part) {
   __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
-  __shared__ float4 red[kLegThreads / 32][kLegChunkL];   // warp sums (re.h, re.l, im.h, im.l)
+  // sums of 4 adjacent lanes (re.h, re.l, im.h, im.l): 8 per warp
+  __shared__ float4 red[kLegThreads / 4][kLegChunkL];
   // blockIdx.y in [0, lmax/2] handles m = y and (if distinct) m = lmax - y,
   // which balances the work per block
   const int chunk = blockIdx.x;
@@ -365,9 +360,15 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
           df_mac(cr, v, f[0]);
           df_mac(ci, v, f[1]);
         }
-        cr = warp_sum_df(cr);
-        ci = warp_sum_df(ci);
-        if (lane == 0) red[warp][t] = make_float4(cr.h, cr.l, ci.h, ci.l);
+        // 4 lanes' sums by two shuffle steps; the block step adds the rest
+#pragma unroll
+        for (int o = 2; o > 0; o >>= 1) {
+          const dfl wr{__shfl_down_sync(0xFFFFFFFFu, cr.h, o), __shfl_down_sync(0xFFFFFFFFu, cr.l, o)};
+          const dfl wi{__shfl_down_sync(0xFFFFFFFFu, ci.h, o), __shfl_down_sync(0xFFFFFFFFu, ci.l, o)};
+          cr = df_add(cr, wr);
+          ci = df_add(ci, wi);
+        }
+        if ((lane & 3) == 0) red[warp * 8 + (lane >> 2)][t] = make_float4(cr.h, cr.l, ci.h, ci.l);
         // keep the mantissas below 2^30 (checked every 4 steps)
         if ((t & 3) == 3) {
 #pragma unroll
@@ -392,7 +393,7 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
       __syncthreads();
       for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         dfl sr{0.f, 0.f}, si{0.f, 0.f};
-        for (int w = 0; w < kLegThreads / 32; ++w) {
+        for (int w = 0; w < kLegThreads / 4; ++w) {
           const float4 v = red[w][t];
           sr = df_add(sr, dfl{v.x, v.y});
           si = df_add(si, dfl{v.z, v.w});
