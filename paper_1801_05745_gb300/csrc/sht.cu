@@ -155,48 +155,72 @@ k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t
       __syncthreads();
     }
   } else {
-    // direct DFT of the real ring (non power-of-two length), accumulated in
-    // double-float on the FP32 pipe: the map values are FP32, the twiddles
-    // are split into double-float pairs
-    // twiddles converted in place (each thread its own, as computed above)
+    // non power-of-two ring (a polar ring, n = 4 i): one radix-4 split,
+    // X_k = sum_{r<4} w_n^{rk} Y_r(k mod i) with Y_r(q) = sum_{a<i} x_{4a+r}
+    // w_n^{4aq} the length-i DFTs of the four sub-sequences (real input:
+    // Y_r(i-q) = conj Y_r(q), so q <= i/2), then k <= min(n/2, lmax) (real
+    // input: X_{n-k} = conj X_k).  Sums in double-float on the FP32 pipe;
+    // the map values are FP32, the twiddles are split into double-float
+    // pairs in place (each thread its own, as computed above).
     float4* wf = reinterpret_cast<float4*>(w);          // [n] (re.h, re.l, im.h, im.l)
-    float* xr = reinterpret_cast<float*>(x + n / 2 + 1);   // real input after X[0..n/2]
-    for (int j = threadIdx.x; j < n; j += blockDim.x) xr[j] = map[g.start + j];
+    float* xr = reinterpret_cast<float*>(x);            // [n] the ring's values
+    const int ni = n / 4, nq = ni / 2 + 1;
+    float4* Y = reinterpret_cast<float4*>(x + n / 4 + 1);   // [4][nq] after xr
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) xr[jj] = map[g.start + jj];
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const double2 t = w[k];
       const dfl re = df_from_d(t.x), im = df_from_d(t.y);
       wf[k] = make_float4(re.h, re.l, im.h, im.l);
     }
     __syncthreads();
-    const int kmax = min(n / 2, lmax);       // X_{n-k} = conj X_k for real input
-    for (int k0 = 0; k0 <= kmax; k0 += 4 * blockDim.x) {
-      int kk[4];
-      dfl ar[4], ai[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        kk[u] = k0 + u * blockDim.x + threadIdx.x;
-        ar[u] = ai[u] = dfl{0.f, 0.f};
+    for (int o = threadIdx.x; o < 4 * nq; o += blockDim.x) {
+      const int r = o / nq, q = o - r * nq;
+      const int step = 4 * q;                  // < n since q <= i/2
+      dfl ar{0.f, 0.f}, ai{0.f, 0.f};
+      int idx = 0;
+      for (int a = 0; a < ni; ++a) {
+        const dfl v{xr[4 * a + r], 0.f};
+        const float4 tw = wf[idx];
+        df_mac(ar, v, dfl{tw.x, tw.y});
+        df_mac(ai, v, dfl{tw.z, tw.w});
+        idx += step;
+        idx -= idx >= n ? n : 0;
       }
-      int idx[4] = {0, 0, 0, 0};
-      for (int j = 0; j < n; ++j) {
-        const dfl v{xr[j], 0.f};
+      ar = df_add(ar, dfl{0.f, 0.f});
+      ai = df_add(ai, dfl{0.f, 0.f});
+      Y[o] = make_float4(ar.h, ar.l, ai.h, ai.l);
+    }
+    __syncthreads();
+    const int kmax = min(n / 2, lmax);
+    double2 out[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float4 tw = wf[idx[u]];
-          df_mac(ar[u], v, dfl{tw.x, tw.y});
-          df_mac(ai[u], v, dfl{tw.z, tw.w});
-          idx[u] += kk[u] <= kmax ? kk[u] : 0;
-          idx[u] -= idx[u] >= n ? n : 0;
-        }
+    for (int u = 0; u < 4; ++u) {
+      const int k = threadIdx.x + u * (int)blockDim.x;
+      if (k > kmax) continue;
+      int q = k % ni;
+      const bool cj = q > ni / 2;
+      if (cj) q = ni - q;
+      dfl xre{0.f, 0.f}, xim{0.f, 0.f};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float4 yv = Y[r * nq + q];
+        const dfl yr{yv.x, yv.y}, yi = cj ? dfl{-yv.z, -yv.w} : dfl{yv.z, yv.w};
+        const float4 tw = wf[(r * k) % n];
+        const dfl tr{tw.x, tw.y}, ti{tw.z, tw.w};
+        df_mac(xre, tr, yr);                   // Re(w Y)
+        df_mac(xre, df_neg(ti), yi);
+        df_mac(xim, tr, yi);                   // Im(w Y)
+        df_mac(xim, ti, yr);
       }
-      __syncthreads();                        // all reads of xr done before X is written
+      xre = df_add(xre, dfl{0.f, 0.f});
+      xim = df_add(xim, dfl{0.f, 0.f});
+      out[u] = make_double2(df_to_d(xre), df_to_d(xim));
+    }
+    __syncthreads();                           // xr and Y are read; X overwrites them
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (kk[u] <= kmax) {
-          const dfl rr = df_add(ar[u], dfl{0.f, 0.f}), ii = df_add(ai[u], dfl{0.f, 0.f});
-          x[kk[u]] = make_double2(df_to_d(rr), df_to_d(ii));
-        }
-      __syncthreads();
+    for (int u = 0; u < 4; ++u) {
+      const int k = threadIdx.x + u * (int)blockDim.x;
+      if (k <= kmax) x[k] = out[u];
     }
   }
   __syncthreads();
