@@ -627,53 +627,84 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
     }
     for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = (float)H[j].x;
   } else {
-    // direct inverse DFT (non power-of-two ring, n = 4i even) in double-float
-    // on the FP32 pipe, from the Hermitian half: map_j = Re H_0
-    // + 2 sum_{k=1}^{n/2-1} Re(H_k w^{jk}) + (-1)^j Re H_{n/2}.  H and the
-    // twiddles are converted in place, each element by one thread (the
-    // twiddles by the thread that computed them)
+    // non power-of-two ring (polar, n = 4 i), from the Hermitian half
+    // (H_{n-k} = conj H_k, the map being real) with one radix-4 split:
+    // map_{4a+r} = Re sum_{q<i} Z_r(q) w^{4aq}, Z_r(q) = sum_{t<4} H_{q+it}
+    // w^{r(q+it)}, and Z_r(i-q) = conj Z_r(q), so
+    // map_{4a+r} = Re Z_r(0) + 2 sum_{0<q<i/2} Re(Z_r(q) w^{4aq})
+    //              + [i even] (-1)^a Re Z_r(i/2).
+    // Double-float on the FP32 pipe; H and the twiddles are converted in
+    // place, each element by one thread (the twiddles by the thread that
+    // computed them).
     float4* wf = reinterpret_cast<float4*>(w);   // (re.h, re.l, im.h, im.l)
-    float4* hf = reinterpret_cast<float4*>(H);
+    float4* hf = reinterpret_cast<float4*>(H);   // [n/2 + 1]
+    const int ni = n / 4, nq = ni / 2 + 1, half = n / 2;
+    float4* Z = hf + half + 1;                   // [4][nq]
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
       const double2 t = w[k];
       const dfl tr = df_from_d(t.x), ti = df_from_d(t.y);
       wf[k] = make_float4(tr.h, tr.l, ti.h, ti.l);
-      if (k <= n / 2) {
+      if (k <= half) {
         const double2 h = H[k];
         const dfl hr = df_from_d(h.x), hi = df_from_d(h.y);
         hf[k] = make_float4(hr.h, hr.l, hi.h, hi.l);
       }
     }
     __syncthreads();
-    const int half = n / 2;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      dfl acc0{0.f, 0.f}, acc1{0.f, 0.f};        // k odd / even: two dependency chains
-      int idx = j;                               // j k mod n, from k = 1
-      int j2 = 2 * j;
-      j2 -= j2 >= n ? n : 0;
-      int k = 1;
-      for (; k + 1 < half; k += 2) {
-        int idx1 = idx + j;
+    for (int o = threadIdx.x; o < 4 * nq; o += blockDim.x) {
+      const int r = o / nq, q = o - r * nq;
+      dfl zr{0.f, 0.f}, zi{0.f, 0.f};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int k = q + ni * t;
+        const bool cj = k > half;
+        const float4 hv = hf[cj ? n - k : k];
+        const dfl hr{hv.x, hv.y}, hi = cj ? dfl{-hv.z, -hv.w} : dfl{hv.z, hv.w};
+        const float4 tw = wf[(r * k) % n];
+        const dfl tr{tw.x, tw.y}, ti{tw.z, tw.w};
+        df_mac(zr, tr, hr);                    // Re(H w)
+        df_mac(zr, df_neg(ti), hi);
+        df_mac(zi, tr, hi);                    // Im(H w)
+        df_mac(zi, ti, hr);
+      }
+      zr = df_add(zr, dfl{0.f, 0.f});
+      zi = df_add(zi, dfl{0.f, 0.f});
+      Z[o] = make_float4(zr.h, zr.l, zi.h, zi.l);
+    }
+    __syncthreads();
+    const int qe = (ni + 1) / 2;                 // q in [1, qe): the doubled terms
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
+      const int a = jj >> 2, r = jj & 3;
+      const float4* Zr = Z + r * nq;
+      const int step = (4 * a) % n;              // w^{4aq}: index 4 a q mod n
+      dfl acc0{0.f, 0.f}, acc1{0.f, 0.f};
+      int idx = step;
+      int q = 1;
+      for (; q + 1 < qe; q += 2) {
+        int idx1 = idx + step;
         idx1 -= idx1 >= n ? n : 0;
-        const float4 h0 = hf[k], t0 = wf[idx], h1 = hf[k + 1], t1 = wf[idx1];
-        df_mac(acc0, dfl{h0.x, h0.y}, dfl{t0.x, t0.y});       // Re(H_k w^{jk})
-        df_mac(acc0, dfl{-h0.z, -h0.w}, dfl{t0.z, t0.w});
-        df_mac(acc1, dfl{h1.x, h1.y}, dfl{t1.x, t1.y});
-        df_mac(acc1, dfl{-h1.z, -h1.w}, dfl{t1.z, t1.w});
-        idx += j2;
+        const float4 z0 = Zr[q], t0 = wf[idx], z1 = Zr[q + 1], t1 = wf[idx1];
+        df_mac(acc0, dfl{z0.x, z0.y}, dfl{t0.x, t0.y});       // Re(Z w)
+        df_mac(acc0, dfl{-z0.z, -z0.w}, dfl{t0.z, t0.w});
+        df_mac(acc1, dfl{z1.x, z1.y}, dfl{t1.x, t1.y});
+        df_mac(acc1, dfl{-z1.z, -z1.w}, dfl{t1.z, t1.w});
+        idx = idx1 + step;
         idx -= idx >= n ? n : 0;
       }
-      if (k < half) {
-        const float4 h0 = hf[k], t0 = wf[idx];
-        df_mac(acc0, dfl{h0.x, h0.y}, dfl{t0.x, t0.y});
-        df_mac(acc0, dfl{-h0.z, -h0.w}, dfl{t0.z, t0.w});
+      if (q < qe) {
+        const float4 z0 = Zr[q], t0 = wf[idx];
+        df_mac(acc0, dfl{z0.x, z0.y}, dfl{t0.x, t0.y});
+        df_mac(acc0, dfl{-z0.z, -z0.w}, dfl{t0.z, t0.w});
       }
       dfl sum = df_add(acc0, acc1);
       sum = df_add(sum, sum);                    // the conjugate half
-      const float4 h0 = hf[0], hn = hf[half];
-      sum = df_add(sum, dfl{h0.x, h0.y});
-      sum = df_add(sum, (j & 1) ? dfl{-hn.x, -hn.y} : dfl{hn.x, hn.y});
-      map[g.start + j] = (float)df_to_d(sum);
+      const float4 z0 = Zr[0];
+      sum = df_add(sum, dfl{z0.x, z0.y});
+      if ((ni & 1) == 0) {                       // the self-conjugate q = i/2
+        const float4 zn = Zr[ni / 2];
+        sum = df_add(sum, (a & 1) ? dfl{-zn.x, -zn.y} : dfl{zn.x, zn.y});
+      }
+      map[g.start + jj] = (float)df_to_d(sum);
     }
   }
 }
