@@ -250,6 +250,19 @@ ufc_status ufc_bin_snapshots(ufc_ctx *ctx, const float *const *xyz_dev,
                              int32_t nsnap, const int32_t *snap_of_shell,
                              const double *chi_edges, int32_t nshell,
                              int32_t nside, int32_t flags, int32_t *counts_dev);
+/* ufc_bin_snapshots from host memory, for snapshot sets beyond device
+ * memory: each run's particles stream through two device buffers of at
+ * most `chunk` particles as in ufc_bin_host_stream (copy of the next chunk
+ * overlapped with the binning of the current one; device memory held:
+ * 2 x 12 chunk bytes plus one chunk's binning workspace).  Counts equal
+ * ufc_bin_snapshots'.  Host buffers as for ufc_bin_host;
+ * UFC_ERR_UNSUPPORTED while the context stream is capturing. */
+ufc_status ufc_bin_snapshots_host(ufc_ctx *ctx, const float *const *xyz_host,
+                                  const int64_t *n, const ufc_box *snap_geom,
+                                  int32_t nsnap, const int32_t *snap_of_shell,
+                                  const double *chi_edges, int32_t nshell,
+                                  int32_t nside, int32_t flags, int64_t chunk,
+                                  int32_t *counts_dev);
 /* Diagnostics of the last ufc_bin/ufc_keys call (synchronises):
  * info[0] invalid particles, info[1] particle-images with a key,
  * info[2] decisions refined past the FP32 stage, info[3] past the

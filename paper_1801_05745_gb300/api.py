@@ -91,6 +91,7 @@ _SIGS = {
     "ufc_bin_info": [P, P],
     "ufc_snapshot_assign": [P, I32, P, I32, P],
     "ufc_bin_snapshots": [P, P, P, P, I32, P, P, I32, I32, I32, P],
+    "ufc_bin_snapshots_host": [P, P, P, P, I32, P, P, I32, I32, I32, I64, P],
     "ufc_kappa_stats": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_kappa_backward": [P, P, I32, I32, P, D, D, D, P, P, P, P, P, P],
     "ufc_welford_update": [P, P, I32, I32, P],
@@ -357,6 +358,31 @@ class Context:
                                         ctypes.cast(arr, P), len(geoms), _np_ptr(sos),
                                         _np_ptr(chi), S, nside, _bin_flags(accumulate, path),
                                         P(counts.data_ptr())), "ufc_bin_snapshots")
+        return counts
+
+    def bin_snapshots_host(self, xyz_list, geoms, snap_of_shell, chi_edges, nside: int,
+                           chunk: int, counts=None, accumulate=False, path: str | None = None):
+        """bin_snapshots with the snapshots in host memory, streamed through two
+        device buffers of `chunk` particles (ufc_bin_snapshots_host)."""
+        import torch
+        chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
+        S = len(chi) - 1
+        npix = 12 * nside * nside
+        sos = np.ascontiguousarray(snap_of_shell, dtype=np.int32)
+        assert len(sos) == S and len(geoms) == len(xyz_list)
+        xs = [_host_f32(x) for x in xyz_list]
+        if counts is None:
+            counts = torch.empty((S, npix), dtype=torch.int32, device=f"cuda:{self.device}")
+        assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.numel() == S * npix
+        ptrs = (P * len(xs))(*[P(a) for a, _ in xs])
+        ns = (I64 * len(xs))(*[m // 3 for _, m in xs])
+        arr = (Box * len(geoms))(*geoms)
+        self._stream()
+        self._ck(_lib.ufc_bin_snapshots_host(self.h, ctypes.cast(ptrs, P), ctypes.cast(ns, P),
+                                             ctypes.cast(arr, P), len(geoms), _np_ptr(sos),
+                                             _np_ptr(chi), S, nside, _bin_flags(accumulate, path),
+                                             int(chunk), P(counts.data_ptr())),
+                 "ufc_bin_snapshots_host")
         return counts
 
     def bin_info(self):

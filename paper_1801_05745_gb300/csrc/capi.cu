@@ -447,14 +447,22 @@ ufc_status ufc_snapshot_assign(const double* z_edges, int32_t nshell, const doub
   return UFC_OK;
 }
 
-ufc_status ufc_bin_snapshots(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
-                             const ufc_box* snap_geom, int32_t nsnap, const int32_t* snap_of_shell,
-                             const double* chi_edges, int32_t nshell, int32_t nside, int32_t flags,
-                             int32_t* counts_dev) {
+}  // extern "C"
+
+// Snapshot-mode binning shared by the device and host-memory entry points:
+// argument checks, then the runs of consecutive shells taken from one
+// snapshot as boxes owning those shells, kMaxBoxes per pass (the passes
+// after the first accumulate).  pass(rx, rn, rb, nrun, flags) bins one pass.
+template <class Pass>
+static ufc_status bin_snapshot_runs(ufc_ctx* c, const char* who, const float* const* xyz,
+                                    const int64_t* n, const ufc_box* snap_geom, int32_t nsnap,
+                                    const int32_t* snap_of_shell, const double* chi_edges,
+                                    int32_t nshell, int32_t nside, int32_t flags,
+                                    int32_t* counts_dev, Pass pass) {
   if (!c) return UFC_ERR_ARG;
   c->err.clear();
-  if (!xyz_dev || !n || !snap_geom || !snap_of_shell || !chi_edges || !counts_dev)
-    return set_err(c, UFC_ERR_ARG, "NULL argument to ufc_bin_snapshots");
+  if (!xyz || !n || !snap_geom || !snap_of_shell || !chi_edges || !counts_dev)
+    return set_err(c, UFC_ERR_ARG, "NULL argument to %s", who);
   if (nsnap < 1) return set_err(c, UFC_ERR_ARG, "nsnap must be >= 1");
   if (nshell < 1 || nshell > UFC_MAX_SHELLS)
     return set_err(c, UFC_ERR_ARG, "nshell must be in [1,%d]", UFC_MAX_SHELLS);
@@ -469,15 +477,13 @@ ufc_status ufc_bin_snapshots(ufc_ctx* c, const float* const* xyz_dev, const int6
       return set_err(c, UFC_ERR_ARG, "snap_of_shell[%d] = %d outside [-1,%d)", b,
                      snap_of_shell[b], nsnap);
   cudaSetDevice(c->device);
-  // runs of consecutive shells from one snapshot, kMaxBoxes per pass
   ufc_box rb[kMaxBoxes];
   const float* rx[kMaxBoxes];
   int64_t rn[kMaxBoxes];
   int nrun = 0, passes = 0;
-  auto pass = [&]() -> ufc_status {
+  auto flush = [&]() -> ufc_status {
     const int32_t f = flags | (passes > 0 ? UFC_BIN_ACCUMULATE : 0);
-    const ufc_status st = run_keys_pipeline(c, 1, rx, rn, rb, nrun, chi_edges, nshell, nside, f,
-                                            counts_dev, nullptr, nullptr);
+    const ufc_status st = pass(rx, rn, rb, nrun, f);
     ++passes;
     nrun = 0;
     return st;
@@ -488,22 +494,59 @@ ufc_status ufc_bin_snapshots(ufc_ctx* c, const float* const* xyz_dev, const int6
     while (e < nshell && snap_of_shell[e] == s) ++e;
     if (s >= 0) {
       if (nrun == kMaxBoxes) {
-        const ufc_status st = pass();
+        const ufc_status st = flush();
         if (st) return st;
       }
       rb[nrun] = snap_geom[s];
       rb[nrun].shell_lo = b;
       rb[nrun].shell_hi = e;
-      rx[nrun] = xyz_dev[s];
+      rx[nrun] = xyz[s];
       rn[nrun] = n[s];
       ++nrun;
     }
     b = e;
   }
-  if (nrun > 0) return pass();
+  if (nrun > 0) return flush();
   if (passes == 0 && !(flags & UFC_BIN_ACCUMULATE))   // no shell has a snapshot
     UFC_CUDA(c, cudaMemsetAsync(counts_dev, 0, (size_t)nshell * 12 * nside * nside * 4, c->stream));
   return UFC_OK;
+}
+
+extern "C" {
+
+ufc_status ufc_bin_snapshots(ufc_ctx* c, const float* const* xyz_dev, const int64_t* n,
+                             const ufc_box* snap_geom, int32_t nsnap, const int32_t* snap_of_shell,
+                             const double* chi_edges, int32_t nshell, int32_t nside, int32_t flags,
+                             int32_t* counts_dev) {
+  return bin_snapshot_runs(
+      c, "ufc_bin_snapshots", xyz_dev, n, snap_geom, nsnap, snap_of_shell, chi_edges, nshell,
+      nside, flags, counts_dev,
+      [&](const float* const* rx, const int64_t* rn, const ufc_box* rb, int nrun, int32_t f) {
+        return run_keys_pipeline(c, 1, rx, rn, rb, nrun, chi_edges, nshell, nside, f, counts_dev,
+                                 nullptr, nullptr);
+      });
+}
+
+ufc_status ufc_bin_snapshots_host(ufc_ctx* c, const float* const* xyz_host, const int64_t* n,
+                                  const ufc_box* snap_geom, int32_t nsnap,
+                                  const int32_t* snap_of_shell, const double* chi_edges,
+                                  int32_t nshell, int32_t nside, int32_t flags, int64_t chunk,
+                                  int32_t* counts_dev) {
+  if (c) {
+    cudaSetDevice(c->device);
+    cudaStreamCaptureStatus cs;
+    UFC_CUDA(c, cudaStreamIsCapturing(c->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return set_err(c, UFC_ERR_UNSUPPORTED, "ufc_bin_snapshots_host cannot be captured into a graph");
+  }
+  if (chunk < 1) return c ? set_err(c, UFC_ERR_ARG, "chunk must be >= 1") : UFC_ERR_ARG;
+  return bin_snapshot_runs(
+      c, "ufc_bin_snapshots_host", xyz_host, n, snap_geom, nsnap, snap_of_shell, chi_edges,
+      nshell, nside, flags, counts_dev,
+      [&](const float* const* rx, const int64_t* rn, const ufc_box* rb, int nrun, int32_t f) {
+        return run_bin_stream(c, rx, rn, rb, nrun, chi_edges, nshell, nside, f, chunk,
+                              counts_dev);
+      });
 }
 
 ufc_status ufc_bin_info(ufc_ctx* c, int64_t info[4]) {
