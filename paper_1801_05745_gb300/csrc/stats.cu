@@ -230,7 +230,9 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
 // column of the tile's pixels, accumulating q n in 64-bit integers (the
 // tile's counts read a second time, mostly from L2).  A bound on the
 // accumulated magnitudes (pixels per lane x tile maximum count x 2^22 per
-// tile) triggers a flush before any 64-bit sum could overflow.
+// tile) triggers a flush before any 64-bit sum could overflow.  More than 96
+// shells take one launch per window of 96 shells (phase 1 reads all shells
+// in each).
 constexpr int kAdjThreads = 1024;         // 32 warps, 4096-pixel tiles
 constexpr int kAdjSpw = 3;                // shells per warp in phase 2 (nshell <= 96)
 
@@ -238,7 +240,7 @@ template <bool USE_G>
 __global__ void __launch_bounds__(kAdjThreads, 1)
 k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
            double* __restrict__ rows_out, double* __restrict__ sumpart,
-           unsigned long long* range_flag) {
+           unsigned long long* range_flag, int s0) {
   extern __shared__ __align__(16) uint8_t adj_sm[];
   constexpr int T = kAdjThreads, NW = T / 32, TP = 4 * T;
   int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP] quantised e, e^2, g
@@ -269,7 +271,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
   auto flush = [&](int s1, int s2, int s3) {
 #pragma unroll
     for (int k = 0; k < kAdjSpw; ++k) {
-      const int b = w + NW * k;
+      const int b = s0 + w + NW * k;
       long long a[NQ + 1];
 #pragma unroll
       for (int j = 0; j <= NQ; ++j) { a[j] = warp_sum_ll(acc[k][j]); acc[k][j] = 0; }
@@ -407,7 +409,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
       for (int j = 0; j < NQ; ++j) qv[j] = q_s[j * TP + pi];
 #pragma unroll
       for (int k = 0; k < kAdjSpw; ++k) {
-        const int b = w + NW * k;
+        const int b = s0 + w + NW * k;
         if (b < S) {
           const long long n = counts[(size_t)b * npix + base + pi];
 #pragma unroll
@@ -422,7 +424,8 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
   flush(scale(Ms[0]), scale(Ms[1]), scale(Ms[2]));
   __syncthreads();
   double* dst = rows_out + (size_t)blockIdx.x * 4 * S;
-  for (int b = threadIdx.x; b < S; b += T) {
+  const int s_end = min(S, s0 + kAdjSpw * NW);   // the shells of this launch: [s0, s_end)
+  for (int b = s0 + threadIdx.x; b < s_end; b += T) {
     dst[4 * b + 0] = i128_to_d(rows[b].s[0], kFrac1);
     dst[4 * b + 1] = i128_to_d(rows[b].s[1], kFrac2);
     dst[4 * b + 2] = USE_G ? i128_to_d(rows[b].s[2], kFrac3) : 0.0;
@@ -786,8 +789,6 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
   if (s) return s;
   if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
   if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
-  if (S > kAdjMaxShells)
-    return set_err(c, UFC_ERR_UNSUPPORTED, "the adjoint supports nshell <= %d", kAdjMaxShells);
   const int npix = 12 * nside * nside;
   Coef cf;
   make_coef(A, C, S, npix, cf);
@@ -808,16 +809,22 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
                        (size_t)S * sizeof(AdjRow);
   {
     ProfScope ps_(c, "k_adj_main");
-    if (g) {
+    if (g)
       UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-      k_adj_main<true><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, g, rows, sums,
-                                                                  &bc->range);
-    } else {
+    else
       UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-      k_adj_main<false><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, nullptr, rows, sums,
-                                                                   &bc->range);
+    // one launch per window of kAdjMaxShells shells (a launch's warps own
+    // 3 shells each); every launch recomputes e from all shells and writes
+    // the same power sums
+    for (int s0 = 0; s0 < S; s0 += kAdjMaxShells) {
+      if (g)
+        k_adj_main<true><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, g, rows, sums,
+                                                                    &bc->range, s0);
+      else
+        k_adj_main<false><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, nullptr, rows,
+                                                                     sums, &bc->range, s0);
     }
   }
   UFC_CUDA(c, cudaGetLastError());

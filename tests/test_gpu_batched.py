@@ -130,10 +130,14 @@ def test_forced_paths_agree_and_autotune(orc, tmp_path, monkeypatch):
     assert autotune.choose_bin_path(ctx, [xd], [b], chi, 128) == p1   # cached
 
 
-def test_autograd_matches_oracle(orc):
+@pytest.mark.parametrize("nshell", [10, 140])
+def test_autograd_matches_oracle(orc, nshell):
+    """Gradients through torch.autograd against the oracle's complex step;
+    140 shells (the paper's Delta z = 0.01 from 0.1 to 1.5) take the
+    adjoint's launches over two windows of shells."""
     api, ctx = api_ctx()
     from paper_1801_05745_gb300 import autodiff
-    nside, nshell, n = 32, 10, 300_000
+    nside, n = 32, 300_000
     x1 = synth.particles_numpy(n, 2000.0, 5.0, 61)
     x2 = synth.particles_numpy(n, 6400.0, 20.0, 62)
     z = np.linspace(0.1, 1.5, nshell + 1)
