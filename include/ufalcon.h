@@ -180,7 +180,8 @@ ufc_status ufc_keys(ufc_ctx *ctx, const float *xyz_dev, int64_t n,
 
 /* Count maps of one lightcone made of nbox boxes: box k's particles are
  * xyz_dev[k] (n[k] of them).  counts_dev [nshell][12 nside^2] is overwritten
- * (or added to with UFC_BIN_ACCUMULATE).  nshell * 12 nside^2 < 2^30.
+ * (or added to with UFC_BIN_ACCUMULATE).  nshell * 12 nside^2 < 2^31 (the
+ * paper's 140 shells at Nside 1024 included).
  * The library picks the output path (L2 atomics for maps up to 32 MB, the
  * dense-key scatter and shared-memory histograms above); the FORCE flags
  * override the choice (used by the autotuner).  Results are identical. */

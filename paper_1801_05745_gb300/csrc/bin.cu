@@ -1365,8 +1365,9 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1)))
     return set_err(c, UFC_ERR_ARG, "nside must be a power of two in [1,%d]", UFC_MAX_NSIDE);
   const int64_t npix = 12ll * nside * nside;
-  if ((int64_t)nshell * npix >= (1ll << 30))
-    return set_err(c, UFC_ERR_ARG, "nshell * 12 nside^2 must be < 2^30");
+  // keys shell * npix + pix are int32 (negative values mark outside/invalid)
+  if ((int64_t)nshell * npix >= (1ll << 31))
+    return set_err(c, UFC_ERR_ARG, "nshell * 12 nside^2 must be < 2^31");
   ShellTable st;
   ufc_status s = make_table(c, chi, nshell, st);
   if (s) return s;

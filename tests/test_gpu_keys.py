@@ -7,6 +7,8 @@ import pytest
 from paper_1801_05745_gb300 import synth
 from tests.gpu_common import api_ctx, boundary_points, both_boxes, to_dev
 
+torch = pytest.importorskip("torch")
+
 pytestmark = pytest.mark.gpu
 
 
@@ -117,3 +119,25 @@ def test_refine_queue_overflow(orc, path):
     info = ctx.bin_info()
     cap1 = max(1 << 20, n // 16)
     assert info["refined"] > cap1 // 2, info          # the queue was (nearly) full
+
+
+def test_paper_shells_at_nside_1024(orc):
+    """The paper's own map geometry: 140 shells of dz = 0.01 from z = 0.1 to
+    1.5 at Nside 1024 (keys above 2^30).  Keys equal the oracle's; the
+    count maps (dense path, 7 GB) hold exactly the oracle's keys."""
+    api, ctx = api_ctx()
+    nside, nshell, n, L = 1024, 140, 2_000_000, 6400.0
+    z = np.array([(10 + b) / 100 for b in range(nshell + 1)])
+    chi = orc.chi_edges(0.3, 0.7, 1, z)
+    xyz = synth.particles_numpy(n, L, 20.0, synth.seed_for(31, 0, 0))
+    ba, bo = both_boxes(api, orc, L, [L / 2] * 3, n, 0, nshell)
+    xd = to_dev(xyz)
+    got = ctx.keys(xd, ba, chi, nside).cpu().numpy()
+    ref = orc.keys(xyz, bo, chi, nside)
+    assert np.array_equal(got, ref.astype(np.int32))
+    assert ref.max() >= 1 << 30
+    counts = ctx.bin([xd], [ba], chi, nside, path="dense").view(-1)
+    keys, cnt = np.unique(ref[ref >= 0], return_counts=True)
+    assert int(counts.sum()) == int(cnt.sum())
+    kt = torch.from_numpy(keys).cuda()
+    assert torch.equal(counts[kt].cpu(), torch.from_numpy(cnt.astype(np.int32)))
