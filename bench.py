@@ -472,6 +472,7 @@ def main():
     ctx.profile(False)
     prof = ctx.profile_read()
     clk = clocks.stop()
+    ctx.synchronize()     # raises if a bounded device wait ran out (counts incomplete)
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
         t = torch.tensor([ms], device=dev)

@@ -103,8 +103,17 @@ ufc_status ufc_create(ufc_ctx **ctx, int32_t device);
 ufc_status ufc_destroy(ufc_ctx *ctx);
 /* Sets the CUDA stream (a cudaStream_t, NULL = legacy default stream). */
 ufc_status ufc_set_stream(ufc_ctx *ctx, void *stream);
-/* Waits for all work enqueued by this context; reports device-side errors. */
+/* Waits for all work enqueued by this context; reports device-side errors:
+ * UFC_ERR_TIMEOUT when a bounded wait of the fast binning stage (on its
+ * particle copies) ran out since the last report, in which case that
+ * binning call's counts are incomplete.  The context stays usable. */
 ufc_status ufc_synchronize(ufc_ctx *ctx);
+/* Self-test of the device-side failure report (no counterpart in the
+ * paper): one kernel waits on a barrier that nothing completes, gives up
+ * after `limit` polls (1 <= limit <= 2^28) and reports it; the next
+ * ufc_synchronize returns UFC_ERR_TIMEOUT.  Faults nothing and leaves the
+ * context usable.  Asynchronous. */
+ufc_status ufc_wait_selftest(ufc_ctx *ctx, int64_t limit);
 /* Message of the last error on this context ("" if none). */
 const char *ufc_last_error(const ufc_ctx *ctx);
 /* Pre-allocates the workspace of a ufc_bin call with up to two boxes and up

@@ -78,6 +78,7 @@ _SIGS = {
     "ufc_destroy": [P],
     "ufc_set_stream": [P, P],
     "ufc_synchronize": [P],
+    "ufc_wait_selftest": [P, I64],
     "ufc_reserve": [P, I32, I32, I64],
     "ufc_chi_edges": [ctypes.POINTER(Cosmo), P, I32, P],
     "ufc_z_of_chi": [ctypes.POINTER(Cosmo), P, I32, P],
@@ -231,6 +232,12 @@ class Context:
 
     def synchronize(self):
         self._ck(_lib.ufc_synchronize(self.h), "ufc_synchronize")
+
+    def wait_selftest(self, limit: int = 1000):
+        """Makes one device-side bounded wait run out (ufc_wait_selftest); the
+        next synchronize() raises UfcError with status UFC_ERR_TIMEOUT."""
+        self._stream()
+        self._ck(_lib.ufc_wait_selftest(self.h, int(limit)), "ufc_wait_selftest")
 
     def profile(self, on: bool = True):
         """Bracket every library kernel launch with CUDA events (tracing)."""

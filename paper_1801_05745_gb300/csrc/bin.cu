@@ -431,6 +431,28 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Self-test of the bounded wait: an mbarrier that expects one arrival which
+// never comes; the wait gives up after `limit` polls and reports it like the
+// fast stage does (the kernel then returns normally).
+__global__ void k_wait_selftest(long long limit, unsigned long long* timeouts) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  bool ok = false;
+  for (long long i = 0; i < limit && !ok; ++i) ok = mbar_try_wait(&bar, 0u);
+  if (!ok) atomicAdd(timeouts, 1ull);
+}
+
+ufc_status run_wait_selftest(ufc_ctx* c, int64_t limit) {
+  if (limit < 1 || limit > kWaitLimit)
+    return set_err(c, UFC_ERR_ARG, "limit must be in [1, %lld]", (long long)kWaitLimit);
+  BinCounters* bc = reinterpret_cast<BinCounters*>(c->counters);
+  k_wait_selftest<<<1, 32, 0, c->stream>>>(limit, &bc->timeouts);
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
 // The FP64 procedure for an image whose queue slot did not fit (rare); kept
 // out of line so that the fast stage's register budget is not spent on it.
 __device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo, int32_t hi,
@@ -1457,7 +1479,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   qs.q2 = (uint64_t*)ws_get(c, kSlotQueue2, z.cap2 * 8);
   if (!qs.q1 || !qs.q2) return UFC_ERR_ALLOC;
   qs.cnt = (BinCounters*)c->counters;
-  UFC_CUDA(c, cudaMemsetAsync(qs.cnt, 0, sizeof(BinCounters), c->stream));
+  UFC_CUDA(c, cudaMemsetAsync(qs.cnt, 0, offsetof(BinCounters, timeouts), c->stream));
   // overflow bits: one per particle of the boxes without periodic images
   int64_t nbits = 0;
   for (int k = 0; k < nbox; ++k) {

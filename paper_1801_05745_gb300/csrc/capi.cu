@@ -36,6 +36,7 @@ ufc_status run_alm2cl(ufc_ctx* c, const double* alm, int lmax, double* cl);
 ufc_status run_cl_bin(ufc_ctx* c, const double* cl, int lmax, int lmin, int dl, int nbins,
                       double* out);
 ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float* map);
+ufc_status run_wait_selftest(ufc_ctx* c, int64_t limit);
 ufc_status run_bin_stream(ufc_ctx* c, const float* const* xyz_host, const int64_t* n,
                           const ufc_box* boxes, int nbox, const double* chi, int nshell,
                           int nside, int flags, int64_t chunk, int32_t* counts);
@@ -190,8 +191,37 @@ ufc_status ufc_set_stream(ufc_ctx* c, void* stream) {
 
 ufc_status ufc_synchronize(ufc_ctx* c) {
   if (!c) return UFC_ERR_ARG;
-  UFC_CUDA(c, cudaStreamSynchronize(c->stream));
+  cudaSetDevice(c->device);
+  // the timeouts of this context and of its batched lanes; each counter is
+  // read and cleared on its own stream, after the work enqueued there
+  unsigned long long t[ufc_ctx::kMaxLanes + 1] = {};
+  ufc_ctx* owners[ufc_ctx::kMaxLanes + 1] = {c};
+  int n = 1;
+  for (int k = 0; k < ufc_ctx::kMaxLanes; ++k)
+    if (c->lanes[k]) owners[n++] = c->lanes[k];
+  for (int k = 0; k < n; ++k) {
+    BinCounters* bc = reinterpret_cast<BinCounters*>(owners[k]->counters);
+    UFC_CUDA(c, cudaMemcpyAsync(&t[k], &bc->timeouts, sizeof t[k], cudaMemcpyDeviceToHost,
+                                owners[k]->stream));
+    UFC_CUDA(c, cudaMemsetAsync(&bc->timeouts, 0, sizeof t[k], owners[k]->stream));
+  }
+  unsigned long long total = 0;
+  for (int k = 0; k < n; ++k) {
+    UFC_CUDA(c, cudaStreamSynchronize(owners[k]->stream));
+    total += t[k];
+  }
+  if (total)
+    return set_err(c, UFC_ERR_TIMEOUT,
+                   "%llu device-side bounded wait(s) ran out since the last report; the "
+                   "binning calls that met them have incomplete counts", total);
   return UFC_OK;
+}
+
+ufc_status ufc_wait_selftest(ufc_ctx* c, int64_t limit) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_wait_selftest(c, limit);
 }
 
 const char* ufc_last_error(const ufc_ctx* c) { return c ? c->err.c_str() : "no context"; }

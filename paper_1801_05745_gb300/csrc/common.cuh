@@ -77,9 +77,11 @@ struct BinCounters {
   unsigned long long q2;        // entries in queue 2
   unsigned long long dense;     // keys written by the compaction stage
   unsigned long long ntiles;    // tiles of the second scatter pass
-  unsigned long long timeouts;  // bounded device waits that ran out
   unsigned long long range;     // adjoint inputs outside the fixed-point range
   unsigned long long ovf;       // images marked for the exact pass (queue 1 was full)
+  // bounded device waits that ran out: last, so that a binning call's reset
+  // (everything before it) keeps it until ufc_synchronize reports it
+  unsigned long long timeouts;
 };
 
 // Queue entry of an undecided particle image: box (4 bits), image (13 bits),

@@ -69,3 +69,51 @@ def test_shard_range_partitions():
             spans = [parallel.shard_range(n, r, world) for r in range(world)]
             assert spans[0][0] == 0 and spans[-1][1] == n
             assert all(spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+
+
+def _failing_worker(rank, world, port, tmp, mode):
+    """Rank 1 fails on the host before the map combination: it raises
+    ("raise") or never joins the all-reduce ("absent").  Rank 0 must get an
+    error from its collective within the short process-group timeout instead
+    of waiting forever."""
+    import datetime
+    import time
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=3))
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from paper_1801_05745_gb300 import parallel
+    if rank == 1:
+        if mode == "raise":
+            raise RuntimeError("rank 1: simulated failure before the all-reduce")
+        time.sleep(10)
+        os._exit(0)
+    t0 = time.monotonic()
+    try:
+        parallel.allreduce_counts(torch.ones(64, dtype=torch.int32))
+        status = 0
+    except Exception:
+        status = 1
+    np.save(os.path.join(tmp, "r0.npy"), np.array([status, time.monotonic() - t0]))
+    os._exit(0)
+
+
+@pytest.mark.parametrize("mode", ["raise", "absent"])
+def test_failed_rank_surfaces_as_error(tmp_path, mode):
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, str(tmp_path), mode))
+             for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(60)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung past the process-group timeout"
+    status, secs = np.load(tmp_path / "r0.npy")
+    assert status == 1, "rank 0's all-reduce completed without its peer"
+    assert secs < 30
