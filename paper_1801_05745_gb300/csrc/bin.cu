@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -484,7 +485,7 @@ constexpr int kWThreads = 768;
 constexpr int kWChunk = 3072;                  // particles per chunk (36 KB)
 constexpr int kWStages = 2;
 constexpr int kWWarps = kWThreads / 32;        // 24
-constexpr int kWPerWarp = kWChunk / kWWarps;   // 64
+constexpr int kWPerWarp = kWChunk / kWWarps;   // 128
 constexpr int kWGroups = kWPerWarp / 32;
 constexpr int kWList = 64;                     // entries of one pending list
 constexpr int kWAgeFlush = 1024;
@@ -580,6 +581,7 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
     const int nvalid = last ? 0 : (fullc ? kWChunk : tail_n);
     const int nsmem = fullc ? kWChunk : tail_smem;      // particles inside the bulk copy
     const float* buf = ring + s * 3 * kWChunk;
+    const uint32_t kqtag = uint32_t(kq & 4095) << 20;
     const int nimg = last ? 1 : bg.nimg;
     const bool drain_all = last || !carry || ((k & (kWAgeFlush - 1)) == kWAgeFlush - 1);
     const int ng = last ? 0 : kWGroups;                  // groups of 32 particles to classify
@@ -598,48 +600,66 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
         if (h < ng) {
           // ---- A: classify 32 particles of this warp's slice
           const int j = warp * kWPerWarp + 32 * h + lane;
-          const bool have = j < nvalid;
-          float x = 0.f, y = 0.f, zc = 0.f;
-          if (j < nsmem) {
+          bool have;
+          float x, y, zc;
+          if (fullc) {                           // every particle inside the bulk copy
+            have = true;
             x = buf[3 * j];
             y = buf[3 * j + 1];
             zc = buf[3 * j + 2];
-          } else if (have) {                     // ragged tail outside the bulk copy
-            x = __ldg(xyz + 3 * (base + j));
-            y = __ldg(xyz + 3 * (base + j) + 1);
-            zc = __ldg(xyz + 3 * (base + j) + 2);
+          } else {
+            have = j < nvalid;
+            x = 0.f; y = 0.f; zc = 0.f;
+            if (j < nsmem) {
+              x = buf[3 * j];
+              y = buf[3 * j + 1];
+              zc = buf[3 * j + 2];
+            } else if (have) {                   // ragged tail outside the bulk copy
+              x = __ldg(xyz + 3 * (base + j));
+              y = __ldg(xyz + 3 * (base + j) + 1);
+              zc = __ldg(xyz + 3 * (base + j) + 2);
+            }
           }
           const float dx = (x + sx) + lx;
           const float dy = (y + sy) + ly;
           const float dz = (zc + sz) + lz;
           const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-          int cls = 0;                           // 0 outside, 1 undecided, 2 belt, 3 cap, 4 invalid
-          int32_t b = 0;
-          if (have) {
-            if (!(r2 <= 3.0e38f)) {              // NaN or overflow: inspect the coordinates
-              if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) cls = 4;
-            } else if (!(r2 >= bd.r2_min)) {     // near the observer (r == 0 is invalid)
-              cls = 1;
-            } else {
-              b = shell_lut(fs, lo, hi, lp.scale, r2);
-              if (b == -2) cls = 1;
-              else if (b >= 0) {
-                const float dz2 = dz * dz;
-                cls = dz2 <= bd.z_eq2 * r2 ? 2 : (dz2 > bd.z_cap2 * r2 ? 3 : 1);
-              }
+          // classification without branches but for the rare edge scan:
+          // outside, undecided (c1), belt (c2) or cap (c3)
+          const bool fin = r2 <= 3.0e38f;                // false for NaN and overflow
+          const bool near = !(r2 >= bd.r2_min);          // near the observer (r == 0 is invalid)
+          const float v = fminf(r2 * lp.scale, float(kLut - 1));
+          const int bin = __float_as_int(v + 8388608.0f) - 0x4B000000;
+          const uint32_t e = fs.lut[bin];
+          int a = int(e & 0x7FFFu) - 1;
+          bool band = false;
+          if ((e & kLutScan) && fin) {           // rare: scan the edges (finite r2 ends at +inf)
+            for (;;) {
+              if (r2 < fs.lo2[a + 1]) break;
+              if (r2 < fs.hi2[a + 1]) { band = true; break; }
+              ++a;
             }
           }
-          if (cls == 4 && img == 0) ++fc.n_invalid;
-          const uint32_t meta = uint32_t(b & 255) | (uint32_t(j) << 8) | (uint32_t(kq & 4095) << 20);
+          const bool inshell = uint32_t(a - lo) < uint32_t(hi - lo);
+          const float dz2 = dz * dz;
+          const bool eqz = dz2 <= bd.z_eq2 * r2;
+          const bool capz = dz2 > bd.z_cap2 * r2;
+          const bool dec = have && fin && !near && !band && inshell;
+          const bool c2 = dec && eqz;
+          const bool c3 = dec && capz;
+          const bool c1 = have && fin && (near || band || (inshell && !eqz && !capz));
+          if (have && !fin && img == 0)          // NaN or overflow: inspect the coordinates
+            if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) ++fc.n_invalid;
+          const uint32_t meta = uint32_t(a & 255) | (uint32_t(j) << 8) | kqtag;
           const float4 ent = make_float4(dx, dy, dz, __uint_as_float(meta));
-          const unsigned meq = __ballot_sync(0xFFFFFFFFu, cls == 2);
-          const unsigned mcap = __ballot_sync(0xFFFFFFFFu, cls == 3);
-          if (cls == 2) list_eq[(he + ne + __popc(meq & lt_mask)) & (kWList - 1)] = ent;
-          if (cls == 3) list_cap[(hc + nc + __popc(mcap & lt_mask)) & (kWList - 1)] = ent;
+          const unsigned meq = __ballot_sync(0xFFFFFFFFu, c2);
+          const unsigned mcap = __ballot_sync(0xFFFFFFFFu, c3);
+          if (c2) list_eq[(he + ne + __popc(meq & lt_mask)) & (kWList - 1)] = ent;
+          if (c3) list_cap[(hc + nc + __popc(mcap & lt_mask)) & (kWList - 1)] = ent;
           ne += __popc(meq);
           nc += __popc(mcap);
           // undecided images wait in queue 1; outside/invalid are final
-          if (!queue_push(fc.qc, cls == 1, qbase + uint64_t(j), qs.q1, qs.cap1, &qs.cnt->q1)) {
+          if (!queue_push(fc.qc, c1, qbase + uint64_t(j), qs.q1, qs.cap1, &qs.cnt->q1)) {
             const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
                                               bg.sh64[1][jj], bg.sh64[2][kk]);
             if (kx == kKeyInvalid) ++fc.n_invalid;
@@ -654,8 +674,9 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
               }
             }
             if (MODE == kModeKeys && have) o.keys[p_off + base + j] = kx;
-          } else if (MODE == kModeKeys && have && cls != 2 && cls != 3) {
-            o.keys[p_off + base + j] = cls == 4 ? kKeyInvalid : (cls == 1 ? kKeyUndecided : kKeyOutside);
+          } else if (MODE == kModeKeys && have && !c2 && !c3) {
+            o.keys[p_off + base + j] = c1 ? kKeyUndecided
+                : ((!fin && !(isfinite(x) && isfinite(y) && isfinite(zc))) ? kKeyInvalid : kKeyOutside);
           }
         }
         __syncwarp();
