@@ -483,7 +483,8 @@ __device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo,
 // element p_off + p of the caller's array (chunked launches of ufc_bin_host).
 constexpr int kWThreads = 768;
 constexpr int kWChunk = 3072;                  // particles per chunk (36 KB)
-constexpr int kWStages = 2;
+constexpr int kWStages = 2;                    // the stage index of the ring loop is k & 1
+static_assert(kWStages == 2, "the ring loop takes the stage of chunk k as k & 1");
 constexpr int kWWarps = kWThreads / 32;        // 24
 constexpr int kWPerWarp = kWChunk / kWWarps;   // 128
 constexpr int kWGroups = kWPerWarp / 32;
@@ -564,11 +565,14 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
   int ii = 0, jj = 0, kk = 0;                  // current image
   bool aborted = false;
   int64_t k = 0;
+  // the shift of the only image when the box has no periodic images
+  const float hsx = fs.shf[0][0], hsy = fs.shf[1][0], hsz = fs.shf[2][0];
+  const float hlx = fs.shlo[0][0], hly = fs.shlo[1][0], hlz = fs.shlo[2][0];
   for (; k <= mine; ++k) {
     const bool last = k == mine;               // the final pass only drains the lists
-    const int s = int(k % kWStages);
+    const int s = int(k & 1);                  // stage (two stages)
     if (!last) {
-      if (!mbar_wait(&bar[s], uint32_t((k / kWStages) & 1))) {   // every lane waits (bounded)
+      if (!mbar_wait(&bar[s], uint32_t(k >> 1) & 1u)) {   // every lane waits (bounded)
         aborted = true;
         abort_s = 1;
       }
@@ -592,8 +596,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
       if (img) {
         if (++kk == n1) { kk = 0; if (++jj == n1) { jj = 0; ++ii; } }
       }
-      const float sx = fs.shf[0][ii], sy = fs.shf[1][jj], sz = fs.shf[2][kk];
-      const float lx = fs.shlo[0][ii], ly = fs.shlo[1][jj], lz = fs.shlo[2][kk];
+      const float sx = IMAGES ? fs.shf[0][ii] : hsx, sy = IMAGES ? fs.shf[1][jj] : hsy,
+                  sz = IMAGES ? fs.shf[2][kk] : hsz;
+      const float lx = IMAGES ? fs.shlo[0][ii] : hlx, ly = IMAGES ? fs.shlo[1][jj] : hly,
+                  lz = IMAGES ? fs.shlo[2][kk] : hlz;
       const uint64_t qbase = qpack(box_id, img, p_off + base);   // + offset in the chunk
 #pragma unroll 1
       for (int h = 0; h < nsteps; ++h) {
@@ -1033,35 +1039,77 @@ constexpr int kScatThreads = 512;
 constexpr int kScatPer = 16;
 constexpr int kScatTile = kScatThreads * kScatPer;   // 8192 keys: ~64 B per destination
 
+// Two-buffer prefetch of scatter tiles: while a block works on one tile, the
+// bulk copy of its tile after next streams into the other buffer (tracked by
+// mbarriers with bounded waits).  A copy moves whole 16-byte units from a
+// 16-byte aligned address; the ragged end of a tile comes from plain loads.
+struct TilePrefetch {
+  uint64_t* bar;        // [2]
+  uint32_t* buf;        // [2][kScatTile + 4]
+  __device__ void init() {
+    if (threadIdx.x == 0) {
+      mbar_init(&bar[0], 1);
+      mbar_init(&bar[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  }
+  // keys [a0, a0 + nkeys) of src (a0 a multiple of 4) into buffer b
+  __device__ void issue(int b, const uint32_t* src, int64_t a0, int nkeys) {
+    const uint32_t bytes = uint32_t(nkeys * 4) & ~15u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bar[b], bytes);
+    if (bytes) bulk_g2s(buf + b * (kScatTile + 4), src + a0, bytes, &bar[b]);
+  }
+  __device__ bool wait(int b, int64_t use) { return mbar_wait(&bar[b], uint32_t(use & 1)); }
+};
+
 // Pass A: dense keys -> grouped array, group = bucket >> kGroupBits.  Two
-// blocks per SM: one block's loads overlap the other's counting, scan and
-// write-out phases.  Each destination's offset is kept as (global base -
-// tile start), one 64-bit shared load per key at write-out.
+// blocks per SM: one block's prefetch and global atomics overlap the other's
+// counting, scan and write-out phases.  Each destination's offset is kept as
+// (global base - tile start), one 64-bit shared load per key at write-out.
 __global__ void __launch_bounds__(kScatThreads, 2)
 k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* dense_count,
-                int64_t dense_cap, int ng, unsigned long long* __restrict__ gcur, uint32_t* __restrict__ out) {
-  extern __shared__ uint32_t sm[];
-  uint32_t* cnt = sm;                      // [ng]
-  uint32_t* start = sm + ng;               // [ng]
-  unsigned long long* base = (unsigned long long*)(sm + 2 * ng);  // [ng], 8-aligned
-  uint32_t* tile = (uint32_t*)(base + ng); // [kScatTile]
+                int64_t dense_cap, int ng, unsigned long long* __restrict__ gcur,
+                uint32_t* __restrict__ out, unsigned long long* timeouts) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  __shared__ __align__(8) uint64_t bar[2];
+  TilePrefetch pf{bar, sm};                // [2][kScatTile + 4]
+  uint32_t* tile = sm + 2 * (kScatTile + 4);                       // [kScatTile]
+  unsigned long long* base = (unsigned long long*)(tile + kScatTile);  // [ng], 8-aligned
+  uint32_t* cnt = (uint32_t*)(base + ng);  // [ng]
+  uint32_t* start = cnt + ng;              // [ng]
   const int64_t total = (int64_t)min(*dense_count, (unsigned long long)dense_cap);
   const int64_t ntiles = (total + kScatTile - 1) / kScatTile;
+  const int64_t mine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int shift = kOffBits + kGroupBits;
+  auto tile_keys = [&](int64_t i) -> int {   // keys of this block's i-th tile
+    const int64_t t0 = (blockIdx.x + i * gridDim.x) * (int64_t)kScatTile;
+    return int(min((int64_t)kScatTile, total - t0));
+  };
+  pf.init();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int64_t i = 0; i < mine && i < 2; ++i)
+      pf.issue(int(i), dense, (blockIdx.x + i * gridDim.x) * (int64_t)kScatTile, tile_keys(i));
   uint32_t v[kScatPer];
-  auto fetch = [&](int64_t t, uint32_t* dst) {
-    const int64_t t0 = t * kScatTile;
+  int64_t i = 0;
+  bool aborted = false;
+  for (; i < mine; ++i) {
+    const int b = int(i & 1);
+    const int64_t t0 = (blockIdx.x + i * gridDim.x) * (int64_t)kScatTile;
+    const int nk = tile_keys(i);
+    const int nsm = (nk * 4 & ~15) / 4;      // keys inside the bulk copy
+    const bool ok = pf.wait(b, i >> 1);
+    const uint32_t* kb = pf.buf + b * (kScatTile + 4);
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k) {
-      const int64_t i = t0 + k * kScatThreads + threadIdx.x;
-      dst[k] = (t < ntiles && i < total) ? __ldcs(dense + i) : kSentinel;
+      const int j = k * kScatThreads + threadIdx.x;
+      v[k] = j < nsm ? kb[j] : (j < nk ? __ldcs(dense + t0 + j) : kSentinel);
     }
-  };
-  int64_t tIdx = blockIdx.x;
-  for (; tIdx < ntiles; tIdx += gridDim.x) {
-    fetch(tIdx, v);
-    for (int i = threadIdx.x; i < ng; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) cnt[g] = 0;
+    if (__syncthreads_or(!ok)) { aborted = true; break; }   // buffer b is free again
+    if (threadIdx.x == 0 && i + 2 < mine)
+      pf.issue(b, dense, t0 + 2ll * gridDim.x * kScatTile, tile_keys(i + 2));
     uint32_t slot[kScatPer];
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k)
@@ -1076,12 +1124,16 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
       if (v[k] != kSentinel) tile[start[v[k] >> shift] + slot[k]] = v[k];
     __syncthreads();
     const uint32_t used = start[ng - 1] + cnt[ng - 1];
-    for (uint32_t i = threadIdx.x; i < used; i += blockDim.x) {
-      const uint32_t val = tile[i];
+    for (uint32_t q = threadIdx.x; q < used; q += blockDim.x) {
+      const uint32_t val = tile[q];
       const uint32_t g = val >> shift;
-      out[base[g] + i] = val;
+      out[base[g] + q] = val;
     }
     __syncthreads();
+  }
+  if (aborted && threadIdx.x == 0) {         // report; wait (bounded) for copies in flight
+    atomicAdd(timeouts, 1ull);
+    for (int64_t q = i; q < mine && q < i + 2; ++q) pf.wait(int(q & 1), q >> 1);
   }
 }
 
@@ -1124,34 +1176,62 @@ __global__ void __launch_bounds__(kTilesThreads) k_tiles(const int64_t* __restri
   if (blockIdx.x == 0 && threadIdx.x == 0) *ntiles = (unsigned long long)total;
 }
 
-// Pass B: grouped keys -> per-bucket u16 offsets (two blocks per SM, as pass A).
+// Pass B: grouped keys -> per-bucket u16 offsets (two blocks per SM and the
+// same tile prefetch as pass A; a tile starts anywhere, so its copy starts
+// at the 16-byte unit holding its first key, and the grouped array has 4
+// keys of slack at its end).
 __global__ void __launch_bounds__(kScatThreads, 2)
 k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ tiles,
                  const unsigned long long* __restrict__ ntiles_p,
-                 unsigned long long* __restrict__ bcur, uint16_t* __restrict__ out) {
+                 unsigned long long* __restrict__ bcur, uint16_t* __restrict__ out,
+                 unsigned long long* timeouts) {
   constexpr int NS = 1 << kGroupBits;
   extern __shared__ __align__(16) uint8_t smb[];
-  unsigned long long* base = reinterpret_cast<unsigned long long*>(smb);    // [NS]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ Tile tb[2];
+  TilePrefetch pf{bar, reinterpret_cast<uint32_t*>(smb)};                  // [2][kScatTile + 4]
+  unsigned long long* base =
+      reinterpret_cast<unsigned long long*>(smb + 2 * (kScatTile + 4) * 4);  // [NS]
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + NS);                  // [NS]
   uint32_t* start = cnt + NS;                                              // [NS]
   uint16_t* tile = reinterpret_cast<uint16_t*>(start + NS);                // [kScatTile]
   uint8_t* tsub = reinterpret_cast<uint8_t*>(tile + kScatTile);            // [kScatTile]
   const int64_t ntiles = (int64_t)*ntiles_p;
+  const int64_t mine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  auto tile_at = [&](int64_t i) -> const Tile& { return tiles[blockIdx.x + i * gridDim.x]; };
+  auto issue = [&](int b, const Tile& t) {   // thread 0
+    tb[b] = t;
+    const int64_t a0 = t.start & ~3ll;
+    pf.issue(b, grouped, a0, int(t.start - a0) + t.len + 3);   // whole units up to the end
+  };
+  pf.init();
+  __syncthreads();
+  Tile nxt{0, 0, 0};                          // thread 0: the tile after next
+  if (threadIdx.x == 0) {
+    for (int64_t i = 0; i < mine && i < 2; ++i) issue(int(i), tile_at(i));
+    if (mine > 2) nxt = tile_at(2);
+  }
+  __syncthreads();
   uint32_t v[kScatPer];
-  Tile T{0, 0, 0};
-  auto fetch = [&](int64_t ti, Tile& tt, uint32_t* dst) {
-    if (ti < ntiles) tt = tiles[ti]; else tt = Tile{0, 0, 0};
+  int64_t i = 0;
+  bool aborted = false;
+  for (; i < mine; ++i) {
+    const int b = int(i & 1);
+    const Tile T = tb[b];
+    const int64_t a0 = T.start & ~3ll;
+    const bool ok = pf.wait(b, i >> 1);
+    const uint32_t* kb = pf.buf + b * (kScatTile + 4) + (T.start - a0);   // the copy holds every key
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k) {
-      const int i = k * kScatThreads + threadIdx.x;
-      dst[k] = i < tt.len ? __ldcs(grouped + tt.start + i) : kSentinel;
+      const int j = k * kScatThreads + threadIdx.x;
+      v[k] = j < T.len ? kb[j] : kSentinel;
     }
-  };
-  int64_t ti = blockIdx.x;
-  for (; ti < ntiles; ti += gridDim.x) {
-    fetch(ti, T, v);
-    for (int i = threadIdx.x; i < NS; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
+    for (int q = threadIdx.x; q < NS; q += blockDim.x) cnt[q] = 0;
+    if (__syncthreads_or(!ok)) { aborted = true; break; }   // buffer b and tb[b] are free
+    if (threadIdx.x == 0 && i + 2 < mine) {
+      issue(b, nxt);
+      if (i + 3 < mine) nxt = tile_at(i + 3);
+    }
     uint32_t slot[kScatPer];
 #pragma unroll
     for (int k = 0; k < kScatPer; ++k)
@@ -1171,11 +1251,15 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
         tsub[pos] = uint8_t(sub);
       }
     __syncthreads();
-    for (int i = threadIdx.x; i < T.len; i += blockDim.x) {
-      const uint32_t sub = tsub[i];
-      out[base[sub] + i] = tile[i];
+    for (int q = threadIdx.x; q < T.len; q += blockDim.x) {
+      const uint32_t sub = tsub[q];
+      out[base[sub] + q] = tile[q];
     }
     __syncthreads();
+  }
+  if (aborted && threadIdx.x == 0) {         // report; wait (bounded) for copies in flight
+    atomicAdd(timeouts, 1ull);
+    for (int64_t q = i; q < mine && q < i + 2; ++q) pf.wait(int(q & 1), q >> 1);
   }
 }
 
@@ -1375,7 +1459,7 @@ ufc_status reserve_bin_workspace(ufc_ctx* c, int64_t fast_launches, int64_t tota
       !ws_get(c, kSlotOvf, (size_t)((total_img + 31) / 32) * 4))   // overflow bits (bound)
     return UFC_ERR_ALLOC;
   if (nside >= 64 && npix * nshell * 4 > (32ll << 20) && z.nb < (1ll << 17)) {
-    if (!ws_get(c, kSlotDense, z.dense_cap * 4) || !ws_get(c, kSlotGrouped, z.dense_cap * 4) ||
+    if (!ws_get(c, kSlotDense, z.dense_cap * 4) || !ws_get(c, kSlotGrouped, (z.dense_cap + 4) * 4) ||
         !ws_get(c, kSlotBucket16, z.dense_cap * 2) || !ws_get(c, kSlotHist, z.nb * 4) ||
         !ws_get(c, kSlotOff, (z.nb + 1) * 8) || !ws_get(c, kSlotCursors, (z.nb + z.ng + 1) * 8) ||
         !ws_get(c, kSlotTiles, (size_t)(z.dense_cap / kScatTile + z.ng + 1) * sizeof(Tile)))
@@ -1670,7 +1754,8 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   const int nb = plan.nbuckets, ng = plan.ng;
   int64_t* off = (int64_t*)ws_get(c, kSlotOff, (size_t)(nb + 1) * 8);
   unsigned long long* cur = (unsigned long long*)ws_get(c, kSlotCursors, (size_t)(nb + ng + 1) * 8);
-  uint32_t* grouped = (uint32_t*)ws_get(c, kSlotGrouped, (size_t)o.dense_cap * 4);
+  // 4 keys of slack: a tile's bulk copy ends at the 16-byte unit holding its last key
+  uint32_t* grouped = (uint32_t*)ws_get(c, kSlotGrouped, (size_t)(o.dense_cap + 4) * 4);
   uint16_t* b16 = (uint16_t*)ws_get(c, kSlotBucket16, (size_t)o.dense_cap * 2);
   const int64_t max_tiles = o.dense_cap / kScatTile + ng + 1;
   Tile* tiles = (Tile*)ws_get(c, kSlotTiles, (size_t)max_tiles * sizeof(Tile));
@@ -1686,26 +1771,26 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     ProfScope ps_(c, "k_cursors");
     k_cursors<<<(std::max(nb, ng) + 255) / 256, 256, 0, c->stream>>>(off, nb, ng, gcur, bcur);
   }
-  const int smemA = (3 * ng + 2) * 8 + kScatTile * 4;
+  const int smemA = 2 * (kScatTile + 4) * 4 + kScatTile * 4 + ng * 16;
   UFC_CUDA(c, cudaFuncSetAttribute(k_scatter_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    smemA));
   {
     ProfScope ps_(c, "k_scatter_group");
     k_scatter_group<<<2 * c->num_sms, kScatThreads, smemA, c->stream>>>(
-        o.dense, o.dense_count, o.dense_cap, ng, gcur, grouped);
+        o.dense, o.dense_count, o.dense_cap, ng, gcur, grouped, &qs.cnt->timeouts);
   }
   {
     ProfScope ps_(c, "k_tiles");
     k_tiles<<<c->num_sms, kTilesThreads, (size_t)(2 * ng + 2) * 8, c->stream>>>(off, nb, ng, tiles,
                                                                               ntiles);
   }
-  const int smemB = (1 << kGroupBits) * 16 + kScatTile * 3;
+  const int smemB = 2 * (kScatTile + 4) * 4 + (1 << kGroupBits) * 16 + kScatTile * 3;
   UFC_CUDA(c, cudaFuncSetAttribute(k_scatter_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    smemB));
   {
     ProfScope ps_(c, "k_scatter_bucket");
-    k_scatter_bucket<<<2 * c->num_sms, kScatThreads, smemB, c->stream>>>(grouped, tiles, ntiles,
-                                                                      bcur, b16);
+    k_scatter_bucket<<<2 * c->num_sms, kScatThreads, smemB, c->stream>>>(
+        grouped, tiles, ntiles, bcur, b16, &qs.cnt->timeouts);
   }
   const int smemH = kBlockPix * 4;
   UFC_CUDA(c, cudaFuncSetAttribute(k_hist_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
