@@ -50,8 +50,8 @@ struct ShellTable {
 struct Bands {
   float z_eq;       // |z| <= z_eq  => equatorial belt for certain
   float z_cap;      // |z| >  z_cap => polar cap for certain
-  float eq;         // absolute band of the equatorial edge coordinates
-  float cap;        // absolute band of the cap edge coordinates
+  float eq;         // 1/2 - (absolute band of the equatorial edge coordinates) - 2^-23
+  float cap;        // 1/2 - (absolute band of the cap edge coordinates) - 2^-23
   float ip_per_ir;  // band of the in-ring coordinate t*ir, per unit of ir
   float r2_min;     // below this squared radius: undecided
   float axy_min;    // max(|dx|,|dy|) below this: undecided

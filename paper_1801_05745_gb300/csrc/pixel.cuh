@@ -149,15 +149,19 @@ __device__ __forceinline__ float i2f_fast(int32_t k) {
   return __fsub_rn(__int_as_float(kMagicBits + k), kMagic);
 }
 
-// Floor of w when w is farther than `band` from every integer, else marks
-// the decision open.
-__device__ __forceinline__ int32_t floor_certain(float w, float band, bool& open) {
+// Floor of w when w is farther than a band b from every integer, else marks
+// the decision open; hmb <= 1/2 - b - 2^-23.  The fraction r = w - floor(w)
+// is exact for |w| < 2^22 (every caller's w is below N + 1 <= 8193 in
+// magnitude, or NaN, which opens the decision), and r - 1/2 rounds by at
+// most 2^-26, so |r - 1/2| <= hmb puts r strictly inside (b, 1 - b).
+__device__ __forceinline__ int32_t floor_certain(float w, float hmb, bool& open) {
   float f;
   const int32_t k = floor_fast(w, f);
-  const float rem = __fsub_rn(w, f);           // exact for |w| < 2^22
-  open |= !(rem >= band) || !(rem < 1.0f - band) || !(fabsf(w) < 4194304.0f);
+  const float rem = __fsub_rn(w, f);
+  open |= !(fabsf(__fsub_rn(rem, 0.5f)) <= hmb);
   return k;
 }
+constexpr float kHalfMargin = 0.5f - 0x1p-23f;   // 1/2 - 2^-23, exact
 
 // atan(q) * 2/pi for q in [0, 1] as q * P(q^2), P of degree 8 with
 // coefficients from a weighted least-squares fit of this library; Horner in
@@ -210,7 +214,7 @@ __device__ __forceinline__ int32_t pixel_fast_eq(int32_t N, const Bands& bd, flo
   const int32_t jp = I0 + floor_certain(fmaf(-n75, z, c), bd.eq, open);
   const int32_t jm = I0 + floor_certain(fmaf(n75, z, c), bd.eq, open);
   const int32_t ir = N + 1 + jp - jm;
-  open |= ir < 1 || ir > 2 * N + 1;
+  open |= uint32_t(ir - 1) > uint32_t(2 * N);
   const int32_t ks = 1 - (ir & 1);
   const int32_t ip = ((jp + jm - N + ks + 1 + 8 * N) >> 1) & (4 * N - 1);
   return open ? kKeyUndecided : 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
@@ -234,7 +238,7 @@ __device__ __forceinline__ int32_t pixel_fast_cap(int32_t N, const Bands& bd, fl
   open |= ir > N;
   ir = ir > N ? N : ir;
   const float fir = i2f_fast(ir);
-  const int32_t fl = floor_certain(az.sa * fir, bd.ip_per_ir * fir, open);
+  const int32_t fl = floor_certain(az.sa * fir, fmaf(-bd.ip_per_ir, fir, kHalfMargin), open);
   int32_t ip = az.base * ir + fl;              // in [-ir, 4.5 ir]
   const int32_t m = 4 * ir;
   ip = ip < 0 ? ip + m : (ip >= m ? ip - m : ip);
