@@ -66,6 +66,8 @@ struct Queues {
 struct WarpChunk {
   int64_t base;   // start of the warp's current chunk (-1: none)
   int32_t fill;
+  bool fits;      // the whole chunk lies below the capacity (always, with the
+                  // workspace's sizes; a chunk that did not would be dropped)
 };
 
 __device__ __forceinline__ uint32_t dense_key(int32_t key, int32_t npix, const KeyOut& o) {
@@ -90,18 +92,18 @@ __device__ __forceinline__ void dense_append(WarpChunk& wc, bool want, uint32_t 
     if (lane == 0) b = atomicAdd(o.dense_count, (unsigned long long)kChunk);
     wc.base = (int64_t)__shfl_sync(full, b, 0);
     wc.fill = 0;
+    wc.fits = wc.base + kChunk <= o.dense_cap;
   }
   int room = kChunk - wc.fill;
-  if (want && rank < room) {
-    int64_t idx = wc.base + wc.fill + rank;
-    if (idx < o.dense_cap) o.dense[idx] = v;
-  }
+  if (want && rank < room && wc.fits) o.dense[wc.base + (wc.fill + rank)] = v;
   if (cnt >= room) {
     unsigned long long b = 0;
     if (lane == 0) b = atomicAdd(o.dense_count, (unsigned long long)kChunk);
     int64_t nb = (int64_t)__shfl_sync(full, b, 0);
-    if (want && rank >= room && nb + (rank - room) < o.dense_cap) o.dense[nb + (rank - room)] = v;
+    const bool nfits = nb + kChunk <= o.dense_cap;
+    if (want && rank >= room && nfits) o.dense[nb + (rank - room)] = v;
     wc.base = nb;
+    wc.fits = nfits;
     wc.fill = cnt - room;
   } else {
     wc.fill += cnt;
