@@ -402,7 +402,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     // phase 2: lane ln takes pixels ln, ln + 32, ... of the tile (L2 re-reads)
     const int base = tile * TP;
     const int valid = min(TP, npix - base);
-#pragma unroll 4
+#pragma unroll 8
     for (int pi = ln; pi < valid; pi += 32) {
       int qv[NQ];
 #pragma unroll
