@@ -302,7 +302,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     f2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     int nmx = 0;
     if (have) {
-#pragma unroll 4
+#pragma unroll 6
       for (int b = 0; b < S; ++b) {
         const int4 n = c4[(size_t)b * ng + gi];
         const float h = ah_s[b], l = al_s[b];
@@ -402,7 +402,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     // phase 2: lane ln takes pixels ln, ln + 32, ... of the tile (L2 re-reads)
     const int base = tile * TP;
     const int valid = min(TP, npix - base);
-#pragma unroll 8
+#pragma unroll 16
     for (int pi = ln; pi < valid; pi += 32) {
       int qv[NQ];
 #pragma unroll
