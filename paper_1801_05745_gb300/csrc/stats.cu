@@ -302,7 +302,10 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     f2 a[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     int nmx = 0;
     if (have) {
-#pragma unroll 6
+      // shells unrolled for loads in flight (fewer with g, whose registers
+      // would spill more)
+      constexpr int kU1 = USE_G ? 6 : 8;
+#pragma unroll kU1
       for (int b = 0; b < S; ++b) {
         const int4 n = c4[(size_t)b * ng + gi];
         const float h = ah_s[b], l = al_s[b];
@@ -403,7 +406,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     const int base = tile * TP;
     const int valid = min(TP, npix - base);
 #pragma unroll 16
-    for (int pi = ln; pi < valid; pi += 32) {
+    for (int pi = ln; pi < valid; pi += 32) {          // 48 count loads in flight per lane
       int qv[NQ];
 #pragma unroll
       for (int j = 0; j < NQ; ++j) qv[j] = q_s[j * TP + pi];
