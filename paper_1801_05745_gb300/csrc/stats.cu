@@ -477,6 +477,16 @@ struct PdfParam {
   int32_t nbins;
 };
 
+// Sum of v[0], v[stride], ..., v[(n - 1) stride] by one warp in a fixed
+// order: lane l adds elements l, l + 32, ... in turn, then a butterfly; every
+// lane ends with the same value (each pairwise sum is formed by both lanes).
+__device__ __forceinline__ double warp_sum_fixed(const double* v, int n, int stride) {
+  double s = 0.0;
+  for (int i = threadIdx.x & 31; i < n; i += 32) s += v[(size_t)i * stride];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  return s;
+}
+
 __global__ void __launch_bounds__(kMT)
 k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ ksum_part,
           int nksum, PdfParam pp, double* __restrict__ part /*[grid][3]*/,
@@ -485,10 +495,9 @@ k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ 
   __shared__ double red[kMT / 32];
   __shared__ double mean_s;
   for (int i = threadIdx.x; i < pp.nbins + 3; i += blockDim.x) hist[i] = 0;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nksum; ++i) s += ksum_part[i];   // fixed order
-    mean_s = s / double(npix);
+  if (threadIdx.x < 32) {
+    const double s = warp_sum_fixed(ksum_part, nksum, 1);   // fixed order
+    if (threadIdx.x == 0) mean_s = s / double(npix);
   }
   __syncthreads();
   const double mean = mean_s;
@@ -536,20 +545,18 @@ k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ 
     if (hist[i]) atomicAdd(pdf + i, (unsigned long long)hist[i]);
 }
 
-// moments[10] from the partial sums (one thread, fixed order).
+// moments[10] from the partial sums (one warp, fixed orders).
 __global__ void k_moments_final(const double* __restrict__ ksum_part, int nksum,
                                 const double* __restrict__ part, int npart, int npix,
                                 double* __restrict__ m) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = 0; i < nksum; ++i) s += ksum_part[i];
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  // one warp, fixed orders (the mean as k_moments forms it)
+  const double s = warp_sum_fixed(ksum_part, nksum, 1);
+  const double s2 = warp_sum_fixed(part, npart, 3);
+  const double s3 = warp_sum_fixed(part + 1, npart, 3);
+  const double s4 = warp_sum_fixed(part + 2, npart, 3);
+  if (threadIdx.x != 0) return;
   const double N = double(npix);
-  double s2 = 0.0, s3 = 0.0, s4 = 0.0;
-  for (int i = 0; i < npart; ++i) {
-    s2 += part[3 * i];
-    s3 += part[3 * i + 1];
-    s4 += part[3 * i + 2];
-  }
   const double mu2 = s2 / N, mu3 = s3 / N, mu4 = s4 / N;
   m[0] = s / N;
   m[1] = mu2;
