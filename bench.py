@@ -365,8 +365,10 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": w.name, "particles": n_total, "nside": w.nside, "nshell": w.nshell},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{2 * m} particles binned per step (scaled to {n_total}) + one "
-                                   f"full Nside {w.nside} kappa map, moments and PDF"},
+                         "sample": f"per-step time EXTRAPOLATED: {2 * m} particles binned per "
+                                   f"step, their time scaled linearly to {n_total} particles, plus "
+                                   f"one full Nside {w.nside} kappa map, moments and PDF (timed "
+                                   f"whole); single thread"},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -116,6 +116,9 @@ ufc_status ufc_synchronize(ufc_ctx *ctx);
 ufc_status ufc_wait_selftest(ufc_ctx *ctx, int64_t limit);
 /* Message of the last error on this context ("" if none). */
 const char *ufc_last_error(const ufc_ctx *ctx);
+/* Device bytes the context holds (workspace, counters and the workspace of
+ * its batched-call lanes) in *bytes.  Host only; enqueues nothing. */
+ufc_status ufc_workspace_bytes(const ufc_ctx *ctx, int64_t *bytes);
 /* Pre-allocates the workspace of a ufc_bin call with up to two boxes and up
  * to n_max particle images (particles times images) at (nside, nshell), so
  * that such calls allocate nothing. */
@@ -307,7 +310,9 @@ ufc_status ufc_kappa_stats(ufc_ctx *ctx, const int32_t *counts_dev,
  *    process exits.  A launch that would need more returns UFC_ERR_CAPACITY.
  *  - The first call on a device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
- *    stream capture on the device.
+ *    stream capture on the device.  A cudaDeviceReset unloads the library's
+ *    device code and can move the array: after a reset this call must not
+ *    be used again in the same process.
  *  - All calls on a device share the array, which keeps the last call's
  *    contents: calls that overlap on the GPU (different streams or contexts)
  *    race on it.  Serialise them.  pdf_dev is cleared by the call itself. */

@@ -109,6 +109,7 @@ _SIGS = {
     "ufc_map_stats": [P, P, I32, D, D, I32, P, P],
     "ufc_profile_enable": [P, I32],
     "ufc_profile_read": [P, I32, P, P, P, P],
+    "ufc_workspace_bytes": [P, P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -258,6 +259,12 @@ class Context:
             nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
             out[nm] = (float(ms[i]), int(cnt[i]))
         return out
+
+    def workspace_bytes(self) -> int:
+        """Device bytes the context holds (ufc_workspace_bytes)."""
+        out = ctypes.c_int64()
+        self._ck(_lib.ufc_workspace_bytes(self.h, ctypes.byref(out)), "ufc_workspace_bytes")
+        return int(out.value)
 
     def reserve(self, nside: int, nshell: int, n_max: int):
         self._ck(_lib.ufc_reserve(self.h, nside, nshell, n_max), "ufc_reserve")

@@ -226,6 +226,20 @@ ufc_status ufc_wait_selftest(ufc_ctx* c, int64_t limit) {
 
 const char* ufc_last_error(const ufc_ctx* c) { return c ? c->err.c_str() : "no context"; }
 
+static int64_t held_bytes(const ufc_ctx* c) {
+  int64_t t = c->counters ? (int64_t)sizeof(BinCounters) : 0;
+  for (int s = 0; s < ufc_ctx::kSlots; ++s) t += (int64_t)c->cap[s];
+  for (int k = 0; k < ufc_ctx::kMaxLanes; ++k)
+    if (c->lanes[k]) t += held_bytes(c->lanes[k]);
+  return t;
+}
+
+ufc_status ufc_workspace_bytes(const ufc_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return UFC_ERR_ARG;
+  *bytes = held_bytes(c);
+  return UFC_OK;
+}
+
 ufc_status ufc_reserve(ufc_ctx* c, int32_t nside, int32_t nshell, int64_t n_max) {
   if (!c || nside < 1 || nshell < 1 || n_max < 0) return UFC_ERR_ARG;
   cudaSetDevice(c->device);

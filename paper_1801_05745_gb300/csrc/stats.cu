@@ -588,10 +588,13 @@ k_welford_update(const double* __restrict__ v, int nvec, int d, double* __restri
   double* dnew = sh + d;
   double* mean = st + 1;
   double* M2 = st + 1 + d;
+  // the count is read once and written once: every thread keeps n in a
+  // register, so no thread can see a count that another one already advanced
+  const double n0 = st[0];
+  __syncthreads();
   for (int r = 0; r < nvec; ++r) {
     const double* x = v + (size_t)r * d;
-    const double n = st[0] + 1.0;
-    __syncthreads();
+    const double n = n0 + double(r + 1);
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
       double delta = x[i] - mean[i];
       double mn = mean[i] + delta / n;
@@ -606,8 +609,8 @@ k_welford_update(const double* __restrict__ v, int nvec, int d, double* __restri
     __syncthreads();
     for (int i = threadIdx.x; i < d; i += blockDim.x) mean[i] += dold[i] / n;
     __syncthreads();
-    if (threadIdx.x == 0) st[0] = n;
   }
+  if (threadIdx.x == 0) st[0] = n0 + double(nvec);
 }
 
 __global__ void __launch_bounds__(1024)
@@ -972,9 +975,13 @@ ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, doub
   if (!v || !st || nvec < 0 || d < 1 || d > 8192)
     return set_err(c, UFC_ERR_ARG, "welford_update: bad arguments");
   if (nvec == 0) return UFC_OK;
+  const int smem = 2 * d * 8;   // up to 128 KB at d = 8192: above the 48 KB default
+  if (smem > 48 * 1024)
+    UFC_CUDA(c, cudaFuncSetAttribute(k_welford_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem));
   {
     ProfScope ps_(c, "k_welford_update");
-    k_welford_update<<<1, 1024, 2 * d * 8, c->stream>>>(v, nvec, d, st);
+    k_welford_update<<<1, 1024, smem, c->stream>>>(v, nvec, d, st);
   }
   UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;

@@ -108,6 +108,44 @@ def test_welford_vs_oracle_covariance(orc):
         assert np.allclose(corr.cpu().numpy(), r_o, rtol=1e-9, atol=1e-12)
 
 
+def test_welford_many_vectors_equal_one_at_a_time():
+    """One update over 64 vectors (the batched call's form) gives the state of
+    64 single-vector updates; repeated, so that a thread that reads the count
+    before another one advanced it (a race within the update) would show."""
+    api, ctx = api_ctx()
+    rng = np.random.default_rng(64)
+    d = 206
+    for rep in range(6):
+        v = rng.normal(size=(64, d)) * rng.uniform(0.1, 10.0, size=d) + rng.normal(size=d)
+        vt = torch.from_numpy(v).cuda()
+        st_many = api.welford_state(d)
+        st_one = api.welford_state(d)
+        ctx.welford_update(vt, st_many)
+        for r in range(64):
+            ctx.welford_update(vt[r:r + 1], st_one)
+        torch.cuda.synchronize()
+        assert st_many[0].item() == 64.0
+        assert torch.allclose(st_many, st_one, rtol=1e-12, atol=1e-12 * float(st_one.abs().max()))
+
+
+def test_welford_at_the_largest_statistics_vector(orc):
+    """d = 6 + 4096 PDF bins: the update's shared memory (2 d doubles) is
+    above the 48 KB default and must still launch; covariance against the
+    oracle on a few rows and columns."""
+    api, ctx = api_ctx()
+    rng = np.random.default_rng(4102)
+    d, R = 6 + 4096, 12
+    v = rng.normal(size=(R, d)) + 3.0
+    st = api.welford_state(d)
+    ctx.welford_update(torch.from_numpy(v).cuda(), st)
+    mean, cov, corr = ctx.welford_finalize(st, d, 1)
+    torch.cuda.synchronize()
+    cols = np.array([0, 1, 5, 6, 777, 4101])
+    m_o, c_o, _ = orc.covariance(v[:, cols], 1)
+    assert np.allclose(mean.cpu().numpy()[cols], m_o, rtol=1e-12, atol=1e-12)
+    assert np.allclose(cov.cpu().numpy()[np.ix_(cols, cols)], c_o, rtol=1e-9, atol=1e-12)
+
+
 @pytest.mark.parametrize("nside,nshell", [(64, 20), (256, 40)])
 def test_delta_map_stats_and_gradient(orc, nside, nshell):
     """Overdensity map of Eq. 7 through ufc_kappa_stats with the library's

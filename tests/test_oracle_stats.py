@@ -124,3 +124,71 @@ def test_complex_step_matches_central_difference(orc, kind, units):
         assert np.any(G[:, 1] != 0.0)
     if kind == 0:
         assert np.all(G[:, 2:] == 0.0)     # a source plane has no n(z) parameters
+
+
+# ---- pins of the unrounded FP64 statistics behind the gradient parity ----
+# (var = mu2 as the reading of Eq. 12, skew = mu3 / mu2^(3/2), and
+# <g, kappa> with kappa_p = sum_b A_b n_bp - C of Eq. 6)
+
+@pytest.mark.parametrize("kind,units", [(0, 1), (1, 1), (1, 0)])
+def test_f64_stats_against_numpy_and_scipy(orc, kind, units):
+    """var and skew against numpy / scipy.stats (population definitions,
+    an independent library), <g, kappa> against a numpy dot product of the
+    map built from the oracle's coefficients (which carry their own pins)."""
+    stats = pytest.importorskip("scipy.stats")
+    counts, z, boxes = _small_map(orc, nside=4, nshell=3, seed=11)
+    src = orc.make_source(kind=kind, z_s=1.1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    rng = np.random.default_rng(12)
+    g = rng.normal(size=counts.shape[1]).astype(np.float32)
+    A, B, C = orc.kappa_coeffs(0.3, 0.7, units, boxes, z, 4, src)
+    k = counts.astype(np.float64).T @ A - C
+    var, skew, gk = orc.kappa_stats_f64(counts, 4, 0.3, 0.7, units, boxes, z, src, g)
+    assert var == pytest.approx(np.var(k), rel=1e-12)
+    assert skew == pytest.approx(stats.skew(k, bias=True), rel=1e-11)
+    assert gk == pytest.approx(float(np.dot(g.astype(np.float64), k)),
+                               rel=1e-12, abs=1e-12 * float(np.abs(g).sum() * np.abs(k).max()))
+    # the map's -C shifts <g, kappa> by -C sum g, but neither var nor skew
+    ones = np.ones_like(g)
+    _, _, s1 = orc.kappa_stats_f64(counts, 4, 0.3, 0.7, units, boxes, z, src, ones)
+    ident = float((A * counts.sum(1)).sum()) - counts.shape[1] * C
+    assert s1 == pytest.approx(ident, rel=1e-12, abs=1e-12 * abs(C) * counts.shape[1])
+
+
+def test_f64_stats_one_nonzero_pixel_closed_form(orc):
+    """Hand-computed case: at Nside 1 (12 pixels) only pixel 0 holds
+    particles (20000 in shell 0, 10000 in shell 1, so that a is of the order
+    of C and the deviations lose no digits), so kappa takes a - C there and
+    -C elsewhere, a = 20000 A_0 + 10000 A_1.  Then mu2 = 11 a^2 / 144 and
+    skew = (N - 2) / sqrt(N - 1) = 10 / sqrt(11), whatever C is;
+    <1, kappa> = a - 12 C.  A divisor N - 1, a skew without the 3/2 power or
+    a dropped -C fails one of these."""
+    counts = np.zeros((2, 12), np.int32)
+    counts[0, 0], counts[1, 0] = 20000, 10000
+    z = np.array([0.3, 0.5, 0.7])
+    boxes = [orc.make_box(2000.0, [1000.0] * 3, 64 ** 3, 0, 2)]
+    src = orc.make_source(kind=0, z_s=1.2)
+    A, B, C = orc.kappa_coeffs(0.3, 0.7, 1, boxes, z, 1, src)
+    a = 20000 * A[0] + 10000 * A[1]
+    assert 0.1 < a / C < 10
+    var, skew, s1 = orc.kappa_stats_f64(counts, 1, 0.3, 0.7, 1, boxes, z, src,
+                                        np.ones(12, np.float32))
+    assert var == pytest.approx(11 * a * a / 144, rel=1e-14)
+    assert skew == pytest.approx(10 / np.sqrt(11), rel=1e-13)
+    assert s1 == pytest.approx(a - 12 * C, rel=1e-13)
+
+
+def test_f64_stats_h_independent_in_mpc_over_h(orc):
+    """Lengths in Mpc/h: c/H0 = 2997.92458 Mpc/h carries no h, so every
+    coefficient and hence every statistic is the same at any h; in Mpc they
+    change with h (the map is then evaluated directly from the coefficients)."""
+    counts, z, boxes = _small_map(orc, nside=4, nshell=3, seed=5)
+    src = orc.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)
+    g = np.linspace(-1, 1, counts.shape[1]).astype(np.float32)
+    a = orc.kappa_stats_f64(counts, 4, 0.3, 0.7, 1, boxes, z, src, g)
+    b = orc.kappa_stats_f64(counts, 4, 0.3, 0.55, 1, boxes, z, src, g)
+    assert np.array_equal(a, b)
+    c = orc.kappa_stats_f64(counts, 4, 0.3, 0.55, 0, boxes, z, src, g)
+    A, B, C = orc.kappa_coeffs(0.3, 0.55, 0, boxes, z, 4, src)
+    k = counts.astype(np.float64).T @ A - C
+    assert c[0] == pytest.approx(np.var(k), rel=1e-12)
+    assert abs(c[0] - a[0]) > 1e-3 * a[0]

@@ -19,12 +19,17 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _call_noalloc(api, ctx, counts, A, C, lo, hi, nbins):
-    S, npix = counts.shape
-    nside = int(round((npix / 12) ** 0.5))
+def _alloc_outputs(counts, nbins):
+    npix = counts.shape[1]
     kap = torch.full((npix,), float("nan"), dtype=torch.float32, device=counts.device)
     mom = torch.full((10,), float("nan"), dtype=torch.float64, device=counts.device)
     pdf = torch.full((nbins + 3,), -1, dtype=torch.int64, device=counts.device)
+    return kap, mom, pdf
+
+
+def _call_noalloc(api, ctx, counts, A, C, lo, hi, nbins, kap, mom, pdf):
+    S, npix = counts.shape
+    nside = int(round((npix / 12) ** 0.5))
     A = np.ascontiguousarray(A, dtype=np.float64)
     ctx._stream()
     st = api._lib.ufc_kappa_stats_noalloc(ctx.h, ctypes.c_void_p(counts.data_ptr()), S, nside,
@@ -33,12 +38,16 @@ def _call_noalloc(api, ctx, counts, A, C, lo, hi, nbins):
                                           ctypes.c_void_p(mom.data_ptr()),
                                           ctypes.c_void_p(pdf.data_ptr()))
     assert st == 0, api._lib.ufc_last_error(ctx.h)
-    return kap, mom, pdf
 
 
 @pytest.mark.parametrize("nside,nshell", [(64, 20), (16, 120)])
 def test_noalloc_matches_allocating_call_twice(orc, nside, nshell):
-    api, ctx = api_ctx()
+    """The variant runs first, on a fresh context that has never allocated
+    its partial-sum workspace: the context's device bytes and the device's
+    free memory stay unchanged across both calls; then the allocating call
+    on the same context (which does grow its workspace) gives the same map,
+    moments and PDF."""
+    api, shared = api_ctx()
     n = 300_000
     x1 = synth.particles_numpy(n, 2000.0, 5.0, 8801)
     x2 = synth.particles_numpy(n, 6400.0, 20.0, 8802)
@@ -47,16 +56,34 @@ def test_noalloc_matches_allocating_call_twice(orc, nside, nshell):
     split = int(np.argmin(np.abs(chi - 1000.0)))
     b1, _ = both_boxes(api, orc, 2000.0, [1000.0] * 3, n, 0, split)
     b2, _ = both_boxes(api, orc, 6400.0, [3200.0] * 3, n, split, nshell)
-    counts = ctx.bin([to_dev(x1), to_dev(x2)], [b1, b2], chi, nside)
+    counts = shared.bin([to_dev(x1), to_dev(x2)], [b1, b2], chi, nside)
     A, B, C = api.kappa_coeffs(api.make_cosmo(), [b1, b2], z, nside,
                                api.make_source(kind=1, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5))
-    kr, mr, pr = ctx.kappa_stats(counts, A, C, -0.05, 0.15, 64)
-    for _ in range(2):
-        kn, mn, pn = _call_noalloc(api, ctx, counts, A, C, -0.05, 0.15, 64)
+    ctx = api.Context(0)
+    try:
+        held0 = ctx.workspace_bytes()
+        outs = []
+        for i in range(2):
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info()[0]
+            kap, mom, pdf = _alloc_outputs(counts, 64)
+            torch.cuda.synchronize()
+            free1 = torch.cuda.mem_get_info()[0]
+            _call_noalloc(api, ctx, counts, A, C, -0.05, 0.15, 64, kap, mom, pdf)
+            torch.cuda.synchronize()
+            assert ctx.workspace_bytes() == held0
+            if i == 1:   # the first call may load the library's device code
+                assert torch.cuda.mem_get_info()[0] == free1, (free0, free1)
+            outs.append((kap, mom, pdf))
+        kr, mr, pr = ctx.kappa_stats(counts, A, C, -0.05, 0.15, 64)
         torch.cuda.synchronize()
-        assert torch.equal(kn, kr)
-        assert np.allclose(mn.cpu().numpy(), mr.cpu().numpy(), rtol=1e-12, atol=0)
-        assert torch.equal(pn, pr)
+        assert ctx.workspace_bytes() > held0   # the allocating call did allocate
+        for kn, mn, pn in outs:
+            assert torch.equal(kn, kr)
+            assert np.allclose(mn.cpu().numpy(), mr.cpu().numpy(), rtol=1e-12, atol=0)
+            assert torch.equal(pn, pr)
+    finally:
+        ctx.close()
 
 
 def test_noalloc_rejects_missing_outputs(orc):
