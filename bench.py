@@ -391,6 +391,13 @@ def main():
     ap.add_argument("--no-snapshots", action="store_true")
     ap.add_argument("--batched-real", type=int, default=150)
     ap.add_argument("--batched-side", type=int, default=512)
+    ap.add_argument("--nshell", type=int, default=None, help="shells (default 60)")
+    ap.add_argument("--path", default=None, choices=["direct", "dense"],
+                    help="force the binning output path (default: the library's choice)")
+    ap.add_argument("--split", default="realisation", choices=["realisation", "subvolume"],
+                    help="multi-GPU decomposition: each rank its own realisation (weak "
+                         "scaling), or each rank a shard of every box whose count maps are "
+                         "summed by one NCCL all-reduce inside the step (Sec. 2.4; strong)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -415,6 +422,9 @@ def main():
     w = workload(args.scale)
     if args.nside:
         w.nside = args.nside
+    if args.nshell:
+        w.nshell = args.nshell
+    sub = args.split == "subvolume"
     ctx = api.context(local)
     cosmo = api.make_cosmo(w.omega_m, w.h, 1)
     z, chi, split = shells(w, api=api)
@@ -425,8 +435,16 @@ def main():
     n_total = sum(b.n for b in w.boxes)
 
     dev = torch.device("cuda", local)
+    # realisation split: rank r draws realisation r; subvolume split: every
+    # rank draws realisation 0 and keeps its shard of each box (shard starts
+    # on multiples of 4 particles, so that the bulk copies stay aligned)
     parts = [synth.particles_torch(w.boxes[k].n, w.boxes[k].L, w.boxes[k].sigma,
-                                   synth.seed_for(3, rank, k), device=dev) for k in range(2)]
+                                   synth.seed_for(3, 0 if sub else rank, k), device=dev)
+             for k in range(2)]
+    if sub:
+        from paper_1801_05745_gb300 import parallel
+        parts = [p[slice(*parallel.shard_range(p.shape[0], rank, world, align=4))] for p in parts]
+    n_local = sum(p.shape[0] for p in parts)
     npix = 12 * w.nside ** 2
     counts = torch.empty((w.nshell, npix), dtype=torch.int32, device=dev)
     kap = torch.empty(npix, dtype=torch.float32, device=dev)
@@ -435,17 +453,23 @@ def main():
     vec = torch.empty(d, dtype=torch.float64, device=dev)
     ctx.reserve(w.nside, w.nshell, max(b.n for b in w.boxes))
 
+    def combine():                               # subvolume maps summed across ranks
+        if sub and dist:
+            dist.all_reduce(counts, op=dist.ReduceOp.SUM)
+
     # PDF range from a first map: mean +- 6 sigma, then fixed
-    ctx.bin(parts, boxes, chi, w.nside, counts=counts)
+    ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=args.path)
+    combine()
     _, mom, _ = ctx.kappa_stats(counts, A, C, -1.0, 1.0, w.pdf_bins, kappa=kap)
     m0 = mom.cpu().numpy()
     lo, hi = float(m0[0] - 6 * m0[1] ** 0.5), float(m0[0] + 6 * m0[1] ** 0.5)
 
     def step(host=None):
         if host is None:
-            ctx.bin(parts, boxes, chi, w.nside, counts=counts)
+            ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=args.path)
         else:                                    # host buffers through ufc_bin_host
-            ctx.bin_host(host, boxes, chi, w.nside, counts=counts)
+            ctx.bin_host(host, boxes, chi, w.nside, counts=counts, path=args.path)
+        combine()
         _, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, w.pdf_bins, kappa=kap)
         ctx.stats_vector(mom, pdf, out=vec)
         ctx.welford_update(vec.view(1, d), wstate)
@@ -481,39 +505,43 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    value = world * n_total / (ms * 1e-3) / 1e9
+    # realisation split: every rank a whole map; subvolume split: one map
+    value = (1 if sub else world) * n_total / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel (by total time in the timed region)
     peak, peak_src = hbm_peak()
     top = max(prof.items(), key=lambda kv: kv[1][0])
     launches = sum(c for _, c in prof.values())
     fast_ms, fast_n = prof.get("k_fast", (0.0, 0))
-    fast_bytes = 12.0 * n_total * args.steps            # particle reads, all launches
+    fast_bytes = 12.0 * n_local * args.steps            # this rank's particle reads, all launches
     bin_kernels = ["k_fast", "k_refine", "k_exact", "k_scan", "k_cursors", "k_scatter_group",
                    "k_tiles", "k_scatter_bucket", "k_hist_block"]
     bin_ms = sum(prof[k][0] for k in bin_kernels if k in prof) / args.steps
-    bin_bytes = 12.0 * n_total + 4.0 * w.nshell * npix
+    bin_bytes = 12.0 * n_local + 4.0 * w.nshell * npix
     kap_ms = sum(prof[k][0] for k in ("k_kappa", "k_moments", "k_moments_final") if k in prof)
     kap_launch = prof.get("k_kappa", (0.0, 1))
     roof = {
         "bound": "hbm", "kernel": "k_fast",
         "achieved": fast_bytes / (fast_ms * 1e-3) / 1e9 if fast_ms else None,
         "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs",
-        "traffic": FAST_TRAFFIC_PER_PARTICLE * n_total / 2,
+        "traffic": FAST_TRAFFIC_PER_PARTICLE * n_local / 2,
         "traffic_source": "ncu dram__bytes_read+write of a 2 x 512^3 capture, scaled per particle",
-        "per_launch_bytes": 12.0 * n_total / 2, "launches": fast_n,
+        "per_launch_bytes": 12.0 * n_local / 2, "launches": fast_n,
         "avg_launch_ms": fast_ms / max(fast_n, 1),
     }
     roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if sub else "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": w.name, "particles_per_gpu": n_total, "boxes": "2000 and 6400 Mpc/h",
+        "config": {"workload": w.name, "particles_per_gpu": n_local, "particles_per_map": n_total,
+                   "boxes": "2000 and 6400 Mpc/h", "path": args.path or "library choice",
                    "nside": w.nside, "nshell": w.nshell, "source": "Smail n(z) a=2 b=1.5 z0=0.5",
-                   "l2": f"inputs larger than L2 ({12 * n_total / 1e9:.1f} GB of particles per step)",
-                   "parallelism": f"realisations x{world}"},
-        "kappa_maps_per_s": world * 1e3 / ms,
+                   "l2": f"inputs larger than L2 ({12 * n_local / 1e9:.1f} GB of particles per step)",
+                   "parallelism": (f"subvolumes x{world} (count maps all-reduced)" if sub
+                                   else f"realisations x{world}")},
+        "kappa_maps_per_s": (1 if sub else world) * 1e3 / ms,
         "roofline": roof,
         "binning": {"ms": bin_ms, "algorithmic_bytes": bin_bytes,
                     "frac_of_peak": bin_bytes / (bin_ms * 1e-3) / 1e9 / peak if bin_ms else None,
@@ -554,10 +582,26 @@ def main():
             t = torch.tensor([ms_e], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_e = float(t.item())
-        line["e2e"] = {"value": world * n_total / (ms_e * 1e-3) / 1e9, "unit": UNIT,
-                       "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in parts)),
+        h2d = int(sum(p.numel() * 4 for p in parts))
+        # the host-to-device link in the same run: one copy per box from the
+        # same pinned buffers into the device particle arrays (same bytes)
+        for h_, p_ in zip(host, parts):
+            p_.copy_(h_, non_blocking=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for h_, p_ in zip(host, parts):
+            p_.copy_(h_, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_link = e0.elapsed_time(e1)
+        link_gbs = h2d / (ms_link * 1e-3) / 1e9
+        line["e2e"] = {"value": (1 if sub else world) * n_total / (ms_e * 1e-3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8 + w.nshell * 8),
-                       "ms_per_step": ms_e}
+                       "ms_per_step": ms_e,
+                       "h2d_link_gbs": link_gbs,
+                       "h2d_link_source": "cudaMemcpyAsync of the same pinned buffers, same run",
+                       "frac_of_link": (h2d / (ms_e * 1e-3) / 1e9) / link_gbs}
         del host
 
     if not args.no_cl:

@@ -445,6 +445,14 @@ ufc_status ufc_welford_merge(ufc_ctx *ctx, double *state_a_dev,
 ufc_status ufc_welford_finalize(ufc_ctx *ctx, const double *state_dev,
                                 int32_t d, int32_t ddof, double *mean_dev,
                                 double *cov_dev, double *corr_dev);
+/* The same update and merge on host memory (no context, no GPU): the
+ * realisation-sharded path of Eq. 10, where processes that hold their own
+ * states (for example ranks exchanging them over a CPU transport) combine
+ * them in rank order.  Same formulas and order as the device calls. */
+ufc_status ufc_welford_update_host(const double *v, int32_t nvec, int32_t d,
+                                   double *state);
+ufc_status ufc_welford_merge_host(double *state_a, const double *state_b,
+                                  int32_t d);
 
 #ifdef __cplusplus
 }

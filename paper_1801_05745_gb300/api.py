@@ -110,6 +110,8 @@ _SIGS = {
     "ufc_profile_enable": [P, I32],
     "ufc_profile_read": [P, I32, P, P, P, P],
     "ufc_workspace_bytes": [P, P],
+    "ufc_welford_update_host": [P, I32, I32, P],
+    "ufc_welford_merge_host": [P, P, I32],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -595,6 +597,24 @@ class Context:
                                            P(cov.data_ptr()), P(corr.data_ptr())),
                  "ufc_welford_finalize")
         return mean, cov, corr
+
+
+def welford_update_host(v: np.ndarray, state: np.ndarray):
+    """ufc_welford_update on host memory: adds the rows of v [nvec, d] to a
+    float64 state of 1 + d + d*d doubles (in place)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert state.dtype == np.float64 and state.flags.c_contiguous
+    nvec, d = v.shape
+    _check(_lib.ufc_welford_update_host(_np_ptr(v), nvec, d, _np_ptr(state)),
+           what="ufc_welford_update_host")
+
+
+def welford_merge_host(a: np.ndarray, b: np.ndarray, d: int):
+    """ufc_welford_merge on host memory: state b merged into state a (in place)."""
+    assert a.dtype == np.float64 and b.dtype == np.float64
+    assert a.flags.c_contiguous and b.flags.c_contiguous
+    _check(_lib.ufc_welford_merge_host(_np_ptr(a), _np_ptr(np.ascontiguousarray(b)), d),
+           what="ufc_welford_merge_host")
 
 
 def welford_state(d: int, device="cuda"):

@@ -19,7 +19,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["bin.cu", "stats.cu", "sht.cu", "capi.cu"]
-CPP = ["cosmo.cpp"]
+CPP = ["cosmo.cpp", "welford.cpp"]
 HEADERS = ["common.cuh", "pixel.cuh", "ctx.h"]
 
 

@@ -13,11 +13,17 @@ averages over independent realisations):
 from __future__ import annotations
 
 
-def shard_range(n: int, rank: int, world: int) -> tuple[int, int]:
-    """[start, stop) of rank's contiguous share of n particles."""
-    base, extra = divmod(n, world)
-    start = rank * base + min(rank, extra)
-    return start, start + base + (1 if rank < extra else 0)
+def shard_range(n: int, rank: int, world: int, align: int = 1) -> tuple[int, int]:
+    """[start, stop) of rank's contiguous share of n particles; every start is
+    a multiple of `align` (4 keeps a shard of 12-byte particles on 16-byte
+    boundaries, which the binning's bulk copies need)."""
+    units, rest = divmod(n, align)
+    base, extra = divmod(units, world)
+    start = (rank * base + min(rank, extra)) * align
+    stop = start + (base + (1 if rank < extra else 0)) * align
+    if rank == world - 1:
+        stop += rest
+    return start, stop
 
 
 def allreduce_counts(counts, group=None):
@@ -39,9 +45,17 @@ def gather_states(state, group=None):
 
 
 def merge_states(ctx, states, d: int):
-    """Chan-merges gathered states in rank order on the device; returns the
-    merged state (a new tensor)."""
+    """Chan-merges gathered states in rank order; returns the merged state (a
+    new tensor).  Device tensors merge on the device (ufc_welford_merge);
+    host tensors, as a CPU transport gathers them, through
+    ufc_welford_merge_host (ctx may then be None)."""
     merged = states[0].clone()
+    if merged.is_cuda:
+        for s in states[1:]:
+            ctx.welford_merge(merged, s, d)
+        return merged
+    from . import api
+    m = merged.numpy()
     for s in states[1:]:
-        ctx.welford_merge(merged, s, d)
+        api.welford_merge_host(m, s.contiguous().numpy(), d)
     return merged

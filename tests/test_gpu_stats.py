@@ -128,6 +128,25 @@ def test_welford_many_vectors_equal_one_at_a_time():
         assert torch.allclose(st_many, st_one, rtol=1e-12, atol=1e-12 * float(st_one.abs().max()))
 
 
+def test_welford_host_calls_match_device_calls():
+    """ufc_welford_update_host / ufc_welford_merge_host (the multi-process
+    path's host states) against the device update and merge."""
+    api, ctx = api_ctx()
+    rng = np.random.default_rng(7)
+    d = 46
+    v = rng.normal(size=(40, d)) * 3.0 + 1.0
+    sd, sd2 = api.welford_state(d), api.welford_state(d)
+    ctx.welford_update(torch.from_numpy(v[:25]).cuda(), sd)
+    ctx.welford_update(torch.from_numpy(v[25:]).cuda(), sd2)
+    ctx.welford_merge(sd, sd2, d)
+    sh, sh2 = np.zeros(1 + d + d * d), np.zeros(1 + d + d * d)
+    api.welford_update_host(v[:25], sh)
+    api.welford_update_host(v[25:], sh2)
+    api.welford_merge_host(sh, sh2, d)
+    torch.cuda.synchronize()
+    assert np.allclose(sd.cpu().numpy(), sh, rtol=1e-12, atol=1e-12 * np.abs(sh).max())
+
+
 def test_welford_at_the_largest_statistics_vector(orc):
     """d = 6 + 4096 PDF bins: the update's shared memory (2 d doubles) is
     above the 48 KB default and must still launch; covariance against the

@@ -66,9 +66,54 @@ def test_shard_range_partitions():
     from paper_1801_05745_gb300 import parallel
     for n in (0, 1, 7, 1000, 1001):
         for world in (1, 2, 3, 8):
-            spans = [parallel.shard_range(n, r, world) for r in range(world)]
-            assert spans[0][0] == 0 and spans[-1][1] == n
-            assert all(spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+            for align in (1, 4):
+                spans = [parallel.shard_range(n, r, world, align) for r in range(world)]
+                assert spans[0][0] == 0 and spans[-1][1] == n
+                assert all(spans[i][1] == spans[i + 1][0] for i in range(world - 1))
+                assert all(a % align == 0 for a, _ in spans)
+
+
+def _welford_worker(rank, world, port, tmp):
+    """Realisation sharding through the library (Eq. 10): each rank adds its
+    own statistics vectors to its own Welford state with the library's host
+    update, the states are gathered in rank order and merged with the
+    library's Chan merge (parallel.merge_states on host tensors)."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle
+    from paper_1801_05745_gb300 import api, parallel
+    d = 9
+    rng = np.random.default_rng(21)
+    v = rng.normal(size=(47, d)) @ rng.normal(size=(d, d)) + 3.0    # all realisations
+    a, b = parallel.shard_range(len(v), rank, world)
+    st = np.zeros(1 + d + d * d)
+    api.welford_update_host(v[a:b], st)
+    states = parallel.gather_states(torch.from_numpy(st))
+    merged = parallel.merge_states(None, states, d).numpy()
+    n = merged[0]
+    mean, M2 = merged[1:1 + d], merged[1 + d:].reshape(d, d)
+    m_o, c_o, _ = oracle.covariance(v, 1)
+    ok = [n == len(v),
+          bool(np.allclose(mean, m_o, rtol=1e-12, atol=1e-12)),
+          bool(np.allclose(M2 / (n - 1), c_o, rtol=1e-11, atol=1e-12))]
+    # a single state over all vectors in rank order agrees with the merge
+    one = np.zeros_like(st)
+    api.welford_update_host(v, one)
+    ok.append(bool(np.allclose(one, merged, rtol=1e-11, atol=1e-11)))
+    np.save(os.path.join(tmp, f"w{rank}.npy"), np.array(ok))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_library_welford_merge(tmp_path):
+    port = _free_port()
+    mp.spawn(_welford_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        ok = np.load(tmp_path / f"w{r}.npy")
+        assert ok.all(), (r, ok)
 
 
 def _failing_worker(rank, world, port, tmp, mode):
