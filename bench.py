@@ -254,9 +254,17 @@ def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8,
         ctx.batched_stats(xyz, boxes, chi, wb.nside, A, C, lo, hi, nb, state, graph=True,
                           counts=counts, kappa=kap)
 
+    def batched_launches(state):
+        ctx.batched_stats(xyz, boxes, chi, wb.nside, A, C, lo, hi, nb, state, graph=True,
+                          counts=counts, kappa=kap, launches=True)
+
+    from paper_1801_05745_gb300 import autotune
+    tsc = api.welford_state(d, dev)
+    tuning = autotune.tune_batch(ctx, lambda: batched(tsc), wb.nside, wb.nshell, n_real, n_tot)
     out = {}
     states = {}
-    for name, fn_ in (("serial", serial), ("batched", batched)):
+    for name, fn_ in (("serial", serial), ("batched", batched),
+                      ("batched_launches", batched_launches)):
         fn_(api.welford_state(d, dev))             # warm-up (graph instantiation, workspace)
         st = api.welford_state(d, dev)
         torch.cuda.synchronize()
@@ -268,9 +276,23 @@ def batched_leg(ctx, api, synth, dev, n_real: int, n_side: int, nbuf: int = 8,
         out[name] = {"ms": ms, "maps_per_s": n_real / (ms * 1e-3),
                      "gparticles_per_s": n_tot / (ms * 1e-3) / 1e9}
         states[name] = st
-    out["states_equal"] = bool(torch.allclose(states["serial"], states["batched"], rtol=1e-9,
-                                              atol=0.0))
+    out["states_equal"] = bool(torch.equal(states["serial"], states["batched"]) and
+                               torch.equal(states["serial"], states["batched_launches"]))
     out["speedup"] = out["serial"]["ms"] / out["batched"]["ms"]
+    out["speedup_launches"] = out["serial"]["ms"] / out["batched_launches"]["ms"]
+    out["tuning"] = {k: tuning[k] for k in ("batch_chunk", "batch_blocks_per_sm", "cached")}
+    out["tuning"]["candidates_ms"] = tuning.get("ms")
+    # GPU time per kernel of the serial run (a separate, profiled pass) and of
+    # the batched call's persistent kernel outside a graph
+    ctx.profile(True)
+    serial(api.welford_state(d, dev))
+    torch.cuda.synchronize()
+    out["serial_kernels_ms"] = {k: round(v[0], 3) for k, v in ctx.profile_read().items()}
+    ctx.batched_stats(xyz, boxes, chi, wb.nside, A, C, lo, hi, nb, api.welford_state(d, dev),
+                      graph=False, counts=counts, kappa=kap)
+    torch.cuda.synchronize()
+    out["batched_kernels_ms"] = {k: round(v[0], 3) for k, v in ctx.profile_read().items()}
+    ctx.profile(False)
     out["config"] = {"workload": wb.name, "realisations": n_real, "nside": wb.nside,
                      "nshell": wb.nshell, "particles": n_tot,
                      "per_box": f"Poisson(f {n_side}^3), f ~ U(0.5, 1.5)",

@@ -391,6 +391,8 @@ ufc_status ufc_map_stats(ufc_ctx *ctx, const float *map_dev, int32_t nside,
 /* ---- covariance over realisations (Eq. 10-11) ------------------------------ */
 
 #define UFC_BATCH_GRAPH 1      /* capture the whole batch into one CUDA graph */
+#define UFC_BATCH_LAUNCHES 2   /* one launch sequence per realisation, never the
+                                  persistent kernel                           */
 
 /* Statistics of nreal realisations in one call (Sec. 3.2 averages over 150
  * realisations).  Realisation r has nbox particle sets xyz_dev[r*nbox + k]
@@ -401,11 +403,22 @@ ufc_status ufc_map_stats(ufc_ctx *ctx, const float *map_dev, int32_t nside,
  * counts_dev (scratch, [nshell][npix]), writes moments_dev[r][10],
  * pdf_dev[r][nbins+3] and stats_dev[r][6 + nbins] (ufc_stats_vector), and
  * finally adds all nreal vectors to the Welford state state_dev in order.
- * Count maps of up to 64 MB run on up to 8 concurrent lanes: realisation r
- * on lane r mod 8, lane 0 being this context with counts_dev and kappa_dev,
- * the others extra contexts owned by this one, each with its own count and
- * kappa maps, workspace and stream (forked from and joined back to the
- * context stream by events); results do not depend on the lanes.
+ * Count maps of up to 64 MB whose boxes have no periodic images, and whose
+ * per-realisation maps fit in 4 GB of workspace together, run as ONE
+ * persistent kernel (unless UFC_BATCH_LAUNCHES): a device work queue of
+ * (realisation, particle chunk) tasks; the block that finishes a
+ * realisation's last chunk builds its kappa map, moments, PDF and
+ * statistics vector, and the block that finishes the last realisation runs
+ * the Welford update in realisation order.  No block waits for another
+ * (completion is counted with atomics).  Its chunk size and blocks per SM
+ * come from ufc_set_tuning.  Results equal the one-at-a-time calls bit for
+ * bit; counts_dev and kappa_dev are then not used (the kernel keeps one map
+ * per realisation in the workspace).  Otherwise count maps of up to 64 MB
+ * run on up to 8 concurrent lanes: realisation r on lane r mod 8, lane 0
+ * being this context with counts_dev and kappa_dev, the others extra
+ * contexts owned by this one, each with its own count and kappa maps,
+ * workspace and stream (forked from and joined back to the context stream
+ * by events); results do not depend on the lanes.
  * The workspace is grown once up front; with UFC_BATCH_GRAPH the per-
  * realisation work is captured into one CUDA graph and launched once (the
  * context stream must not be capturing already; on the legacy default
@@ -424,6 +437,17 @@ ufc_status ufc_batched_stats(ufc_ctx *ctx, int32_t nreal, int32_t nbox,
                              int32_t nbins, int32_t *counts_dev, float *kappa_dev,
                              double *moments_dev, int64_t *pdf_dev,
                              double *stats_dev, double *state_dev, int32_t flags);
+
+/* Tuning of a context (no counterpart in the paper; an autotuner picks the
+ * values by timing candidates): batch_chunk = particles per task of the
+ * persistent batch kernel (0: 8192), batch_blocks_per_sm = its resident
+ * blocks per SM (0: 2; at most 2).  Host only. */
+typedef struct {
+  int32_t batch_chunk;
+  int32_t batch_blocks_per_sm;
+} ufc_tuning;
+ufc_status ufc_set_tuning(ufc_ctx *ctx, const ufc_tuning *t);
+ufc_status ufc_get_tuning(const ufc_ctx *ctx, ufc_tuning *t);
 
 /* Statistics vector of one map, the quantity whose covariance over
  * realisations is estimated: v_dev[6 + nbins] = (mean, mu2, mu3, mu4, skew,

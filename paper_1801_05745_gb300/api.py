@@ -34,9 +34,15 @@ UFC_BIN_ACCUMULATE = 1
 UFC_BIN_FORCE_DIRECT = 2
 UFC_BIN_FORCE_DENSE = 4
 UFC_BATCH_GRAPH = 1
+UFC_BATCH_LAUNCHES = 2
 NMOMENTS = 10
 MOMENT_NAMES = ("mean", "mu2", "mu3", "mu4", "skew", "kurt", "s2_expect", "var_s2",
                 "s2_over_var_s2", "n")
+
+
+class Tuning(ctypes.Structure):
+    """ufc_tuning: chunk size and blocks per SM of the persistent batch kernel (0 = default)."""
+    _fields_ = [("batch_chunk", I32), ("batch_blocks_per_sm", I32)]
 
 
 class Cosmo(ctypes.Structure):
@@ -111,6 +117,8 @@ _SIGS = {
     "ufc_profile_read": [P, I32, P, P, P, P],
     "ufc_workspace_bytes": [P, P],
     "ufc_welford_update_host": [P, I32, I32, P],
+    "ufc_set_tuning": [P, P],
+    "ufc_get_tuning": [P, P],
     "ufc_welford_merge_host": [P, P, I32],
 }
 for _name, _args in _SIGS.items():
@@ -451,14 +459,34 @@ class Context:
         return grad, G, H.value
 
     # -- batched realisations --
+    def set_tuning(self, batch_chunk: int = 0, batch_blocks_per_sm: int = 0):
+        """ufc_set_tuning (0 = library default)."""
+        t = Tuning(int(batch_chunk), int(batch_blocks_per_sm))
+        self._ck(_lib.ufc_set_tuning(self.h, ctypes.byref(t)), "ufc_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        self._ck(_lib.ufc_get_tuning(self.h, ctypes.byref(t)), "ufc_get_tuning")
+        return dict(batch_chunk=t.batch_chunk, batch_blocks_per_sm=t.batch_blocks_per_sm)
+
     def batched_stats(self, xyz, boxes, chi_edges, nside, A, C, pdf_lo, pdf_hi, nbins,
-                      state, graph=True, counts=None, kappa=None):
+                      state, graph=True, counts=None, kappa=None, launches=False):
         """Statistics of many realisations in one call (ufc_batched_stats).
         xyz[r][k]: particles of realisation r, box k; boxes[r][k]: its box;
         A [nreal, nshell], C [nreal].  Returns (moments [nreal,10],
-        pdf [nreal, nbins+3], stats [nreal, 6+nbins]); updates `state`."""
+        pdf [nreal, nbins+3], stats [nreal, 6+nbins]); updates `state`.
+        launches=True: one launch sequence per realisation instead of the
+        persistent kernel (UFC_BATCH_LAUNCHES).  The autotuner's cached
+        tuning for this shape, if any, is applied first (autotune.tune_batch
+        makes it)."""
         import torch
         nreal, nbox = len(xyz), len(xyz[0])
+        if not launches:
+            from . import autotune
+            tuned = autotune.cached_batch_tuning(self, nside, len(chi_edges) - 1, nreal,
+                                                 sum(x.numel() // 3 for row in xyz for x in row))
+            if tuned:
+                self.set_tuning(*tuned)
         chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
         S = len(chi) - 1
         npix = 12 * nside * nside
@@ -482,7 +510,9 @@ class Context:
                                         _np_ptr(C), float(pdf_lo), float(pdf_hi), nbins,
                                         P(counts.data_ptr()), P(kappa.data_ptr()), P(mom.data_ptr()),
                                         P(pdf.data_ptr()), P(stats.data_ptr()), P(state.data_ptr()),
-                                        UFC_BATCH_GRAPH if graph else 0), "ufc_batched_stats")
+                                        (UFC_BATCH_GRAPH if graph else 0) |
+                                        (UFC_BATCH_LAUNCHES if launches else 0)),
+                 "ufc_batched_stats")
         return mom, pdf, stats
 
     # -- full-sky power spectrum --

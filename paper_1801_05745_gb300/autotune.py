@@ -1,8 +1,11 @@
-"""Choice of the binning output path (L2 atomics vs dense-key scatter with
-shared-memory histograms) by timing both once per (GPU, Nside, shells,
-particle count) and caching the winner in a JSON file.
+"""Autotuner of the library's launch choices, by timing candidates once per
+shape and caching the winner in a JSON file:
+  - the binning output path (L2 atomics vs dense-key scatter with
+    shared-memory histograms) per (GPU, Nside, shells, particle count);
+  - the persistent batch kernel's particles per task and blocks per SM
+    (ufc_set_tuning) per (GPU, Nside, shells, realisations, particle count).
 
-Both paths give identical count maps; only speed differs.  The cache lives in
+Every choice gives identical results; only speed differs.  The cache lives in
 $UFC_AUTOTUNE_CACHE, else ~/.cache/ufalcon_gb300/autotune.json.
 """
 from __future__ import annotations
@@ -76,3 +79,59 @@ def choose_bin_path(ctx, xyz_list, boxes, chi_edges, nside: int, counts=None, re
         cache[key] = {"path": best, "ms": times}
         _store(cache)
     return best
+
+
+BATCH_CHUNKS = (2048, 8192, 32768)
+BATCH_BLOCKS = (1, 2)
+
+
+def batch_key(gpu_name: str, nside: int, nshell: int, nreal: int, n_total: int) -> str:
+    nb = int(math.log2(max(1, n_total)))
+    return f"batch|{gpu_name}|nside={nside}|nshell={nshell}|nreal={nreal}|log2n={nb}"
+
+
+def cached_batch_tuning(ctx, nside: int, nshell: int, nreal: int, n_total: int):
+    """The cached (batch_chunk, batch_blocks_per_sm) for this shape, or None."""
+    import torch
+    key = batch_key(torch.cuda.get_device_name(ctx.device), nside, nshell, nreal, n_total)
+    with _lock:
+        e = _load().get(key)
+    return (e["batch_chunk"], e["batch_blocks_per_sm"]) if e else None
+
+
+def tune_batch(ctx, run, nside: int, nshell: int, nreal: int, n_total: int, reps: int = 2,
+               force_retune: bool = False) -> dict:
+    """Times run() (one batched call) under every candidate tuning of the
+    persistent batch kernel, keeps the fastest in the context and the cache;
+    returns {"batch_chunk", "batch_blocks_per_sm", "ms": {candidate: ms},
+    "cached": bool}."""
+    import torch
+    key = batch_key(torch.cuda.get_device_name(ctx.device), nside, nshell, nreal, n_total)
+    with _lock:
+        e = _load().get(key)
+    if e and not force_retune:
+        ctx.set_tuning(e["batch_chunk"], e["batch_blocks_per_sm"])
+        return dict(e, cached=True)
+    times = {}
+    for c in BATCH_CHUNKS:
+        for b in BATCH_BLOCKS:
+            ctx.set_tuning(c, b)
+            run()                                  # warm-up (graph, workspace)
+            torch.cuda.synchronize(ctx.device)
+            s = torch.cuda.Event(enable_timing=True)
+            t = torch.cuda.Event(enable_timing=True)
+            s.record()
+            for _ in range(reps):
+                run()
+            t.record()
+            torch.cuda.synchronize(ctx.device)
+            times[f"{c}x{b}"] = s.elapsed_time(t) / reps
+    best = min(times, key=times.get)
+    c, b = (int(v) for v in best.split("x"))
+    ctx.set_tuning(c, b)
+    entry = {"batch_chunk": c, "batch_blocks_per_sm": b, "ms": times}
+    with _lock:
+        cache = _load()
+        cache[key] = entry
+        _store(cache)
+    return dict(entry, cached=False)

@@ -1481,6 +1481,20 @@ static cudaEvent_t copy_event(ufc_ctx* c, size_t i) {
   return c->copy_events[i];
 }
 
+// Shell table and box geometry of a batched call's boxes (the persistent
+// batch kernel of stats.cu keys particles with the same stages).
+ufc_status batch_geometry(ufc_ctx* c, const double* chi, int nshell, const ufc_box* boxes,
+                          int nbox, ShellTable& st, BoxGeom* bg) {
+  ufc_status s = make_table(c, chi, nshell, st);
+  if (s) return s;
+  for (int k = 0; k < nbox; ++k) {
+    s = make_box(c, boxes[k], nshell, bg[k]);
+    if (s) return s;
+  }
+  return UFC_OK;
+}
+void batch_bands(int nside, float smax, Bands& bd) { make_bands(nside, smax, bd); }
+
 // Runs the key pipeline for nbox boxes.  counts (DIRECT/DENSE) or keys (KEYS).
 // xyz_host (non-NULL, ufc_bin_host): positions in host memory, copied into
 // the staging slot chunk by chunk on the copy stream while the fast stage of

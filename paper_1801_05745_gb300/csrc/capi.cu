@@ -27,6 +27,14 @@ ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int
                                    const double* A, double C, double lo, double hi, int nbins,
                                    float* kappa, double* moments, int64_t* pdf);
 ufc_status run_welford_merge(ufc_ctx* c, double* a, const double* b, int d);
+void batch_persistent_bytes(const ufc_ctx* c, int nreal, int nbox, int S, int nside,
+                            size_t* maps, size_t* desc);
+ufc_status batch_persistent_prepare(ufc_ctx* c, int nreal, int nbox, const float* const* xyz,
+                                    const int64_t* n, const ufc_box* boxes, const double* chi,
+                                    int S, int nside, const double* A, const double* C, double lo,
+                                    double hi, int nbins, double* moments, int64_t* pdf,
+                                    double* stats, double* state, char* maps, char* desc);
+ufc_status batch_persistent_enqueue(ufc_ctx* c, char* maps, char* desc);
 ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, double* mean,
                                 double* cov, double* corr);
 ufc_status reserve_bin_workspace(ufc_ctx* c, int64_t fast_launches, int64_t total_img,
@@ -237,6 +245,23 @@ static int64_t held_bytes(const ufc_ctx* c) {
 ufc_status ufc_workspace_bytes(const ufc_ctx* c, int64_t* bytes) {
   if (!c || !bytes) return UFC_ERR_ARG;
   *bytes = held_bytes(c);
+  return UFC_OK;
+}
+
+ufc_status ufc_set_tuning(ufc_ctx* c, const ufc_tuning* t) {
+  if (!c || !t) return UFC_ERR_ARG;
+  if (t->batch_chunk < 0 || t->batch_chunk > (1 << 24) || t->batch_blocks_per_sm < 0 ||
+      t->batch_blocks_per_sm > 2)
+    return set_err(c, UFC_ERR_ARG, "tuning out of range (chunk <= 2^24, blocks per SM <= 2)");
+  c->batch_chunk = t->batch_chunk;
+  c->batch_blocks_per_sm = t->batch_blocks_per_sm;
+  return UFC_OK;
+}
+
+ufc_status ufc_get_tuning(const ufc_ctx* c, ufc_tuning* t) {
+  if (!c || !t) return UFC_ERR_ARG;
+  t->batch_chunk = c->batch_chunk;
+  t->batch_blocks_per_sm = c->batch_blocks_per_sm;
   return UFC_OK;
 }
 
@@ -691,7 +716,7 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
   if (nreal < 1 || nbox < 1 || !xyz || !n || !boxes || !chi || !A || !C || !counts || !kappa ||
       !moments || !pdf || !stats || !state)
     return set_err(c, UFC_ERR_ARG, "ufc_batched_stats: bad arguments");
-  if (flags & ~UFC_BATCH_GRAPH) return set_err(c, UFC_ERR_ARG, "unknown flags");
+  if (flags & ~(UFC_BATCH_GRAPH | UFC_BATCH_LAUNCHES)) return set_err(c, UFC_ERR_ARG, "unknown flags");
   if (nshell < 1 || nshell > UFC_MAX_SHELLS) return set_err(c, UFC_ERR_ARG, "bad nshell");
   if (nbins < 1 || nbins > 4096) return set_err(c, UFC_ERR_ARG, "bad nbins");
   cudaSetDevice(c->device);
@@ -705,11 +730,35 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
     }
     max_img = std::max(max_img, t);
   }
-  ufc_status s = reserve_bin_workspace(c, nbox, max_img, nshell, nside);
-  if (s) return s;
-  // per-block partial sums of the kappa and moment kernels
-  if (!ws_get(c, kSlotPartials, (size_t)16 * c->num_sms * 8)) return UFC_ERR_ALLOC;
   const int d = 6 + nbins;
+  const int64_t npix_b = 12ll * nside * nside;
+  // one persistent kernel for small maps without periodic images whose maps
+  // fit in 4 GB of workspace together
+  bool persistent = !(flags & UFC_BATCH_LAUNCHES) && (size_t)nshell * npix_b * 4 <= kLaneMapMax;
+  for (int i = 0; i < nreal * nbox && persistent; ++i) persistent = boxes[i].replicate == 0;
+  size_t pmaps = 0, pdesc = 0;
+  if (persistent) {
+    batch_persistent_bytes(c, nreal, nbox, nshell, nside, &pmaps, &pdesc);
+    persistent = pmaps <= (4ull << 30);
+  }
+  char* bmaps = nullptr;
+  char* bdesc = nullptr;
+  ufc_status s = UFC_OK;
+  if (persistent) {
+    bmaps = (char*)ws_get(c, kSlotBatchMaps, pmaps);
+    bdesc = (char*)ws_get(c, kSlotBatchDesc, pdesc);
+    if (!bmaps || !bdesc) return UFC_ERR_ALLOC;
+    // descriptors uploaded now, before any capture (also before a cached
+    // graph's relaunch, which reads them)
+    s = batch_persistent_prepare(c, nreal, nbox, xyz, n, boxes, chi, nshell, nside, A, C, lo, hi,
+                                 nbins, moments, pdf, stats, state, bmaps, bdesc);
+    if (s) return s;
+  } else {
+    s = reserve_bin_workspace(c, nbox, max_img, nshell, nside);
+    if (s) return s;
+    // per-block partial sums of the kappa and moment kernels
+    if (!ws_get(c, kSlotPartials, (size_t)16 * c->num_sms * 8)) return UFC_ERR_ALLOC;
+  }
   // small maps: realisation r runs on lane r mod nlane, the lanes concurrently
   // (lane 0 is this context with the caller's scratch maps; the others have
   // their own count and kappa maps, workspace and stream)
@@ -717,7 +766,8 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
   const size_t map_bytes = (size_t)nshell * npix * 4;
   // (and a bound of 8 GB on the lanes' binning workspace, ~16 B per image)
   const int64_t ws_lanes = std::max<int64_t>(1, (8ll << 30) / std::max<int64_t>(1, 16 * max_img));
-  const int nlane = map_bytes <= kLaneMapMax
+  const int nlane = persistent ? 1
+                   : map_bytes <= kLaneMapMax
                         ? (int)std::min<int64_t>({ufc_ctx::kMaxLanes, nreal, ws_lanes})
                         : 1;
   ufc_ctx* lane[ufc_ctx::kMaxLanes] = {c};
@@ -765,6 +815,8 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
     };
     const size_t nrb = (size_t)nreal * nbox;
     put(&nreal, 4); put(&nbox, 4); put(&nshell, 4); put(&nside, 4); put(&nbins, 4);
+    const int32_t mode[3] = {persistent ? 1 : 0, c->batch_chunk, c->batch_blocks_per_sm};
+    put(mode, sizeof mode);
     put(&lo, 8); put(&hi, 8);
     put(xyz, nrb * sizeof(void*)); put(n, nrb * 8);
     for (size_t i = 0; i < nrb; ++i) {
@@ -797,7 +849,8 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
     UFC_CUDA(c, cudaEventRecord(c->lane_ev[0], c->stream));
     for (int k = 1; k < nlane; ++k) UFC_CUDA(c, cudaStreamWaitEvent(lane[k]->stream, c->lane_ev[0], 0));
   }
-  for (int r = 0; r < nreal && !s; ++r) {
+  if (persistent) s = batch_persistent_enqueue(c, bmaps, bdesc);
+  for (int r = 0; r < nreal && !s && !persistent; ++r) {
     ufc_ctx* lc = lane[r % nlane];
     int32_t* cnt = lane_counts[r % nlane];
     float* kap = lane_kappa[r % nlane];
@@ -816,7 +869,7 @@ ufc_status ufc_batched_stats(ufc_ctx* c, int32_t nreal, int32_t nbox, const floa
     if (e == cudaSuccess) cudaStreamWaitEvent(c->stream, c->lane_ev[k], 0);
     else if (!s) s = set_err(c, UFC_ERR_CUDA, "lane join: %s", cudaGetErrorString(e));
   }
-  if (!s) s = run_welford_update(c, stats, nreal, d, state);
+  if (!s && !persistent) s = run_welford_update(c, stats, nreal, d, state);
   if (graph) {
     cudaStream_t cap = c->stream;
     c->stream = user;

@@ -17,7 +17,7 @@ struct ufc_ctx {
   int num_sms = 0;
   int smem_optin = 0;            // shared memory per block with opt-in (bytes)
   // grow-only device buffers, one per slot
-  static constexpr int kSlots = 16;
+  static constexpr int kSlots = 18;
   void* buf[kSlots] = {};
   size_t cap[kSlots] = {};
   void* counters = nullptr;      // ufc::BinCounters of the last binning call
@@ -48,6 +48,10 @@ struct ufc_ctx {
   cudaStream_t lane_stream[kMaxLanes] = {};
   cudaEvent_t lane_ev[kMaxLanes + 1] = {};
   ufc_ctx* owner = nullptr;
+  // tuning (ufc_set_tuning) and the prepared launch of the persistent
+  // batch kernel (descriptors uploaded, launch arguments kept here)
+  int32_t batch_chunk = 0, batch_blocks_per_sm = 0;
+  std::vector<unsigned char> batch_launch;
 };
 
 namespace ufc {
@@ -69,6 +73,8 @@ enum Slot {
   kSlotSht,        // ring transforms, Legendre seeds, partial a_lm (ufc_map2alm)
   kSlotOvf,        // one bit per particle image: left undecided when queue 1 was full
   kSlotLaneMap,    // a lane's count map and kappa map (ufc_batched_stats)
+  kSlotBatchMaps,  // persistent batch kernel: per-realisation maps and partial sums
+  kSlotBatchDesc,  // persistent batch kernel: task descriptors and queue counters
 };
 
 inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {

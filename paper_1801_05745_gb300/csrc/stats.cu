@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "ctx.h"
+#include "pixel.cuh"
 
 namespace ufc {
 
@@ -86,11 +87,9 @@ struct Coef {
 // counts in exact integer arithmetic.
 constexpr int kKT = 256;   // threads of the scalar-load kappa kernel
 
-// Exact FP32 helpers that avoid the conversion instructions (float->int,
-// round-to-integral), which GB300 executes on its narrow FP64 pipe.
-constexpr float kMagic = 12582912.0f;          // 1.5 * 2^23
-constexpr int32_t kMagicBits = 0x4B400000;
-// round(x) as int for |x| < 2^22, and the rounded value as float
+// round(x) as int for |x| < 2^22, and the rounded value as float (the FP32
+// magic-number form of pixel.cuh: no conversion instruction, which GB300
+// executes on its narrow FP64 pipe)
 __device__ __forceinline__ int32_t round_fast(float x, float& xr) {
   const float r = __fadd_rn(x, kMagic);
   xr = __fsub_rn(r, kMagic);
@@ -183,19 +182,17 @@ __device__ __forceinline__ float kappa_round(f2 a, f2 mc) {
   const f2 e = f2_add(f2_norm(a.h, a.l), mc);   // e = acc - C (unrounded)
   return __fadd_rn(e.h, e.l);
 }
-__global__ void __launch_bounds__(kKV)
-k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
-            double* __restrict__ ksum_part) {
-  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
-  __shared__ double red[kKV / 32];
-  const int S = cf.nshell;
-  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
-  __syncthreads();
-  const int ng = cf.npix >> 2;
+// One block's share of the vector-load forward pass: block vb of a grid of nb
+// blocks of kKV threads (every thread of the block calls it); returns the
+// block's sum of the FP32 kappa values, valid in thread 0.
+__device__ __forceinline__ double kappa_vec_block(const int32_t* __restrict__ counts,
+                                                  const float* ah_s, const float* al_s, int S,
+                                                  int npix, f2 mc, float* __restrict__ kappa,
+                                                  int vb, int nb, double* red) {
+  const int ng = npix >> 2;
   const int4* c4 = reinterpret_cast<const int4*>(counts);
-  const f2 mc{-cf.ch, -cf.cl};
   f2 ks{0.f, 0.f};
-  for (int g = blockIdx.x * kKV + threadIdx.x; g < ng; g += gridDim.x * kKV) {
+  for (int g = vb * kKV + threadIdx.x; g < ng; g += nb * kKV) {
     f2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
 #pragma unroll 8
     for (int b = 0; b < S; ++b) {
@@ -211,7 +208,19 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
     reinterpret_cast<float4*>(kappa)[g] = kv;
     ks = f2_add(ks, f2_add(f2_two_sum(kv.x, kv.y), f2_two_sum(kv.z, kv.w)));
   }
-  const double t = block_sum_d<kKV>(f2_to_d(ks), red);
+  return block_sum_d<kKV>(f2_to_d(ks), red);
+}
+
+__global__ void __launch_bounds__(kKV)
+k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kappa,
+            double* __restrict__ ksum_part) {
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ double red[kKV / 32];
+  const int S = cf.nshell;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+  __syncthreads();
+  const double t = kappa_vec_block(counts, ah_s, al_s, S, cf.npix, f2{-cf.ch, -cf.cl}, kappa,
+                                   blockIdx.x, gridDim.x, red);
   if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
 }
 
@@ -487,6 +496,50 @@ __device__ __forceinline__ double warp_sum_fixed(const double* v, int n, int str
   return s;
 }
 
+// PDF slot of one FP32 value: floor((k - lo) * scale) in FP64, decided in FP32
+// unless k lies within a proven band of a bin edge; under/overflow and NaN.
+__device__ __forceinline__ int pdf_slot(float k, const PdfParam& pp) {
+  // k < lo and k >= hi decided in FP32 unless k lies between the FP32
+  // neighbours of lo (resp. hi)
+  const bool under = k < pp.lo_dn || (k < pp.lo_up && (double)k < pp.lo);
+  const bool over = k >= pp.hi_up || (k >= pp.hi_dn && (double)k >= pp.hi);
+  if (isnan(k)) return pp.nbins + 2;
+  if (under) return pp.nbins;
+  if (over) return pp.nbins + 1;
+  const float x = (k - pp.lo_f) * pp.scale_f;   // in [-1, nbins + 1] up to rounding
+  float xr;
+  int b = round_fast(x, xr);
+  if (xr > x) { b -= 1; xr -= 1.0f; }          // floor
+  const float rem = x - xr;
+  const float band = pp.band_rel * (fabsf(x) + 1.0f);
+  if (!(rem >= band && rem < 1.0f - band))
+    b = (int)floor(__dmul_rn(__dsub_rn((double)k, pp.lo), pp.scale));
+  return b >= pp.nbins ? pp.nbins - 1 : (b < 0 ? 0 : b);
+}
+
+// One block's share of the moment pass: block vb of a grid of nb blocks of
+// kMT threads (every thread calls it).  Central power sums about `mean` into
+// out[0..2] (valid in thread 0); PDF counts into the shared histogram.
+__device__ __forceinline__ void moments_block(const float* __restrict__ kappa, int npix,
+                                              double mean, const PdfParam& pp, int vb, int nb,
+                                              unsigned int* hist, double* red, double* out) {
+  const float mh = (float)mean;
+  const float ml = (float)(mean - (double)mh);
+  f2 a2{0.f, 0.f}, a3{0.f, 0.f}, a4{0.f, 0.f};
+  for (int p = vb * kMT + threadIdx.x; p < npix; p += nb * kMT) {
+    const float k = kappa[p];
+    f2 d = f2_add(f2_two_sum(k, -mh), f2{-ml, 0.f});
+    f2 d2 = f2_mul(d, d);
+    a2 = f2_add(a2, d2);
+    a3 = f2_add(a3, f2_mul(d2, d));
+    a4 = f2_add(a4, f2_mul(d2, d2));
+    atomicAdd(hist + pdf_slot(k, pp), 1u);
+  }
+  out[0] = block_sum_d<kMT>(f2_to_d(a2), red);
+  out[1] = block_sum_d<kMT>(f2_to_d(a3), red);
+  out[2] = block_sum_d<kMT>(f2_to_d(a4), red);
+}
+
 __global__ void __launch_bounds__(kMT)
 k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ ksum_part,
           int nksum, PdfParam pp, double* __restrict__ part /*[grid][3]*/,
@@ -500,57 +553,24 @@ k_moments(const float* __restrict__ kappa, int npix, const double* __restrict__ 
     if (threadIdx.x == 0) mean_s = s / double(npix);
   }
   __syncthreads();
-  const double mean = mean_s;
-  const float mh = (float)mean;
-  const float ml = (float)(mean - (double)mh);
-  f2 a2{0.f, 0.f}, a3{0.f, 0.f}, a4{0.f, 0.f};
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
-    const float k = kappa[p];
-    f2 d = f2_add(f2_two_sum(k, -mh), f2{-ml, 0.f});
-    f2 d2 = f2_mul(d, d);
-    a2 = f2_add(a2, d2);
-    a3 = f2_add(a3, f2_mul(d2, d));
-    a4 = f2_add(a4, f2_mul(d2, d2));
-    // PDF
-    int slot;
-    // k < lo and k >= hi decided in FP32 unless k lies between the FP32
-    // neighbours of lo (resp. hi)
-    const bool under = k < pp.lo_dn || (k < pp.lo_up && (double)k < pp.lo);
-    const bool over = k >= pp.hi_up || (k >= pp.hi_dn && (double)k >= pp.hi);
-    if (isnan(k)) slot = pp.nbins + 2;
-    else if (under) slot = pp.nbins;
-    else if (over) slot = pp.nbins + 1;
-    else {
-      const float x = (k - pp.lo_f) * pp.scale_f;   // in [-1, nbins + 1] up to rounding
-      float xr;
-      int b = round_fast(x, xr);
-      if (xr > x) { b -= 1; xr -= 1.0f; }          // floor
-      const float rem = x - xr;
-      const float band = pp.band_rel * (fabsf(x) + 1.0f);
-      if (!(rem >= band && rem < 1.0f - band))
-        b = (int)floor(__dmul_rn(__dsub_rn((double)k, pp.lo), pp.scale));
-      b = b >= pp.nbins ? pp.nbins - 1 : (b < 0 ? 0 : b);
-      slot = b;
-    }
-    atomicAdd(hist + slot, 1u);
+  double o[3];
+  moments_block(kappa, npix, mean_s, pp, blockIdx.x, gridDim.x, hist, red, o);
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = o[0];
+    part[3 * blockIdx.x + 1] = o[1];
+    part[3 * blockIdx.x + 2] = o[2];
   }
-  double v2 = block_sum_d<kMT>(f2_to_d(a2), red);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 0] = v2;
-  double v3 = block_sum_d<kMT>(f2_to_d(a3), red);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = v3;
-  double v4 = block_sum_d<kMT>(f2_to_d(a4), red);
-  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = v4;
   __syncthreads();
   for (int i = threadIdx.x; i < pp.nbins + 3; i += blockDim.x)
     if (hist[i]) atomicAdd(pdf + i, (unsigned long long)hist[i]);
 }
 
-// moments[10] from the partial sums (one warp, fixed orders).
-__global__ void k_moments_final(const double* __restrict__ ksum_part, int nksum,
-                                const double* __restrict__ part, int npart, int npix,
-                                double* __restrict__ m) {
-  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
-  // one warp, fixed orders (the mean as k_moments forms it)
+// moments[10] from the partial sums (one warp, fixed orders; every lane of
+// warp 0 calls it, lane 0 writes).
+__device__ __forceinline__ void moments_final_warp(const double* ksum_part, int nksum,
+                                                   const double* part, int npart, int npix,
+                                                   double* m) {
+  // the mean as k_moments forms it
   const double s = warp_sum_fixed(ksum_part, nksum, 1);
   const double s2 = warp_sum_fixed(part, npart, 3);
   const double s3 = warp_sum_fixed(part + 1, npart, 3);
@@ -565,10 +585,21 @@ __global__ void k_moments_final(const double* __restrict__ ksum_part, int nksum,
   m[4] = mu3 / (mu2 * sqrt(mu2));
   m[5] = mu4 / (mu2 * mu2) - 3.0;
   m[6] = (N - 1.0) * mu2 / N;
-  const double N3 = N * N * N;
-  m[7] = (N - 1.0) * (N - 1.0) / N3 * mu4 - (N - 1.0) * (N - 3.0) / N3 * mu2 * mu2;
+  // Eq. 13 with every product and difference rounded on its own (explicit
+  // intrinsics: no contraction can differ between the copies of this code)
+  const double N3 = __dmul_rn(__dmul_rn(N, N), N);
+  const double c1 = __ddiv_rn(__dmul_rn(N - 1.0, N - 1.0), N3);
+  const double c2 = __ddiv_rn(__dmul_rn(N - 1.0, N - 3.0), N3);
+  m[7] = __dsub_rn(__dmul_rn(c1, mu4), __dmul_rn(__dmul_rn(c2, mu2), mu2));
   m[8] = mu2 / m[7];
   m[9] = N;
+}
+
+__global__ void k_moments_final(const double* __restrict__ ksum_part, int nksum,
+                                const double* __restrict__ part, int npart, int npix,
+                                double* __restrict__ m) {
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  moments_final_warp(ksum_part, nksum, part, npart, npix, m);
 }
 
 // Statistics vector of one map for the covariance (Eq. 10): the first six
@@ -581,36 +612,60 @@ __global__ void k_stats_vector(const double* __restrict__ m, const unsigned long
 }
 
 // ---------------------------------------------------------- Welford -----
-__global__ void __launch_bounds__(1024)
-k_welford_update(const double* __restrict__ v, int nvec, int d, double* __restrict__ st) {
-  extern __shared__ double sh[];   // delta_old[d], delta_new[d]
-  double* dold = sh;
-  double* dnew = sh + d;
+// Welford update of st by the nvec vectors v [nvec][d] in order (every thread
+// of the block calls it; sh holds 2 rc d doubles).  Runs of rc vectors: the
+// deltas of each vector against the running mean (dold = x - mean before,
+// dnew = x - mean after) are formed in order into shared memory, the mean
+// updated as they are; then every element of M2 takes the run's products
+// as one chain of fused multiply-adds in a register, one global read and
+// write per run instead of per vector.  The chain per element is the same as
+// one vector at a time, so the result does not depend on rc or on the block
+// size.  The count is read once and written once.
+__device__ __forceinline__ void welford_update_block(const double* v, int nvec, int d, double* st,
+                                                     double* sh, int rc) {
   double* mean = st + 1;
   double* M2 = st + 1 + d;
-  // the count is read once and written once: every thread keeps n in a
-  // register, so no thread can see a count that another one already advanced
   const double n0 = st[0];
   __syncthreads();
-  for (int r = 0; r < nvec; ++r) {
-    const double* x = v + (size_t)r * d;
-    const double n = n0 + double(r + 1);
+  for (int r0 = 0; r0 < nvec; r0 += rc) {
+    const int nr = min(rc, nvec - r0);
+    // the run's deltas, in vector order (thread i owns mean[i] throughout)
     for (int i = threadIdx.x; i < d; i += blockDim.x) {
-      double delta = x[i] - mean[i];
-      double mn = mean[i] + delta / n;
-      dold[i] = delta;
-      dnew[i] = x[i] - mn;
+      double m = mean[i];
+      for (int q = 0; q < nr; ++q) {
+        const double x = v[(size_t)(r0 + q) * d + i];
+        const double n = n0 + double(r0 + q + 1);
+        const double delta = x - m;
+        m = m + delta / n;
+        sh[(size_t)q * d + i] = delta;                 // dold
+        sh[(size_t)(rc + q) * d + i] = x - m;          // dnew
+      }
+      mean[i] = m;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < d * d; k += blockDim.x) {
       const int i = k / d, j = k - i * d;
-      M2[k] += dold[i] * dnew[j];
+      double acc = M2[k];
+      for (int q = 0; q < nr; ++q)
+        acc = __fma_rn(sh[(size_t)q * d + i], sh[(size_t)(rc + q) * d + j], acc);
+      M2[k] = acc;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < d; i += blockDim.x) mean[i] += dold[i] / n;
     __syncthreads();
   }
   if (threadIdx.x == 0) st[0] = n0 + double(nvec);
+}
+
+// Vectors per run of the Welford update for d-dimensional states: the run's
+// deltas (2 rc d doubles) within 48 KB of shared memory, at most 16.
+__host__ __device__ inline int welford_run(int d) {
+  const int rc = 49152 / (16 * d);
+  return rc < 1 ? 1 : (rc > 16 ? 16 : rc);
+}
+
+__global__ void __launch_bounds__(1024)
+k_welford_update(const double* __restrict__ v, int nvec, int d, double* __restrict__ st) {
+  extern __shared__ double sh[];   // the run's deltas: dold[rc][d], dnew[rc][d]
+  welford_update_block(v, nvec, d, st, sh, welford_run(d));
 }
 
 __global__ void __launch_bounds__(1024)
@@ -644,6 +699,178 @@ k_welford_final(const double* __restrict__ st, int d, int ddof, double* __restri
     const int i = k / d, j = k - i * d;
     const double q = sqrt((st[1 + d + i * d + i] / den) * (st[1 + d + j * d + j] / den));
     corr[k] = q > 0.0 ? (st[1 + d + k] / den) / q : 0.0;
+  }
+}
+
+// ------------------------------------------------ persistent batch kernel --
+// All realisations of a batched call (Sec. 3.2: statistics over many
+// realisations) in one launch.  A device work queue hands out tasks of
+// `chunk` particles of one (realisation, box); a block bins its task's
+// particles with the three-stage key (FP32, double-float and FP64 stages
+// inline: the same keys as the binning call) and adds them to the
+// realisation's count map with global atomics.  The block that finishes the
+// last task of a realisation then computes its kappa map, moments, PDF and
+// statistics vector by running, one after the other, every block of the
+// serial kappa and moment passes (kappa_vec_block and moments_block with the
+// serial grids), so that the results equal the one-at-a-time calls bit for
+// bit.  The block that finishes the last realisation runs the Welford
+// update over all of them in realisation order.  No block ever waits for
+// another one: completion is detected with atomic counters and fences.
+struct BatchItem {          // one (realisation, box) of a batched call
+  const float* xyz;
+  int64_t n;
+  int64_t task0;            // first task of this item (ascending over the items)
+  int32_t real;
+  int32_t shell_lo, shell_hi;
+  float shf[3], shlo[3];    // the box's shift split as in BoxGeom (no periodic images)
+  double sh64[3];
+};
+struct BatchArgs {
+  const BatchItem* items;
+  int32_t nitems, chunk;
+  int64_t ntasks;
+  const Coef* coef;         // [nreal]
+  const int32_t* ntask_r;   // [nreal] tasks of each realisation
+  int32_t nreal, S, N, npix;
+  int32_t* counts;          // [nreal][S][npix], zero at the launch
+  float* kappa;             // [nreal][npix]
+  double* ksum;             // [nreal][gk]
+  double* mpart;            // [nreal][3 gm]
+  int32_t gk, gm;           // grids of the serial kappa and moment passes
+  double* moments;          // [nreal][10]
+  int64_t* pdf;             // [nreal][nbins + 3]
+  double* stats;            // [nreal][d]
+  double* state;            // Welford state (1 + d + d^2)
+  int32_t nbins, d;
+  unsigned long long* queue;   // [0] next task, [1] realisations finished (zero at launch)
+  unsigned int* done;          // [nreal] tasks finished (zero at launch)
+};
+constexpr int kBT = 256;
+static_assert(kBT == kKV && kBT == kMT, "the persistent blocks reproduce the serial blocks");
+
+// Key of one particle: FP32 stage, then the double-float and FP64 stages for
+// what it leaves undecided (shell_fast: binary search over the FP32 bands).
+__device__ __forceinline__ int32_t batch_key(float x, float y, float zc, const BatchItem& it,
+                                             const float* lo2, const float* hi2,
+                                             const ShellTable& st, const Bands& bd, int32_t N,
+                                             int32_t npix) {
+  const int lo = it.shell_lo, hi = it.shell_hi;
+  const float dx = (x + it.shf[0]) + it.shlo[0];
+  const float dy = (y + it.shf[1]) + it.shlo[1];
+  const float dz = (zc + it.shf[2]) + it.shlo[2];
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  int32_t key = kKeyUndecided;
+  if (r2 >= bd.r2_min && r2 <= 3.0e38f) {
+    const int32_t b = shell_fast(lo2, hi2, lo, hi, r2);
+    if (b == -1) {
+      key = kKeyOutside;
+    } else if (b >= 0) {
+      const int32_t pix = pixel_fast(N, bd, dx, dy, dz, r2);
+      if (pix != kKeyUndecided) key = b * npix + pix;
+    }
+  }
+  if (key == kKeyUndecided)
+    key = key_refine(st, lo, hi, N, npix, x, y, zc, it.shf[0], it.shf[1], it.shf[2], it.shlo[0],
+                     it.shlo[1], it.shlo[2]);
+  if (key == kKeyUndecided)
+    key = key_exact(st, lo, hi, N, npix, x, y, zc, it.sh64[0], it.sh64[1], it.sh64[2]);
+  return key;
+}
+
+__global__ void __launch_bounds__(kBT)
+k_batch_persistent(BatchArgs ba, ShellTable st, Bands bd, PdfParam pp) {
+  extern __shared__ __align__(16) uint8_t bsm[];   // PDF histogram, then Welford scratch
+  __shared__ float lo2_s[kMaxShells + 2], hi2_s[kMaxShells + 2];
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  __shared__ double red[kBT / 32];
+  __shared__ long long task_s;
+  __shared__ int flag_s;
+  __shared__ double mean_s;
+  for (int i = threadIdx.x; i <= st.nshell; i += kBT) { lo2_s[i] = st.lo2[i]; hi2_s[i] = st.hi2[i]; }
+  const int S = ba.S, npix = ba.npix, ng = npix >> 2;
+  for (;;) {
+    if (threadIdx.x == 0) task_s = (long long)atomicAdd(&ba.queue[0], 1ull);
+    __syncthreads();
+    const long long t = task_s;
+    if (t >= ba.ntasks) break;
+    // the task's item: the last one whose first task is <= t
+    int a = 0, b = ba.nitems;
+    while (b - a > 1) {
+      const int m = (a + b) >> 1;
+      if (ba.items[m].task0 <= t) a = m; else b = m;
+    }
+    const BatchItem it = ba.items[a];
+    const int r = it.real;
+    const int64_t p0 = (t - it.task0) * ba.chunk;
+    const int64_t cnt = min((int64_t)ba.chunk, it.n - p0);
+    int32_t* cmap = ba.counts + (size_t)r * S * npix;
+    for (int64_t i = threadIdx.x; i < cnt; i += kBT) {
+      const float* q = it.xyz + 3 * (p0 + i);
+      const int32_t key = batch_key(__ldg(q), __ldg(q + 1), __ldg(q + 2), it, lo2_s, hi2_s, st, bd,
+                                    ba.N, npix);
+      if (key >= 0) atomicAdd(cmap + key, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();                       // this block's keys before its count of the task
+      flag_s = atomicAdd(&ba.done[r], 1u) == (unsigned)(ba.ntask_r[r] - 1);
+    }
+    __syncthreads();
+    if (!flag_s) continue;
+    // ---- the last task of realisation r: its map, moments, PDF, statistics
+    __threadfence();                         // every block's keys of r are visible
+    const Coef& cf = ba.coef[r];
+    for (int i = threadIdx.x; i < S; i += kBT) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+    __syncthreads();
+    const f2 mc{-cf.ch, -cf.cl};
+    float* kap = ba.kappa + (size_t)r * npix;
+    double* ks = ba.ksum + (size_t)r * ba.gk;
+    for (int vb = 0; vb < ba.gk; ++vb) {
+      if (vb * kKV < ng) {                   // uniform; the serial blocks past the map add 0.0
+        const double v = kappa_vec_block(cmap, ah_s, al_s, S, npix, mc, kap, vb, ba.gk, red);
+        if (threadIdx.x == 0) ks[vb] = v;
+      } else if (threadIdx.x == 0) {
+        ks[vb] = 0.0;
+      }
+    }
+    unsigned int* hist = reinterpret_cast<unsigned int*>(bsm);
+    for (int i = threadIdx.x; i < ba.nbins + 3; i += kBT) hist[i] = 0u;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const double sum = warp_sum_fixed(ks, ba.gk, 1);      // fixed order, as k_moments
+      if (threadIdx.x == 0) mean_s = sum / double(npix);
+    }
+    __syncthreads();
+    double* mp = ba.mpart + (size_t)r * 3 * ba.gm;
+    for (int vb = 0; vb < ba.gm; ++vb) {
+      if (vb * kMT < npix) {
+        double o[3];
+        moments_block(kap, npix, mean_s, pp, vb, ba.gm, hist, red, o);
+        if (threadIdx.x == 0) { mp[3 * vb] = o[0]; mp[3 * vb + 1] = o[1]; mp[3 * vb + 2] = o[2]; }
+      } else if (threadIdx.x == 0) {
+        mp[3 * vb] = 0.0; mp[3 * vb + 1] = 0.0; mp[3 * vb + 2] = 0.0;
+      }
+    }
+    __syncthreads();
+    double* mo = ba.moments + 10 * (size_t)r;
+    int64_t* pd = ba.pdf + (size_t)(ba.nbins + 3) * r;
+    if (threadIdx.x < 32) moments_final_warp(ks, ba.gk, mp, ba.gm, npix, mo);
+    for (int i = threadIdx.x; i < ba.nbins + 3; i += kBT) pd[i] = (int64_t)hist[i];
+    __syncthreads();
+    double* v = ba.stats + (size_t)ba.d * r;
+    for (int i = threadIdx.x; i < ba.d; i += kBT) v[i] = i < 6 ? mo[i] : double(pd[i - 6]) / mo[9];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();                       // r's results before its count
+      flag_s = atomicAdd(&ba.queue[1], 1ull) == (unsigned long long)(ba.nreal - 1);
+    }
+    __syncthreads();
+    if (flag_s) {                            // the last realisation: the covariance update
+      __threadfence();
+      welford_update_block(ba.stats, ba.nreal, ba.d, ba.state, reinterpret_cast<double*>(bsm),
+                           welford_run(ba.d));
+    }
+    __syncthreads();
   }
 }
 
@@ -695,9 +922,7 @@ static ufc_status launch_kappa_fwd(ufc_ctx* c, const int32_t* counts, const Coef
 
 // Moments and PDF of an FP32 map whose per-block sums (grid of them) are in
 // ksum: the second pass over the map and the final reduction.
-static ufc_status launch_moments(ufc_ctx* c, const float* kmap, int npix, const double* ksum,
-                                 int grid, double lo, double hi, int nbins, double* mpart,
-                                 int mgrid, double* moments, int64_t* pdf, bool timed) {
+static PdfParam make_pdf_param(double lo, double hi, int nbins) {
   PdfParam pp;
   pp.lo = lo;
   pp.hi = hi;
@@ -715,6 +940,13 @@ static ufc_status launch_moments(ufc_ctx* c, const float* kmap, int npix, const 
   pp.lo_up = fup(lo);
   pp.hi_dn = fdn(hi);
   pp.hi_up = fup(hi);
+  return pp;
+}
+
+static ufc_status launch_moments(ufc_ctx* c, const float* kmap, int npix, const double* ksum,
+                                 int grid, double lo, double hi, int nbins, double* mpart,
+                                 int mgrid, double* moments, int64_t* pdf, bool timed) {
+  const PdfParam pp = make_pdf_param(lo, hi, nbins);
   UFC_CUDA(c, cudaMemsetAsync(pdf, 0, (size_t)(nbins + 3) * 8, c->stream));
   const int smem = (nbins + 3) * 4;
   {
@@ -975,10 +1207,9 @@ ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, doub
   if (!v || !st || nvec < 0 || d < 1 || d > 8192)
     return set_err(c, UFC_ERR_ARG, "welford_update: bad arguments");
   if (nvec == 0) return UFC_OK;
-  const int smem = 2 * d * 8;   // up to 128 KB at d = 8192: above the 48 KB default
-  if (smem > 48 * 1024)
-    UFC_CUDA(c, cudaFuncSetAttribute(k_welford_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     smem));
+  const int smem = 2 * welford_run(d) * d * 8;   // up to 128 KB at d = 8192
+  UFC_CUDA(c, cudaFuncSetAttribute(k_welford_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem));
   {
     ProfScope ps_(c, "k_welford_update");
     k_welford_update<<<1, 1024, smem, c->stream>>>(v, nvec, d, st);
@@ -1007,4 +1238,154 @@ ufc_status run_welford_finalize(ufc_ctx* c, const double* st, int d, int ddof, d
   return UFC_OK;
 }
 
+// ---- persistent batched call: host side ------------------------------------
+ufc_status batch_geometry(ufc_ctx* c, const double* chi, int nshell, const ufc_box* boxes,
+                          int nbox, ShellTable& st, BoxGeom* bg);
+void batch_bands(int nside, float smax, Bands& bd);
+
+// Workspace of the persistent batch kernel: per realisation a count map, a
+// kappa map and the partial sums of the serial grids (256-byte aligned
+// pieces), and the descriptors.
+static size_t batch_map_stride(int S, int nside) {
+  return ((size_t)S * 12 * nside * nside * 4 + 255) / 256 * 256;
+}
+void batch_persistent_bytes(const ufc_ctx* c, int nreal, int nbox, int S, int nside,
+                            size_t* maps, size_t* desc) {
+  const size_t npix = 12ull * nside * nside;
+  const size_t kap_b = (npix * 4 + 255) / 256 * 256;
+  const size_t part_b = ((size_t)(8 * c->num_sms + 3 * 2 * c->num_sms) * 8 + 255) / 256 * 256;
+  *maps = (batch_map_stride(S, nside) + kap_b + part_b) * nreal;
+  *desc = ((size_t)nreal * nbox * sizeof(BatchItem) + 255) / 256 * 256 +
+          ((size_t)nreal * sizeof(Coef) + 255) / 256 * 256 + ((size_t)nreal * 4 + 255) / 256 * 256 +
+          16 + (size_t)nreal * 4 + 256;
+}
+
+struct BatchLaunch {
+  BatchArgs ba;
+  ShellTable st;
+  Bands bd;
+  PdfParam pp;
+  size_t zero_maps;          // bytes of count maps to clear at each launch
+  size_t q_off, q_bytes;     // queue counters in the descriptor buffer
+  int grid, smem;
+};
+
+// Host set-up of a persistent batched call: geometry, descriptors uploaded
+// into `desc` (synchronises the context stream; never under stream capture),
+// launch arguments kept in the context.
+ufc_status batch_persistent_prepare(ufc_ctx* c, int nreal, int nbox, const float* const* xyz,
+                                    const int64_t* n, const ufc_box* boxes, const double* chi,
+                                    int S, int nside, const double* A, const double* C, double lo,
+                                    double hi, int nbins, double* moments, int64_t* pdf,
+                                    double* stats, double* state, char* maps, char* desc) {
+  const int npix = 12 * nside * nside;
+  const int nitems = nreal * nbox;
+  const int chunk = c->batch_chunk > 0 ? c->batch_chunk : 8192;
+  const int bps = c->batch_blocks_per_sm > 0 ? c->batch_blocks_per_sm : 2;
+  std::vector<BoxGeom> bg(nbox);
+  BatchLaunch L;
+  std::memset(&L, 0, sizeof L);
+  std::vector<BatchItem> items(nitems);
+  std::vector<int32_t> ntask_r(nreal, 0);
+  float smax = 0.f;
+  int64_t task = 0;
+  for (int r = 0; r < nreal; ++r) {
+    ufc_status s = batch_geometry(c, chi, S, boxes + (size_t)r * nbox, nbox, L.st, bg.data());
+    if (s) return s;
+    for (int k = 0; k < nbox; ++k) {
+      const size_t i = (size_t)r * nbox + k;
+      BatchItem& it = items[i];
+      const BoxGeom& g = bg[k];
+      if (n[i] < 0) return set_err(c, UFC_ERR_ARG, "n[%zu] < 0", i);
+      if (n[i] > 0 && !xyz[i]) return set_err(c, UFC_ERR_ARG, "xyz[%zu] is NULL", i);
+      smax = std::max(smax, g.smax);
+      it.xyz = xyz[i];
+      it.n = n[i];
+      it.task0 = task;
+      it.real = r;
+      it.shell_lo = g.shell_lo;
+      it.shell_hi = g.shell_hi;
+      for (int ax = 0; ax < 3; ++ax) {
+        it.shf[ax] = g.shf[ax][0];
+        it.shlo[ax] = g.shlo[ax][0];
+        it.sh64[ax] = g.sh64[ax][0];
+      }
+      const int64_t nt = std::max<int64_t>(1, (it.n + chunk - 1) / chunk);   // empty: one task
+      task += nt;
+      ntask_r[r] += (int32_t)nt;
+    }
+  }
+  batch_bands(nside, smax, L.bd);        // the bands of the largest shift of all the boxes
+  std::vector<Coef> coef(nreal);
+  for (int r = 0; r < nreal; ++r) make_coef(A + (size_t)r * S, C[r], S, npix, coef[r]);
+  const size_t o_coef = ((size_t)nitems * sizeof(BatchItem) + 255) / 256 * 256;
+  const size_t o_nt = o_coef + ((size_t)nreal * sizeof(Coef) + 255) / 256 * 256;
+  const size_t o_q = o_nt + ((size_t)nreal * 4 + 255) / 256 * 256;
+  std::vector<char> host(o_q);
+  std::memcpy(host.data(), items.data(), (size_t)nitems * sizeof(BatchItem));
+  std::memcpy(host.data() + o_coef, coef.data(), (size_t)nreal * sizeof(Coef));
+  std::memcpy(host.data() + o_nt, ntask_r.data(), (size_t)nreal * 4);
+  UFC_CUDA(c, cudaMemcpyAsync(desc, host.data(), host.size(), cudaMemcpyHostToDevice, c->stream));
+  UFC_CUDA(c, cudaStreamSynchronize(c->stream));   // (host staging leaves scope)
+  const int gk = kappa_fwd_grid(c), gm = 2 * c->num_sms;
+  const size_t map_b = batch_map_stride(S, nside);
+  const size_t kap_b = ((size_t)npix * 4 + 255) / 256 * 256;
+  BatchArgs& ba = L.ba;
+  ba.items = reinterpret_cast<const BatchItem*>(desc);
+  ba.nitems = nitems;
+  ba.chunk = chunk;
+  ba.ntasks = task;
+  ba.coef = reinterpret_cast<const Coef*>(desc + o_coef);
+  ba.ntask_r = reinterpret_cast<const int32_t*>(desc + o_nt);
+  ba.nreal = nreal;
+  ba.S = S;
+  ba.N = nside;
+  ba.npix = npix;
+  ba.counts = reinterpret_cast<int32_t*>(maps);
+  ba.kappa = reinterpret_cast<float*>(maps + map_b * nreal);
+  ba.ksum = reinterpret_cast<double*>(maps + (map_b + kap_b) * nreal);
+  ba.mpart = ba.ksum + (size_t)gk * nreal;
+  ba.gk = gk;
+  ba.gm = gm;
+  ba.moments = moments;
+  ba.pdf = pdf;
+  ba.stats = stats;
+  ba.state = state;
+  ba.nbins = nbins;
+  ba.d = 6 + nbins;
+  ba.queue = reinterpret_cast<unsigned long long*>(desc + o_q);
+  ba.done = reinterpret_cast<unsigned int*>(desc + o_q + 16);
+  if (map_b != (size_t)S * npix * 4)      // maps are indexed as [nreal][S][npix]
+    return set_err(c, UFC_ERR_UNSUPPORTED, "persistent batch: map size not a multiple of 256 B");
+  L.pp = make_pdf_param(lo, hi, nbins);
+  L.zero_maps = map_b * nreal;
+  L.q_off = o_q;
+  L.q_bytes = 16 + (size_t)nreal * 4;
+  L.grid = std::min(bps, 2) * c->num_sms;
+  L.smem = std::max((nbins + 3) * 4, 2 * welford_run(6 + nbins) * (6 + nbins) * 8);
+  c->batch_launch.resize(sizeof L);
+  std::memcpy(c->batch_launch.data(), &L, sizeof L);
+  // (static plus dynamic shared memory may pass the 48 KB default)
+  UFC_CUDA(c, cudaFuncSetAttribute(k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   L.smem));
+  return UFC_OK;
+}
+
+// The launch itself (capturable): clear the maps and the queue, run the kernel.
+ufc_status batch_persistent_enqueue(ufc_ctx* c, char* maps, char* desc) {
+  if (c->batch_launch.size() != sizeof(BatchLaunch))
+    return set_err(c, UFC_ERR_ARG, "persistent batch: no prepared launch");
+  BatchLaunch L;
+  std::memcpy(&L, c->batch_launch.data(), sizeof L);
+  UFC_CUDA(c, cudaMemsetAsync(maps, 0, L.zero_maps, c->stream));
+  UFC_CUDA(c, cudaMemsetAsync(desc + L.q_off, 0, L.q_bytes, c->stream));
+  {
+    ProfScope ps_(c, "k_batch_persistent");
+    k_batch_persistent<<<L.grid, kBT, L.smem, c->stream>>>(L.ba, L.st, L.bd, L.pp);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
 }  // namespace ufc
+

@@ -34,14 +34,16 @@ def _realisations(orc, api, nreal, nside, nshell, nbase):
     return z, chi, xs, bxs, np.array(As), np.array(Cs)
 
 
-@pytest.mark.parametrize("graph,side_stream,nreal", [(False, True, 5), (True, True, 5),
-                                                    (True, False, 5), (True, True, 19),
-                                                    (False, False, 19)])
-def test_batched_equals_serial(orc, graph, side_stream, nreal):
+@pytest.mark.parametrize("graph,side_stream,nreal,launches",
+                         [(False, True, 5, False), (True, True, 5, False), (True, False, 5, False),
+                          (True, True, 19, False), (False, False, 19, False),
+                          (False, True, 5, True), (True, True, 19, True), (False, False, 19, True)])
+def test_batched_equals_serial(orc, graph, side_stream, nreal, launches):
     """Batched call = the same maps one at a time, bit for bit; with the
     graph on a side stream and on the legacy default stream (captured on
-    the context's own stream, joined by events).  Small maps run on up to 8
-    concurrent lanes: 19 realisations use every lane more than once."""
+    the context's own stream, joined by events).  Small maps run as one
+    persistent kernel, or (launches) on up to 8 concurrent lanes: 19
+    realisations use every lane more than once."""
     api, ctx = api_ctx()
     nside, nshell, nb = 64, 12, 100_000
     z, chi, xs, bxs, A, C = _realisations(orc, api, nreal, nside, nshell, nb)
@@ -63,11 +65,11 @@ def test_batched_equals_serial(orc, graph, side_stream, nreal):
         stream = torch.cuda.Stream()
         with torch.cuda.stream(stream):
             mom, pdf, stats = ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, st_b,
-                                                graph=graph)
+                                                graph=graph, launches=launches)
         stream.synchronize()
     else:
         mom, pdf, stats = ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, st_b,
-                                            graph=graph)
+                                            graph=graph, launches=launches)
         # ordered on the default stream: no explicit synchronisation before use
         mom, pdf, stats = mom.clone(), pdf.clone(), stats.clone()
         torch.cuda.synchronize()
@@ -75,7 +77,7 @@ def test_batched_equals_serial(orc, graph, side_stream, nreal):
         assert torch.equal(mom[r], serial[r][0])
         assert torch.equal(pdf[r], serial[r][1])
         assert torch.equal(stats[r], serial[r][2])
-    assert torch.allclose(st_b, st_s, rtol=1e-12, atol=0)
+    assert torch.equal(st_b, st_s)             # the same update, in the same order
     mean, cov, corr = ctx.welford_finalize(st_b, d, 1)
     m_o, c_o, r_o = orc.covariance(stats.cpu().numpy(), 1)
     assert np.allclose(cov.cpu().numpy(), c_o, rtol=1e-9, atol=1e-15)
@@ -212,3 +214,32 @@ def test_batched_lanes_grow_between_graph_calls(orc):
             counts = ctx.bin(xs[r], bxs[r], chi, nside)
             _, m1, p1 = ctx.kappa_stats(counts, A[r], C[r], lo, hi, nbins)
             assert torch.equal(mom[r], m1) and torch.equal(pdf[r], p1)
+
+
+@pytest.mark.parametrize("chunk,bps", [(1000, 1), (8192, 2), (100_000, 2)])
+def test_persistent_batch_tuning_keeps_results(orc, chunk, bps):
+    """The persistent kernel's chunk size and blocks per SM (the autotuner's
+    choices) change only the speed: every setting gives the serial results
+    bit for bit, including realisations whose boxes hold no particle."""
+    api, ctx = api_ctx()
+    nreal, nside, nshell = 7, 32, 9
+    z, chi, xs, bxs, A, C = _realisations(orc, api, nreal, nside, nshell, 30_000)
+    xs[3] = [x[:0] for x in xs[3]]             # an empty realisation (its moments are NaN)
+    nbins, lo, hi, d = 17, -0.05, 0.2, 6 + 17
+    ref = []
+    for r in range(nreal):
+        counts = ctx.bin(xs[r], bxs[r], chi, nside)
+        _, m, p = ctx.kappa_stats(counts, A[r], C[r], lo, hi, nbins)
+        ref.append((m.clone(), p.clone()))
+    old = ctx.get_tuning()
+    try:
+        ctx.set_tuning(chunk, bps)
+        st = api.welford_state(d)
+        mom, pdf, stats = ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, st, graph=False)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_tuning(**old)
+    for r in range(nreal):       # bit patterns (NaN included)
+        assert torch.equal(mom[r].view(torch.int64), ref[r][0].view(torch.int64)), r
+        assert torch.equal(pdf[r], ref[r][1]), r
+    assert st[0].item() == nreal
