@@ -479,8 +479,12 @@ def main():
         if sub and dist:
             dist.all_reduce(counts, op=dist.ReduceOp.SUM)
 
+    # binning path: the autotuner's choice for this shape (timed once, cached),
+    # unless --path forces one
+    from paper_1801_05745_gb300 import autotune
+    bin_path = args.path or autotune.choose_bin_path(ctx, parts, boxes, chi, w.nside, counts=counts)
     # PDF range from a first map: mean +- 6 sigma, then fixed
-    ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=args.path)
+    ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=bin_path)
     combine()
     _, mom, _ = ctx.kappa_stats(counts, A, C, -1.0, 1.0, w.pdf_bins, kappa=kap)
     m0 = mom.cpu().numpy()
@@ -488,9 +492,9 @@ def main():
 
     def step(host=None):
         if host is None:
-            ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=args.path)
+            ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=bin_path)
         else:                                    # host buffers through ufc_bin_host
-            ctx.bin_host(host, boxes, chi, w.nside, counts=counts, path=args.path)
+            ctx.bin_host(host, boxes, chi, w.nside, counts=counts, path=bin_path)
         combine()
         _, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, w.pdf_bins, kappa=kap)
         ctx.stats_vector(mom, pdf, out=vec)
@@ -558,7 +562,8 @@ def main():
         "scaling": "strong" if sub else "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": w.name, "particles_per_gpu": n_local, "particles_per_map": n_total,
-                   "boxes": "2000 and 6400 Mpc/h", "path": args.path or "library choice",
+                   "boxes": "2000 and 6400 Mpc/h",
+                   "bin_path": bin_path + (" (forced)" if args.path else " (autotuned)"),
                    "nside": w.nside, "nshell": w.nshell, "source": "Smail n(z) a=2 b=1.5 z0=0.5",
                    "l2": f"inputs larger than L2 ({12 * n_local / 1e9:.1f} GB of particles per step)",
                    "parallelism": (f"subvolumes x{world} (count maps all-reduced)" if sub

@@ -295,12 +295,16 @@ class Context:
     def bin(self, xyz_list, boxes, chi_edges, nside: int, counts=None, accumulate=False,
             path: str | None = None):
         """int32 [nshell, 12 nside^2] count maps of the lightcone (Eq. 5, 8).
-        path: None (library choice), "direct" or "dense" (see UFC_BIN_FORCE_*)."""
+        path: None (the autotuner's cached choice for this shape if there is
+        one, else the library's), "direct" or "dense" (UFC_BIN_FORCE_*)."""
         import torch
         chi = np.ascontiguousarray(chi_edges, dtype=np.float64)
         S = len(chi) - 1
         npix = 12 * nside * nside
         xs = [_dev_f32(x, self.device) for x in xyz_list]
+        if path is None:
+            from . import autotune
+            path = autotune.cached_bin_path(self, nside, S, sum(x.numel() // 3 for x in xs))
         if counts is None:
             counts = torch.empty((S, npix), dtype=torch.int32, device=f"cuda:{self.device}")
         assert counts.dtype == torch.int32 and counts.is_contiguous() and counts.numel() == S * npix

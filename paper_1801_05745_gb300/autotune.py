@@ -24,12 +24,33 @@ def cache_path() -> str:
                                        "autotune.json"))
 
 
+_memo: dict = {}     # path -> (mtime, contents): the cache file is read once per change
+_names: dict = {}    # device index -> GPU name
+
+
 def _load() -> dict:
+    p = cache_path()
     try:
-        with open(cache_path()) as f:
-            return json.load(f)
+        mt = os.path.getmtime(p)
+    except OSError:
+        return {}
+    hit = _memo.get(p)
+    if hit and hit[0] == mt:
+        return dict(hit[1])
+    try:
+        with open(p) as f:
+            d = json.load(f)
     except Exception:
         return {}
+    _memo[p] = (mt, d)
+    return dict(d)
+
+
+def _gpu_name(device: int) -> str:
+    if device not in _names:
+        import torch
+        _names[device] = torch.cuda.get_device_name(device)
+    return _names[device]
 
 
 def _store(d: dict) -> None:
@@ -45,6 +66,14 @@ def tune_key(gpu_name: str, nside: int, nshell: int, n_total: int) -> str:
     """Particle counts are bucketed by powers of 2."""
     nb = int(math.log2(max(1, n_total)))
     return f"{gpu_name}|nside={nside}|nshell={nshell}|log2n={nb}"
+
+
+def cached_bin_path(ctx, nside: int, nshell: int, n_total: int):
+    """The cached binning path ('direct' or 'dense') for this shape, or None."""
+    key = tune_key(_gpu_name(ctx.device), nside, nshell, n_total)
+    with _lock:
+        e = _load().get(key)
+    return e["path"] if e else None
 
 
 def choose_bin_path(ctx, xyz_list, boxes, chi_edges, nside: int, counts=None, reps: int = 2,
@@ -92,8 +121,7 @@ def batch_key(gpu_name: str, nside: int, nshell: int, nreal: int, n_total: int) 
 
 def cached_batch_tuning(ctx, nside: int, nshell: int, nreal: int, n_total: int):
     """The cached (batch_chunk, batch_blocks_per_sm) for this shape, or None."""
-    import torch
-    key = batch_key(torch.cuda.get_device_name(ctx.device), nside, nshell, nreal, n_total)
+    key = batch_key(_gpu_name(ctx.device), nside, nshell, nreal, n_total)
     with _lock:
         e = _load().get(key)
     return (e["batch_chunk"], e["batch_blocks_per_sm"]) if e else None

@@ -380,7 +380,9 @@ constexpr float kRefineRel = 9.3132257e-10f;   // 2^-30
 
 // Key of one particle image by the refine stage: shell*npix + pix,
 // kKeyOutside, or kKeyUndecided.  d = x + (shf + shlo) per axis.
-__device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
+// (chih, chil: the shell edges as double-float, ShellTable's arrays or a
+// shared-memory copy of them, which lane-divergent indexing favours)
+__device__ __forceinline__ int32_t key_refine(const float* chih, const float* chil, int32_t lo,
                                               int32_t hi, int32_t N, int32_t npix,
                                               float x, float y, float zc,
                                               float shx, float shy, float shz,
@@ -399,12 +401,12 @@ __device__ __forceinline__ int32_t key_refine(const ShellTable& st, int32_t lo,
   int32_t cand = lo - 1;
   for (int32_t L = lo, H = hi; L <= H;) {
     const int32_t mid = (L + H) >> 1;
-    if (st.chih[mid] <= r.h) { cand = mid; L = mid + 1; } else { H = mid - 1; }
+    if (chih[mid] <= r.h) { cand = mid; L = mid + 1; } else { H = mid - 1; }
   }
   const int32_t e0 = cand - 1 > lo ? cand - 1 : lo;
   int32_t b = e0 - 1;                                // lo - 1: below the first edge
   for (int32_t e = e0; e <= hi; ++e) {
-    df c = {st.chih[e], st.chil[e]};
+    df c = {chih[e], chil[e]};
     df dd = df_sub(r, c);
     float tol = 4.0f * kRefineRel * r.h;
     if (fabsf(dd.h) <= tol) return kKeyUndecided;
