@@ -490,16 +490,25 @@ def main():
     m0 = mom.cpu().numpy()
     lo, hi = float(m0[0] - 6 * m0[1] ** 0.5), float(m0[0] + 6 * m0[1] ** 0.5)
 
+    nvtx = torch.cuda.nvtx
+
     def step(host=None):
+        # NVTX ranges of the step's phases (the library adds one per kernel)
+        nvtx.range_push("bin")
         if host is None:
             ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=bin_path)
         else:                                    # host buffers through ufc_bin_host
             ctx.bin_host(host, boxes, chi, w.nside, counts=counts, path=bin_path)
         combine()
+        nvtx.range_pop()
+        nvtx.range_push("kappa_stats_covariance")
         _, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, w.pdf_bins, kappa=kap)
         ctx.stats_vector(mom, pdf, out=vec)
         ctx.welford_update(vec.view(1, d), wstate)
+        nvtx.range_pop()
+        nvtx.range_push("adjoint")
         grad, _, _ = ctx.kappa_backward(counts, A, C, dA, dC, 1.0, 1.0)
+        nvtx.range_pop()
         return mom, pdf, grad
 
     for _ in range(args.warmup):

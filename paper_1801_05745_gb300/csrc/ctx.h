@@ -7,6 +7,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/ufalcon.h"
 
@@ -95,15 +96,24 @@ inline ufc_status set_err(ufc_ctx* c, ufc_status s, const char* fmt, ...) {
                             cudaGetErrorString(e_), __FILE__, __LINE__);        \
   } while (0)
 
-// Kernel timing.  prof_begin/prof_end bracket one launch on the context's
-// stream when timing is enabled (ufc_profile_enable).
+// Kernel timing and tracing.  prof_begin/prof_end bracket one launch on the
+// context's stream with CUDA events when timing is enabled
+// (ufc_profile_enable).  Every launch is also an NVTX range named after its
+// kernel (header-only NVTX 3: a no-op unless a tool such as Nsight Systems
+// is attached), so a timeline shows the library's steps.
 void prof_begin(ufc_ctx* c, const char* name);
 void prof_end(ufc_ctx* c);
 
 struct ProfScope {
   ufc_ctx* c;
-  ProfScope(ufc_ctx* c_, const char* name) : c(c_) { prof_begin(c, name); }
-  ~ProfScope() { prof_end(c); }
+  ProfScope(ufc_ctx* c_, const char* name) : c(c_) {
+    nvtxRangePushA(name);
+    prof_begin(c, name);
+  }
+  ~ProfScope() {
+    prof_end(c);
+    nvtxRangePop();
+  }
 };
 
 // Ensures slot `s` holds at least `bytes`; returns nullptr (and sets the

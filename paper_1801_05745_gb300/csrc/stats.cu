@@ -242,16 +242,23 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
 // tile) triggers a flush before any 64-bit sum could overflow.  More than 96
 // shells take one launch per window of 96 shells (phase 1 reads all shells
 // in each).
-constexpr int kAdjThreads = 1024;         // 32 warps, 4096-pixel tiles
-constexpr int kAdjSpw = 3;                // shells per warp in phase 2 (nshell <= 96)
+// Block sizes (4 pixels per thread, 3 shells per warp): 640 threads (2560-
+// pixel tiles, 60 shells per launch) for maps of up to 60 shells, 768 (3072-
+// pixel tiles, 72 shells) above.  Measured at 60 shells, Nside 1024: 1024
+// threads 1.34 ms, 896 1.34, 832 1.30, 768 1.08, 704 1.20, 640 1.04 (12
+// shells unrolled in phase 1); the tiles in flight of the smaller blocks
+// (152 x 2560 pixels x 60 shells x 4 B = 93 MB) stay in L2 for phase 2.
+constexpr int kAdjThreadsSmall = 640;
+constexpr int kAdjThreadsLarge = 768;
+constexpr int kAdjSpw = 3;                // shells per warp in phase 2
 
-template <bool USE_G>
-__global__ void __launch_bounds__(kAdjThreads, 1)
+template <bool USE_G, int NT>
+__global__ void __launch_bounds__(NT, 1)
 k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
            double* __restrict__ rows_out, double* __restrict__ sumpart,
            unsigned long long* range_flag, int s0) {
   extern __shared__ __align__(16) uint8_t adj_sm[];
-  constexpr int T = kAdjThreads, NW = T / 32, TP = 4 * T;
+  constexpr int T = NT, NW = T / 32, TP = 4 * T;
   int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP] quantised e, e^2, g
   float* ef_s = reinterpret_cast<float*>(adj_sm);            // the same memory: e, e^2 as floats
   float* ps_s = reinterpret_cast<float*>(adj_sm + 24 * TP);   // [8][T] this thread's power sums
@@ -313,7 +320,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
     if (have) {
       // shells unrolled for loads in flight (fewer with g, whose registers
       // would spill more)
-      constexpr int kU1 = USE_G ? 6 : 8;
+      constexpr int kU1 = USE_G ? 6 : 12;
 #pragma unroll kU1
       for (int b = 0; b < S; ++b) {
         const int4 n = c4[(size_t)b * ng + gi];
@@ -910,7 +917,6 @@ static ufc_status check_kappa_args(ufc_ctx* c, const int32_t* counts, int S, int
   return UFC_OK;
 }
 
-constexpr int kAdjMaxShells = kAdjSpw * (kAdjThreads / 32);
 
 // Forward kappa pass shared by ufc_kappa_stats and its allocation-free
 // variant (identical results): grid blocks, one partial sum each in ksum.
@@ -1056,28 +1062,28 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
   double* sums = part + nrow;
   BinCounters* bc = reinterpret_cast<BinCounters*>(c->counters);
   UFC_CUDA(c, cudaMemsetAsync(&bc->range, 0, sizeof(unsigned long long), c->stream));
-  // q_s, the threads' power sums, rows
-  const size_t smem2 = (size_t)24 * 4 * kAdjThreads + (size_t)32 * kAdjThreads +
-                       (size_t)S * sizeof(AdjRow);
+  // q_s, the threads' power sums, rows; one launch per window of shells
+  // (a launch's warps own 3 shells each); every launch recomputes e from all
+  // shells and writes the same power sums
+  const bool small = S <= kAdjSpw * (kAdjThreadsSmall / 32);
+  const int nt = small ? kAdjThreadsSmall : kAdjThreadsLarge;
+  const int win = kAdjSpw * (nt / 32);
+  const size_t smem2 = (size_t)24 * 4 * nt + (size_t)32 * nt + (size_t)S * sizeof(AdjRow);
   {
     ProfScope ps_(c, "k_adj_main");
-    if (g)
-      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-    else
-      UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));
-    // one launch per window of kAdjMaxShells shells (a launch's warps own
-    // 3 shells each); every launch recomputes e from all shells and writes
-    // the same power sums
-    for (int s0 = 0; s0 < S; s0 += kAdjMaxShells) {
-      if (g)
-        k_adj_main<true><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, g, rows, sums,
-                                                                    &bc->range, s0);
-      else
-        k_adj_main<false><<<grid2, kAdjThreads, smem2, c->stream>>>(counts, cf, nullptr, rows,
-                                                                     sums, &bc->range, s0);
-    }
+#define UFC_ADJ(G, NT_)                                                                           \
+  do {                                                                                            \
+    UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<G, NT_>,                                          \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));   \
+    for (int s0 = 0; s0 < S; s0 += win)                                                           \
+      k_adj_main<G, NT_><<<grid2, NT_, smem2, c->stream>>>(counts, cf, g, rows, sums, &bc->range, \
+                                                           s0);                                   \
+  } while (0)
+    if (g && small) UFC_ADJ(true, kAdjThreadsSmall);
+    else if (g) UFC_ADJ(true, kAdjThreadsLarge);
+    else if (small) UFC_ADJ(false, kAdjThreadsSmall);
+    else UFC_ADJ(false, kAdjThreadsLarge);
+#undef UFC_ADJ
   }
   UFC_CUDA(c, cudaGetLastError());
   std::vector<double> hp(nrow + nsum);
