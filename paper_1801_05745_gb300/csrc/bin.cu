@@ -484,11 +484,11 @@ __device__ __noinline__ int32_t key_exact_slow(const ShellTable& st, int32_t lo,
 // are drained after every (chunk, image) pass.  Particle p of the launch is
 // element p_off + p of the caller's array (chunked launches of ufc_bin_host).
 constexpr int kWThreads = 768;
-constexpr int kWChunk = 3072;                  // particles per chunk (36 KB)
+constexpr int kWChunk = 3840;                  // particles per chunk (45 KB)
 constexpr int kWStages = 2;                    // the stage index of the ring loop is k & 1
 static_assert(kWStages == 2, "the ring loop takes the stage of chunk k as k & 1");
 constexpr int kWWarps = kWThreads / 32;        // 24
-constexpr int kWPerWarp = kWChunk / kWWarps;   // 128
+constexpr int kWPerWarp = kWChunk / kWWarps;   // 160
 constexpr int kWGroups = kWPerWarp / 32;
 constexpr int kWList = 64;                     // entries of one pending list
 constexpr int kWAgeFlush = 1024;
