@@ -38,6 +38,11 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # launches of 134.2M particles: 1.868 and 1.838 GB); scaled to a launch by
 # its particle count.  Retake it whenever k_fast_tma changes.
 FAST_TRAFFIC_PER_PARTICLE = (1.611006e9 + 256.809728e6 + 1.611055e9 + 226.770176e6) / 2 / 134217728
+# DRAM bytes of every binning kernel above the algorithmic ones (particles
+# read, count maps written), per keyed particle: ncu dram__bytes_read+write
+# of one binning call of two boxes of 512^3 particles at Nside 1024, 60
+# shells (8.802 GB measured, 6.241 GB algorithmic, 125.0M keyed particles)
+BIN_SCRATCH_PER_KEY = (4.695745792e9 + 4.106062848e9 - 6.241124352e9) / 125014670
 
 
 def hbm_peak():
@@ -580,6 +585,10 @@ def main():
         "kappa_maps_per_s": (1 if sub else world) * 1e3 / ms,
         "roofline": roof,
         "binning": {"ms": bin_ms, "algorithmic_bytes": bin_bytes,
+                    "traffic": bin_bytes + BIN_SCRATCH_PER_KEY * info["keyed"],
+                    "traffic_source": "algorithmic bytes + scratch bytes per keyed particle "
+                                      "from an ncu capture of every binning kernel (2 x 512^3, "
+                                      "Nside 1024), times this step's keyed particles",
                     "frac_of_peak": bin_bytes / (bin_ms * 1e-3) / 1e9 / peak if bin_ms else None,
                     "refined": info["refined"], "exact": info["exact"], "keyed": info["keyed"]},
         "kappa_stats": {"ms": kap_ms / args.steps,
