@@ -344,6 +344,23 @@ ufc_status ufc_kappa_backward(ufc_ctx *ctx, const int32_t *counts_dev,
                               const double *dC, double *grad_theta, double *G,
                               double *H);
 
+/* ufc_kappa_stats and ufc_kappa_backward in one read of the counts: the
+ * adjoint's pass over the counts also rounds the unrounded map e_p (built in
+ * the same shell order as the forward pass) to the FP32 kappa_dev
+ * ([npix], 16-byte aligned, required), so kappa_dev, pdf_dev and the
+ * gradient outputs equal those of the two separate calls bit for bit;
+ * moments_dev equal them to the last bits only (the map's mean is summed
+ * over a different grid of partial sums).  Arguments as for the two calls.
+ * Synchronises. */
+ufc_status ufc_kappa_stats_backward(ufc_ctx *ctx, const int32_t *counts_dev,
+                                    int32_t nshell, int32_t nside, const double *A,
+                                    double C, double pdf_lo, double pdf_hi,
+                                    int32_t nbins, double w_var, double w_skew,
+                                    const float *g_kappa_dev, const double *dA,
+                                    const double *dC, float *kappa_dev,
+                                    double *moments_dev, int64_t *pdf_dev,
+                                    double *grad_theta, double *G, double *H);
+
 /* ---- full-sky power spectrum (Sec. 3.2, Eq. 10-11) ------------------------- */
 
 /* Spherical-harmonic coefficients of a RING map (FP32 [12 nside^2], e.g.

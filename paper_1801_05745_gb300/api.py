@@ -101,6 +101,7 @@ _SIGS = {
     "ufc_bin_snapshots_host": [P, P, P, P, I32, P, P, I32, I32, I32, I64, P],
     "ufc_kappa_stats": [P, P, I32, I32, P, D, D, D, I32, P, P, P],
     "ufc_kappa_backward": [P, P, I32, I32, P, D, D, D, P, P, P, P, P, P],
+    "ufc_kappa_stats_backward": [P, P, I32, I32, P, D, D, D, I32, D, D, P, P, P, P, P, P, P, P, P],
     "ufc_welford_update": [P, P, I32, I32, P],
     "ufc_welford_merge": [P, P, P, I32],
     "ufc_welford_finalize": [P, P, I32, I32, P, P, P],
@@ -461,6 +462,36 @@ class Context:
                                          _np_ptr(dC), _np_ptr(grad), _np_ptr(G), ctypes.byref(H)),
                  "ufc_kappa_backward")
         return grad, G, H.value
+
+    def kappa_stats_backward(self, counts, A, C, dA, dC, pdf_lo, pdf_hi, nbins=200,
+                             w_var=0.0, w_skew=0.0, g_kappa=None, kappa=None):
+        """kappa_stats and kappa_backward in one read of the counts
+        (ufc_kappa_stats_backward): (kappa, moments, pdf, grad [5], G, H)."""
+        import torch
+        S, npix = counts.shape
+        nside = int(round((npix / 12) ** 0.5))
+        dev = counts.device
+        if kappa is None:
+            kappa = torch.empty(npix, dtype=torch.float32, device=dev)
+        mom = torch.empty(NMOMENTS, dtype=torch.float64, device=dev)
+        pdf = torch.empty(nbins + 3, dtype=torch.int64, device=dev)
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        dA = np.ascontiguousarray(dA, dtype=np.float64)
+        dC = np.ascontiguousarray(dC, dtype=np.float64)
+        grad, G, H = np.empty(5), np.empty(S), ctypes.c_double()
+        gp = None
+        if g_kappa is not None:
+            g_kappa = _dev_f32(g_kappa, self.device)
+            if g_kappa.data_ptr() % 16:
+                g_kappa = g_kappa.clone()
+            gp = P(g_kappa.data_ptr())
+        self._stream()
+        self._ck(_lib.ufc_kappa_stats_backward(
+            self.h, P(counts.data_ptr()), S, nside, _np_ptr(A), float(C), float(pdf_lo),
+            float(pdf_hi), nbins, float(w_var), float(w_skew), gp, _np_ptr(dA), _np_ptr(dC),
+            P(kappa.data_ptr()), P(mom.data_ptr()), P(pdf.data_ptr()), _np_ptr(grad), _np_ptr(G),
+            ctypes.byref(H)), "ufc_kappa_stats_backward")
+        return kappa, mom, pdf, grad, G, H.value
 
     # -- batched realisations --
     def set_tuning(self, batch_chunk: int = 0, batch_blocks_per_sm: int = 0):

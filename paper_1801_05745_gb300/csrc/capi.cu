@@ -21,6 +21,11 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
                               const double* A, double C, double w_var, double w_skew,
                               const float* g, const double* dA, const double* dC,
                               double* grad, double* G, double* H);
+ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                 const double* A, double C, double w_var, double w_skew,
+                                 const float* g, const double* dA, const double* dC,
+                                 double* grad, double* G, double* H, float* kappa, double lo,
+                                 double hi, int nbins, double* moments, int64_t* pdf);
 ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, double* st);
 ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins, double* v);
 ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int nside,
@@ -667,6 +672,23 @@ ufc_status ufc_kappa_backward(ufc_ctx* c, const int32_t* counts_dev, int32_t nsh
   cudaSetDevice(c->device);
   return run_kappa_backward(c, counts_dev, nshell, nside, A, C, w_var, w_skew, g_kappa_dev, dA,
                             dC, grad_theta, G, H);
+}
+
+ufc_status ufc_kappa_stats_backward(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell,
+                                    int32_t nside, const double* A, double C, double pdf_lo,
+                                    double pdf_hi, int32_t nbins, double w_var, double w_skew,
+                                    const float* g_kappa_dev, const double* dA, const double* dC,
+                                    float* kappa_dev, double* moments_dev, int64_t* pdf_dev,
+                                    double* grad_theta, double* G, double* H) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  if (!std::isfinite(w_var) || !std::isfinite(w_skew))
+    return set_err(c, UFC_ERR_ARG, "weights must be finite");
+  if (!kappa_dev) return set_err(c, UFC_ERR_ARG, "kappa_dev is NULL");
+  cudaSetDevice(c->device);
+  return run_kappa_backward_ex(c, counts_dev, nshell, nside, A, C, w_var, w_skew, g_kappa_dev, dA,
+                               dC, grad_theta, G, H, kappa_dev, pdf_lo, pdf_hi, nbins, moments_dev,
+                               pdf_dev);
 }
 
 ufc_status ufc_stats_vector(ufc_ctx* c, const double* moments_dev, const int64_t* pdf_dev,

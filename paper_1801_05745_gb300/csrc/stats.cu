@@ -256,7 +256,8 @@ template <bool USE_G, int NT>
 __global__ void __launch_bounds__(NT, 1)
 k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
            double* __restrict__ rows_out, double* __restrict__ sumpart,
-           unsigned long long* range_flag, int s0) {
+           unsigned long long* range_flag, int s0, float* __restrict__ kappa_out,
+           double* __restrict__ ksum_out) {
   extern __shared__ __align__(16) uint8_t adj_sm[];
   constexpr int T = NT, NW = T / 32, TP = 4 * T;
   int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP] quantised e, e^2, g
@@ -309,6 +310,7 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
   const f2 mc{-cf.ch, -cf.cl};
   const int ntile = (npix + TP - 1) / TP;
   double bound = 0.0;                      // bound on |any 64-bit sum|, uniform
+  f2 ks{0.f, 0.f};                         // this thread's sum of the FP32 map (kappa_out)
   for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     // phase 1: e of 4 adjacent pixels per thread (the shells in order, as in
     // the forward pass), the power sums and the tile's maxima; e and e^2
@@ -336,9 +338,11 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
     const float gs[4] = {gv4.x, gv4.y, gv4.z, gv4.w};
     float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+    float kv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       f2 e = f2_add(f2_norm(a[i].h, a[i].l), mc);
+      kv[i] = __fadd_rn(e.h, e.l);             // the FP32 map, as the forward pass rounds it
       f2 e2 = f2_mul(e, e);
       if (!have) { e = f2{0.f, 0.f}; e2 = f2{0.f, 0.f}; }
       t1 = fmaxf(t1, fabsf(e.h));
@@ -349,6 +353,10 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
       ef_s[TP + px] = e.l;
       ef_s[2 * TP + px] = e2.h;
       ef_s[3 * TP + px] = e2.l;
+    }
+    if (kappa_out && have) {                   // (uniform) the map itself, with its sum
+      reinterpret_cast<float4*>(kappa_out)[gi] = make_float4(kv[0], kv[1], kv[2], kv[3]);
+      ks = f2_add(ks, f2_add(f2_two_sum(kv[0], kv[1]), f2_two_sum(kv[2], kv[3])));
     }
     if (have) {
       f2 p1{ps_s[threadIdx.x], ps_s[T + threadIdx.x]};
@@ -452,6 +460,10 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
   }
   const f2 p1{ps_s[threadIdx.x], ps_s[T + threadIdx.x]}, p2{ps_s[2 * T + threadIdx.x], ps_s[3 * T + threadIdx.x]};
   const f2 p3{ps_s[4 * T + threadIdx.x], ps_s[5 * T + threadIdx.x]}, qg{ps_s[6 * T + threadIdx.x], ps_s[7 * T + threadIdx.x]};
+  if (kappa_out) {                         // (uniform)
+    const double vk = block_sum_d<T>(f2_to_d(ks), red);
+    if (threadIdx.x == 0) ksum_out[blockIdx.x] = vk;
+  }
   const double v1 = block_sum_d<T>(f2_to_d(p1), red);
   if (threadIdx.x == 0) sumpart[4 * blockIdx.x + 0] = v1;
   const double v2 = block_sum_d<T>(f2_to_d(p2), red);
@@ -1039,14 +1051,27 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
 }
 
 // Adjoint sums -> gradients (host FP64 assembly).  Synchronises.
-ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nside,
-                              const double* A, double C, double w_var, double w_skew,
-                              const float* g, const double* dA, const double* dC,
-                              double* grad, double* G, double* H) {
+// The adjoint sums of ufc_kappa_backward; with kappa (non-NULL) the same
+// launch also writes the FP32 map and its block sums, and the moment pass
+// gives moments and PDF (ufc_kappa_stats_backward).
+ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                 const double* A, double C, double w_var, double w_skew,
+                                 const float* g, const double* dA, const double* dC,
+                                 double* grad, double* G, double* H, float* kappa, double lo,
+                                 double hi, int nbins, double* moments, int64_t* pdf) {
   ufc_status s = check_kappa_args(c, counts, S, nside, A, C);
   if (s) return s;
   if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
   if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
+  if (kappa) {
+    if (!moments || !pdf) return set_err(c, UFC_ERR_ARG, "moments_dev and pdf_dev are required");
+    if (reinterpret_cast<uintptr_t>(kappa) & 15)
+      return set_err(c, UFC_ERR_ARG, "kappa_dev must be 16-byte aligned");
+    if (nbins < 1 || nbins > kMaxBins)
+      return set_err(c, UFC_ERR_ARG, "nbins must be in [1,%d]", kMaxBins);
+    if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+      return set_err(c, UFC_ERR_ARG, "PDF range needs finite lo < hi");
+  }
   const int npix = 12 * nside * nside;
   Coef cf;
   make_coef(A, C, S, npix, cf);
@@ -1056,10 +1081,14 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
     return set_err(c, UFC_ERR_ARG, "g_dev must be 16-byte aligned");
   const int grid2 = c->num_sms;                            // one block per SM
   const size_t nrow = (size_t)grid2 * 4 * S, nsum = (size_t)grid2 * 4;
-  double* part = (double*)ws_get(c, kSlotPartials, (nrow + nsum) * 8);
+  const int mgrid = 2 * c->num_sms;
+  const size_t nmap = kappa ? (size_t)grid2 + 3 * (size_t)mgrid : 0;   // map sums, moment partials
+  double* part = (double*)ws_get(c, kSlotPartials, (nrow + nsum + nmap) * 8);
   if (!part) return UFC_ERR_ALLOC;
   double* rows = part;
   double* sums = part + nrow;
+  double* ksum = sums + nsum;
+  double* mpart = ksum + grid2;
   BinCounters* bc = reinterpret_cast<BinCounters*>(c->counters);
   UFC_CUDA(c, cudaMemsetAsync(&bc->range, 0, sizeof(unsigned long long), c->stream));
   // q_s, the threads' power sums, rows; one launch per window of shells
@@ -1077,7 +1106,7 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));   \
     for (int s0 = 0; s0 < S; s0 += win)                                                           \
       k_adj_main<G, NT_><<<grid2, NT_, smem2, c->stream>>>(counts, cf, g, rows, sums, &bc->range, \
-                                                           s0);                                   \
+                                                           s0, s0 == 0 ? kappa : nullptr, ksum);  \
   } while (0)
     if (g && small) UFC_ADJ(true, kAdjThreadsSmall);
     else if (g) UFC_ADJ(true, kAdjThreadsLarge);
@@ -1086,6 +1115,11 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
 #undef UFC_ADJ
   }
   UFC_CUDA(c, cudaGetLastError());
+  if (kappa) {                             // moments and PDF of the map just written
+    s = launch_moments(c, kappa, npix, ksum, grid2, lo, hi, nbins, mpart, mgrid, moments, pdf,
+                       true);
+    if (s) return s;
+  }
   std::vector<double> hp(nrow + nsum);
   unsigned long long range_hits = 0;
   UFC_CUDA(c, cudaMemcpyAsync(hp.data(), part, hp.size() * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -1140,6 +1174,14 @@ ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nsid
     for (int b = 0; b < S; ++b) G[b] = Gb[b];
   if (H) *H = Hs;
   return UFC_OK;
+}
+
+ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                              const double* A, double C, double w_var, double w_skew,
+                              const float* g, const double* dA, const double* dC,
+                              double* grad, double* G, double* H) {
+  return run_kappa_backward_ex(c, counts, S, nside, A, C, w_var, w_skew, g, dA, dC, grad, G, H,
+                               nullptr, 0.0, 1.0, 1, nullptr, nullptr);
 }
 
 // ---- variant of ufc_kappa_stats that allocates nothing -------------------

@@ -229,3 +229,29 @@ def test_backward_large_counts_flush_path(orc):
     ref = G_or[0] + 0.5 * G_or[1]
     scale = np.abs(G_or[0]).max() + 0.5 * np.abs(G_or[1]).max()
     assert np.allclose(grad, ref, rtol=1e-8, atol=1e-9 * scale), (grad, ref)
+
+
+@pytest.mark.parametrize("nside,nshell,use_g", [(64, 20, False), (128, 60, True), (64, 80, False)])
+def test_fused_map_and_adjoint_equal_separate_calls(orc, nside, nshell, use_g):
+    """ufc_kappa_stats_backward (one read of the counts) against
+    ufc_kappa_stats then ufc_kappa_backward: the FP32 map, the PDF and the
+    gradient with G_b and H bit for bit; the moments to the last bits (the
+    mean's partial sums run over another grid) and against the oracle on
+    the map.  80 shells take two launch windows of the adjoint."""
+    api, ctx = api_ctx()
+    counts, z, ba, bo, kw = _map(orc, api, ctx, nside, nshell, 300_000, 99 + nshell)
+    A, B, C, dA, dC = api.kappa_coeffs(api.make_cosmo(), list(ba), z, nside,
+                                       api.make_source(**kw), derivs=True)
+    npix = 12 * nside * nside
+    g = torch.linspace(-1.0, 1.0, npix, device="cuda") if use_g else None
+    lo, hi = -0.02, 0.1
+    kap, mom, pdf = ctx.kappa_stats(counts, A, C, lo, hi, 64)
+    grad, G, H = ctx.kappa_backward(counts, A, C, dA, dC, 0.7, 1.3, g)
+    kf, mf, pf, gf, Gf, Hf = ctx.kappa_stats_backward(counts, A, C, dA, dC, lo, hi, 64, 0.7, 1.3, g)
+    torch.cuda.synchronize()
+    assert torch.equal(kf, kap)
+    assert torch.equal(pf, pdf)
+    assert np.array_equal(gf, grad) and np.array_equal(Gf, G) and Hf == H
+    mo = orc.moments(kf.cpu().numpy())
+    assert np.allclose(mf.cpu().numpy(), mom.cpu().numpy(), rtol=1e-13, atol=1e-18)
+    assert np.allclose(mf.cpu().numpy(), mo, rtol=1e-9, atol=1e-15)
