@@ -634,24 +634,30 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_e = float(t.item())
         h2d = int(sum(p.numel() * 4 for p in parts))
-        # the host-to-device link in the same run: one copy per box from the
-        # same pinned buffers into the device particle arrays (same bytes)
-        for h_, p_ in zip(host, parts):
-            p_.copy_(h_, non_blocking=True)
+        # the host-to-device link in the same run: the same pinned buffers
+        # copied into the device particle arrays (same bytes) in the
+        # library's staging chunks of 2^25 particles, best of two passes
+        def link_pass():
+            for h_, p_ in zip(host, parts):
+                for a in range(0, h_.shape[0], 1 << 25):
+                    p_[a:a + (1 << 25)].copy_(h_[a:a + (1 << 25)], non_blocking=True)
+        link_pass()
         torch.cuda.synchronize()
-        e0.record(stream)
-        for h_, p_ in zip(host, parts):
-            p_.copy_(h_, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_link = e0.elapsed_time(e1)
+        ms_link = float("inf")
+        for _ in range(2):
+            e0.record(stream)
+            link_pass()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_link = min(ms_link, e0.elapsed_time(e1))
         link_gbs = h2d / (ms_link * 1e-3) / 1e9
         line["e2e"] = {"value": (1 if sub else world) * n_total / (ms_e * 1e-3) / 1e9, "unit": UNIT,
                        "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": int(out_h.numel() * 8 + 5 * 8 + w.nshell * 8),
                        "ms_per_step": ms_e,
                        "h2d_link_gbs": link_gbs,
-                       "h2d_link_source": "cudaMemcpyAsync of the same pinned buffers, same run",
+                       "h2d_link_source": "cudaMemcpyAsync of the same pinned buffers in 2^25-particle "
+                                          "chunks, best of two passes, same run",
                        "frac_of_link": (h2d / (ms_e * 1e-3) / 1e9) / link_gbs}
         del host
 

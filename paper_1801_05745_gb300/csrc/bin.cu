@@ -1187,7 +1187,9 @@ __global__ void __launch_bounds__(kTilesThreads) k_tiles(const int64_t* __restri
 // Pass B: grouped keys -> per-bucket u16 offsets (two blocks per SM and the
 // same tile prefetch as pass A; a tile starts anywhere, so its copy starts
 // at the 16-byte unit holding its first key, and the grouped array has 4
-// keys of slack at its end).
+// keys of slack at its end).  The tile keeps each whole key, so that one
+// 32-bit shared store per key places it and the write-out reads the
+// destination digit back from the key.
 __global__ void __launch_bounds__(kScatThreads, 2)
 k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ tiles,
                  const unsigned long long* __restrict__ ntiles_p,
@@ -1202,8 +1204,7 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
       reinterpret_cast<unsigned long long*>(smb + 2 * (kScatTile + 4) * 4);  // [NS]
   uint32_t* cnt = reinterpret_cast<uint32_t*>(base + NS);                  // [NS]
   uint32_t* start = cnt + NS;                                              // [NS]
-  uint16_t* tile = reinterpret_cast<uint16_t*>(start + NS);                // [kScatTile]
-  uint8_t* tsub = reinterpret_cast<uint8_t*>(tile + kScatTile);            // [kScatTile]
+  uint32_t* tile = start + NS;                                             // [kScatTile]
   const int64_t ntiles = (int64_t)*ntiles_p;
   const int64_t mine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   auto tile_at = [&](int64_t i) -> const Tile& { return tiles[blockIdx.x + i * gridDim.x]; };
@@ -1254,14 +1255,12 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
     for (int k = 0; k < kScatPer; ++k)
       if (v[k] != kSentinel) {
         const uint32_t sub = (v[k] >> kOffBits) & (NS - 1);
-        const uint32_t pos = start[sub] + slot[k];
-        tile[pos] = uint16_t(v[k] & ((1u << kOffBits) - 1u));
-        tsub[pos] = uint8_t(sub);
+        tile[start[sub] + slot[k]] = v[k];
       }
     __syncthreads();
     for (int q = threadIdx.x; q < T.len; q += blockDim.x) {
-      const uint32_t sub = tsub[q];
-      out[base[sub] + q] = tile[q];
+      const uint32_t val = tile[q];
+      out[base[(val >> kOffBits) & (NS - 1)] + q] = uint16_t(val & ((1u << kOffBits) - 1u));
     }
     __syncthreads();
   }
@@ -1808,7 +1807,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
     k_tiles<<<c->num_sms, kTilesThreads, (size_t)(2 * ng + 2) * 8, c->stream>>>(off, nb, ng, tiles,
                                                                               ntiles);
   }
-  const int smemB = 2 * (kScatTile + 4) * 4 + (1 << kGroupBits) * 16 + kScatTile * 3;
+  const int smemB = 2 * (kScatTile + 4) * 4 + (1 << kGroupBits) * 16 + kScatTile * 4;
   UFC_CUDA(c, cudaFuncSetAttribute(k_scatter_bucket, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    smemB));
   {
