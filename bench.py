@@ -480,10 +480,9 @@ def main():
     wstate = api.welford_state(d, dev)
     vec = torch.empty(d, dtype=torch.float64, device=dev)
     ctx.reserve(w.nside, w.nshell, max(b.n for b in w.boxes))
-
-    def combine():                               # subvolume maps summed across ranks
-        if sub and dist:
-            dist.all_reduce(counts, op=dist.ReduceOp.SUM)
+    # subvolume split: the ranks' FP64 partial kappa sums (8 B per pixel) and
+    # the adjoint's per-shell sums are all-reduced, not the count maps
+    partial = torch.empty(npix, dtype=torch.float64, device=dev) if sub else None
 
     # binning path: the autotuner's choice for this shape (timed once, cached),
     # unless --path forces one
@@ -491,8 +490,11 @@ def main():
     bin_path = args.path or autotune.choose_bin_path(ctx, parts, boxes, chi, w.nside, counts=counts)
     # PDF range from a first map: mean +- 6 sigma, then fixed
     ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=bin_path)
-    combine()
-    _, mom, _ = ctx.kappa_stats(counts, A, C, -1.0, 1.0, w.pdf_bins, kappa=kap)
+    if sub:
+        _, mom, _ = parallel.subvolume_kappa(ctx, counts, A, C, -1.0, 1.0, w.pdf_bins, kappa=kap,
+                                             partial=partial)
+    else:
+        _, mom, _ = ctx.kappa_stats(counts, A, C, -1.0, 1.0, w.pdf_bins, kappa=kap)
     m0 = mom.cpu().numpy()
     lo, hi = float(m0[0] - 6 * m0[1] ** 0.5), float(m0[0] + 6 * m0[1] ** 0.5)
 
@@ -505,13 +507,19 @@ def main():
             ctx.bin(parts, boxes, chi, w.nside, counts=counts, path=bin_path)
         else:                                    # host buffers through ufc_bin_host
             ctx.bin_host(host, boxes, chi, w.nside, counts=counts, path=bin_path)
-        combine()
         nvtx.range_pop()
         # kappa map, moments, PDF and the adjoint of var + skew in one read of
-        # the counts (ufc_kappa_stats_backward), then the covariance update
+        # the counts (ufc_kappa_stats_backward; with the subvolume split the
+        # partial sums' all-reduce first, then ufc_kappa_adjoint_sums and the
+        # per-shell sums' all-reduce), then the covariance update
         nvtx.range_push("kappa_stats_adjoint")
-        _, mom, pdf, grad, _, _ = ctx.kappa_stats_backward(counts, A, C, dA, dC, lo, hi,
-                                                           w.pdf_bins, 1.0, 1.0, kappa=kap)
+        if sub:
+            _, mom, pdf, grad, _, _ = parallel.subvolume_kappa(
+                ctx, counts, A, C, lo, hi, w.pdf_bins, dA=dA, dC=dC, w_var=1.0, w_skew=1.0,
+                kappa=kap, partial=partial)
+        else:
+            _, mom, pdf, grad, _, _ = ctx.kappa_stats_backward(counts, A, C, dA, dC, lo, hi,
+                                                               w.pdf_bins, 1.0, 1.0, kappa=kap)
         nvtx.range_pop()
         nvtx.range_push("covariance")
         ctx.stats_vector(mom, pdf, out=vec)
@@ -561,7 +569,8 @@ def main():
                    "k_tiles", "k_scatter_bucket", "k_hist_block"]
     bin_ms = sum(prof[k][0] for k in bin_kernels if k in prof) / args.steps
     bin_bytes = 12.0 * n_local + 4.0 * w.nshell * npix
-    kap_ms = sum(prof[k][0] for k in ("k_adj_main", "k_moments", "k_moments_final") if k in prof)
+    kap_ms = sum(prof[k][0] for k in ("k_kappa_partial", "k_adj_main", "k_moments",
+                                      "k_moments_final") if k in prof)
     adj_launch = prof.get("k_adj_main", (0.0, 1))
     roof = {
         "bound": "hbm", "kernel": "k_fast",
@@ -583,8 +592,8 @@ def main():
                    "bin_path": bin_path + (" (forced)" if args.path else " (autotuned)"),
                    "nside": w.nside, "nshell": w.nshell, "source": "Smail n(z) a=2 b=1.5 z0=0.5",
                    "l2": f"inputs larger than L2 ({12 * n_local / 1e9:.1f} GB of particles per step)",
-                   "parallelism": (f"subvolumes x{world} (count maps all-reduced)" if sub
-                                   else f"realisations x{world}")},
+                   "parallelism": (f"subvolumes x{world} (FP64 partial kappa and adjoint sums "
+                                   "all-reduced)" if sub else f"realisations x{world}")},
         "kappa_maps_per_s": (1 if sub else world) * 1e3 / ms,
         "roofline": roof,
         "binning": {"ms": bin_ms, "algorithmic_bytes": bin_bytes,
@@ -596,10 +605,14 @@ def main():
                     "refined": info["refined"], "exact": info["exact"], "keyed": info["keyed"]},
         "kappa_stats_adjoint": {
             "ms": kap_ms / args.steps,
-            "k_adj_main_frac_of_peak": (4.0 * w.nshell * npix + 4.0 * npix) /
+            "k_adj_main_frac_of_peak": (4.0 * w.nshell * npix + (12.0 if sub else 4.0) * npix) /
             (adj_launch[0] / adj_launch[1] * 1e-3) / 1e9 / peak if adj_launch[0] else None,
-            "note": "one pass over the counts builds the FP32 map and the adjoint sums "
-                    "(counts 4 S B + map 4 B per pixel), then the moment pass"},
+            "note": ("one pass over the counts builds the FP32 map and the adjoint sums "
+                     "(counts 4 S B + map 4 B per pixel), then the moment pass" if not sub else
+                     "the partial sum of the rank's counts (counts 4 S B read + 8 B written per "
+                     "pixel), its all-reduce, then one pass over the counts and the summed "
+                     "partials (4 S + 8 B read, map 4 B written per pixel) for the map and the "
+                     "rank's adjoint sums, the moment pass, the adjoint sums' all-reduce")},
         "kernels_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
         "top_kernel": top[0],
         "gpu_launches": launches,

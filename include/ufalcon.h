@@ -361,6 +361,75 @@ ufc_status ufc_kappa_stats_backward(ufc_ctx *ctx, const int32_t *counts_dev,
                                     double *moments_dev, int64_t *pdf_dev,
                                     double *grad_theta, double *G, double *H);
 
+/* ---- subvolume combination (Sec. 2.4) -------------------------------------- */
+
+/* Sec. 2.4 processes subvolumes of a simulation independently and combines
+ * their maps.  kappa_p = sum_b A_b n_bp - C is linear in the counts, so a
+ * process that binned one subvolume contributes its partial sum
+ *   partial_p = sum_b A_b n_bp        (no -C; A from ufc_kappa_coeffs with the
+ *                                      WHOLE simulation's n_total per box)
+ * accumulated in double-float over the shells in order (as ufc_kappa_stats)
+ * and stored as FP64 in partial_dev ([12 nside^2], 16-byte aligned, 8 B per
+ * pixel: 100 MB at Nside 1024, against 4 nshell B per pixel for the count
+ * maps).  The partials of all subvolumes are summed in FP64 by the caller
+ * (an all-reduce across processes), then ufc_kappa_stats_partial finishes
+ * the map.  counts_dev 16-byte aligned.  Asynchronous. */
+ufc_status ufc_kappa_partial(ufc_ctx *ctx, const int32_t *counts_dev,
+                             int32_t nshell, int32_t nside, const double *A,
+                             double *partial_dev);
+
+/* The FP32 map kappa_p = E_p - C from the summed partials E (partial_dev,
+ * the sum over subvolumes of ufc_kappa_partial), subtracted in double-float
+ * and rounded once to FP32, with the moments and PDF of ufc_kappa_stats
+ * (same definitions and outputs; kappa_dev 16-byte aligned, all three
+ * outputs required).  The map equals ufc_kappa_stats' map of the summed
+ * counts except where a value lies within about 2^-48 (relative) of an FP32
+ * rounding boundary; there the two may differ by one FP32 unit.
+ * Asynchronous. */
+ufc_status ufc_kappa_stats_partial(ufc_ctx *ctx, const double *partial_dev,
+                                   int32_t nside, double C, double pdf_lo,
+                                   double pdf_hi, int32_t nbins,
+                                   float *kappa_dev, double *moments_dev,
+                                   int64_t *pdf_dev);
+
+/* The adjoint of ufc_kappa_backward for a map combined from subvolumes.
+ * The gradient of L needs G_b = sum_p gbar_p n_bp over the whole
+ * simulation's counts, with gbar from the whole map; G_b is linear in the
+ * counts, so each process forms its subvolume's share from its own counts
+ * (counts_dev) and the summed partials (partial_dev, e_p = E_p - C):
+ *   sums[4 b + 0..3] = sum_p e_p n_bp, sum_p e_p^2 n_bp, sum_p g_p n_bp,
+ *                      sum_p n_bp                      (b < nshell; the
+ *                                                      subvolume's share)
+ *   sums[4 nshell + 0..3] = sum_p e_p, sum_p e_p^2, sum_p e_p^3, sum_p g_p
+ *                                                      (whole map; the same
+ *                                                      in every process)
+ * (host array of 4 nshell + 4 FP64, exact fixed-point sums rounded once, as
+ * in ufc_kappa_backward).  The caller sums the first 4 nshell entries over
+ * the processes and passes the result to ufc_kappa_grad_from_sums.  With
+ * kappa_dev non-NULL the same read of the counts also writes the FP32 map
+ * (equal to ufc_kappa_stats_partial's bit for bit) with its moments and PDF
+ * (moments_dev, pdf_dev then required).  g_kappa_dev as in
+ * ufc_kappa_backward, may be NULL.  Synchronises. */
+ufc_status ufc_kappa_adjoint_sums(ufc_ctx *ctx, const int32_t *counts_dev,
+                                  int32_t nshell, int32_t nside,
+                                  const double *partial_dev, double C,
+                                  const float *g_kappa_dev, double pdf_lo,
+                                  double pdf_hi, int32_t nbins,
+                                  float *kappa_dev, double *moments_dev,
+                                  int64_t *pdf_dev, double *sums);
+
+/* dL/dtheta of ufc_kappa_backward from adjoint sums (layout of
+ * ufc_kappa_adjoint_sums, the per-shell entries summed over subvolumes):
+ * the central moments of the map from its power sums, then
+ *   G_b = w_var dvar_b + w_skew dskew_b + sum_p g_p n_bp,  H = sum_p g_p,
+ *   grad_theta[j] = sum_b dA[j][b] G_b - dC[j] H.
+ * Host only (no device, no context); G [nshell] and H may be NULL.
+ * UFC_ERR_ARG for NULL inputs, bad sizes or non-finite sums. */
+ufc_status ufc_kappa_grad_from_sums(const double *sums, int32_t nshell,
+                                    int32_t nside, double w_var, double w_skew,
+                                    const double *dA, const double *dC,
+                                    double *grad_theta, double *G, double *H);
+
 /* ---- full-sky power spectrum (Sec. 3.2, Eq. 10-11) ------------------------- */
 
 /* Spherical-harmonic coefficients of a RING map (FP32 [12 nside^2], e.g.

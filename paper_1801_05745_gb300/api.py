@@ -121,6 +121,10 @@ _SIGS = {
     "ufc_set_tuning": [P, P],
     "ufc_get_tuning": [P, P],
     "ufc_welford_merge_host": [P, P, I32],
+    "ufc_kappa_partial": [P, P, I32, I32, P, P],
+    "ufc_kappa_stats_partial": [P, P, I32, D, D, D, I32, P, P, P],
+    "ufc_kappa_adjoint_sums": [P, P, I32, I32, P, D, P, D, D, I32, P, P, P, P],
+    "ufc_kappa_grad_from_sums": [P, I32, I32, D, D, P, P, P, P, P],
 }
 for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -493,6 +497,73 @@ class Context:
             ctypes.byref(H)), "ufc_kappa_stats_backward")
         return kappa, mom, pdf, grad, G, H.value
 
+    # -- subvolume combination (Sec. 2.4) --
+    def kappa_partial(self, counts, A, out=None):
+        """ufc_kappa_partial: FP64 [npix] partial sum sum_b A_b n_bp of one
+        subvolume's counts (no -C), to be summed over subvolumes."""
+        import torch
+        S, npix = counts.shape
+        nside = int(round((npix / 12) ** 0.5))
+        if out is None:
+            out = torch.empty(npix, dtype=torch.float64, device=counts.device)
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        self._stream()
+        self._ck(_lib.ufc_kappa_partial(self.h, P(counts.data_ptr()), S, nside, _np_ptr(A),
+                                        P(out.data_ptr())), "ufc_kappa_partial")
+        return out
+
+    def kappa_stats_partial(self, partial, C, pdf_lo, pdf_hi, nbins=200, kappa=None):
+        """ufc_kappa_stats_partial: (kappa, moments, pdf) of the map from the
+        summed partials."""
+        import torch
+        npix = partial.shape[0]
+        nside = int(round((npix / 12) ** 0.5))
+        dev = partial.device
+        if kappa is None:
+            kappa = torch.empty(npix, dtype=torch.float32, device=dev)
+        mom = torch.empty(NMOMENTS, dtype=torch.float64, device=dev)
+        pdf = torch.empty(nbins + 3, dtype=torch.int64, device=dev)
+        self._stream()
+        self._ck(_lib.ufc_kappa_stats_partial(self.h, P(partial.data_ptr()), nside, float(C),
+                                              float(pdf_lo), float(pdf_hi), nbins,
+                                              P(kappa.data_ptr()), P(mom.data_ptr()),
+                                              P(pdf.data_ptr())), "ufc_kappa_stats_partial")
+        return kappa, mom, pdf
+
+    def kappa_adjoint_sums(self, counts, partial, C, g_kappa=None, pdf_lo=None, pdf_hi=None,
+                           nbins=200, kappa=None, want_map=False):
+        """ufc_kappa_adjoint_sums: the adjoint sums (FP64 [4 nshell + 4], the
+        per-shell part this subvolume's share) of the summed partials'
+        map; with want_map also (kappa, moments, pdf) from the same read.
+        Returns (sums, kappa, moments, pdf), the last three None without
+        want_map."""
+        import torch
+        S, npix = counts.shape
+        nside = int(round((npix / 12) ** 0.5))
+        dev = counts.device
+        sums = np.empty(4 * S + 4)
+        mom = pdf = None
+        if want_map:
+            if kappa is None:
+                kappa = torch.empty(npix, dtype=torch.float32, device=dev)
+            mom = torch.empty(NMOMENTS, dtype=torch.float64, device=dev)
+            pdf = torch.empty(nbins + 3, dtype=torch.int64, device=dev)
+        else:
+            kappa = None
+        gp = None
+        if g_kappa is not None:
+            g_kappa = _dev_f32(g_kappa, self.device)
+            if g_kappa.data_ptr() % 16:
+                g_kappa = g_kappa.clone()
+            gp = P(g_kappa.data_ptr())
+        self._stream()
+        self._ck(_lib.ufc_kappa_adjoint_sums(
+            self.h, P(counts.data_ptr()), S, nside, P(partial.data_ptr()), float(C), gp,
+            float(pdf_lo if want_map else 0.0), float(pdf_hi if want_map else 1.0), nbins,
+            P(kappa.data_ptr()) if want_map else None, P(mom.data_ptr()) if want_map else None,
+            P(pdf.data_ptr()) if want_map else None, _np_ptr(sums)), "ufc_kappa_adjoint_sums")
+        return sums, kappa, mom, pdf
+
     # -- batched realisations --
     def set_tuning(self, batch_chunk: int = 0, batch_blocks_per_sm: int = 0):
         """ufc_set_tuning (0 = library default)."""
@@ -680,6 +751,22 @@ def welford_merge_host(a: np.ndarray, b: np.ndarray, d: int):
     assert a.flags.c_contiguous and b.flags.c_contiguous
     _check(_lib.ufc_welford_merge_host(_np_ptr(a), _np_ptr(np.ascontiguousarray(b)), d),
            what="ufc_welford_merge_host")
+
+
+def kappa_grad_from_sums(sums: np.ndarray, nshell: int, nside: int, dA, dC, w_var=0.0,
+                         w_skew=0.0):
+    """ufc_kappa_grad_from_sums (host only): (dL/dtheta [5], G [nshell], H)
+    from adjoint sums whose per-shell part is summed over subvolumes."""
+    sums = np.ascontiguousarray(sums, dtype=np.float64)
+    dA = np.ascontiguousarray(dA, dtype=np.float64)
+    dC = np.ascontiguousarray(dC, dtype=np.float64)
+    assert sums.shape == (4 * nshell + 4,) and dA.size == 5 * nshell and dC.size == 5
+    grad, G, H = np.empty(5), np.empty(nshell), ctypes.c_double()
+    _check(_lib.ufc_kappa_grad_from_sums(_np_ptr(sums), nshell, nside, float(w_var),
+                                         float(w_skew), _np_ptr(dA), _np_ptr(dC), _np_ptr(grad),
+                                         _np_ptr(G), ctypes.byref(H)),
+           what="ufc_kappa_grad_from_sums")
+    return grad, G, H.value
 
 
 def welford_state(d: int, device="cuda"):

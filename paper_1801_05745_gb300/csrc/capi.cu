@@ -26,6 +26,17 @@ ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int n
                                  const float* g, const double* dA, const double* dC,
                                  double* grad, double* G, double* H, float* kappa, double lo,
                                  double hi, int nbins, double* moments, int64_t* pdf);
+ufc_status run_kappa_partial(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                             const double* A, double* partial);
+ufc_status run_kappa_stats_partial(ufc_ctx* c, const double* partial, int nside, double C,
+                                   double lo, double hi, int nbins, float* kappa,
+                                   double* moments, int64_t* pdf);
+ufc_status run_kappa_adjoint_sums(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                  const double* partial, double C, const float* g, float* kappa,
+                                  double lo, double hi, int nbins, double* moments, int64_t* pdf,
+                                  double* sums);
+void grad_from_sums(const double* sm, int S, int npix, double w_var, double w_skew,
+                    const double* dA, const double* dC, double* grad, double* G, double* H);
 ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, double* st);
 ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins, double* v);
 ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int nside,
@@ -689,6 +700,49 @@ ufc_status ufc_kappa_stats_backward(ufc_ctx* c, const int32_t* counts_dev, int32
   return run_kappa_backward_ex(c, counts_dev, nshell, nside, A, C, w_var, w_skew, g_kappa_dev, dA,
                                dC, grad_theta, G, H, kappa_dev, pdf_lo, pdf_hi, nbins, moments_dev,
                                pdf_dev);
+}
+
+ufc_status ufc_kappa_partial(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell,
+                             int32_t nside, const double* A, double* partial_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_kappa_partial(c, counts_dev, nshell, nside, A, partial_dev);
+}
+
+ufc_status ufc_kappa_stats_partial(ufc_ctx* c, const double* partial_dev, int32_t nside,
+                                   double C, double pdf_lo, double pdf_hi, int32_t nbins,
+                                   float* kappa_dev, double* moments_dev, int64_t* pdf_dev) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_kappa_stats_partial(c, partial_dev, nside, C, pdf_lo, pdf_hi, nbins, kappa_dev,
+                                 moments_dev, pdf_dev);
+}
+
+ufc_status ufc_kappa_adjoint_sums(ufc_ctx* c, const int32_t* counts_dev, int32_t nshell,
+                                  int32_t nside, const double* partial_dev, double C,
+                                  const float* g_kappa_dev, double pdf_lo, double pdf_hi,
+                                  int32_t nbins, float* kappa_dev, double* moments_dev,
+                                  int64_t* pdf_dev, double* sums) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_kappa_adjoint_sums(c, counts_dev, nshell, nside, partial_dev, C, g_kappa_dev,
+                                kappa_dev, pdf_lo, pdf_hi, nbins, moments_dev, pdf_dev, sums);
+}
+
+ufc_status ufc_kappa_grad_from_sums(const double* sums, int32_t nshell, int32_t nside,
+                                    double w_var, double w_skew, const double* dA,
+                                    const double* dC, double* grad_theta, double* G, double* H) {
+  if (!sums || !dA || !dC || !grad_theta) return UFC_ERR_ARG;
+  if (nshell < 1 || nshell > kMaxShells) return UFC_ERR_ARG;
+  if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1))) return UFC_ERR_ARG;
+  if (!std::isfinite(w_var) || !std::isfinite(w_skew)) return UFC_ERR_ARG;
+  for (int k = 0; k < 4 * nshell + 4; ++k)
+    if (!std::isfinite(sums[k])) return UFC_ERR_ARG;
+  grad_from_sums(sums, nshell, 12 * nside * nside, w_var, w_skew, dA, dC, grad_theta, G, H);
+  return UFC_OK;
 }
 
 ufc_status ufc_stats_vector(ufc_ctx* c, const double* moments_dev, const int64_t* pdf_dev,

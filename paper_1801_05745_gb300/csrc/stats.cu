@@ -224,6 +224,66 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
   if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
 }
 
+// ----------------------------------------- subvolume partial sums -----
+// Sec. 2.4 processes subvolumes independently and combines their maps; kappa
+// is linear in the counts, so a subvolume contributes its partial sum
+// e_p = sum_b A_b n_bp (no -C) and the map is kappa_p = (sum over
+// subvolumes of e_p) - C.  The partial is accumulated in double-float over
+// the shells in order, as the forward pass does, and stored as FP64 (the
+// pair's sum), so that the subvolumes' partials add in FP64.
+// An FP64 value as a double-float pair (h + l within 2^-48 relative).
+__device__ __forceinline__ f2 d_to_f2(double v) {
+  const float h = __double2float_rn(v);
+  return {h, __double2float_rn(__dsub_rn(v, (double)h))};
+}
+
+__global__ void __launch_bounds__(kKV)
+k_kappa_partial(const int32_t* __restrict__ counts, Coef cf, double* __restrict__ part) {
+  __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
+  const int S = cf.nshell, ng = cf.npix >> 2;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) { ah_s[i] = cf.ah[i]; al_s[i] = cf.al[i]; }
+  __syncthreads();
+  const int4* c4 = reinterpret_cast<const int4*>(counts);
+  double2* o2 = reinterpret_cast<double2*>(part);
+  for (int g = blockIdx.x * kKV + threadIdx.x; g < ng; g += gridDim.x * kKV) {
+    f2 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+#pragma unroll 8
+    for (int b = 0; b < S; ++b) {
+      const int4 n = __ldcs(c4 + (size_t)b * ng + g);
+      const float h = ah_s[b], l = al_s[b];
+      f2_mac(a0, h, l, float(n.x));
+      f2_mac(a1, h, l, float(n.y));
+      f2_mac(a2, h, l, float(n.z));
+      f2_mac(a3, h, l, float(n.w));
+    }
+    o2[2 * g] = make_double2(f2_to_d(f2_norm(a0.h, a0.l)), f2_to_d(f2_norm(a1.h, a1.l)));
+    o2[2 * g + 1] = make_double2(f2_to_d(f2_norm(a2.h, a2.l)), f2_to_d(f2_norm(a3.h, a3.l)));
+  }
+}
+
+// The FP32 map from the summed partials: kappa_p = (E_p - C) in double-float
+// (E_p split into a pair), rounded once to FP32, with the per-block sums of
+// the map over the same grid and in the same order as k_kappa_vec, so that
+// the moment pass treats it exactly as a map from the counts.
+__global__ void __launch_bounds__(kKV)
+k_kappa_finish(const double* __restrict__ part, float ch, float cl, int npix,
+               float* __restrict__ kappa, double* __restrict__ ksum_part) {
+  __shared__ double red[kKV / 32];
+  const int ng = npix >> 2;
+  const f2 mc{-ch, -cl};
+  const double2* p2 = reinterpret_cast<const double2*>(part);
+  f2 ks{0.f, 0.f};
+  for (int g = blockIdx.x * kKV + threadIdx.x; g < ng; g += gridDim.x * kKV) {
+    const double2 d01 = __ldcs(p2 + 2 * g), d23 = __ldcs(p2 + 2 * g + 1);
+    const float4 kv = make_float4(kappa_round(d_to_f2(d01.x), mc), kappa_round(d_to_f2(d01.y), mc),
+                                  kappa_round(d_to_f2(d23.x), mc), kappa_round(d_to_f2(d23.y), mc));
+    reinterpret_cast<float4*>(kappa)[g] = kv;
+    ks = f2_add(ks, f2_add(f2_two_sum(kv.x, kv.y), f2_two_sum(kv.z, kv.w)));
+  }
+  const double t = block_sum_d<kKV>(f2_to_d(ks), red);
+  if (threadIdx.x == 0) ksum_part[blockIdx.x] = t;
+}
+
 // --------------------------------------------------------- adjoint -----
 // One pass (k_adj_main) over 4096-pixel tiles, one block per SM.  Phase 1:
 // e_p = sum_b A_b n_bp - C unrounded (double-float, the shells in order, as
@@ -241,7 +301,11 @@ k_kappa_vec(const int32_t* __restrict__ counts, Coef cf, float* __restrict__ kap
 // accumulated magnitudes (pixels per lane x tile maximum count x 2^22 per
 // tile) triggers a flush before any 64-bit sum could overflow.  More than 96
 // shells take one launch per window of 96 shells (phase 1 reads all shells
-// in each).
+// in each).  With EXT, e comes from summed subvolume partials E_p (e =
+// E_p - C, the same double-float subtraction as k_kappa_finish) and the
+// counts, those of one subvolume, enter phase 1 only through their maximum:
+// the per-shell sums are then that subvolume's share, and they add over
+// subvolumes.
 // Block sizes (4 pixels per thread, 3 shells per warp): 640 threads (2560-
 // pixel tiles, 60 shells per launch) for maps of up to 60 shells, 768 (3072-
 // pixel tiles, 72 shells) above.  Measured at 60 shells, Nside 1024: 1024
@@ -252,12 +316,12 @@ constexpr int kAdjThreadsSmall = 640;
 constexpr int kAdjThreadsLarge = 768;
 constexpr int kAdjSpw = 3;                // shells per warp in phase 2
 
-template <bool USE_G, int NT>
+template <bool USE_G, int NT, bool EXT>
 __global__ void __launch_bounds__(NT, 1)
 k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict__ g,
            double* __restrict__ rows_out, double* __restrict__ sumpart,
            unsigned long long* range_flag, int s0, float* __restrict__ kappa_out,
-           double* __restrict__ ksum_out) {
+           double* __restrict__ ksum_out, const double* __restrict__ ext) {
   extern __shared__ __align__(16) uint8_t adj_sm[];
   constexpr int T = NT, NW = T / 32, TP = 4 * T;
   int* q_s = reinterpret_cast<int*>(adj_sm);                 // [6][TP] quantised e, e^2, g
@@ -326,12 +390,22 @@ k_adj_main(const int32_t* __restrict__ counts, Coef cf, const float* __restrict_
 #pragma unroll kU1
       for (int b = 0; b < S; ++b) {
         const int4 n = c4[(size_t)b * ng + gi];
-        const float h = ah_s[b], l = al_s[b];
         nmx = max(nmx, max(max(n.x, n.y), max(n.z, n.w)));
-        f2_mac(a[0], h, l, float(n.x));
-        f2_mac(a[1], h, l, float(n.y));
-        f2_mac(a[2], h, l, float(n.z));
-        f2_mac(a[3], h, l, float(n.w));
+        if constexpr (!EXT) {
+          const float h = ah_s[b], l = al_s[b];
+          f2_mac(a[0], h, l, float(n.x));
+          f2_mac(a[1], h, l, float(n.y));
+          f2_mac(a[2], h, l, float(n.z));
+          f2_mac(a[3], h, l, float(n.w));
+        }
+      }
+      if constexpr (EXT) {
+        const double2 d01 = reinterpret_cast<const double2*>(ext)[2 * gi];
+        const double2 d23 = reinterpret_cast<const double2*>(ext)[2 * gi + 1];
+        a[0] = d_to_f2(d01.x);
+        a[1] = d_to_f2(d01.y);
+        a[2] = d_to_f2(d23.x);
+        a[3] = d_to_f2(d23.y);
       }
     }
     const float4 gv4 = (USE_G && have) ? reinterpret_cast<const float4*>(g)[gi]
@@ -1050,19 +1124,17 @@ ufc_status run_kappa_stats(ufc_ctx* c, const int32_t* counts, int S, int nside,
                         true);
 }
 
-// Adjoint sums -> gradients (host FP64 assembly).  Synchronises.
-// The adjoint sums of ufc_kappa_backward; with kappa (non-NULL) the same
-// launch also writes the FP32 map and its block sums, and the moment pass
-// gives moments and PDF (ufc_kappa_stats_backward).
-ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int nside,
-                                 const double* A, double C, double w_var, double w_skew,
-                                 const float* g, const double* dA, const double* dC,
-                                 double* grad, double* G, double* H, float* kappa, double lo,
-                                 double hi, int nbins, double* moments, int64_t* pdf) {
-  ufc_status s = check_kappa_args(c, counts, S, nside, A, C);
-  if (s) return s;
-  if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
-  if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
+// The adjoint's device pass and its reduction to the sums
+// out[4 b + k] (b < S: S1_b = sum_p e_p n_bp, S2_b = sum_p e_p^2 n_bp,
+// T_b = sum_p g_p n_bp, N_b = sum_p n_bp) and out[4 S + k] (P1, P2, P3 =
+// sum_p e_p^k, Q = sum_p g_p).  e is built from the counts with A (ext NULL)
+// or taken from summed subvolume partials ext (e = ext - C).  With kappa
+// (non-NULL) the same launch writes the FP32 map and its block sums and the
+// moment pass gives moments and PDF.  Synchronises.
+static ufc_status adjoint_sums(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                               const Coef& cf, const double* ext, const float* g, float* kappa,
+                               double lo, double hi, int nbins, double* moments, int64_t* pdf,
+                               double* out) {
   if (kappa) {
     if (!moments || !pdf) return set_err(c, UFC_ERR_ARG, "moments_dev and pdf_dev are required");
     if (reinterpret_cast<uintptr_t>(kappa) & 15)
@@ -1072,13 +1144,13 @@ ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int n
     if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
       return set_err(c, UFC_ERR_ARG, "PDF range needs finite lo < hi");
   }
-  const int npix = 12 * nside * nside;
-  Coef cf;
-  make_coef(A, C, S, npix, cf);
   if (reinterpret_cast<uintptr_t>(counts) & 15)
     return set_err(c, UFC_ERR_ARG, "counts_dev must be 16-byte aligned");
   if (g && (reinterpret_cast<uintptr_t>(g) & 15))
     return set_err(c, UFC_ERR_ARG, "g_dev must be 16-byte aligned");
+  if (ext && (reinterpret_cast<uintptr_t>(ext) & 15))
+    return set_err(c, UFC_ERR_ARG, "partial_dev must be 16-byte aligned");
+  const int npix = 12 * nside * nside;
   const int grid2 = c->num_sms;                            // one block per SM
   const size_t nrow = (size_t)grid2 * 4 * S, nsum = (size_t)grid2 * 4;
   const int mgrid = 2 * c->num_sms;
@@ -1100,24 +1172,30 @@ ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int n
   const size_t smem2 = (size_t)24 * 4 * nt + (size_t)32 * nt + (size_t)S * sizeof(AdjRow);
   {
     ProfScope ps_(c, "k_adj_main");
-#define UFC_ADJ(G, NT_)                                                                           \
+#define UFC_ADJ(G, NT_, X)                                                                        \
   do {                                                                                            \
-    UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<G, NT_>,                                          \
+    UFC_CUDA(c, cudaFuncSetAttribute(k_adj_main<G, NT_, X>,                                       \
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2));   \
     for (int s0 = 0; s0 < S; s0 += win)                                                           \
-      k_adj_main<G, NT_><<<grid2, NT_, smem2, c->stream>>>(counts, cf, g, rows, sums, &bc->range, \
-                                                           s0, s0 == 0 ? kappa : nullptr, ksum);  \
+      k_adj_main<G, NT_, X><<<grid2, NT_, smem2, c->stream>>>(                                    \
+          counts, cf, g, rows, sums, &bc->range, s0, s0 == 0 ? kappa : nullptr, ksum, ext);       \
   } while (0)
-    if (g && small) UFC_ADJ(true, kAdjThreadsSmall);
-    else if (g) UFC_ADJ(true, kAdjThreadsLarge);
-    else if (small) UFC_ADJ(false, kAdjThreadsSmall);
-    else UFC_ADJ(false, kAdjThreadsLarge);
+#define UFC_ADJ_X(G, NT_)                                                                         \
+  do {                                                                                            \
+    if (ext) UFC_ADJ(G, NT_, true);                                                               \
+    else UFC_ADJ(G, NT_, false);                                                                  \
+  } while (0)
+    if (g && small) UFC_ADJ_X(true, kAdjThreadsSmall);
+    else if (g) UFC_ADJ_X(true, kAdjThreadsLarge);
+    else if (small) UFC_ADJ_X(false, kAdjThreadsSmall);
+    else UFC_ADJ_X(false, kAdjThreadsLarge);
+#undef UFC_ADJ_X
 #undef UFC_ADJ
   }
   UFC_CUDA(c, cudaGetLastError());
   if (kappa) {                             // moments and PDF of the map just written
-    s = launch_moments(c, kappa, npix, ksum, grid2, lo, hi, nbins, mpart, mgrid, moments, pdf,
-                       true);
+    ufc_status s = launch_moments(c, kappa, npix, ksum, grid2, lo, hi, nbins, mpart, mgrid,
+                                  moments, pdf, true);
     if (s) return s;
   }
   std::vector<double> hp(nrow + nsum);
@@ -1128,26 +1206,24 @@ ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int n
   if (range_hits)
     return set_err(c, UFC_ERR_UNSUPPORTED,
                    "adjoint needs |kappa_p| < 2^14 and |g_p| < 2^14 (fixed-point range)");
-  std::vector<double> S1(S, 0.0), S2(S, 0.0), T(S, 0.0), Nb(S, 0.0);
-  double P1 = 0, P2 = 0, P3 = 0, Q = 0;
-  for (int i = 0; i < grid2; ++i) {
+  for (int k = 0; k < 4 * S + 4; ++k) out[k] = 0.0;
+  for (int i = 0; i < grid2; ++i) {        // blocks in order: a fixed summation order
     const double* r = hp.data() + (size_t)i * 4 * S;
-    for (int b = 0; b < S; ++b) {
-      S1[b] += r[4 * b];
-      S2[b] += r[4 * b + 1];
-      T[b] += r[4 * b + 2];
-      Nb[b] += r[4 * b + 3];
-    }
+    for (int k = 0; k < 4 * S; ++k) out[k] += r[k];
   }
   for (int i = 0; i < grid2; ++i) {
     const double* r = hp.data() + nrow + 4 * (size_t)i;
-    P1 += r[0];
-    P2 += r[1];
-    P3 += r[2];
-    Q += r[3];
+    for (int k = 0; k < 4; ++k) out[4 * S + k] += r[k];
   }
+  return UFC_OK;
+}
+
+// dL/dtheta from the adjoint sums (layout of adjoint_sums), host FP64.
+void grad_from_sums(const double* sm, int S, int npix, double w_var, double w_skew,
+                    const double* dA, const double* dC, double* grad, double* G, double* H) {
   // central moments of the unrounded map from the raw sums about 0
   const double N = npix;
+  const double P1 = sm[4 * S], P2 = sm[4 * S + 1], P3 = sm[4 * S + 2], Q = sm[4 * S + 3];
   const double m1 = P1 / N, r2 = P2 / N, r3 = P3 / N;
   const double mu2 = r2 - m1 * m1;
   const double mu3 = r3 - 3.0 * m1 * r2 + 2.0 * m1 * m1 * m1;
@@ -1158,11 +1234,12 @@ ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int n
   const double i32 = 1.0 / (mu2 * std::sqrt(mu2));
   const double i52 = i32 / mu2;
   for (int b = 0; b < S; ++b) {
-    const double c1 = S1[b] - m1 * Nb[b];                             // sum (k-m) n
-    const double c2 = S2[b] - 2.0 * m1 * S1[b] + m1 * m1 * Nb[b];     // sum (k-m)^2 n
+    const double S1 = sm[4 * b], S2 = sm[4 * b + 1], T = sm[4 * b + 2], Nb = sm[4 * b + 3];
+    const double c1 = S1 - m1 * Nb;                             // sum (k-m) n
+    const double c2 = S2 - 2.0 * m1 * S1 + m1 * m1 * Nb;        // sum (k-m)^2 n
     const double gv = 2.0 * c1 / N;
-    const double gs = 3.0 * (c2 - mu2 * Nb[b]) * i32 / N - 3.0 * mu3 * i52 * c1 / N;
-    Gb[b] = w_var * gv + w_skew * gs + T[b];
+    const double gs = 3.0 * (c2 - mu2 * Nb) * i32 / N - 3.0 * mu3 * i52 * c1 / N;
+    Gb[b] = w_var * gv + w_skew * gs + T;
   }
   const double Hs = Q;   // var and skew are shift invariant: their H is 0
   for (int j = 0; j < 5; ++j) {
@@ -1173,7 +1250,105 @@ ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int n
   if (G)
     for (int b = 0; b < S; ++b) G[b] = Gb[b];
   if (H) *H = Hs;
+}
+
+// Adjoint sums -> gradients (host FP64 assembly).  Synchronises.
+// With kappa (non-NULL) the same launch also writes the FP32 map and its
+// block sums, and the moment pass gives moments and PDF
+// (ufc_kappa_stats_backward).
+ufc_status run_kappa_backward_ex(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                 const double* A, double C, double w_var, double w_skew,
+                                 const float* g, const double* dA, const double* dC,
+                                 double* grad, double* G, double* H, float* kappa, double lo,
+                                 double hi, int nbins, double* moments, int64_t* pdf) {
+  ufc_status s = check_kappa_args(c, counts, S, nside, A, C);
+  if (s) return s;
+  if (!grad) return set_err(c, UFC_ERR_ARG, "grad_theta is NULL");
+  if (!dA || !dC) return set_err(c, UFC_ERR_ARG, "dA and dC are required");
+  const int npix = 12 * nside * nside;
+  Coef cf;
+  make_coef(A, C, S, npix, cf);
+  std::vector<double> sm(4 * (size_t)S + 4);
+  s = adjoint_sums(c, counts, S, nside, cf, nullptr, g, kappa, lo, hi, nbins, moments, pdf,
+                   sm.data());
+  if (s) return s;
+  grad_from_sums(sm.data(), S, npix, w_var, w_skew, dA, dC, grad, G, H);
   return UFC_OK;
+}
+
+// ---- subvolume partial sums (Sec. 2.4) --------------------------------------
+ufc_status run_kappa_partial(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                             const double* A, double* partial) {
+  ufc_status s = check_kappa_args(c, counts, S, nside, A, 0.0);
+  if (s) return s;
+  if (!partial) return set_err(c, UFC_ERR_ARG, "partial_dev is NULL");
+  if ((reinterpret_cast<uintptr_t>(counts) & 15) || (reinterpret_cast<uintptr_t>(partial) & 15))
+    return set_err(c, UFC_ERR_ARG, "counts_dev and partial_dev must be 16-byte aligned");
+  const int npix = 12 * nside * nside;
+  Coef cf;
+  make_coef(A, 0.0, S, npix, cf);
+  {
+    ProfScope ps_(c, "k_kappa_partial");
+    k_kappa_partial<<<kappa_fwd_grid(c), kKV, 0, c->stream>>>(counts, cf, partial);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
+
+static ufc_status check_partial_args(ufc_ctx* c, const double* partial, int nside, double C) {
+  if (!partial) return set_err(c, UFC_ERR_ARG, "partial_dev is NULL");
+  if (reinterpret_cast<uintptr_t>(partial) & 15)
+    return set_err(c, UFC_ERR_ARG, "partial_dev must be 16-byte aligned");
+  if (nside < 1 || nside > UFC_MAX_NSIDE || (nside & (nside - 1)))
+    return set_err(c, UFC_ERR_ARG, "nside must be a power of two in [1,%d]", UFC_MAX_NSIDE);
+  if (!std::isfinite(C)) return set_err(c, UFC_ERR_ARG, "C is not finite");
+  return UFC_OK;
+}
+
+ufc_status run_kappa_stats_partial(ufc_ctx* c, const double* partial, int nside, double C,
+                                   double lo, double hi, int nbins, float* kappa,
+                                   double* moments, int64_t* pdf) {
+  ufc_status s = check_partial_args(c, partial, nside, C);
+  if (s) return s;
+  if (!kappa || !moments || !pdf)
+    return set_err(c, UFC_ERR_ARG, "kappa_dev, moments_dev and pdf_dev are required");
+  if (reinterpret_cast<uintptr_t>(kappa) & 15)
+    return set_err(c, UFC_ERR_ARG, "kappa_dev must be 16-byte aligned");
+  if (nbins < 1 || nbins > kMaxBins)
+    return set_err(c, UFC_ERR_ARG, "nbins must be in [1,%d]", kMaxBins);
+  if (!(hi > lo) || !std::isfinite(lo) || !std::isfinite(hi))
+    return set_err(c, UFC_ERR_ARG, "PDF range needs finite lo < hi");
+  const int npix = 12 * nside * nside;
+  const int grid = kappa_fwd_grid(c), mgrid = 2 * c->num_sms;
+  double* ksum = (double*)ws_get(c, kSlotPartials, (size_t)(grid + 3 * mgrid) * 8);
+  if (!ksum) return UFC_ERR_ALLOC;
+  const float ch = (float)C, cl = (float)(C - (double)ch);
+  {
+    ProfScope ps_(c, "k_kappa_finish");
+    k_kappa_finish<<<grid, kKV, 0, c->stream>>>(partial, ch, cl, npix, kappa, ksum);
+  }
+  UFC_CUDA(c, cudaGetLastError());
+  return launch_moments(c, kappa, npix, ksum, grid, lo, hi, nbins, ksum + grid, mgrid, moments,
+                        pdf, true);
+}
+
+ufc_status run_kappa_adjoint_sums(ufc_ctx* c, const int32_t* counts, int S, int nside,
+                                  const double* partial, double C, const float* g, float* kappa,
+                                  double lo, double hi, int nbins, double* moments, int64_t* pdf,
+                                  double* sums) {
+  ufc_status s = check_partial_args(c, partial, nside, C);
+  if (s) return s;
+  if (!counts) return set_err(c, UFC_ERR_ARG, "counts_dev is NULL");
+  if (S < 1 || S > kMaxShells) return set_err(c, UFC_ERR_ARG, "nshell must be in [1,%d]", kMaxShells);
+  if ((int64_t)S * 12 * nside * nside >= (1ll << 31))
+    return set_err(c, UFC_ERR_ARG, "nshell * 12 nside^2 must be < 2^31");
+  if (!sums) return set_err(c, UFC_ERR_ARG, "sums is NULL");
+  const int npix = 12 * nside * nside;
+  std::vector<double> zeros(S, 0.0);
+  Coef cf;
+  make_coef(zeros.data(), C, S, npix, cf);   // A unused: e comes from the partials
+  return adjoint_sums(c, counts, S, nside, cf, partial, g, kappa, lo, hi, nbins, moments, pdf,
+                      sums);
 }
 
 ufc_status run_kappa_backward(ufc_ctx* c, const int32_t* counts, int S, int nside,

@@ -116,6 +116,70 @@ def test_two_rank_library_welford_merge(tmp_path):
         assert ok.all(), (r, ok)
 
 
+def _adjoint_worker(rank, world, port, tmp):
+    """Subvolume sharding of the map and its gradient (Sec. 2.4) through the
+    library's host pieces: each rank bins its shard (oracle), adds its FP64
+    partial sum_b A_b n_bp into the all-reduce, forms its share of the
+    adjoint sums against the whole map (the definition of
+    ufc_kappa_adjoint_sums, in numpy); parallel.allreduce_adjoint_sums
+    combines the shares and ufc_kappa_grad_from_sums gives the gradient,
+    which must equal the oracle's complex-step gradient of the whole counts.
+    Power sums that differ between ranks must raise on every rank."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle
+    from paper_1801_05745_gb300 import api, parallel, synth
+    n, nside, S = 60_000, 8, 6
+    x = synth.particles_numpy(n, 2000.0, 5.0, 777)
+    z = np.linspace(0.05, 0.23, S + 1)
+    chi = oracle.chi_edges(0.3, 0.7, 0, z)                # Mpc: the gradient in h is not 0
+    box_o = oracle.make_box(2000.0, [1000.0] * 3, n, 0, S)
+    box_a = api.make_box(2000.0, [1000.0] * 3, n, 0, S)
+    a, b = parallel.shard_range(n, rank, world, align=4)
+    mine, _ = oracle.bin_counts(x[a:b], box_o, chi, nside)
+    full, _ = oracle.bin_counts(x, box_o, chi, nside)
+    src = dict(kind=1, z_s=1.5, alpha=2.0, beta=1.5, z0=0.5, z_max=1.5)   # Smail n(z)
+    A, B, C, dA, dC = api.kappa_coeffs(api.make_cosmo(0.3, 0.7, 0), [box_a], z, nside,
+                                       api.make_source(**src), derivs=True)
+    partial = torch.from_numpy(A @ mine.astype(np.float64))
+    dist.all_reduce(partial)
+    e = partial.numpy() - C                              # the whole map, unrounded
+    g = np.random.default_rng(4).normal(size=e.size).astype(np.float32)
+    m = mine.astype(np.float64)
+    share = np.stack([m @ e, m @ (e * e), m @ g.astype(np.float64), m.sum(1)], axis=1).ravel()
+    sums = np.concatenate([share, [e.sum(), (e * e).sum(), (e ** 3).sum(), g.sum(dtype=np.float64)]])
+    tot = parallel.allreduce_adjoint_sums(sums, S)
+    ok = [bool(np.array_equal(tot[3:4 * S:4], full.sum(1).astype(np.float64)))]
+    grad, G, H = api.kappa_grad_from_sums(tot, S, nside, dA, dC, 0.7, 1.3)
+    G_or = oracle.kappa_stat_grads(full, nside, 0.3, 0.7, 0, [box_o], z,
+                                   oracle.make_source(**src), g)
+    want = 0.7 * G_or[0] + 1.3 * G_or[1] + G_or[2]
+    sc = 0.7 * np.abs(G_or[0]).max() + 1.3 * np.abs(G_or[1]).max() + np.abs(G_or[2]).max()
+    ok.append(bool(np.allclose(grad, want, rtol=1e-9, atol=1e-9 * sc)))
+    ok.append(bool(np.all(np.abs(want) > 1e-6 * sc)))   # every parameter's gradient is live
+    bad = sums.copy()
+    bad[4 * S] += rank * 1e-3 * abs(bad[4 * S])          # rank 1 disagrees on sum_p e_p
+    try:
+        parallel.allreduce_adjoint_sums(bad, S)
+        ok.append(False)
+    except RuntimeError:
+        ok.append(True)
+    np.save(os.path.join(tmp, f"a{rank}.npy"), np.array(ok))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_subvolume_gradient(tmp_path):
+    port = _free_port()
+    mp.spawn(_adjoint_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        ok = np.load(tmp_path / f"a{r}.npy")
+        assert ok.all(), (r, ok)
+
+
 def _failing_worker(rank, world, port, tmp, mode):
     """Rank 1 fails on the host before the map combination: it raises
     ("raise") or never joins the all-reduce ("absent").  Rank 0 must get an
