@@ -130,3 +130,20 @@ def test_volume_reading_coeffs_vs_oracle(api, orc):
     with pytest.raises(api.UfcError):
         api.kappa_coeffs(api.make_cosmo(0.3, 0.7, 1, density_volume=2), boxes_a, z, 512,
                          api.make_source(**kw))
+
+
+def test_grad_from_sums_rejects_bad_input(api):
+    """ufc_kappa_grad_from_sums is host-only: it runs without a GPU and
+    rejects non-finite sums and sizes it cannot hold (its values are checked
+    against the oracle's complex step in tests/test_parallel_gloo.py)."""
+    S, nside = 3, 4
+    sums = np.ones(4 * S + 4)
+    sums[4 * S:] = [0.5, 2.0, 1.0, 0.0]                  # a map with positive variance
+    grad, G, H = api.kappa_grad_from_sums(sums, S, nside, np.ones(5 * S), np.zeros(5))
+    assert np.all(np.isfinite(grad)) and H == 0.0
+    bad = sums.copy()
+    bad[5] = np.inf
+    with pytest.raises(api.UfcError):
+        api.kappa_grad_from_sums(bad, S, nside, np.ones(5 * S), np.zeros(5))
+    with pytest.raises(api.UfcError):
+        api.kappa_grad_from_sums(sums, S, 3, np.ones(5 * S), np.zeros(5))   # nside not 2^k
