@@ -243,3 +243,30 @@ def test_persistent_batch_tuning_keeps_results(orc, chunk, bps):
         assert torch.equal(mom[r].view(torch.int64), ref[r][0].view(torch.int64)), r
         assert torch.equal(pdf[r], ref[r][1]), r
     assert st[0].item() == nreal
+
+
+def test_batched_run_resumed_from_checkpoint(orc, tmp_path):
+    """A batched covariance run stopped after 5 of 12 realisations, saved,
+    and resumed in a new context from the checkpoint reaches the state of
+    one uninterrupted batched call bit for bit (the updates run in the same
+    order)."""
+    from paper_1801_05745_gb300 import checkpoint
+    api, ctx = api_ctx()
+    nside, nshell, nb = 64, 12, 80_000
+    z, chi, xs, bxs, A, C = _realisations(orc, api, 12, nside, nshell, nb)
+    nbins, lo, hi = 40, -0.05, 0.2
+    d = 6 + nbins
+    full = api.welford_state(d)
+    ctx.batched_stats(xs, bxs, chi, nside, A, C, lo, hi, nbins, full)
+    st = api.welford_state(d)
+    ctx.batched_stats(xs[:5], bxs[:5], chi, nside, A[:5], C[:5], lo, hi, nbins, st)
+    cfg = {"nside": nside, "nshell": nshell, "nbins": nbins, "lo": lo, "hi": hi}
+    path = str(tmp_path / "run.npz")
+    checkpoint.save(path, st, d, 5, cfg)
+    ctx2 = api.context(0)
+    host, k = checkpoint.load(path, d, cfg)
+    st2 = torch.from_numpy(host).cuda()
+    ctx2.batched_stats(xs[k:], bxs[k:], chi, nside, A[k:], C[k:], lo, hi, nbins, st2)
+    torch.cuda.synchronize()
+    assert torch.equal(st2, full)
+    ctx2.close()
