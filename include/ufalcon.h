@@ -51,7 +51,8 @@ typedef enum {
   UFC_ERR_ALLOC = 3,        /* device workspace could not be allocated    */
   UFC_ERR_TIMEOUT = 4,      /* a device-side bounded wait ran out         */
   UFC_ERR_UNSUPPORTED = 5,  /* valid request this build does not handle   */
-  UFC_ERR_CAPACITY = 6      /* a caller-sized or fixed buffer is too small */
+  UFC_ERR_CAPACITY = 6,     /* a caller-sized or fixed buffer is too small */
+  UFC_ERR_INTERNAL = 7      /* an index test of a checked build failed    */
 } ufc_status;
 
 typedef struct ufc_ctx ufc_ctx;
@@ -106,7 +107,9 @@ ufc_status ufc_set_stream(ufc_ctx *ctx, void *stream);
 /* Waits for all work enqueued by this context; reports device-side errors:
  * UFC_ERR_TIMEOUT when a bounded wait of the fast binning stage (on its
  * particle copies) ran out since the last report, in which case that
- * binning call's counts are incomplete.  The context stays usable. */
+ * binning call's counts are incomplete; else UFC_ERR_INTERNAL when an index
+ * test failed since the last report (checked builds, and
+ * ufc_check_selftest).  The context stays usable. */
 ufc_status ufc_synchronize(ufc_ctx *ctx);
 /* Self-test of the device-side failure report (no counterpart in the
  * paper): one kernel waits on a barrier that nothing completes, gives up
@@ -116,6 +119,20 @@ ufc_status ufc_synchronize(ufc_ctx *ctx);
 ufc_status ufc_wait_selftest(ufc_ctx *ctx, int64_t limit);
 /* Message of the last error on this context ("" if none). */
 const char *ufc_last_error(const ufc_ctx *ctx);
+
+/* Index tests.  A library built with -DUFC_CHECKED (build.py checked=True,
+ * libufalcon_gb300_checked.so; the Python binding loads it when the
+ * environment sets UFC_CHECKED=1) tests the computed indices of the binning
+ * kernels (count-map cells, buckets, bucket groups, scatter destinations,
+ * histogram offsets) and of the batched kernel's count maps before each
+ * access; a failed test records its site, index and bound, skips the access
+ * and lets the kernel finish.  ufc_synchronize then returns
+ * UFC_ERR_INTERNAL with the first failure in ufc_last_error.  Other builds
+ * compile the tests away.  The record is one per device, shared by the
+ * contexts on it.  ufc_check_selftest fails one test on purpose (index
+ * against bound, in every build; nothing is accessed) so that the report
+ * path can be exercised.  Asynchronous. */
+ufc_status ufc_check_selftest(ufc_ctx *ctx, int64_t index, int64_t bound);
 /* Device bytes the context holds (workspace, counters and the workspace of
  * its batched-call lanes) in *bytes.  Host only; enqueues nothing. */
 ufc_status ufc_workspace_bytes(const ufc_ctx *ctx, int64_t *bytes);

@@ -15,11 +15,15 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libufalcon_gb300.so")
+# UFC_CHECKED=1 loads the checked build (index tests in the kernels), made
+# by build.build(checked=True)
+CHECKED = os.environ.get("UFC_CHECKED", "0") == "1"
+LIB_PATH = os.path.join(_HERE, "_build", "libufalcon_gb300_checked.so" if CHECKED
+                        else "libufalcon_gb300.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError(f"libufalcon_gb300.so is not built ({LIB_PATH}); run "
-                      "paper_1801_05745_gb300.build.build() or __graft_entry__.build()")
+    raise ImportError(f"{os.path.basename(LIB_PATH)} is not built ({LIB_PATH}); run "
+                      "paper_1801_05745_gb300.build.build(checked=...) or __graft_entry__.build()")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -121,6 +125,7 @@ _SIGS = {
     "ufc_set_tuning": [P, P],
     "ufc_get_tuning": [P, P],
     "ufc_welford_merge_host": [P, P, I32],
+    "ufc_check_selftest": [P, I64, I64],
     "ufc_kappa_partial": [P, P, I32, I32, P, P],
     "ufc_kappa_stats_partial": [P, P, I32, D, D, D, I32, P, P, P],
     "ufc_kappa_adjoint_sums": [P, P, I32, I32, P, D, P, D, D, I32, P, P, P, P],
@@ -254,6 +259,12 @@ class Context:
         next synchronize() raises UfcError with status UFC_ERR_TIMEOUT."""
         self._stream()
         self._ck(_lib.ufc_wait_selftest(self.h, int(limit)), "ufc_wait_selftest")
+
+    def check_selftest(self, index: int, bound: int):
+        """ufc_check_selftest: one failed index test (reported by the next
+        synchronize as UFC_ERR_INTERNAL)."""
+        self._stream()
+        self._ck(_lib.ufc_check_selftest(self.h, int(index), int(bound)), "ufc_check_selftest")
 
     def profile(self, on: bool = True):
         """Bracket every library kernel launch with CUDA events (tracing)."""

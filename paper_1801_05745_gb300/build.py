@@ -3,6 +3,11 @@
 nvcc compiles each CUDA translation unit for sm_103a only; g++ compiles the
 host cosmology; the objects are linked into one shared library.  No cmake,
 no torch extension machinery: the library has a plain C ABI.
+
+build(checked=True) makes libufalcon_gb300_checked.so (objects in
+_build/checked/): the same library compiled with -DUFC_CHECKED, whose
+kernels test their computed indices before each access (ufc_synchronize
+reports a failed test as UFC_ERR_INTERNAL).
 """
 from __future__ import annotations
 
@@ -37,34 +42,38 @@ def _run(cmd: list[str]) -> None:
         raise RuntimeError("compile failed: " + " ".join(cmd))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib = os.path.join(BUILD, "libufalcon_gb300_checked.so") if checked else LIB
+    defs = ["-DUFC_CHECKED"] if checked else []
+    os.makedirs(bdir, exist_ok=True)
     include = os.path.join(os.path.dirname(HERE), "include", "ufalcon.h")
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [include]
     jobs = []
     objs = []
     for f in CU:
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f + ".o")
+        obj = os.path.join(bdir, f + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            jobs.append([NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                         "-Xptxas", "-v" if verbose else "-O3", "-c", src, "-o", obj])
+            jobs.append([NVCC, *ARCH, *defs, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler",
+                         "-fPIC", "-Xptxas", "-v" if verbose else "-O3", "-c", src, "-o", obj])
     for f in CPP:
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f + ".o")
+        obj = os.path.join(bdir, f + ".o")
         objs.append(obj)
         if force or _stale(obj, [src, include]):
             jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off",
                          "-fno-fast-math", "-c", src, "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         list(ex.map(_run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

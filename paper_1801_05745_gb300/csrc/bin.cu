@@ -51,6 +51,7 @@ struct KeyOut {
   int32_t shell0;              // DENSE: first shell of the call's window; buckets
                                // count blocks from shell0 * nblk
   int32_t smem_hist;           // 1: histogram in shared memory
+  int64_t ncell;               // cells of the count map (checked builds' bound)
 };
 
 struct Queues {
@@ -318,12 +319,14 @@ __device__ __forceinline__ void fast_particle(bool have, float x, float y, float
     if (MODE == kModeKeys) {
       if (have) o.keys[p] = finite ? key : kKeyInvalid;
     } else if (MODE == kModeDirect) {
-      if (key >= 0) atomicAdd(o.counts + key, 1);
+      if (key >= 0 && UFC_IDX_OK(key, o.ncell, 2)) atomicAdd(o.counts + key, 1);
     } else {
       if (key >= 0) {
         const uint32_t bucket = dkey >> kOffBits;
-        if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
-        else atomicAdd(o.hist + bucket, 1u);
+        if (UFC_IDX_OK(bucket, o.nbuckets, 1)) {
+          if (o.smem_hist) atomicAdd(hist_s + bucket, 1u);
+          else atomicAdd(o.hist + bucket, 1u);
+        }
       }
       dense_append(fc.wc, key >= 0, dkey, o);
     }
@@ -673,10 +676,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
             if (kx == kKeyInvalid) ++fc.n_invalid;
             if (kx >= 0) {
               ++fc.n_keyed;
-              if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
+              if (MODE == kModeDirect && UFC_IDX_OK(kx, o.ncell, 2)) atomicAdd(o.counts + kx, 1);
               if (MODE == kModeDense) {            // rare: straight to the global histogram
                 const uint32_t dk = dense_key(kx, npix, o);
-                atomicAdd(ghist + (dk >> kOffBits), 1u);
+                if (UFC_IDX_OK(dk >> kOffBits, o.nbuckets, 1)) atomicAdd(ghist + (dk >> kOffBits), 1u);
                 const unsigned long long at = atomicAdd(o.dense_count, 1ull);
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
               }
@@ -739,10 +742,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
                                               bg.sh64[1][jj], bg.sh64[2][kk]);
             if (kx >= 0) {
               ++fc.n_keyed;
-              if (MODE == kModeDirect) atomicAdd(o.counts + kx, 1);
+              if (MODE == kModeDirect && UFC_IDX_OK(kx, o.ncell, 2)) atomicAdd(o.counts + kx, 1);
               if (MODE == kModeDense) {
                 const uint32_t dk = dense_key(kx, npix, o);
-                atomicAdd(ghist + (dk >> kOffBits), 1u);
+                if (UFC_IDX_OK(dk >> kOffBits, o.nbuckets, 1)) atomicAdd(ghist + (dk >> kOffBits), 1u);
                 const unsigned long long at = atomicAdd(o.dense_count, 1ull);
                 if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
               }
@@ -752,15 +755,17 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           if (MODE == kModeKeys) {
             if (have && queued) o.keys[p_off + local_index()] = ok ? key : kKeyUndecided;
           } else if (MODE == kModeDirect) {
-            if (ok) atomicAdd(o.counts + key, 1);
+            if (ok && UFC_IDX_OK(key, o.ncell, 2)) atomicAdd(o.counts + key, 1);
           } else {
             uint32_t dk = 0u;
             if (ok) {
               const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
               const uint32_t bucket = uint32_t(b - o.shell0) * uint32_t(o.nblk) + blk;
               dk = (bucket << kOffBits) | (uint32_t(pix) - blk * uint32_t(kBlockPix));
-              if (o.smem_hist) hist16_inc(h32, ghist, bucket);
-              else atomicAdd(ghist + bucket, 1u);
+              if (UFC_IDX_OK(bucket, o.nbuckets, 1)) {
+                if (o.smem_hist) hist16_inc(h32, ghist, bucket);
+                else atomicAdd(ghist + bucket, 1u);
+              }
             }
             dense_append(fc.wc, ok, dk, o);
           }
@@ -819,10 +824,10 @@ __device__ __forceinline__ void emit_late(int32_t key, int64_t p, int32_t npix,
   if (MODE == kModeKeys) {
     o.keys[p] = key;
   } else if (MODE == kModeDirect) {
-    if (key >= 0) atomicAdd(o.counts + key, 1);
+    if (key >= 0 && UFC_IDX_OK(key, o.ncell, 2)) atomicAdd(o.counts + key, 1);
   } else {
     uint32_t dk = key >= 0 ? dense_key(key, npix, o) : 0u;
-    if (key >= 0) atomicAdd(o.hist + (dk >> kOffBits), 1u);
+    if (key >= 0 && UFC_IDX_OK(dk >> kOffBits, o.nbuckets, 1)) atomicAdd(o.hist + (dk >> kOffBits), 1u);
     dense_append(wc, key >= 0, dk, o);
   }
 }
@@ -977,10 +982,10 @@ k_overflow(BoxesParam bp, int nbox, ShellTable st, int32_t N, int32_t npix, KeyO
       if (MODE == kModeKeys) o.keys[p] = key;
       if (key >= 0) {
         ++n_keyed;
-        if (MODE == kModeDirect) atomicAdd(o.counts + key, 1);
+        if (MODE == kModeDirect && UFC_IDX_OK(key, o.ncell, 2)) atomicAdd(o.counts + key, 1);
         if (MODE == kModeDense) {
           const uint32_t dk = dense_key(key, npix, o);
-          atomicAdd(o.hist + (dk >> kOffBits), 1u);
+          if (UFC_IDX_OK(dk >> kOffBits, o.nbuckets, 1)) atomicAdd(o.hist + (dk >> kOffBits), 1u);
           const unsigned long long at = atomicAdd(o.dense_count, 1ull);
           if ((int64_t)at < o.dense_cap) o.dense[at] = dk;
         }
@@ -1113,6 +1118,7 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
     for (int k = 0; k < kScatPer; ++k) {
       const int j = k * kScatThreads + threadIdx.x;
       v[k] = j < nsm ? kb[j] : (j < nk ? __ldcs(dense + t0 + j) : kSentinel);
+      if (v[k] != kSentinel && !UFC_IDX_OK(v[k] >> shift, ng, 3)) v[k] = kSentinel;
     }
     for (int g = threadIdx.x; g < ng; g += blockDim.x) cnt[g] = 0;
     if (__syncthreads_or(!ok)) { aborted = true; break; }   // buffer b is free again
@@ -1135,7 +1141,7 @@ k_scatter_group(const uint32_t* __restrict__ dense, const unsigned long long* de
     for (uint32_t q = threadIdx.x; q < used; q += blockDim.x) {
       const uint32_t val = tile[q];
       const uint32_t g = val >> shift;
-      out[base[g] + q] = val;
+      if (UFC_IDX_OK(base[g] + q, dense_cap, 4)) out[base[g] + q] = val;
     }
     __syncthreads();
   }
@@ -1194,7 +1200,7 @@ __global__ void __launch_bounds__(kScatThreads, 2)
 k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ tiles,
                  const unsigned long long* __restrict__ ntiles_p,
                  unsigned long long* __restrict__ bcur, uint16_t* __restrict__ out,
-                 unsigned long long* timeouts) {
+                 int64_t out_cap, unsigned long long* timeouts) {
   constexpr int NS = 1 << kGroupBits;
   extern __shared__ __align__(16) uint8_t smb[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -1260,7 +1266,8 @@ k_scatter_bucket(const uint32_t* __restrict__ grouped, const Tile* __restrict__ 
     __syncthreads();
     for (int q = threadIdx.x; q < T.len; q += blockDim.x) {
       const uint32_t val = tile[q];
-      out[base[(val >> kOffBits) & (NS - 1)] + q] = uint16_t(val & ((1u << kOffBits) - 1u));
+      const unsigned long long dst = base[(val >> kOffBits) & (NS - 1)] + q;
+      if (UFC_IDX_OK(dst, out_cap, 5)) out[dst] = uint16_t(val & ((1u << kOffBits) - 1u));
     }
     __syncthreads();
   }
@@ -1280,19 +1287,27 @@ constexpr int kHistThreads = 512;
 constexpr int kHistVec = 8;
 __global__ void __launch_bounds__(kHistThreads)
 k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off, int nb,
-             int32_t* __restrict__ counts, int accumulate) {
+             int32_t* __restrict__ counts, int accumulate, int64_t offs_cap) {
   extern __shared__ uint32_t h[];   // [kBlockPix]
   uint4* h4 = reinterpret_cast<uint4*>(h);
   for (int i = threadIdx.x; i < kBlockPix / 4; i += blockDim.x) h4[i] = make_uint4(0, 0, 0, 0);
   __syncthreads();
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
-    const int64_t a = off[b], e = off[b + 1];
+    const int64_t a = off[b];
+    int64_t e = off[b + 1];
+    if (e > a && !UFC_IDX_OK(e - 1, offs_cap, 6)) e = a;   // (checked) a bucket beyond the array
     if (accumulate && a == e) continue;          // nothing to add (uniform over the block)
     const int64_t a8r = (a + 7) & ~7ll, e8r = e & ~7ll;
     const int64_t a8 = a8r < e ? a8r : e;                  // first 16-byte boundary
     const int64_t e8 = e8r > a8 ? e8r : a8;                // last one
-    if (threadIdx.x < a8 - a) atomicAdd(h + offs[a + threadIdx.x], 1u);
-    if (threadIdx.x < e - e8) atomicAdd(h + offs[e8 + threadIdx.x], 1u);
+    if (threadIdx.x < a8 - a) {
+      const uint32_t v = offs[a + threadIdx.x];
+      if (UFC_IDX_OK(v, kBlockPix, 7)) atomicAdd(h + v, 1u);
+    }
+    if (threadIdx.x < e - e8) {
+      const uint32_t v = offs[e8 + threadIdx.x];
+      if (UFC_IDX_OK(v, kBlockPix, 7)) atomicAdd(h + v, 1u);
+    }
     const uint4* body = reinterpret_cast<const uint4*>(offs + a8);
     const int64_t nvec = (e8 - a8) >> 3;
     for (int64_t i0 = threadIdx.x; i0 < nvec; i0 += kHistVec * kHistThreads) {
@@ -1308,8 +1323,8 @@ k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off,
           const uint32_t w[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            atomicAdd(h + (w[j] & 0xFFFFu), 1u);
-            atomicAdd(h + (w[j] >> 16), 1u);
+            if (UFC_IDX_OK(w[j] & 0xFFFFu, kBlockPix, 7)) atomicAdd(h + (w[j] & 0xFFFFu), 1u);
+            if (UFC_IDX_OK(w[j] >> 16, kBlockPix, 7)) atomicAdd(h + (w[j] >> 16), 1u);
           }
         }
       }
@@ -1331,6 +1346,21 @@ k_hist_block(const uint16_t* __restrict__ offs, const int64_t* __restrict__ off,
 }
 
 // ================================================================ host ======
+
+// Index-check record of this translation unit (checked builds), read and
+// cleared on the context stream.
+cudaError_t take_checks_bin(CheckRec* out, cudaStream_t s) { return take_check_rec(out, s); }
+
+// A failed index test on purpose (every build): index i against bound n at
+// site 0.  The test records and skips; nothing is accessed.
+__global__ void k_check_selftest(long long i, long long n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) check_idx(i, n, 0);
+}
+ufc_status run_check_selftest(ufc_ctx* c, int64_t index, int64_t bound) {
+  k_check_selftest<<<1, 32, 0, c->stream>>>((long long)index, (long long)bound);
+  UFC_CUDA(c, cudaGetLastError());
+  return UFC_OK;
+}
 
 static float f_down(double v) {
   float f = (float)v;
@@ -1624,6 +1654,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   std::memset(&o, 0, sizeof o);
   o.keys = keys;
   o.counts = counts;
+  o.ncell = (int64_t)nshell * npix;
   o.dense_count = &qs.cnt->dense;
   int smem = 0;
   if (plan.mode == kModeDense) {
@@ -1813,7 +1844,7 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   {
     ProfScope ps_(c, "k_scatter_bucket");
     k_scatter_bucket<<<2 * c->num_sms, kScatThreads, smemB, c->stream>>>(
-        grouped, tiles, ntiles, bcur, b16, &qs.cnt->timeouts);
+        grouped, tiles, ntiles, bcur, b16, o.dense_cap, &qs.cnt->timeouts);
   }
   const int smemH = kBlockPix * 4;
   UFC_CUDA(c, cudaFuncSetAttribute(k_hist_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1821,7 +1852,8 @@ ufc_status run_keys_pipeline(ufc_ctx* c, int mode_req, const float* const* xyz,
   {
     ProfScope ps_(c, "k_hist_block");
     k_hist_block<<<2 * c->num_sms, kHistThreads, smemH, c->stream>>>(
-        b16, off, nb, counts + (int64_t)plan.shell0 * npix, (flags & UFC_BIN_ACCUMULATE) ? 1 : 0);
+        b16, off, nb, counts + (int64_t)plan.shell0 * npix, (flags & UFC_BIN_ACCUMULATE) ? 1 : 0,
+        o.dense_cap);
   }
   UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;

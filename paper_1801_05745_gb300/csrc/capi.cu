@@ -37,6 +37,9 @@ ufc_status run_kappa_adjoint_sums(ufc_ctx* c, const int32_t* counts, int S, int 
                                   double* sums);
 void grad_from_sums(const double* sm, int S, int npix, double w_var, double w_skew,
                     const double* dA, const double* dC, double* grad, double* G, double* H);
+cudaError_t take_checks_bin(CheckRec* out, cudaStream_t s);
+cudaError_t take_checks_stats(CheckRec* out, cudaStream_t s);
+ufc_status run_check_selftest(ufc_ctx* c, int64_t index, int64_t bound);
 ufc_status run_welford_update(ufc_ctx* c, const double* v, int nvec, int d, double* st);
 ufc_status run_stats_vector(ufc_ctx* c, const double* m, const int64_t* pdf, int nbins, double* v);
 ufc_status run_kappa_stats_noalloc(ufc_ctx* c, const int32_t* counts, int S, int nside,
@@ -234,11 +237,29 @@ ufc_status ufc_synchronize(ufc_ctx* c) {
     UFC_CUDA(c, cudaStreamSynchronize(owners[k]->stream));
     total += t[k];
   }
+  // index-test records (per device and translation unit), after all the work
+  CheckRec rec[2] = {};
+  UFC_CUDA(c, take_checks_bin(&rec[0], c->stream));
+  UFC_CUDA(c, take_checks_stats(&rec[1], c->stream));
+  UFC_CUDA(c, cudaStreamSynchronize(c->stream));
   if (total)
     return set_err(c, UFC_ERR_TIMEOUT,
                    "%llu device-side bounded wait(s) ran out since the last report; the "
                    "binning calls that met them have incomplete counts", total);
+  for (const CheckRec& r : rec)
+    if (r.count)
+      return set_err(c, UFC_ERR_INTERNAL,
+                     "%llu index test(s) failed since the last report; first at site %lld: "
+                     "index %lld, bound %lld (the accesses were skipped)",
+                     r.count, r.site, r.index, r.bound);
   return UFC_OK;
+}
+
+ufc_status ufc_check_selftest(ufc_ctx* c, int64_t index, int64_t bound) {
+  if (!c) return UFC_ERR_ARG;
+  c->err.clear();
+  cudaSetDevice(c->device);
+  return run_check_selftest(c, index, bound);
 }
 
 ufc_status ufc_wait_selftest(ufc_ctx* c, int64_t limit) {

@@ -84,6 +84,43 @@ struct BinCounters {
   unsigned long long timeouts;
 };
 
+// ---- index checks of checked builds ----------------------------------------
+// A build with -DUFC_CHECKED tests computed indices at the sites marked
+// UFC_IDX_OK(index, bound, site): a failed test counts in its translation
+// unit's record, which keeps the first failure's site, index and bound, and
+// the access is skipped, so the kernel runs to its end; ufc_synchronize
+// reports the failure (UFC_ERR_INTERNAL).  Other builds compile the tests
+// away (UFC_IDX_OK is the constant true).  The record is one per device and
+// translation unit, shared by the contexts on that device.
+struct CheckRec {
+  unsigned long long count;
+  long long site, index, bound;
+};
+static __device__ CheckRec g_check;
+__device__ __forceinline__ bool check_idx(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&g_check.count, 1ull) == 0ull) {
+    g_check.site = site;
+    g_check.index = i;
+    g_check.bound = n;
+  }
+  return false;
+}
+#ifdef UFC_CHECKED
+#define UFC_IDX_OK(i, n, site) (::ufc::check_idx((long long)(i), (long long)(n), (site)))
+#else
+#define UFC_IDX_OK(i, n, site) true
+#endif
+// Reads this translation unit's record into *out and clears it, on stream s
+// (the caller synchronises).
+static inline cudaError_t take_check_rec(CheckRec* out, cudaStream_t s) {
+  static const CheckRec zero{};
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_check, sizeof(CheckRec), 0,
+                                            cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbolAsync(g_check, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, s);
+}
+
 // Queue entry of an undecided particle image: box (4 bits), image (13 bits),
 // particle index (47 bits).
 __host__ __device__ inline uint64_t qpack(int box, int img, int64_t p) {

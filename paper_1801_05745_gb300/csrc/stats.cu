@@ -908,7 +908,7 @@ k_batch_persistent(BatchArgs ba, ShellTable st, Bands bd, PdfParam pp) {
       const float* q = it.xyz + 3 * (p0 + i);
       const int32_t key = batch_key(__ldg(q), __ldg(q + 1), __ldg(q + 2), it, lo2_s, hi2_s,
                                     chih_s, chil_s, st, bd, ba.N, npix);
-      if (key >= 0) atomicAdd(cmap + key, 1);
+      if (key >= 0 && UFC_IDX_OK(key, (int64_t)S * npix, 8)) atomicAdd(cmap + key, 1);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -975,6 +975,10 @@ k_batch_persistent(BatchArgs ba, ShellTable st, Bands bd, PdfParam pp) {
 }
 
 // ============================================================== host =====
+
+// Index-check record of this translation unit (checked builds), read and
+// cleared on the context stream.
+cudaError_t take_checks_stats(CheckRec* out, cudaStream_t s) { return take_check_rec(out, s); }
 
 static void make_coef(const double* A, double C, int S, int npix, Coef& cf) {
   std::memset(&cf, 0, sizeof cf);

@@ -263,7 +263,7 @@ def test_batched_run_resumed_from_checkpoint(orc, tmp_path):
     cfg = {"nside": nside, "nshell": nshell, "nbins": nbins, "lo": lo, "hi": hi}
     path = str(tmp_path / "run.npz")
     checkpoint.save(path, st, d, 5, cfg)
-    ctx2 = api.context(0)
+    ctx2 = api.Context(0)                        # a context of its own (not the shared one)
     host, k = checkpoint.load(path, d, cfg)
     st2 = torch.from_numpy(host).cuda()
     ctx2.batched_stats(xs[k:], bxs[k:], chi, nside, A[k:], C[k:], lo, hi, nbins, st2)
