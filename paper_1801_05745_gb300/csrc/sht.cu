@@ -30,6 +30,7 @@ constexpr int kShtMaxNside = 1024;     // shared-memory FFT of the 4 nside-pixel
 constexpr int kLegThreads = 256;       // threads per k_legendre block
 constexpr int kLegPPT = 4;             // ring pairs per thread
 constexpr int kLegChunkL = 32;         // l values per reduction round
+static_assert(kLegChunkL == 32, "the block reduction gives each degree of a round one lane");
 
 struct Ring {
   int64_t start;   // first pixel
@@ -293,7 +294,8 @@ __global__ void k_leg_coef(int32_t lmax, float4* __restrict__ coef) {
 // factor 2^e folded into the pair's F while e > -120 (below, the pair's
 // terms are under 2^-58 |F| and are left out until e grows).  Each degree's
 // sum over the pairs: a thread's pairs, then groups of 4 lanes (shuffles),
-// then the block's 64 group sums in shared memory, all in double-float
+// then the block's 64 group sums in shared memory (8 per warp, then the 8
+// warps' partials, so that the whole block takes part), all in double-float
 // (FP64 only for the block's result:
 // an FP64 instruction costs the FP32 pipe's time for about 64).  Output:
 // partial sums (without the 4 pi / N_pix factor) part[chunk][idx(l, m)].
@@ -305,6 +307,7 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
   __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
   // sums of 4 adjacent lanes (re.h, re.l, im.h, im.l): 8 per warp
   __shared__ float4 red[kLegThreads / 4][kLegChunkL];
+  __shared__ float4 red2[kLegThreads / 32][kLegChunkL];   // partials of the 8 warps
   // blockIdx.y in [0, lmax/2] handles m = y and (if distinct) m = lmax - y,
   // which balances the work per block
   const int chunk = blockIdx.x;
@@ -415,10 +418,25 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
         }
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      // the 64 group sums of each degree t: warp j adds groups j, j + 8, ...
+      // (lane t: conflict-free rows), then 8 partials per degree
+      if (lane < cnt) {
         dfl sr{0.f, 0.f}, si{0.f, 0.f};
-        for (int w = 0; w < kLegThreads / 4; ++w) {
-          const float4 v = red[w][t];
+#pragma unroll
+        for (int w = warp; w < kLegThreads / 4; w += kLegThreads / 32) {
+          const float4 v = red[w][lane];
+          sr = df_add(sr, dfl{v.x, v.y});
+          si = df_add(si, dfl{v.z, v.w});
+        }
+        red2[warp][lane] = make_float4(sr.h, sr.l, si.h, si.l);
+      }
+      __syncthreads();
+      if (threadIdx.x < cnt) {
+        const int t = threadIdx.x;
+        dfl sr{0.f, 0.f}, si{0.f, 0.f};
+#pragma unroll
+        for (int w = 0; w < kLegThreads / 32; ++w) {
+          const float4 v = red2[w][t];
           sr = df_add(sr, dfl{v.x, v.y});
           si = df_add(si, dfl{v.z, v.w});
         }
