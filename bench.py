@@ -721,6 +721,20 @@ def main():
                       "maps_per_s": 1e3 / ms_cl,
                       "kernels_ms_per_map": {k: round(v[0] / 3, 3) for k, v in cprof.items()},
                       "k_legendre_fp64_equiv_tflops": fp64 / (leg[0] / 3 * 1e-3) / 1e12 if leg[0] else None}
+        # k_legendre against the FP32 pipe: the double-float code's FP32
+        # instructions per (l, m, ring pair) for l >= m + 2, as written
+        # (three pair products of 7, one pair sum of 11, two multiply-adds
+        # into the pair sums of 13), against 128 FP32 lanes per SM at the
+        # maximum SM clock sampled during the main timed region
+        if leg[0]:
+            ops = 58.0 * npairs * (nalm - (2 * lmax + 1))
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            mhz = float(clk.get("sm_max_mhz") or 2070.0) if isinstance(clk, dict) else 2070.0
+            peak_alu = nsm * 128 * mhz * 1e6
+            got = ops / (leg[0] / 3 * 1e-3)
+            line["cl"]["roofline"] = {"bound": "alu", "kernel": "k_legendre", "achieved": got,
+                                      "peak": peak_alu, "unit": "FP32 op/s", "frac": got / peak_alu,
+                                      "peak_source": f"{nsm} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
 
     if not args.no_batched:
         line["batched_vs_serial"] = batched_leg(ctx, api, synth, dev, args.batched_real,
