@@ -5,10 +5,13 @@
 //   C_l  = (|a_l0|^2 + 2 sum_{m>0} |a_lm|^2) / (2l + 1),
 // evaluated ring by ring in FP64, with the long sums and recurrences in
 // double-float (pairs of FP32, about 48 bits) on the FP32 pipe:
+//   k_root_table     : the 8 Nside unit roots e^{-2 pi i j / (8 Nside)}.
 //   k_ring_transform : per ring, F_m = sum_j map_j e^{-i m phi_j}
 //                      = e^{-i m phi_0} X_{m mod n}, X the ring's DFT (radix-2
-//                      FFT in shared memory for power-of-two rings, direct
-//                      DFT otherwise); F stored m-major.
+//                      FFT in shared memory in double-float for power-of-two
+//                      rings, twiddles and phases from the root table;
+//                      radix-4 split and direct DFTs otherwise); F stored
+//                      m-major.
 //   k_lmm            : lambda_mm(z) of every north/south ring pair for every m,
 //                      as mantissa x 2^exponent (no underflow near the poles).
 //   k_legendre       : per (m, chunk of ring pairs) the recurrence over l of
@@ -115,30 +118,58 @@ __device__ __forceinline__ void df_mac(dfl& acc, dfl a, dfl b) {
   acc.l = __fadd_rn(acc.l, __fadd_rn(se, __fadd_rn(pe, cross)));
 }
 
+// Complex numbers with double-float parts, (re.h, re.l, im.h, im.l) in a float4.
+__device__ __forceinline__ float4 cdf_pack(dfl re, dfl im) { return make_float4(re.h, re.l, im.h, im.l); }
+// a * b
+__device__ __forceinline__ float4 cdf_mul(float4 a, float4 b) {
+  const dfl ar{a.x, a.y}, ai{a.z, a.w}, br{b.x, b.y}, bi{b.z, b.w};
+  return cdf_pack(df_add(df_mul(ar, br), df_neg(df_mul(ai, bi))),
+                  df_add(df_mul(ar, bi), df_mul(ai, br)));
+}
+__device__ __forceinline__ float4 cdf_add(float4 a, float4 b) {
+  return cdf_pack(df_add(dfl{a.x, a.y}, dfl{b.x, b.y}), df_add(dfl{a.z, a.w}, dfl{b.z, b.w}));
+}
+__device__ __forceinline__ float4 cdf_sub(float4 a, float4 b) {
+  return cdf_pack(df_add(dfl{a.x, a.y}, dfl{-b.x, -b.y}), df_add(dfl{a.z, a.w}, dfl{-b.z, -b.w}));
+}
+__device__ __forceinline__ float4 cdf_conj(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+
+// Unit roots e^{-2 pi i j / (8N)}, j < 8N, as double-float complex numbers
+// (FP64 sincospi, split once).  Every power-of-two ring (n = 4N, or n = 4i
+// with i a power of two) has n | 8N: its FFT twiddles are T[k 8N/n] and the
+// phase of its first pixel, e^{-i m phi_0} with phi_0 = pi/n, is
+// T[m 4N/n mod 8N].
+__global__ void k_root_table(int32_t N, float4* __restrict__ T) {
+  const int n8 = 8 * N;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n8; j += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)j / (double)n8, &sn, &cs);
+    T[j] = cdf_pack(df_from_d(cs), df_from_d(sn));
+  }
+}
+
 // One block per ring.  Shared memory: twiddles w_k = e^{-2 pi i k / n} and the
 // ring's values (real, or complex for the FFT).
 __global__ void __launch_bounds__(512)
-k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t nrings,
-                 double2* __restrict__ F) {
+k_ring_transform(const float* __restrict__ map, const float4* __restrict__ T, int32_t N,
+                 int32_t lmax, int32_t nrings, double2* __restrict__ F) {
   extern __shared__ __align__(16) double2 sh[];
   const int r = blockIdx.x;
   const Ring g = ring_geom(N, r);
   const int n = g.n;
-  double2* w = sh;            // [n]
-  double2* x = sh + n;        // [n]
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double sn, cs;
-    sincospi(-2.0 * (double)k / (double)n, &sn, &cs);
-    w[k] = make_double2(cs, sn);
-  }
-  const bool fft = is_pow2(n);
-  if (fft) {
-    // bit-reversed load, then radix-2 decimation-in-time stages
+  if (is_pow2(n)) {
+    // radix-2 decimation-in-time FFT in double-float on the FP32 pipe
+    // (an FP64 instruction costs the FP32 pipe's time for about 64):
+    // bit-reversed load, then the stages; twiddles from the root table
+    float4* xd = reinterpret_cast<float4*>(sh);   // [n]
+    float4* wd = xd + n;                          // [n/2] e^{-2 pi i k / n}
+    const int ts = 8 * N / n;
+    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) wd[k] = T[k * ts];
     int bits = 0;
     while ((1 << bits) < n) ++bits;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const int rj = __brev(j) >> (32 - bits);
-      x[rj] = make_double2((double)map[g.start + j], 0.0);
+      xd[rj] = make_float4(map[g.start + j], 0.f, 0.f, 0.f);
     }
     __syncthreads();
     for (int len = 2; len <= n; len <<= 1) {
@@ -146,16 +177,31 @@ k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t
       for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
         const int grp = t / half, pos = t - grp * half;
         const int a = grp * len + pos, b = a + half;
-        const double2 tw = w[pos * step];
-        const double2 xb = x[b];
-        const double2 p = make_double2(tw.x * xb.x - tw.y * xb.y, tw.x * xb.y + tw.y * xb.x);
-        const double2 xa = x[a];
-        x[a] = make_double2(xa.x + p.x, xa.y + p.y);
-        x[b] = make_double2(xa.x - p.x, xa.y - p.y);
+        const float4 p = cdf_mul(wd[pos * step], xd[b]);
+        const float4 xa = xd[a];
+        xd[a] = cdf_add(xa, p);
+        xd[b] = cdf_sub(xa, p);
       }
       __syncthreads();
     }
-  } else {
+    // F_m = e^{-i m phi_0} X_{m mod n} (phi_0 = 0 or pi/n)
+    const bool shifted = g.phi0_pi != 0.0;
+    const int ps = 4 * N / n;
+    for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
+      float4 X = xd[m & (n - 1)];
+      if (shifted) X = cdf_mul(T[(m * ps) & (8 * N - 1)], X);
+      F[(size_t)m * nrings + r] = make_double2(df_to_d(dfl{X.x, X.y}), df_to_d(dfl{X.z, X.w}));
+    }
+    return;
+  }
+  double2* w = sh;            // [n]
+  double2* x = sh + n;        // [n]
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)k / (double)n, &sn, &cs);
+    w[k] = make_double2(cs, sn);
+  }
+  {
     // non power-of-two ring (a polar ring, n = 4 i): one radix-4 split,
     // X_k = sum_{r<4} w_n^{rk} Y_r(k mod i) with Y_r(q) = sum_{a<i} x_{4a+r}
     // w_n^{4aq} the length-i DFTs of the four sub-sequences (real input:
@@ -229,7 +275,7 @@ k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t
   for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
     const int k = m % n;
     double2 X;
-    if (fft || k <= n / 2) X = x[k];
+    if (k <= n / 2) X = x[k];
     else { X = x[n - k]; X.y = -X.y; }
     double sn, cs;
     sincospi(-(double)m * g.phi0_pi, &sn, &cs);
@@ -238,22 +284,79 @@ k_ring_transform(const float* __restrict__ map, int32_t N, int32_t lmax, int32_t
 }
 
 // lambda_mm of every ring pair p (north ring p) for m = 0..lmax, as
-// mu * 2^e with |mu| in [2^-500, 1): lambda_00 = 1/sqrt(4 pi),
+// mu * 2^e: lambda_00 = 1/sqrt(4 pi),
 // lambda_mm = -sqrt((2m+1)/(2m)) sin(theta) lambda_{m-1,m-1}.
-__global__ void k_lmm(int32_t N, int32_t lmax, int32_t npairs, double* __restrict__ mu,
-                      int32_t* __restrict__ ex) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= npairs) return;
-  const Ring g = ring_geom(N, p);
-  double v = 0.28209479177387814347;   // 1 / sqrt(4 pi)
-  int e = 0;
-  for (int m = 0; m <= lmax; ++m) {
-    if (m > 0) {
-      v *= -sqrt((2.0 * m + 1.0) / (2.0 * m)) * g.s;
-      if (fabs(v) < 0x1p-500) { v *= 0x1p500; e -= 500; }
+// Each thread owns one pair and a run of kLmmRun orders m0 = kLmmRun j ..
+// m0 + kLmmRun - 1; it starts from
+//   lambda_{m0 m0} = lambda_00 C_j sin(theta)^{m0}        (m0 even: no sign),
+//   C_j = prod_{k=1}^{m0} sqrt((2k+1)/(2k))               (pair-independent),
+// with sin(theta)^{m0} by repeated squaring, everything as (mantissa in
+// [1/2, 1), binary exponent) so that nothing underflows, and then steps
+// through its run with the recurrence (the stored mantissas are rescaled
+// by 2^500 when they fall below 2^-500).  The block forms the factors
+// sqrt((2k+1)/(2k)) and C_j in shared memory: the factors in parallel, one
+// run's product per thread, then the prefix products in order by one
+// thread.
+constexpr int kLmmRun = 64;
+constexpr int kLmmMaxRuns = 4 * kShtMaxNside / kLmmRun + 1;   // lmax <= 4 nside
+static_assert(kLmmRun % 2 == 0, "runs start at even orders");
+struct MantExp { double m; int e; };
+__device__ __forceinline__ MantExp me_mul(MantExp a, MantExp b) {
+  int d;
+  const double x = frexp(a.m * b.m, &d);
+  return {x, a.e + b.e + d};
+}
+__global__ void __launch_bounds__(256)
+k_lmm(int32_t N, int32_t lmax, int32_t npairs, double* __restrict__ mu, int32_t* __restrict__ ex) {
+  __shared__ double cm[kLmmMaxRuns];
+  __shared__ int ce[kLmmMaxRuns];
+  __shared__ double fk[4 * kShtMaxNside + 1];   // fk[k] = sqrt((2k+1)/(2k)), k >= 1
+  const int nrun = lmax / kLmmRun + 1;
+  for (int k = 1 + threadIdx.x; k <= lmax; k += blockDim.x) fk[k] = sqrt((2.0 * k + 1.0) / (2.0 * k));
+  __syncthreads();
+  for (int j = threadIdx.x; j < nrun; j += blockDim.x) {   // run j-1's factors
+    double v = 1.0;
+    if (j > 0)
+      for (int k = kLmmRun * (j - 1) + 1; k <= kLmmRun * j; ++k) v *= fk[k];
+    int d;
+    cm[j] = frexp(v, &d);
+    ce[j] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int j = 1; j < nrun; ++j) {
+      const MantExp c = me_mul({cm[j - 1], ce[j - 1]}, {cm[j], ce[j]});
+      cm[j] = c.m;
+      ce[j] = c.e;
     }
-    mu[(size_t)m * npairs + p] = v;
-    ex[(size_t)m * npairs + p] = e;
+  __syncthreads();
+  const int64_t total = (int64_t)npairs * nrun;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int p = int(t % npairs), j = int(t / npairs);
+    const Ring g = ring_geom(N, p);
+    const int m0 = kLmmRun * j;
+    MantExp r{0.5, 1};                          // 1
+    MantExp b;
+    b.m = frexp(g.s, &b.e);
+    for (int k = m0; k; k >>= 1) {              // s^{m0}
+      if (k & 1) r = me_mul(r, b);
+      b = me_mul(b, b);
+    }
+    MantExp l00;
+    l00.m = frexp(0.28209479177387814347, &l00.e);   // 1 / sqrt(4 pi)
+    const MantExp st = me_mul(me_mul(l00, {cm[j], ce[j]}), r);
+    double v = st.m;
+    int e = st.e;
+    const int mend = min(lmax, m0 + kLmmRun - 1);
+    for (int m = m0; m <= mend; ++m) {
+      if (m > m0) {
+        v *= -fk[m] * g.s;
+        if (fabs(v) < 0x1p-500) { v *= 0x1p500; e -= 500; }
+      }
+      mu[(size_t)m * npairs + p] = v;
+      ex[(size_t)m * npairs + p] = e;
+    }
   }
 }
 
@@ -460,16 +563,19 @@ __global__ void k_alm_sum(const double2* __restrict__ part, int nchunk, int64_t 
   }
 }
 
+// One warp per degree l: lane k adds the orders m = k, k + 32, ... (their
+// loads in flight together), then a fixed shuffle tree.
 __global__ void k_alm2cl(const double2* __restrict__ alm, int32_t lmax, double* __restrict__ cl) {
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l > lmax) return;
+  const int l = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (l > lmax) return;                        // (uniform over the warp)
   double s = 0.0;
-  for (int m = 0; m <= l; ++m) {
+  for (int m = lane; m <= l; m += 32) {
     const double2 a = alm[(size_t)m * (2 * lmax + 1 - m) / 2 + l];
     const double q = a.x * a.x + a.y * a.y;
     s += m == 0 ? q : 2.0 * q;
   }
-  cl[l] = s / (2.0 * l + 1.0);
+  s = warp_sum_dd(s);
+  if (lane == 0) cl[l] = s / (2.0 * l + 1.0);
 }
 
 // ------------------------------------------------------------ synthesis --
@@ -478,7 +584,9 @@ __global__ void k_alm2cl(const double2* __restrict__ alm, int32_t lmax, double* 
 //   k_legendre_synth : G_m(ring) = sum_l a_lm lambda_lm(z_ring), per (m, ring
 //                      pair) with the even/odd split of the mirror rings;
 //   k_ring_synth     : map_j = sum_{|m| <= lmax} G_m e^{i m phi_j}, folding
-//                      m onto the ring's n frequencies and an inverse DFT.
+//                      m onto the ring's n frequencies and an inverse DFT
+//                      (double-float radix-2 FFT with root-table twiddles for
+//                      power-of-two rings, radix-4 split otherwise).
 __global__ void __launch_bounds__(kLegThreads)
 k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
                  const int32_t* __restrict__ ex, const float4* __restrict__ coef, int32_t N,
@@ -588,12 +696,52 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
 // e^{2 pi i k j / n} (inverse radix-2 FFT for power-of-two rings, direct
 // sum otherwise).  Each H_k is summed by one thread in increasing m.
 __global__ void __launch_bounds__(512)
-k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nrings,
-             float* __restrict__ map) {
+k_ring_synth(const double2* __restrict__ G, const float4* __restrict__ T, int32_t N,
+             int32_t lmax, int32_t nrings, float* __restrict__ map) {
   extern __shared__ __align__(16) double2 sh[];
   const int r = blockIdx.x;
   const Ring g = ring_geom(N, r);
   const int n = g.n;
+  if (is_pow2(n)) {
+    // double-float on the FP32 pipe; twiddles e^{+2 pi i k / n} and phases
+    // e^{+i m phi_0} (phi_0 = 0 or pi/n) are conjugates of root-table
+    // entries; H_k into bit-reversed order, then the inverse FFT stages
+    float4* hd = reinterpret_cast<float4*>(sh);   // [n]
+    float4* wd = hd + n;                          // [n/2]
+    const int ts = 8 * N / n, ps = 4 * N / n;
+    const bool shifted = g.phi0_pi != 0.0;
+    for (int k = threadIdx.x; k < n / 2; k += blockDim.x) wd[k] = cdf_conj(T[k * ts]);
+    int bits = 0;
+    while ((1 << bits) < n) ++bits;
+    auto term = [&](int m) {                    // G_m e^{i m phi_0}
+      const double2 gm = G[(size_t)m * nrings + r];
+      float4 t = cdf_pack(df_from_d(gm.x), df_from_d(gm.y));
+      if (shifted) t = cdf_mul(cdf_conj(T[(m * ps) & (8 * N - 1)]), t);
+      return t;
+    };
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int m = k; m <= lmax; m += n) h = cdf_add(h, term(m));            // m = k mod n
+      for (int m = (n - k) % n; m <= lmax; m += n)                           // -m = k mod n
+        if (m != 0) h = cdf_add(h, cdf_conj(term(m)));
+      hd[__brev(k) >> (32 - bits)] = h;
+    }
+    __syncthreads();
+    for (int len = 2; len <= n; len <<= 1) {
+      const int half = len >> 1, step = n / len;
+      for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
+        const int grp = t / half, pos = t - grp * half;
+        const int a = grp * len + pos, b = a + half;
+        const float4 p = cdf_mul(wd[pos * step], hd[b]);
+        const float4 xa = hd[a];
+        hd[a] = cdf_add(xa, p);
+        hd[b] = cdf_sub(xa, p);
+      }
+      __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = __fadd_rn(hd[j].x, hd[j].y);
+    return;
+  }
   double2* w = sh;            // [n]: e^{+2 pi i k / n}
   double2* H = sh + n;        // [n]
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -601,13 +749,9 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
     sincospi(2.0 * (double)k / (double)n, &sn, &cs);
     w[k] = make_double2(cs, sn);
   }
-  const bool fft = is_pow2(n);
-  int bits = 0;
-  while ((1 << bits) < n) ++bits;
   // the map is real, so H_{n-k} = conj(H_k): the direct transform below
   // needs H_k for k <= n/2 only
-  const int kend = fft ? n : n / 2 + 1;
-  for (int k = threadIdx.x; k < kend; k += blockDim.x) {
+  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
     double hx = 0.0, hy = 0.0;
     for (int m = k; m <= lmax; m += n) {              // m = k mod n
       const double2 gm = G[(size_t)m * nrings + r];
@@ -624,27 +768,10 @@ k_ring_synth(const double2* __restrict__ G, int32_t N, int32_t lmax, int32_t nri
       hx += cs * gm.x - sn * gm.y;                    // conj(G_m e^{i m phi_0})
       hy -= cs * gm.y + sn * gm.x;
     }
-    const int dst = fft ? (int)(__brev(k) >> (32 - bits)) : k;
-    H[dst] = make_double2(hx, hy);
+    H[k] = make_double2(hx, hy);
   }
   __syncthreads();
-  if (fft) {
-    for (int len = 2; len <= n; len <<= 1) {
-      const int half = len >> 1, step = n / len;
-      for (int t = threadIdx.x; t < n / 2; t += blockDim.x) {
-        const int grp = t / half, pos = t - grp * half;
-        const int a = grp * len + pos, b = a + half;
-        const double2 tw = w[pos * step];
-        const double2 xb = H[b];
-        const double2 p = make_double2(tw.x * xb.x - tw.y * xb.y, tw.x * xb.y + tw.y * xb.x);
-        const double2 xa = H[a];
-        H[a] = make_double2(xa.x + p.x, xa.y + p.y);
-        H[b] = make_double2(xa.x - p.x, xa.y - p.y);
-      }
-      __syncthreads();
-    }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = (float)H[j].x;
-  } else {
+  {
     // non power-of-two ring (polar, n = 4 i), from the Hermitian half
     // (H_{n-k} = conj H_k, the map being real) with one radix-4 split:
     // map_{4a+r} = Re sum_{q<i} Z_r(q) w^{4aq}, Z_r(q) = sum_{t<4} H_{q+it}
@@ -774,7 +901,8 @@ ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double
   const size_t lbytes = (size_t)(lmax + 1) * npairs * (sizeof(double) + sizeof(int32_t));
   const size_t pbytes = (size_t)nchunk * nalm * sizeof(double2);
   const size_t cbytes = (size_t)nalm * sizeof(float4);
-  char* ws = (char*)ws_get(c, kSlotSht, fbytes + lbytes + pbytes + cbytes + 512);
+  const size_t tbytes = (size_t)8 * nside * sizeof(float4);
+  char* ws = (char*)ws_get(c, kSlotSht, fbytes + lbytes + pbytes + cbytes + tbytes + 512);
   if (!ws) return UFC_ERR_ALLOC;
   double2* F = reinterpret_cast<double2*>(ws);
   double* mu = reinterpret_cast<double*>(ws + fbytes);
@@ -783,16 +911,23 @@ ufc_status run_map2alm(ufc_ctx* c, const float* map, int nside, int lmax, double
   pp += (16 - (reinterpret_cast<uintptr_t>(pp) & 15)) & 15;
   double2* part = reinterpret_cast<double2*>(pp);
   float4* coef = reinterpret_cast<float4*>(pp + pbytes);
+  float4* roots = coef + nalm;
   const int smem = 2 * 4 * nside * (int)sizeof(double2);
   UFC_CUDA(c, cudaFuncSetAttribute(k_ring_transform, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    smem));
   {
+    ProfScope ps_(c, "k_root_table");
+    k_root_table<<<(8 * nside + 255) / 256, 256, 0, c->stream>>>(nside, roots);
+  }
+  {
     ProfScope ps_(c, "k_ring_transform");
-    k_ring_transform<<<nrings, 512, smem, c->stream>>>(map, nside, lmax, nrings, F);
+    k_ring_transform<<<nrings, 512, smem, c->stream>>>(map, roots, nside, lmax, nrings, F);
   }
   {
     ProfScope ps_(c, "k_lmm");
-    k_lmm<<<(npairs + 127) / 128, 128, 0, c->stream>>>(nside, lmax, npairs, mu, ex);
+    const int64_t lt = (int64_t)npairs * (lmax / kLmmRun + 1);
+    k_lmm<<<(int)std::min<int64_t>((lt + 255) / 256, 8 * c->num_sms), 256, 0, c->stream>>>(
+        nside, lmax, npairs, mu, ex);
   }
   {
     ProfScope ps_(c, "k_leg_coef");
@@ -838,7 +973,8 @@ ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float
   const size_t lbytes = (size_t)(lmax + 1) * npairs * (sizeof(double) + sizeof(int32_t));
   const int64_t nalm = (int64_t)(lmax + 1) * (lmax + 2) / 2;
   const size_t cbytes = (size_t)nalm * sizeof(float4);
-  char* ws = (char*)ws_get(c, kSlotSht, gbytes + lbytes + cbytes + 512);
+  const size_t tbytes = (size_t)8 * nside * sizeof(float4);
+  char* ws = (char*)ws_get(c, kSlotSht, gbytes + lbytes + cbytes + tbytes + 512);
   if (!ws) return UFC_ERR_ALLOC;
   double2* Gm = reinterpret_cast<double2*>(ws);
   double* mu = reinterpret_cast<double*>(ws + gbytes);
@@ -846,13 +982,20 @@ ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float
   char* cp = ws + gbytes + lbytes;
   cp += (16 - (reinterpret_cast<uintptr_t>(cp) & 15)) & 15;
   float4* coef = reinterpret_cast<float4*>(cp);
+  float4* roots = coef + nalm;
+  {
+    ProfScope ps_(c, "k_root_table");
+    k_root_table<<<(8 * nside + 255) / 256, 256, 0, c->stream>>>(nside, roots);
+  }
   {
     ProfScope ps_(c, "k_leg_coef");
     k_leg_coef<<<dim3(4, lmax + 1), 256, 0, c->stream>>>(lmax, coef);
   }
   {
     ProfScope ps_(c, "k_lmm");
-    k_lmm<<<(npairs + 127) / 128, 128, 0, c->stream>>>(nside, lmax, npairs, mu, ex);
+    const int64_t lt = (int64_t)npairs * (lmax / kLmmRun + 1);
+    k_lmm<<<(int)std::min<int64_t>((lt + 255) / 256, 8 * c->num_sms), 256, 0, c->stream>>>(
+        nside, lmax, npairs, mu, ex);
   }
   {
     ProfScope ps_(c, "k_legendre_synth");
@@ -864,7 +1007,7 @@ ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float
   UFC_CUDA(c, cudaFuncSetAttribute(k_ring_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   {
     ProfScope ps_(c, "k_ring_synth");
-    k_ring_synth<<<nrings, 512, smem, c->stream>>>(Gm, nside, lmax, nrings, map);
+    k_ring_synth<<<nrings, 512, smem, c->stream>>>(Gm, roots, nside, lmax, nrings, map);
   }
   UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;
@@ -889,7 +1032,7 @@ ufc_status run_alm2cl(ufc_ctx* c, const double* alm, int lmax, double* cl) {
   if ((reinterpret_cast<uintptr_t>(alm) & 15))
     return set_err(c, UFC_ERR_ARG, "alm_dev must be 16-byte aligned");
   ProfScope ps_(c, "k_alm2cl");
-  k_alm2cl<<<(lmax + 256) / 256, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(alm), lmax,
+  k_alm2cl<<<(lmax + 8) / 8, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(alm), lmax,
                                                         cl);
   UFC_CUDA(c, cudaGetLastError());
   return UFC_OK;
