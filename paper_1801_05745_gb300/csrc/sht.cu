@@ -194,92 +194,94 @@ k_ring_transform(const float* __restrict__ map, const float4* __restrict__ T, in
     }
     return;
   }
-  double2* w = sh;            // [n]
-  double2* x = sh + n;        // [n]
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  // non power-of-two ring (a polar ring, n = 4 i): one radix-4 split,
+  // X_k = sum_{r<4} w_n^{rk} Y_r(k mod i) with Y_r(q) = sum_{a<i} x_{4a+r}
+  // w_n^{4aq} the length-i DFTs of the four sub-sequences (real input:
+  // Y_r(i-q) = conj Y_r(q), so q <= i/2), then k <= min(n/2, lmax) (real
+  // input: X_{n-k} = conj X_k).  Double-float on the FP32 pipe; the map
+  // values are FP32.  The twiddles w_n^k come from FP64 sincospi for the
+  // first quarter k < i only (w_n^{k + q i} = (-i)^q w_n^k), and the phase
+  // e^{-i m phi_0} = w_{2n}^m (phi_0 = pi/n) is w_n^{m/2}, times w_{2n} for
+  // odd m.
+  float4* wf = reinterpret_cast<float4*>(sh);             // [n] w_n^k
+  double2* x = sh + n;
+  float* xr = reinterpret_cast<float*>(x);                // [n] the ring's values
+  const int ni = n / 4, nq = ni / 2 + 1;
+  float4* Y = reinterpret_cast<float4*>(x + n / 4 + 1);   // [4][nq] after xr
+  float4* Xf = reinterpret_cast<float4*>(x);              // [n/2 + 1], once xr and Y are read
+  for (int jj = threadIdx.x; jj < n; jj += blockDim.x) xr[jj] = map[g.start + jj];
+  for (int k = threadIdx.x; k < ni; k += blockDim.x) {
     double sn, cs;
     sincospi(-2.0 * (double)k / (double)n, &sn, &cs);
-    w[k] = make_double2(cs, sn);
+    const dfl c = df_from_d(cs), sv = df_from_d(sn);
+    wf[k] = cdf_pack(c, sv);                              // (c, s)
+    wf[k + ni] = cdf_pack(sv, dfl{-c.h, -c.l});           // -i (c + i s)
+    wf[k + 2 * ni] = cdf_pack(dfl{-c.h, -c.l}, dfl{-sv.h, -sv.l});
+    wf[k + 3 * ni] = cdf_pack(dfl{-sv.h, -sv.l}, c);
   }
-  {
-    // non power-of-two ring (a polar ring, n = 4 i): one radix-4 split,
-    // X_k = sum_{r<4} w_n^{rk} Y_r(k mod i) with Y_r(q) = sum_{a<i} x_{4a+r}
-    // w_n^{4aq} the length-i DFTs of the four sub-sequences (real input:
-    // Y_r(i-q) = conj Y_r(q), so q <= i/2), then k <= min(n/2, lmax) (real
-    // input: X_{n-k} = conj X_k).  Sums in double-float on the FP32 pipe;
-    // the map values are FP32, the twiddles are split into double-float
-    // pairs in place (each thread its own, as computed above).
-    float4* wf = reinterpret_cast<float4*>(w);          // [n] (re.h, re.l, im.h, im.l)
-    float* xr = reinterpret_cast<float*>(x);            // [n] the ring's values
-    const int ni = n / 4, nq = ni / 2 + 1;
-    float4* Y = reinterpret_cast<float4*>(x + n / 4 + 1);   // [4][nq] after xr
-    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) xr[jj] = map[g.start + jj];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const double2 t = w[k];
-      const dfl re = df_from_d(t.x), im = df_from_d(t.y);
-      wf[k] = make_float4(re.h, re.l, im.h, im.l);
+  __syncthreads();
+  for (int o = threadIdx.x; o < 4 * nq; o += blockDim.x) {
+    const int r = o / nq, q = o - r * nq;
+    const int step = 4 * q;                  // < n since q <= i/2
+    dfl ar{0.f, 0.f}, ai{0.f, 0.f};
+    int idx = 0;
+    for (int a = 0; a < ni; ++a) {
+      const dfl v{xr[4 * a + r], 0.f};
+      const float4 tw = wf[idx];
+      df_mac(ar, v, dfl{tw.x, tw.y});
+      df_mac(ai, v, dfl{tw.z, tw.w});
+      idx += step;
+      idx -= idx >= n ? n : 0;
     }
-    __syncthreads();
-    for (int o = threadIdx.x; o < 4 * nq; o += blockDim.x) {
-      const int r = o / nq, q = o - r * nq;
-      const int step = 4 * q;                  // < n since q <= i/2
-      dfl ar{0.f, 0.f}, ai{0.f, 0.f};
-      int idx = 0;
-      for (int a = 0; a < ni; ++a) {
-        const dfl v{xr[4 * a + r], 0.f};
-        const float4 tw = wf[idx];
-        df_mac(ar, v, dfl{tw.x, tw.y});
-        df_mac(ai, v, dfl{tw.z, tw.w});
-        idx += step;
-        idx -= idx >= n ? n : 0;
-      }
-      ar = df_add(ar, dfl{0.f, 0.f});
-      ai = df_add(ai, dfl{0.f, 0.f});
-      Y[o] = make_float4(ar.h, ar.l, ai.h, ai.l);
-    }
-    __syncthreads();
-    const int kmax = min(n / 2, lmax);
-    double2 out[4];
+    ar = df_add(ar, dfl{0.f, 0.f});
+    ai = df_add(ai, dfl{0.f, 0.f});
+    Y[o] = make_float4(ar.h, ar.l, ai.h, ai.l);
+  }
+  __syncthreads();
+  const int kmax = min(n / 2, lmax);
+  float4 out[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = threadIdx.x + u * (int)blockDim.x;
-      if (k > kmax) continue;
-      int q = k % ni;
-      const bool cj = q > ni / 2;
-      if (cj) q = ni - q;
-      dfl xre{0.f, 0.f}, xim{0.f, 0.f};
+  for (int u = 0; u < 4; ++u) {
+    const int k = threadIdx.x + u * (int)blockDim.x;
+    if (k > kmax) continue;
+    int q = k % ni;
+    const bool cj = q > ni / 2;
+    if (cj) q = ni - q;
+    dfl xre{0.f, 0.f}, xim{0.f, 0.f};
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const float4 yv = Y[r * nq + q];
-        const dfl yr{yv.x, yv.y}, yi = cj ? dfl{-yv.z, -yv.w} : dfl{yv.z, yv.w};
-        const float4 tw = wf[(r * k) % n];
-        const dfl tr{tw.x, tw.y}, ti{tw.z, tw.w};
-        df_mac(xre, tr, yr);                   // Re(w Y)
-        df_mac(xre, df_neg(ti), yi);
-        df_mac(xim, tr, yi);                   // Im(w Y)
-        df_mac(xim, ti, yr);
-      }
-      xre = df_add(xre, dfl{0.f, 0.f});
-      xim = df_add(xim, dfl{0.f, 0.f});
-      out[u] = make_double2(df_to_d(xre), df_to_d(xim));
+    for (int r = 0; r < 4; ++r) {
+      const float4 yv = Y[r * nq + q];
+      const dfl yr{yv.x, yv.y}, yi = cj ? dfl{-yv.z, -yv.w} : dfl{yv.z, yv.w};
+      const float4 tw = wf[(r * k) % n];
+      const dfl tr{tw.x, tw.y}, ti{tw.z, tw.w};
+      df_mac(xre, tr, yr);                   // Re(w Y)
+      df_mac(xre, df_neg(ti), yi);
+      df_mac(xim, tr, yi);                   // Im(w Y)
+      df_mac(xim, ti, yr);
     }
-    __syncthreads();                           // xr and Y are read; X overwrites them
+    out[u] = cdf_pack(df_add(xre, dfl{0.f, 0.f}), df_add(xim, dfl{0.f, 0.f}));
+  }
+  __syncthreads();                           // xr and Y are read; X overwrites them
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = threadIdx.x + u * (int)blockDim.x;
-      if (k <= kmax) x[k] = out[u];
-    }
+  for (int u = 0; u < 4; ++u) {
+    const int k = threadIdx.x + u * (int)blockDim.x;
+    if (k <= kmax) Xf[k] = out[u];
   }
   __syncthreads();
   // F_m = e^{-i m phi_0} X_{m mod n}, m = 0..lmax
+  float4 h1;                                 // w_{2n} = e^{-i pi / n}
+  {
+    double sn, cs;
+    sincospi(-1.0 / (double)n, &sn, &cs);
+    h1 = cdf_pack(df_from_d(cs), df_from_d(sn));
+  }
   for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
     const int k = m % n;
-    double2 X;
-    if (k <= n / 2) X = x[k];
-    else { X = x[n - k]; X.y = -X.y; }
-    double sn, cs;
-    sincospi(-(double)m * g.phi0_pi, &sn, &cs);
-    F[(size_t)m * nrings + r] = make_double2(cs * X.x - sn * X.y, cs * X.y + sn * X.x);
+    const float4 X = k <= n / 2 ? Xf[k] : cdf_conj(Xf[n - k]);
+    float4 ph = wf[(m >> 1) % n];
+    if (m & 1) ph = cdf_mul(ph, h1);
+    const float4 v = cdf_mul(ph, X);
+    F[(size_t)m * nrings + r] = make_double2(df_to_d(dfl{v.x, v.y}), df_to_d(dfl{v.z, v.w}));
   }
 }
 
@@ -742,35 +744,6 @@ k_ring_synth(const double2* __restrict__ G, const float4* __restrict__ T, int32_
     for (int j = threadIdx.x; j < n; j += blockDim.x) map[g.start + j] = __fadd_rn(hd[j].x, hd[j].y);
     return;
   }
-  double2* w = sh;            // [n]: e^{+2 pi i k / n}
-  double2* H = sh + n;        // [n]
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    double sn, cs;
-    sincospi(2.0 * (double)k / (double)n, &sn, &cs);
-    w[k] = make_double2(cs, sn);
-  }
-  // the map is real, so H_{n-k} = conj(H_k): the direct transform below
-  // needs H_k for k <= n/2 only
-  for (int k = threadIdx.x; k <= n / 2; k += blockDim.x) {
-    double hx = 0.0, hy = 0.0;
-    for (int m = k; m <= lmax; m += n) {              // m = k mod n
-      const double2 gm = G[(size_t)m * nrings + r];
-      double sn, cs;
-      sincospi((double)m * g.phi0_pi, &sn, &cs);
-      hx += cs * gm.x - sn * gm.y;
-      hy += cs * gm.y + sn * gm.x;
-    }
-    for (int m = (n - k) % n; m <= lmax; m += n) {    // -m = k mod n
-      if (m == 0) continue;
-      const double2 gm = G[(size_t)m * nrings + r];
-      double sn, cs;
-      sincospi((double)m * g.phi0_pi, &sn, &cs);
-      hx += cs * gm.x - sn * gm.y;                    // conj(G_m e^{i m phi_0})
-      hy -= cs * gm.y + sn * gm.x;
-    }
-    H[k] = make_double2(hx, hy);
-  }
-  __syncthreads();
   {
     // non power-of-two ring (polar, n = 4 i), from the Hermitian half
     // (H_{n-k} = conj H_k, the map being real) with one radix-4 split:
@@ -778,22 +751,42 @@ k_ring_synth(const double2* __restrict__ G, const float4* __restrict__ T, int32_
     // w^{r(q+it)}, and Z_r(i-q) = conj Z_r(q), so
     // map_{4a+r} = Re Z_r(0) + 2 sum_{0<q<i/2} Re(Z_r(q) w^{4aq})
     //              + [i even] (-1)^a Re Z_r(i/2).
-    // Double-float on the FP32 pipe; H and the twiddles are converted in
-    // place, each element by one thread (the twiddles by the thread that
-    // computed them).
-    float4* wf = reinterpret_cast<float4*>(w);   // (re.h, re.l, im.h, im.l)
-    float4* hf = reinterpret_cast<float4*>(H);   // [n/2 + 1]
+    // Double-float on the FP32 pipe.  The twiddles w^k = e^{+2 pi i k / n}
+    // come from FP64 sincospi for k < i only (w^{k + q i} = i^q w^k); the
+    // phases e^{+i m phi_0} = e^{+i pi m / n} are w^{m/2}, times e^{+i pi / n}
+    // for odd m.
+    float4* wf = reinterpret_cast<float4*>(sh);   // [n] (re.h, re.l, im.h, im.l)
+    float4* hf = wf + n;                          // [n/2 + 1]
     const int ni = n / 4, nq = ni / 2 + 1, half = n / 2;
-    float4* Z = hf + half + 1;                   // [4][nq]
-    for (int k = threadIdx.x; k < n; k += blockDim.x) {
-      const double2 t = w[k];
-      const dfl tr = df_from_d(t.x), ti = df_from_d(t.y);
-      wf[k] = make_float4(tr.h, tr.l, ti.h, ti.l);
-      if (k <= half) {
-        const double2 h = H[k];
-        const dfl hr = df_from_d(h.x), hi = df_from_d(h.y);
-        hf[k] = make_float4(hr.h, hr.l, hi.h, hi.l);
-      }
+    float4* Z = hf + half + 1;                    // [4][nq]
+    for (int k = threadIdx.x; k < ni; k += blockDim.x) {
+      double sn, cs;
+      sincospi(2.0 * (double)k / (double)n, &sn, &cs);
+      const dfl c = df_from_d(cs), sv = df_from_d(sn);
+      wf[k] = cdf_pack(c, sv);
+      wf[k + ni] = cdf_pack(dfl{-sv.h, -sv.l}, c);                    // i (c + i s)
+      wf[k + 2 * ni] = cdf_pack(dfl{-c.h, -c.l}, dfl{-sv.h, -sv.l});
+      wf[k + 3 * ni] = cdf_pack(sv, dfl{-c.h, -c.l});
+    }
+    float4 h1;                                    // e^{+i pi / n}
+    {
+      double sn, cs;
+      sincospi(1.0 / (double)n, &sn, &cs);
+      h1 = cdf_pack(df_from_d(cs), df_from_d(sn));
+    }
+    __syncthreads();
+    auto term = [&](int m) {                      // G_m e^{i m phi_0}
+      const double2 gm = G[(size_t)m * nrings + r];
+      float4 ph = wf[(m >> 1) % n];
+      if (m & 1) ph = cdf_mul(ph, h1);
+      return cdf_mul(ph, cdf_pack(df_from_d(gm.x), df_from_d(gm.y)));
+    };
+    for (int k = threadIdx.x; k <= half; k += blockDim.x) {
+      float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int m = k; m <= lmax; m += n) h = cdf_add(h, term(m));          // m = k mod n
+      for (int m = (n - k) % n; m <= lmax; m += n)                         // -m = k mod n
+        if (m != 0) h = cdf_add(h, cdf_conj(term(m)));
+      hf[k] = h;
     }
     __syncthreads();
     for (int o = threadIdx.x; o < 4 * nq; o += blockDim.x) {
