@@ -347,8 +347,8 @@ ufc_status ufc_kappa_stats_noalloc(ufc_ctx *ctx, const int32_t *counts_dev,
  *   dL/dtheta = sum_b dA_b/dtheta G_b - dC/dtheta H,
  *   G_b = sum_p gbar_p n_bp,  H = sum_p gbar_p,  gbar = dL/dkappa.
  * g_kappa_dev (FP32 [npix], 16-byte aligned) may be NULL.  counts_dev must
- * be 16-byte aligned; above 96 shells the counts are read once per window
- * of 96 shells.  dA [5][nshell], dC [5] come from ufc_kappa_coeffs (or
+ * be 16-byte aligned; above 72 shells the counts are read once per window
+ * of 72 shells (60 shells or fewer take one window).  dA [5][nshell], dC [5] come from ufc_kappa_coeffs (or
  * ufc_delta_coeffs).  grad_theta [5] (host) receives
  * dL/dtheta; G [nshell] and H (host) may be NULL.  The per-shell sums are
  * exact 128-bit fixed-point sums of the map quantised to 44 bits relative to

@@ -285,7 +285,8 @@ k_kappa_finish(const double* __restrict__ part, float ch, float cl, int npix,
 }
 
 // --------------------------------------------------------- adjoint -----
-// One pass (k_adj_main) over 4096-pixel tiles, one block per SM.  Phase 1:
+// One pass (k_adj_main) over tiles of 4 pixels per thread (2560 or 3072
+// pixels, the block sizes below), one block per SM.  Phase 1:
 // e_p = sum_b A_b n_bp - C unrounded (double-float, the shells in order, as
 // the forward pass), e_p^2, the power sums P1..P3 = sum_p e_p^k and
 // Q = sum_p g_p, and the tile's maxima of |e|, e^2, |g|.  Each quantity is
@@ -295,13 +296,14 @@ k_kappa_finish(const double* __restrict__ part, float ch, float cl, int npix,
 // flushed at the old scale into the block's 128-bit fixed-point rows, which
 // take every flush at its own scale exactly.  Every pixel is therefore
 // quantised at least as finely as a single scale from the global maxima
-// would.  Phase 2: warp w owns shells w, w + 32, w + 64 and each lane a
+// would.  Phase 2: warp w of NW owns shells w, w + NW, w + 2 NW (of the
+// launch's window) and each lane a
 // column of the tile's pixels, accumulating q n in 64-bit integers (the
 // tile's counts read a second time, mostly from L2).  A bound on the
 // accumulated magnitudes (pixels per lane x tile maximum count x 2^22 per
-// tile) triggers a flush before any 64-bit sum could overflow.  More than 96
-// shells take one launch per window of 96 shells (phase 1 reads all shells
-// in each).  With EXT, e comes from summed subvolume partials E_p (e =
+// tile) triggers a flush before any 64-bit sum could overflow.  A launch
+// covers 3 NW shells (60 at 640 threads, 72 at 768); more shells take one
+// launch per window (phase 1 reads all shells in each).  With EXT, e comes from summed subvolume partials E_p (e =
 // E_p - C, the same double-float subtraction as k_kappa_finish) and the
 // counts, those of one subvolume, enter phase 1 only through their maximum:
 // the per-shell sums are then that subvolume's share, and they add over
