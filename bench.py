@@ -424,8 +424,9 @@ def main():
                     help="force the binning output path (default: the library's choice)")
     ap.add_argument("--split", default="realisation", choices=["realisation", "subvolume"],
                     help="multi-GPU decomposition: each rank its own realisation (weak "
-                         "scaling), or each rank a shard of every box whose count maps are "
-                         "summed by one NCCL all-reduce inside the step (Sec. 2.4; strong)")
+                         "scaling), or each rank a shard of every box, the FP64 partial kappa "
+                         "sums and the adjoint's per-shell sums all-reduced inside the step "
+                         "(Sec. 2.4; strong)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -622,8 +623,26 @@ def main():
     # end to end: particles from pinned host memory through the C ABI each
     # step (ufc_bin_host copies them in chunks, overlapped with the binning),
     # moments and PDF back to pinned host memory
+    host = None
     if not args.no_e2e:
-        host = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True) for p in parts]
+        # pinned copies of this rank's particles; every rank must have them,
+        # or no rank runs the leg (its timing takes a collective)
+        err = None
+        try:
+            host = [torch.empty(p.shape, dtype=torch.float32, pin_memory=True) for p in parts]
+        except RuntimeError as e:
+            host, err = None, str(e).splitlines()[0][:160] if str(e) else type(e).__name__
+        ok = torch.tensor([0 if host is None else 1], device=dev)
+        if dist:
+            dist.all_reduce(ok, op=dist.ReduceOp.MIN)
+        if not int(ok.item()):
+            host = None
+            gb = sum(p.numel() * 4 for p in parts) / 1e9
+            line["e2e"] = {"value": None, "unit": UNIT,
+                           "unavailable": f"pinned host buffers of {gb:.1f} GB per rank could "
+                                          "not be allocated" + (f": {err}" if err else
+                                                                " on another rank")}
+    if host is not None:
         for h_, p_ in zip(host, parts):
             h_.copy_(p_)
         out_h = torch.empty(10 + w.pdf_bins + 3, dtype=torch.float64, pin_memory=True)
