@@ -72,3 +72,17 @@ def test_checked_build_runs_clean():
     r = subprocess.run([sys.executable, "-c", _SCRIPT, ROOT], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0 and "CHECKED-OK" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+
+
+def test_binning_suites_on_checked_build():
+    """The binning, key and snapshot test files run on the checked library;
+    every test ends with a synchronize that would report a failed index test
+    (tests/conftest.py)."""
+    from paper_1801_05745_gb300 import build
+    build.build(checked=True)
+    env = dict(os.environ, UFC_CHECKED="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "gpu",
+                        "-p", "no:cacheprovider", "tests/test_gpu_bin.py",
+                        "tests/test_gpu_keys.py", "tests/test_gpu_snapshot.py"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
