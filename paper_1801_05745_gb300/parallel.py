@@ -65,7 +65,7 @@ def merge_states(ctx, states, d: int):
     return merged
 
 
-def _active(group) -> bool:
+def _active() -> bool:
     import torch.distributed as dist
     return dist.is_available() and dist.is_initialized()
 
@@ -85,7 +85,7 @@ def allreduce_adjoint_sums(sums, nshell: int, group=None, device=None):
     sums = np.ascontiguousarray(sums, dtype=np.float64)
     if sums.shape != (4 * nshell + 4,):
         raise ValueError("adjoint sums need 4 nshell + 4 entries")
-    if not _active(group):
+    if not _active():
         return sums.copy()
     import torch.distributed as dist
     t = torch.from_numpy(sums.copy())
@@ -116,7 +116,7 @@ def subvolume_kappa(ctx, counts, A, C, pdf_lo, pdf_hi, nbins, dA=None, dC=None, 
     Returns (kappa, moments, pdf) or (kappa, moments, pdf, grad, G, H)."""
     from . import api
     partial = ctx.kappa_partial(counts, A, out=partial)
-    if _active(group):
+    if _active():
         import torch.distributed as dist
         dist.all_reduce(partial, op=dist.ReduceOp.SUM, group=group)
     if dA is None:
