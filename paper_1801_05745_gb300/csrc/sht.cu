@@ -31,7 +31,9 @@ namespace ufc {
 
 constexpr int kShtMaxNside = 1024;     // shared-memory FFT of the 4 nside-pixel rings
 constexpr int kLegThreads = 256;       // threads per k_legendre block
-constexpr int kLegPPT = 4;             // ring pairs per thread
+constexpr int kLegPPT = 4;             // ring pairs per thread (analysis)
+constexpr int kSynPPT = 2;             // ring pairs per thread (synthesis: 64 registers,
+                                       // 32 warps per SM; 4 pairs take 1.4% longer)
 constexpr int kLegChunkL = 32;         // l values per reduction round
 static_assert(kLegChunkL == 32, "the block reduction gives each degree of a round one lane");
 
@@ -596,23 +598,23 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
   __shared__ dfl ra[kLegChunkL], rb[kLegChunkL];
   __shared__ dfl as[kLegChunkL][2];
   const int chunk = blockIdx.x;
-  int pp[kLegPPT];
-  bool have[kLegPPT];
-  dfl z[kLegPPT];
+  int pp[kSynPPT];
+  bool have[kSynPPT];
+  dfl z[kSynPPT];
 #pragma unroll
-  for (int q = 0; q < kLegPPT; ++q) {
-    pp[q] = chunk * kLegThreads * kLegPPT + q * kLegThreads + threadIdx.x;
+  for (int q = 0; q < kSynPPT; ++q) {
+    pp[q] = chunk * kLegThreads * kSynPPT + q * kLegThreads + threadIdx.x;
     have[q] = pp[q] < npairs;
     z[q] = df_from_d(have[q] ? ring_geom(N, pp[q]).z : 0.0);
   }
   for (int pass = 0; pass < 2; ++pass) {
     const int m = pass == 0 ? (int)blockIdx.y : lmax - (int)blockIdx.y;
     if (pass == 1 && m <= (int)blockIdx.y) break;
-    dfl v1[kLegPPT], v2[kLegPPT];
-    int e[kLegPPT];
-    dfl ge[kLegPPT][2], go[kLegPPT][2];   // sums over l + m even / odd, in units of 2^e
+    dfl v1[kSynPPT], v2[kSynPPT];
+    int e[kSynPPT];
+    dfl ge[kSynPPT][2], go[kSynPPT][2];   // sums over l + m even / odd, in units of 2^e
 #pragma unroll
-    for (int q = 0; q < kLegPPT; ++q) {
+    for (int q = 0; q < kSynPPT; ++q) {
       double mant = 0.0;
       int ee = 0;
       if (have[q]) mant = frexp(mu[(size_t)m * npairs + pp[q]], &ee);   // [0.5, 1) 2^ee
@@ -642,7 +644,7 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
         const dfl ax = as[t][0], ay = as[t][1];
         const bool odd = (l + m) & 1;
 #pragma unroll
-        for (int q = 0; q < kLegPPT; ++q) {
+        for (int q = 0; q < kSynPPT; ++q) {
           dfl v;
           if (l == m) {
             v = v1[q];
@@ -665,7 +667,7 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
         // 2^-30 below the current scale may lose bits: they are negligible)
         if ((t & 3) == 3 || t == cnt - 1) {
 #pragma unroll
-          for (int q = 0; q < kLegPPT; ++q) {
+          for (int q = 0; q < kSynPPT; ++q) {
             while (fabsf(v1[q].h) > 0x1p30f || fabsf(v2[q].h) > 0x1p30f) {
               v1[q] = df_scale(v1[q], 0x1p-30f);
               v2[q] = df_scale(v2[q], 0x1p-30f);
@@ -680,7 +682,7 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
       }
     }
 #pragma unroll
-    for (int q = 0; q < kLegPPT; ++q) {
+    for (int q = 0; q < kSynPPT; ++q) {
       if (!have[q]) continue;
       const double sc = e[q] > -1070 ? ldexp(1.0, e[q]) : 0.0;
       const double er = df_to_d(ge[q][0]), ei = df_to_d(ge[q][1]);
@@ -961,7 +963,7 @@ ufc_status run_alm2map(ufc_ctx* c, const double* alm, int nside, int lmax, float
   if ((reinterpret_cast<uintptr_t>(alm) & 15))
     return set_err(c, UFC_ERR_ARG, "alm_dev must be 16-byte aligned");
   const int nrings = 4 * nside - 1, npairs = 2 * nside;
-  const int nchunk = (npairs + kLegThreads * kLegPPT - 1) / (kLegThreads * kLegPPT);
+  const int nchunk = (npairs + kLegThreads * kSynPPT - 1) / (kLegThreads * kSynPPT);
   const size_t gbytes = (size_t)(lmax + 1) * nrings * sizeof(double2);
   const size_t lbytes = (size_t)(lmax + 1) * npairs * (sizeof(double) + sizeof(int32_t));
   const int64_t nalm = (int64_t)(lmax + 1) * (lmax + 2) / 2;
