@@ -1384,6 +1384,14 @@ static float f_up(double v) {
 // the fraction test of the fast stage takes.
 static void make_bands(int N, float smax, Bands& bd) {
   const double u = std::ldexp(1.0, -24);
+  bd.fN = (float)N;
+  bd.n75 = 0.75f * (float)N;
+  bd.c0 = N == 1 ? 0.5f : 0.0f;
+  bd.nhalf = N >> 1;
+  bd.ring0 = 2 * N * (N - 1);
+  bd.four_n = 4 * N;
+  bd.eight_n = 8 * N;
+  bd.npix = 12 * N * N;
   const double two3 = 2.0 / 3.0;
   bd.z_eq = f_down(two3 / (1.0 + 21.0 * u) * (1.0 - 1e-12));
   bd.z_cap = f_up(two3 / (1.0 - 21.0 * u) * (1.0 + 1e-12));

@@ -57,6 +57,16 @@ struct Bands {
   float axy_min;    // max(|dx|,|dy|) below this: undecided
   float z_eq2;      // dz^2 <= z_eq2 r2  => equatorial belt for certain
   float z_cap2;     // dz^2 >  z_cap2 r2 => polar cap for certain
+  // constants of the pixel arithmetic for the map's N, read as kernel
+  // parameters instead of being recomputed per group
+  float fN;         // N
+  float n75;        // 3N/4 (exact)
+  float c0;         // 1/2 when N = 1, else 0
+  int32_t nhalf;    // N >> 1
+  int32_t ring0;    // 2 N (N - 1), the first pixel of the belt
+  int32_t four_n;   // 4 N
+  int32_t eight_n;  // 8 N
+  int32_t npix;     // 12 N^2
 };
 
 struct GeomAll {

@@ -194,9 +194,14 @@ __device__ __forceinline__ Azim azimuth_fast(float dx, float dy, const Bands& bd
   Azim r;
   r.a = atanq_poly(q);                         // quarter turns, [0, 1/2]
   const bool xp = dx >= 0.0f, yp = dy >= 0.0f;
-  // (base, sgn): Q0 (0,+)|(1,-)  Q1 (2,-)|(1,+)  Q2 (2,+)|(3,-)  Q3 (4,-)|(3,+)
-  r.base = xp ? (yp ? (sw ? 1 : 0) : (sw ? 3 : 4)) : (yp ? (sw ? 1 : 2) : (sw ? 3 : 2));
-  r.sgn_pos = (xp == yp) != sw;
+  // (base, sgn): Q0 (0,+)|(1,-)  Q1 (2,-)|(1,+)  Q2 (2,+)|(3,-)  Q3 (4,-)|(3,+),
+  // one nibble (base | sgn << 3) per (xp, yp, sw) in a 32-bit table:
+  // base = xp ? (yp ? (sw ? 1 : 0) : (sw ? 3 : 4)) : (yp ? (sw ? 1 : 2) : (sw ? 3 : 2)),
+  // sgn = (xp == yp) != sw
+  const uint32_t idx = (xp ? 4u : 0u) | (yp ? 2u : 0u) | (sw ? 1u : 0u);
+  const uint32_t nib = (0x18B4923Au >> (4u * idx)) & 15u;
+  r.base = int32_t(nib & 7u);
+  r.sgn_pos = nib >= 8u;
   r.sa = r.sgn_pos ? r.a : -r.a;
   return r;
 }
@@ -206,18 +211,17 @@ __device__ __forceinline__ int32_t pixel_fast_eq(int32_t N, const Bands& bd, flo
                                                  float z) {
   bool open = false;
   const Azim az = azimuth_fast(dx, dy, bd, open);
-  // floor(N(1/2 + t) -+ 0.75 N z) = I0 + floor(N sa (+1/2 if N = 1) -+ 0.75 N z)
-  const float fN = i2f_fast(N);
-  const float c = fmaf(fN, az.sa, N == 1 ? 0.5f : 0.0f);
-  const int32_t I0 = (N == 1) ? az.base : (N >> 1) * (2 * az.base + 1);
-  const float n75 = 0.75f * fN;
-  const int32_t jp = I0 + floor_certain(fmaf(-n75, z, c), bd.eq, open);
-  const int32_t jm = I0 + floor_certain(fmaf(n75, z, c), bd.eq, open);
+  // floor(N(1/2 + t) -+ 0.75 N z) = I0 + floor(N sa (+1/2 if N = 1) -+ 0.75 N z),
+  // I0 = N base + N/2 (N even; base when N = 1)
+  const float c = fmaf(bd.fN, az.sa, bd.c0);
+  const int32_t I0 = N * az.base + bd.nhalf;
+  const int32_t jp = I0 + floor_certain(fmaf(-bd.n75, z, c), bd.eq, open);
+  const int32_t jm = I0 + floor_certain(fmaf(bd.n75, z, c), bd.eq, open);
   const int32_t ir = N + 1 + jp - jm;
   open |= uint32_t(ir - 1) > uint32_t(2 * N);
   const int32_t ks = 1 - (ir & 1);
-  const int32_t ip = ((jp + jm - N + ks + 1 + 8 * N) >> 1) & (4 * N - 1);
-  return open ? kKeyUndecided : 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
+  const int32_t ip = ((jp + jm - N + ks + 1 + bd.eight_n) >> 1) & (bd.four_n - 1);
+  return open ? kKeyUndecided : bd.ring0 + (ir - 1) * bd.four_n + ip;
 }
 
 // Polar-cap pixel (|z| certainly > 2/3), or kKeyUndecided.
@@ -229,7 +233,7 @@ __device__ __forceinline__ int32_t pixel_fast_cap(int32_t N, const Bands& bd, fl
   const float r = r2 * rinv;
   const float omz = __fdividef(s2, r * (r + fabsf(dz)));
   const float o3 = 3.0f * omz;
-  float tmp = i2f_fast(N) * (o3 * rsqrtf(o3));
+  float tmp = bd.fN * (o3 * rsqrtf(o3));
   if (!(o3 > 0.0f)) { tmp = 0.0f; open = true; }
   const float tp = az.sgn_pos ? az.a : 1.0f - az.a;
   const int32_t jp = floor_certain(tp * tmp, bd.cap, open);
@@ -242,7 +246,7 @@ __device__ __forceinline__ int32_t pixel_fast_cap(int32_t N, const Bands& bd, fl
   int32_t ip = az.base * ir + fl;              // in [-ir, 4.5 ir]
   const int32_t m = 4 * ir;
   ip = ip < 0 ? ip + m : (ip >= m ? ip - m : ip);
-  const int32_t pix = (z > 0.0f) ? 2 * ir * (ir - 1) + ip : 12 * N * N - 2 * ir * (ir + 1) + ip;
+  const int32_t pix = (z > 0.0f) ? 2 * ir * (ir - 1) + ip : bd.npix - 2 * ir * (ir + 1) + ip;
   return open ? kKeyUndecided : pix;
 }
 
