@@ -1380,8 +1380,9 @@ static float f_up(double v) {
 //  cap : |v - V| <= 29u N        -> band 58u N + 2u
 //  ip  : |w3 - W3| <= 7.5u ir    -> band 15u ir (+2u)
 // plus guards that keep the absolute input error (2u^2 smax) negligible.
-// The eq and cap fields hold 1/2 - band - 2^-23 (rounded down), the form
-// the fraction test of the fast stage takes.
+// The eq and cap fields hold 1/2 - band - 2^-23 (rounded down); eq_d and
+// cap_d are 1/2 minus them (at least band + 2^-23), the least distance from
+// the nearest integer that the fast stage's floor test accepts.
 static void make_bands(int N, float smax, Bands& bd) {
   const double u = std::ldexp(1.0, -24);
   bd.fN = (float)N;
@@ -1397,6 +1398,8 @@ static void make_bands(int N, float smax, Bands& bd) {
   bd.z_cap = f_up(two3 / (1.0 - 21.0 * u) * (1.0 + 1e-12));
   bd.eq = f_down(0.5 - f_up(28.0 * u * N + 2.0 * u) - std::ldexp(1.0, -23));
   bd.cap = f_down(0.5 - f_up(58.0 * u * N + 2.0 * u) - std::ldexp(1.0, -23));
+  bd.eq_d = 0.5f - bd.eq;     // exact (Sterbenz)
+  bd.cap_d = 0.5f - bd.cap;
   bd.ip_per_ir = f_up(17.0 * u);
   double g = std::ldexp(1.0, 11) * u * std::max<double>(smax, 1.0);
   bd.r2_min = f_up(g * g);

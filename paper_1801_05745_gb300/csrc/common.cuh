@@ -52,6 +52,9 @@ struct Bands {
   float z_cap;      // |z| >  z_cap => polar cap for certain
   float eq;         // 1/2 - (absolute band of the equatorial edge coordinates) - 2^-23
   float cap;        // 1/2 - (absolute band of the cap edge coordinates) - 2^-23
+  float eq_d;       // 1/2 - eq: least distance of a certain equatorial edge coordinate
+                    // from the nearest integer
+  float cap_d;      // 1/2 - cap, the same for the cap edge coordinates
   float ip_per_ir;  // band of the in-ring coordinate t*ir, per unit of ir
   float r2_min;     // below this squared radius: undecided
   float axy_min;    // max(|dx|,|dy|) below this: undecided

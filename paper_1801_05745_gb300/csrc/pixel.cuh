@@ -150,18 +150,18 @@ __device__ __forceinline__ float i2f_fast(int32_t k) {
 }
 
 // Floor of w when w is farther than a band b from every integer, else marks
-// the decision open; hmb <= 1/2 - b - 2^-23.  The fraction r = w - floor(w)
-// is exact for |w| < 2^22 (every caller's w is below N + 1 <= 8193 in
-// magnitude, or NaN, which opens the decision), and r - 1/2 rounds by at
-// most 2^-26, so |r - 1/2| <= hmb puts r strictly inside (b, 1 - b).
-__device__ __forceinline__ int32_t floor_certain(float w, float hmb, bool& open) {
-  float f;
-  const int32_t k = floor_fast(w, f);
-  const float rem = __fsub_rn(w, f);
-  open |= !(fabsf(__fsub_rn(rem, 0.5f)) <= hmb);
-  return k;
+// the decision open; dmin >= b + 2^-23.  r = w + 1.5 2^23 rounds w to the
+// nearest integer n (every caller's |w| is below N + 1 <= 8193, far below
+// 2^22), d = w - n is exact (both are multiples of ulp(w) and |d| <= 1/2),
+// floor(w) = n - [d < 0], and the floor is certain when the distance |d| to
+// the nearest integer is at least dmin.  NaN opens the decision.
+__device__ __forceinline__ int32_t floor_certain_d(float w, float dmin, bool& open) {
+  const float r = __fadd_rn(w, kMagic);
+  const float n = __fsub_rn(r, kMagic);
+  const float d = __fsub_rn(w, n);
+  open |= !(fabsf(d) >= dmin);
+  return (__float_as_int(r) - kMagicBits) - (d < 0.0f ? 1 : 0);
 }
-constexpr float kHalfMargin = 0.5f - 0x1p-23f;   // 1/2 - 2^-23, exact
 
 // atan(q) * 2/pi for q in [0, 1] as q * P(q^2), P of degree 8 with
 // coefficients from a weighted least-squares fit of this library; Horner in
@@ -215,8 +215,8 @@ __device__ __forceinline__ int32_t pixel_fast_eq(int32_t N, const Bands& bd, flo
   // I0 = N base + N/2 (N even; base when N = 1)
   const float c = fmaf(bd.fN, az.sa, bd.c0);
   const int32_t I0 = N * az.base + bd.nhalf;
-  const int32_t jp = I0 + floor_certain(fmaf(-bd.n75, z, c), bd.eq, open);
-  const int32_t jm = I0 + floor_certain(fmaf(bd.n75, z, c), bd.eq, open);
+  const int32_t jp = I0 + floor_certain_d(fmaf(-bd.n75, z, c), bd.eq_d, open);
+  const int32_t jm = I0 + floor_certain_d(fmaf(bd.n75, z, c), bd.eq_d, open);
   const int32_t ir = N + 1 + jp - jm;
   open |= uint32_t(ir - 1) > uint32_t(2 * N);
   const int32_t ks = 1 - (ir & 1);
@@ -236,13 +236,13 @@ __device__ __forceinline__ int32_t pixel_fast_cap(int32_t N, const Bands& bd, fl
   float tmp = bd.fN * (o3 * rsqrtf(o3));
   if (!(o3 > 0.0f)) { tmp = 0.0f; open = true; }
   const float tp = az.sgn_pos ? az.a : 1.0f - az.a;
-  const int32_t jp = floor_certain(tp * tmp, bd.cap, open);
-  const int32_t jm = floor_certain((1.0f - tp) * tmp, bd.cap, open);
+  const int32_t jp = floor_certain_d(tp * tmp, bd.cap_d, open);
+  const int32_t jm = floor_certain_d((1.0f - tp) * tmp, bd.cap_d, open);
   int32_t ir = jp + jm + 1;
   open |= ir > N;
   ir = ir > N ? N : ir;
   const float fir = i2f_fast(ir);
-  const int32_t fl = floor_certain(az.sa * fir, fmaf(-bd.ip_per_ir, fir, kHalfMargin), open);
+  const int32_t fl = floor_certain_d(az.sa * fir, fmaf(bd.ip_per_ir, fir, 0x1p-23f), open);
   int32_t ip = az.base * ir + fl;              // in [-ir, 4.5 ir]
   const int32_t m = 4 * ir;
   ip = ip < 0 ? ip + m : (ip >= m ? ip - m : ip);
