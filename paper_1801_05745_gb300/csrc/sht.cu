@@ -471,6 +471,9 @@ k_legendre(const double2* __restrict__ F, const double* __restrict__ mu,
         rb[t] = dfl{cv.z, cv.w};
       }
       __syncthreads();
+      // two degrees per iteration: (l + m) even, then odd (l0 - m is a
+      // multiple of 32), so each half selects its even/odd terms statically
+#pragma unroll 2
       for (int t = 0; t < cnt; ++t) {
         const int l = l0 + t;
         const dfl at = ra[t], bt = rb[t];
@@ -638,6 +641,9 @@ k_legendre_synth(const double2* __restrict__ alm, const double* __restrict__ mu,
         rb[t] = dfl{cv.z, cv.w};
       }
       __syncthreads();
+      // two degrees per iteration: (l + m) even, then odd (l0 - m is a
+      // multiple of 32), so each half selects its even/odd terms statically
+#pragma unroll 2
       for (int t = 0; t < cnt; ++t) {
         const int l = l0 + t;
         const dfl at = ra[t], bt = rb[t];
