@@ -644,11 +644,15 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           const uint32_t e = fs.lut[bin];
           int a = int(e & 0x7FFFu) - 1;
           bool band = false;
-          if ((e & kLutScan) && fin) {           // rare: scan the edges (finite r2 ends at +inf)
-            for (;;) {
-              if (r2 < fs.lo2[a + 1]) break;
-              if (r2 < fs.hi2[a + 1]) { band = true; break; }
-              ++a;
+          // rare: scan the edges (finite r2 ends at +inf); a warp-uniform
+          // test first, so that the common case is one vote and a branch
+          if (__any_sync(0xFFFFFFFFu, (e & kLutScan) && fin)) {
+            if ((e & kLutScan) && fin) {
+              for (;;) {
+                if (r2 < fs.lo2[a + 1]) break;
+                if (r2 < fs.hi2[a + 1]) { band = true; break; }
+                ++a;
+              }
             }
           }
           const bool inshell = uint32_t(a - lo) < uint32_t(hi - lo);
@@ -658,9 +662,11 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           const bool dec = have && fin && !near && !band && inshell;
           const bool c2 = dec && eqz;
           const bool c3 = dec && capz;
-          const bool c1 = have && fin && (near || band || (inshell && !eqz && !capz));
-          if (have && !fin && img == 0)          // NaN or overflow: inspect the coordinates
-            if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) ++fc.n_invalid;
+          // NaN or overflowing r2 (rare) goes to the queue as well, once per
+          // particle (its first image): the FP64 stage returns the invalid
+          // key for non-finite coordinates and decides a finite overflow
+          const bool c1 = have && (fin ? (near || band || (inshell && !eqz && !capz))
+                                       : (!IMAGES || img == 0));
           const uint32_t meta = uint32_t(a & 255) | (uint32_t(j) << 8) | kqtag;
           const float4 ent = make_float4(dx, dy, dz, __uint_as_float(meta));
           const unsigned meq = __ballot_sync(0xFFFFFFFFu, c2);
@@ -670,7 +676,10 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           ne += __popc(meq);
           nc += __popc(mcap);
           // undecided images wait in queue 1; outside/invalid are final
-          if (!queue_push(fc.qc, c1, qbase + uint64_t(j), qs.q1, qs.cap1, &qs.cnt->q1)) {
+          bool pushed = true;                    // (a warp-uniform test first, as above)
+          if (__any_sync(0xFFFFFFFFu, c1))
+            pushed = queue_push(fc.qc, c1, qbase + uint64_t(j), qs.q1, qs.cap1, &qs.cnt->q1);
+          if (!pushed) {
             const int32_t kx = key_exact_slow(st, lo, hi, N, npix, x, y, zc, bg.sh64[0][ii],
                                               bg.sh64[1][jj], bg.sh64[2][kk]);
             if (kx == kKeyInvalid) ++fc.n_invalid;
@@ -725,14 +734,16 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           };
           const int32_t key = b * npix + pix;
           bool queued = true;
-          if constexpr (IMAGES) {
-            queued = queue_push_f(
-                fc.qc, have && !ok, [&]() { return qpack(box_id, img, p_off + local_index()); },
-                qs.q1, qs.cap1, &qs.cnt->q1);
-          } else {                               // queue full: left to the exact pass
-            queue_push_mark(
-                fc.qc, have && !ok, [&]() { return qpack(box_id, 0, p_off + local_index()); },
-                qs.q1, qs.cap1, &qs.cnt->q1, qs.ovf, qs.ovf_base, &qs.cnt->ovf);
+          if (__any_sync(0xFFFFFFFFu, have && !ok)) {   // rare: a warp-uniform test first
+            if constexpr (IMAGES) {
+              queued = queue_push_f(
+                  fc.qc, have && !ok, [&]() { return qpack(box_id, img, p_off + local_index()); },
+                  qs.q1, qs.cap1, &qs.cnt->q1);
+            } else {                             // queue full: left to the exact pass
+              queue_push_mark(
+                  fc.qc, have && !ok, [&]() { return qpack(box_id, 0, p_off + local_index()); },
+                  qs.q1, qs.cap1, &qs.cnt->q1, qs.ovf, qs.ovf_base, &qs.cnt->ovf);
+            }
           }
           if (!queued) {                         // queue full: the FP64 procedure here
             const int64_t pl = local_index();

@@ -116,6 +116,7 @@ __device__ __forceinline__ int32_t key_exact(const ShellTable& st, int32_t lo,
                                              int32_t hi, int32_t N, int32_t npix,
                                              float x, float y, float zc,
                                              double shx, double shy, double shz) {
+  if (!isfinite(x) || !isfinite(y) || !isfinite(zc)) return kKeyInvalid;
   double dx = __dadd_rn(double(x), shx);
   double dy = __dadd_rn(double(y), shy);
   double dz = __dadd_rn(double(zc), shz);
