@@ -501,13 +501,17 @@ static_assert(kWAgeFlush < 4096, "chunk tags are 12-bit");
 
 constexpr int kWSmemBase = kWStages * kWChunk * 12 + kWWarps * 2 * kWList * 16;   // ring + lists
 
-__device__ __forceinline__ void hist16_inc(uint32_t* h32, uint32_t* ghist, uint32_t bucket) {
+// One increment of a 16-bit counter held in half of a 32-bit word; true when it wrapped the
+// half, which hist16_carry then settles (the low half's carry undone, 65536 added globally).
+__device__ __forceinline__ bool hist16_add(uint32_t* h32, uint32_t bucket) {
   const uint32_t shift = (bucket & 1u) << 4;
   const uint32_t old = atomicAdd(h32 + (bucket >> 1), 1u << shift);
-  if (((old >> shift) & 0xFFFFu) == 0xFFFFu) {           // this increment wrapped the half
-    if (shift == 0) atomicSub(h32 + (bucket >> 1), 1u << 16);   // undo the carry
-    atomicAdd(ghist + bucket, 65536u);
-  }
+  return ((old >> shift) & 0xFFFFu) == 0xFFFFu;
+}
+
+__device__ __forceinline__ void hist16_carry(uint32_t* h32, uint32_t* ghist, uint32_t bucket) {
+  if ((bucket & 1u) == 0u) atomicSub(h32 + (bucket >> 1), 1u << 16);
+  atomicAdd(ghist + bucket, 65536u);
 }
 
 template <int MODE, bool IMAGES>
@@ -768,16 +772,19 @@ k_fast_tma(const float* __restrict__ xyz, int64_t n, int64_t p_off, int32_t box_
           } else if (MODE == kModeDirect) {
             if (ok && UFC_IDX_OK(key, o.ncell, 2)) atomicAdd(o.counts + key, 1);
           } else {
-            uint32_t dk = 0u;
+            uint32_t dk = 0u, bucket = 0u;
+            bool wrapped = false;
             if (ok) {
               const uint32_t blk = uint32_t(pix >> 13) / 3u;       // pix / 24576
-              const uint32_t bucket = uint32_t(b - o.shell0) * uint32_t(o.nblk) + blk;
+              bucket = uint32_t(b - o.shell0) * uint32_t(o.nblk) + blk;
               dk = (bucket << kOffBits) | (uint32_t(pix) - blk * uint32_t(kBlockPix));
               if (UFC_IDX_OK(bucket, o.nbuckets, 1)) {
-                if (o.smem_hist) hist16_inc(h32, ghist, bucket);
+                if (o.smem_hist) wrapped = hist16_add(h32, bucket);
                 else atomicAdd(ghist + bucket, 1u);
               }
             }
+            // rare (one increment in 65536 per counter): a warp-uniform test first
+            if (__any_sync(0xFFFFFFFFu, wrapped) && wrapped) hist16_carry(h32, ghist, bucket);
             dense_append(fc.wc, ok, dk, o);
           }
           fc.n_keyed += ok;

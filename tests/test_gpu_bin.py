@@ -83,3 +83,34 @@ def test_empty_and_invalid_inputs(orc):
         ctx.bin([to_dev(x)], [ba], np.array([100.0, 90.0, 300.0]), 16)
     with pytest.raises(UfcError):
         ctx.bin([to_dev(x)], [ba], chi, 12)
+
+
+def test_crowded_buckets_wrap_shared_counters(orc):
+    """Every particle in two neighbouring pixel blocks of one shell, about
+    2 x 65536 per block and CTA: the dense path's shared-memory bucket
+    counters hold 16 bits, two to a 32-bit word, so each CTA's counters of
+    both halves wrap and carry into the global histogram; the count map
+    stays exact (Eq. 5)."""
+    api, ctx = api_ctx()
+    nside, L = 512, 2000.0
+    chi = orc.chi_edges(0.3, 0.7, 1, np.linspace(0.1, 0.33, 11))
+    r = 0.5 * (chi[4] + chi[5])
+    blk_pix = 24576                         # pixels of one bucket's block
+    b0 = 64                                 # an even block: the low halves of a counter word
+    pix = np.array([b0 * blk_pix + 100, b0 * blk_pix + 5000,
+                    (b0 + 1) * blk_pix + 300, (b0 + 1) * blk_pix + 7000])
+    pts = np.array([1000.0 + r * orc.pix2vec(nside, int(p)) for p in pix], np.float32)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = 4 * 65536 * sms                      # ~2 x 65536 per block and CTA (one CTA per SM)
+    xyz = np.tile(pts, (n // len(pts), 1))
+    n = len(xyz)
+    ba, bo = both_boxes(api, orc, L, [L / 2] * 3, n, 0, 10)
+    k = orc.keys(pts, bo, chi, nside)
+    npix = 12 * nside * nside
+    assert np.array_equal(k, 4 * npix + pix)        # the intended shell and pixels
+    ref = np.zeros((10, npix), np.int32)
+    np.add.at(ref.reshape(-1), k, n // len(pts))
+    got = ctx.bin([to_dev(xyz)], [ba], chi, nside, path="dense")
+    info = ctx.bin_info()
+    assert np.array_equal(got.cpu().numpy(), ref)
+    assert info["keyed"] == n
