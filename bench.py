@@ -38,7 +38,7 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # capture of k_fast_tma on two boxes of 512^3 particles at Nside 512 (two
 # launches of 134.2M particles: 1.868 and 1.838 GB); scaled to a launch by
 # its particle count.  Retake it whenever k_fast_tma changes.
-FAST_TRAFFIC_PER_PARTICLE = (1.610940e9 + 256.870144e6 + 1.610980e9 + 227.203840e6) / 2 / 134217728
+FAST_TRAFFIC_PER_PARTICLE = (1.610987e9 + 257.307648e6 + 1.611105e9 + 227.374336e6) / 2 / 134217728
 # DRAM bytes of every binning kernel above the algorithmic ones (particles
 # read, count maps written), per keyed particle: ncu dram__bytes_read+write
 # of one binning call of two boxes of 512^3 particles at Nside 1024, 60
