@@ -319,20 +319,26 @@ __device__ __forceinline__ df df_mulf(df x, float y) {
   p.l = __fmaf_rn(x.l, y, p.l);
   return quick_two_sum(p.h, p.l);
 }
+// Quotient and root estimates need only be within a few ulp: each is
+// followed by a residual computed in double-float and a correction, so the
+// result's error is set by the double-float residuals (about 2^-44
+// relative) and not by the estimate.  The fast approximate division and
+// reciprocal square root (at most 2 ulp at the magnitudes met here: no
+// divisor near 2^126) therefore replace the correctly rounded ones.
 __device__ __forceinline__ df df_div(df x, df y) {
-  float q1 = __fdiv_rn(x.h, y.h);
+  float q1 = __fdividef(x.h, y.h);
   df r = df_sub(x, df_mulf(y, q1));
-  float q2 = __fdiv_rn(r.h, y.h);
+  float q2 = __fdividef(r.h, y.h);
   r = df_sub(r, df_mulf(y, q2));
-  float q3 = __fdiv_rn(r.h, y.h);
+  float q3 = __fdividef(r.h, y.h);
   df q = quick_two_sum(q1, q2);
   return df_add(q, {q3, 0.0f});
 }
 __device__ __forceinline__ df df_sqrt(df x) {
   if (!(x.h > 0.0f)) return {0.0f, 0.0f};
-  float s = __fsqrt_rn(x.h);
+  float s = __fmul_rn(x.h, rsqrtf(x.h));     // NaN for +inf: the callers' r > 0 test fails
   df e = df_sub(x, two_prod(s, s));
-  float c = __fdiv_rn(e.h, __fmul_rn(2.0f, s));
+  float c = __fdividef(e.h, __fmul_rn(2.0f, s));
   return df_add({s, 0.0f}, {c, 0.0f});
 }
 // Double-float constants folded at compile time (no conversion at run time).
