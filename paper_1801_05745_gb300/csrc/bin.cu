@@ -861,10 +861,12 @@ template <int MODE>
 __global__ void __launch_bounds__(256)
 k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues qs) {
   __shared__ float chih_s[kMaxShells + 1], chil_s[kMaxShells + 1];
+  __shared__ float2 atab_s[kAtanTab];
   for (int i = threadIdx.x; i <= st.nshell; i += blockDim.x) {
     chih_s[i] = st.chih[i];
     chil_s[i] = st.chil[i];
   }
+  fill_atan_table(atab_s);
   __syncthreads();
   const unsigned long long total = qs.cnt->q1;
   const int64_t m = (int64_t)min((unsigned long long)qs.cap1, total);
@@ -892,7 +894,7 @@ k_refine(BoxesParam bp, ShellTable st, int32_t N, int32_t npix, KeyOut o, Queues
       }
       const float* xp = bp.xyz[b] + 3 * p;
       float x = xp[0], y = xp[1], zc = xp[2];
-      key = key_refine(chih_s, chil_s, g.shell_lo, g.shell_hi, N, npix, x, y, zc, g.shf[0][ii],
+      key = key_refine(chih_s, chil_s, atab_s, g.shell_lo, g.shell_hi, N, npix, x, y, zc, g.shf[0][ii],
                        g.shf[1][jj], g.shf[2][kk], g.shlo[0][ii], g.shlo[1][jj],
                        g.shlo[2][kk]);
       ++n_ref;

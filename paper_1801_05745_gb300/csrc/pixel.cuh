@@ -349,28 +349,39 @@ __host__ __device__ constexpr dfc make_dfc(double v) {
 __device__ __forceinline__ df to_df(dfc c) { return {c.h, c.l}; }
 
 
-// atan(u) in quarter turns for u in [0,1] by the same two half-angle steps
-// and a 9-term Maclaurin sum (w < tan(pi/16): truncation below 2^-40).
-__device__ __forceinline__ df atanq_df(df u) {
+// Table of the refine stage's arctangent: atan(k/32) in quarter turns for
+// k = 0..32, double-float pairs of the FP64 procedure's values (within a few
+// units of 2^-53 of the exact ones).  Every block fills its shared-memory
+// copy once (then a barrier before the first key_refine).
+constexpr int kAtanTab = 33;
+__device__ __forceinline__ void fill_atan_table(float2* tab) {
+  for (int k = threadIdx.x; k < kAtanTab; k += blockDim.x) {
+    const double v = atanq_exact(double(k) * 0.03125);
+    const float h = __double2float_rn(v);
+    tab[k] = make_float2(h, __double2float_rn(__dsub_rn(v, double(h))));
+  }
+}
+
+// atan(u) in quarter turns for u in [0,1] by table reduction: c = k/32 the
+// table point nearest u, atan(u) = atan(c) + atan(t) with
+// t = (u - c)/(1 + u c), |t| <= 1/64, and atan(t)/t = 1 - s/3 + s^2/5 -
+// s^3/7 + ... (s = t^2 <= 2^-12): the omitted terms lie below 2^-50, the
+// s^2 and s^3 terms are taken in FP32 (their rounding, times s, below
+// 2^-49) and the rest in double-float, so the result keeps the refine
+// stage's 2^-44-level error.  (A NaN u gives k = 0 and a NaN result.)
+__device__ __forceinline__ df atanq_df(df u, const float2* tab) {
   if (u.h == 1.0f && u.l == 0.0f) return {0.5f, 0.0f};
-  const df one = {1.0f, 0.0f};
-  df v = df_div(u, df_add(one, df_sqrt(df_add(one, df_mul(u, u)))));
-  df w = df_div(v, df_add(one, df_sqrt(df_add(one, df_mul(v, v)))));
-  df s = df_mul(w, w);
-  constexpr dfc c17 = make_dfc(1.0 / 17.0), c15 = make_dfc(-1.0 / 15.0),
-                c13 = make_dfc(1.0 / 13.0), c11 = make_dfc(-1.0 / 11.0), c9 = make_dfc(1.0 / 9.0),
-                c7 = make_dfc(-1.0 / 7.0), c5 = make_dfc(1.0 / 5.0), c3 = make_dfc(-1.0 / 3.0);
-  df p = to_df(c17);
-  p = df_add(df_mul(p, s), to_df(c15));
-  p = df_add(df_mul(p, s), to_df(c13));
-  p = df_add(df_mul(p, s), to_df(c11));
-  p = df_add(df_mul(p, s), to_df(c9));
-  p = df_add(df_mul(p, s), to_df(c7));
-  p = df_add(df_mul(p, s), to_df(c5));
-  p = df_add(df_mul(p, s), to_df(c3));
-  p = df_add(df_mul(p, s), one);
-  constexpr dfc k8pi = make_dfc(0x1.45f306dc9c883p+1);
-  return df_mul(df_mul(w, p), to_df(k8pi));
+  int k = __float2int_rn(__fmul_rn(u.h, 32.0f));
+  k = k < 0 ? 0 : (k > kAtanTab - 1 ? kAtanTab - 1 : k);
+  const float c = __fmul_rn(float(k), 0.03125f);           // exact
+  const df t = df_div(df_add(u, {-c, 0.0f}), df_add({1.0f, 0.0f}, df_mulf(u, c)));
+  const df s = df_mul(t, t);
+  const float tail = __fmul_rn(s.h, __fmaf_rn(s.h, -1.0f / 7.0f, 0.2f));   // s/5 - s^2/7
+  constexpr dfc c3 = make_dfc(-1.0 / 3.0);
+  const df p = df_add({1.0f, 0.0f}, df_mul(s, df_add(to_df(c3), {tail, 0.0f})));
+  constexpr dfc k2pi = make_dfc(0x1.45f306dc9c883p-1);    // 2/pi
+  const float2 a0 = tab[k];
+  return df_add({a0.x, a0.y}, df_mul(df_mul(t, p), to_df(k2pi)));
 }
 
 // Floor of v when v is farther than band from every integer.
@@ -390,10 +401,12 @@ __device__ __forceinline__ int32_t floor_df_certain(df v, float band, bool& open
 constexpr float kRefineRel = 9.3132257e-10f;   // 2^-30
 
 // Key of one particle image by the refine stage: shell*npix + pix,
-// kKeyOutside, or kKeyUndecided.  d = x + (shf + shlo) per axis.
+// kKeyOutside, or kKeyUndecided.  d = x + (shf + shlo) per axis; atab is
+// the block's copy of the arctangent table (fill_atan_table).
 // (chih, chil: the shell edges as double-float, ShellTable's arrays or a
 // shared-memory copy of them, which lane-divergent indexing favours)
-__device__ __forceinline__ int32_t key_refine(const float* chih, const float* chil, int32_t lo,
+__device__ __forceinline__ int32_t key_refine(const float* chih, const float* chil,
+                                              const float2* atab, int32_t lo,
                                               int32_t hi, int32_t N, int32_t npix,
                                               float x, float y, float zc,
                                               float shx, float shy, float shz,
@@ -437,7 +450,7 @@ __device__ __forceinline__ int32_t key_refine(const float* chih, const float* ch
   if (ax == 0.0f || ay == 0.0f) return kKeyUndecided;
   bool sw = ay > ax;
   df q = sw ? df_div(axd, ayd) : df_div(ayd, axd);
-  df a = atanq_df(q);
+  df a = atanq_df(q, atab);
   int32_t base;
   float sgn;
   if (dx.h >= 0.0f) {

@@ -848,6 +848,7 @@ static_assert(kBT == kKV && kBT == kMT, "the persistent blocks reproduce the ser
 __device__ __forceinline__ int32_t batch_key(float x, float y, float zc, const BatchItem& it,
                                              const float* lo2, const float* hi2,
                                              const float* chih, const float* chil,
+                                             const float2* atab,
                                              const ShellTable& st, const Bands& bd, int32_t N,
                                              int32_t npix) {
   const int lo = it.shell_lo, hi = it.shell_hi;
@@ -866,7 +867,7 @@ __device__ __forceinline__ int32_t batch_key(float x, float y, float zc, const B
     }
   }
   if (key == kKeyUndecided)
-    key = key_refine(chih, chil, lo, hi, N, npix, x, y, zc, it.shf[0], it.shf[1], it.shf[2], it.shlo[0],
+    key = key_refine(chih, chil, atab, lo, hi, N, npix, x, y, zc, it.shf[0], it.shf[1], it.shf[2], it.shlo[0],
                      it.shlo[1], it.shlo[2]);
   if (key == kKeyUndecided)
     key = key_exact(st, lo, hi, N, npix, x, y, zc, it.sh64[0], it.sh64[1], it.sh64[2]);
@@ -878,6 +879,7 @@ k_batch_persistent(BatchArgs ba, ShellTable st, Bands bd, PdfParam pp) {
   extern __shared__ __align__(16) uint8_t bsm[];   // PDF histogram, then Welford scratch
   __shared__ float lo2_s[kMaxShells + 2], hi2_s[kMaxShells + 2];
   __shared__ float chih_s[kMaxShells + 1], chil_s[kMaxShells + 1];
+  __shared__ float2 atab_s[kAtanTab];
   __shared__ float ah_s[kMaxShells], al_s[kMaxShells];
   __shared__ double red[kBT / 32];
   __shared__ long long task_s;
@@ -889,6 +891,7 @@ k_batch_persistent(BatchArgs ba, ShellTable st, Bands bd, PdfParam pp) {
     chih_s[i] = st.chih[i];
     chil_s[i] = st.chil[i];
   }
+  fill_atan_table(atab_s);                 // (the task loop's first barrier follows)
   const int S = ba.S, npix = ba.npix, ng = npix >> 2;
   for (;;) {
     if (threadIdx.x == 0) task_s = (long long)atomicAdd(&ba.queue[0], 1ull);
@@ -909,7 +912,7 @@ k_batch_persistent(BatchArgs ba, ShellTable st, Bands bd, PdfParam pp) {
     for (int64_t i = threadIdx.x; i < cnt; i += kBT) {
       const float* q = it.xyz + 3 * (p0 + i);
       const int32_t key = batch_key(__ldg(q), __ldg(q + 1), __ldg(q + 2), it, lo2_s, hi2_s,
-                                    chih_s, chil_s, st, bd, ba.N, npix);
+                                    chih_s, chil_s, atab_s, st, bd, ba.N, npix);
       if (key >= 0 && UFC_IDX_OK(key, (int64_t)S * npix, 8)) atomicAdd(cmap + key, 1);
     }
     __syncthreads();
