@@ -360,6 +360,8 @@ def run_reference(args):
     from paper_1801_05745_gb300 import synth
     oracle.build()
     w = workload(args.scale)
+    if args.nside:
+        w.nside = args.nside
     z, chi, split = shells(w, orc=oracle)
     boxes = [oracle.make_box(2000.0, [1000.0] * 3, w.boxes[0].n, 0, split),
              oracle.make_box(6400.0, [3200.0] * 3, w.boxes[1].n, split, w.nshell)]
